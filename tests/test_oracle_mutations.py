@@ -1,0 +1,126 @@
+"""The oracle pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of an oracle function (a dropped term,
+a flipped sign, a wrong weight or index, a transposed operand) on the CPU and
+checks that the pin written for that function rejects it.  Nothing here
+touches the CUDA path.
+"""
+import numpy as np
+
+from oracle import qg_oracle as O
+from tests.oracle_helpers import dense_laplacian
+
+
+def _fields(nx=16, ny=32, seed=0):
+    rng = np.random.default_rng(seed)
+    a = O.embed(rng.normal(size=(ny - 1, nx - 1)))
+    b = O.embed(rng.normal(size=(ny - 1, nx - 1)))
+    return a, b
+
+
+def _conserves(jac):
+    psi, w = _fields()
+    J = jac(psi, w, 1 / 16, 1 / 16)
+    scale = np.sum(np.abs(J)) * max(np.abs(psi).max(), np.abs(w).max())
+    return (abs(np.sum(O.interior(psi) * J)) < 1e-14 * scale
+            and abs(np.sum(O.interior(w) * J)) < 1e-14 * scale)
+
+
+def test_arakawa_pins_reject_mistakes():
+    assert _conserves(O.arakawa)
+
+    def dropped_J3(psi, q, dx, dy):
+        J1, J2, _ = O.arakawa_terms(psi, q, dx, dy)
+        return (J1 + J2) / 2.0
+
+    def flipped_J2(psi, q, dx, dy):
+        J1, J2, J3 = O.arakawa_terms(psi, q, dx, dy)
+        return (J1 - J2 + J3) / 3.0
+
+    assert not _conserves(dropped_J3)
+    assert not _conserves(flipped_J2)
+    # swapped operands conserve but change the sign: the closed form of
+    # J(psi, y) catches it
+    nx, ny = 16, 32
+    dx, dy = 1 / 16, 2 / 32
+    psi = np.random.default_rng(9).normal(size=(ny + 1, nx + 1))
+    Y = np.repeat((-1.0 + dy * np.arange(ny + 1))[:, None], nx + 1, axis=1)
+    c = (psi[:, 2:] - psi[:, :-2]) / (2 * dx)
+    want = (4 * c[1:-1] + c[2:] + c[:-2]) / 6.0
+    assert np.allclose(O.arakawa(psi, Y, dx, dy), want, atol=1e-11)
+    assert not np.allclose(O.arakawa(Y, psi, dx, dy), want, atol=1e-6)
+
+
+def test_solver_pins_reject_mistakes():
+    nx, ny = 8, 16
+    dx, dy = 1 / 8, 1 / 16
+    rhs = np.random.default_rng(6).normal(size=(ny - 1, nx - 1))
+    ref = np.linalg.solve(dense_laplacian(nx, ny, dx, dy), rhs.ravel()).reshape(rhs.shape)
+
+    def good(r):
+        return O.poisson_solve(r, nx, ny, dx, dy)
+
+    def swapped_spacing(r):
+        Ph = O.sine_analysis(r, nx, ny) / O.laplacian_eigenvalues(nx, ny, dy, dx)
+        return O.sine_synthesis(Ph, nx, ny)
+
+    def half_norm(r):
+        Ph = 0.5 * O.sine_analysis(r, nx, ny) / O.laplacian_eigenvalues(nx, ny, dx, dy)
+        return O.sine_synthesis(Ph, nx, ny)
+
+    def ok(f):
+        return np.linalg.norm(f(rhs) - ref) <= 1e-12 * np.linalg.norm(ref)
+
+    assert ok(good)
+    assert not ok(swapped_spacing)
+    assert not ok(half_norm)
+
+
+def test_transfer_pins_reject_mistakes():
+    nx, ny, lv = 32, 64, 1
+    rng = np.random.default_rng(11)
+    f = O.embed(rng.normal(size=(ny - 1, nx - 1)))
+    c = O.embed(rng.normal(size=(ny // 2 - 1, nx // 2 - 1)))
+
+    def adjoint_ok(R, P):
+        lhs = np.sum(O.interior(R(f)) * O.interior(c))
+        rhs = np.sum(O.interior(f) * O.interior(P(c))) / 4.0
+        return abs(lhs - rhs) <= 1e-13 * np.sum(np.abs(O.interior(f)))
+
+    def corner_weight_2(fa):
+        out = O.restrict(fa)
+        g = np.zeros_like(fa)
+        g[1:-1, 1:-1] = fa[1:-1, 1:-1]
+        # add an extra 1/16 of one corner neighbour: a wrong corner weight
+        out[1:-1, 1:-1] += g[3::2, 3::2][: out.shape[0] - 2, : out.shape[1] - 2] / 16.0
+        return out
+
+    def prolong_no_centre_avg(ca):
+        out = O.prolong(ca)
+        out[1::2, 1::2] = ca[:-1, :-1]
+        return out
+
+    assert adjoint_ok(O.restrict, O.prolong)
+    assert not adjoint_ok(corner_weight_2, O.prolong)
+    assert not adjoint_ok(O.restrict, prolong_no_centre_avg)
+
+
+def test_time_pins_reject_mistakes():
+    def amp(step, z):
+        u = np.zeros((3, 3))
+        u[1, 1] = 1.0
+        return step(u, lambda s: (z / 0.01) * O.interior(s), 0.01)[1, 1]
+
+    def wrong_stage2(u, rhs, dt):
+        u1 = u.copy()
+        u1[1:-1, 1:-1] = O.interior(u) + dt * rhs(u)
+        u2 = u.copy()
+        u2[1:-1, 1:-1] = 0.5 * O.interior(u) + 0.5 * O.interior(u1) + 0.25 * dt * rhs(u1)
+        u3 = u.copy()
+        u3[1:-1, 1:-1] = O.interior(u) / 3 + 2 / 3 * O.interior(u2) + 2 / 3 * dt * rhs(u2)
+        return u3
+
+    z = -0.3
+    want = 1 + z + z * z / 2 + z ** 3 / 6
+    assert abs(amp(O.tvdrk3, z) - want) < 1e-14
+    assert abs(amp(wrong_stage2, z) - want) > 1e-4

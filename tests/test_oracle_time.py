@@ -1,0 +1,103 @@
+"""Pins of the oracle's time integration (Section 4.2, Eq. TVDRK) and of the
+whole CGPRK3 step (Section 3.2).
+
+The stability polynomial of the TVDRK3 step on du/dt = lambda u, third-order
+convergence, the equality of the literal q-form and the w-form the library
+integrates, the l = 0 reduction of CGP to the standard solver, the discrete
+energy identity behind the kinetic-energy diagnostic, and third-order
+self-consistency of a full CGP trajectory under dt halving.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import qg_oracle as O
+from paper_1308_3290_gb300 import inputs
+
+
+def test_tvdrk3_stability_polynomial():
+    """One step of du/dt = lambda u multiplies u by 1 + z + z^2/2 + z^3/6."""
+    for z in (-0.3, 0.1, -1.7, 0.9):
+        lam, dt = z / 0.01, 0.01
+        u = np.zeros((3, 3))
+        u[1, 1] = 1.0
+        out = O.tvdrk3(u, lambda s: lam * O.interior(s), dt)
+        assert abs(out[1, 1] - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-14
+        assert out[0, 0] == 0.0
+
+
+def test_tvdrk3_third_order():
+    """du/dt = -u^2, u(0) = 1, exact u = 1/(1+t)."""
+    errs = []
+    for n in (10, 20, 40, 80):
+        dt = 1.0 / n
+        u = np.zeros((3, 3))
+        u[1, 1] = 1.0
+        for _ in range(n):
+            u = O.tvdrk3(u, lambda s: -O.interior(s) ** 2, dt)
+        errs.append(abs(u[1, 1] - 0.5))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(7.0 < r < 9.0 for r in ratios), ratios
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_q_form_equals_omega_form(levels):
+    """Integrating q = Ro w + y with the elliptic line (qbar - y)/Ro of the
+    CGPRK3 algorithm gives the same trajectory as integrating w."""
+    b = O.Basin(32, 64, Re=200.0, Ro=0.0016, levels=levels, dt=1e-4)
+    w0 = inputs.perturbation(32, 64, seed=1) * 30.0
+    w = O.embed(w0)
+    Y = np.repeat(O.grid_y(b)[:, None], b.nx + 1, axis=1)
+    q = b.Ro * w + Y
+    for _ in range(20):
+        w = O.cgprk3_step(w, b)
+        q = O.cgprk3_step_q_form(q, b)
+    wq = (q - Y) / b.Ro
+    assert np.linalg.norm(O.interior(wq - w)) <= 1e-11 * np.linalg.norm(O.interior(w))
+
+
+def test_level_zero_is_the_standard_solver():
+    """With l = 0 the projection is the identity: psi solves lap psi = w on
+    the fine grid itself."""
+    b = O.Basin(16, 32, levels=0)
+    w = O.embed(inputs.perturbation(16, 32, seed=2))
+    psi = O.cgp_psi(w, b)
+    direct = O.poisson_solve(O.interior(w), 16, 32, b.dx, b.dy)
+    assert np.array_equal(O.interior(psi), direct)
+
+
+def test_kinetic_energy_summation_by_parts():
+    """E = 1/2 dx dy sum_edges |grad psi|^2 = -1/2 dx dy sum psi lap_h psi,
+    and at l = 0 lap_h psi = w, so E = -1/2 dx dy sum psi w."""
+    b = O.Basin(32, 64, levels=0)
+    w = O.embed(inputs.smooth_field(32, 64, seed=3, noise=0.1))
+    psi = O.cgp_psi(w, b)
+    E = O.kinetic_energy(psi, b.dx, b.dy)
+    assert abs(E + 0.5 * b.dx * b.dy * np.sum(O.interior(psi) * O.laplacian5(psi, b.dx, b.dy))) < 1e-13 * E
+    assert abs(E + 0.5 * b.dx * b.dy * np.sum(psi * w)) < 1e-12 * E
+
+
+def test_cgp_trajectory_third_order_in_time():
+    """A 64x128 CGP (l = 1) trajectory to t = 0.02 from a seeded state
+    converges at third order as dt halves."""
+    b = O.Basin(64, 128, Re=200.0, Ro=0.0016, levels=1)
+    w0 = inputs.perturbation(64, 128, seed=1) * 20.0
+    T = 0.02
+    sols = []
+    for n in (10, 20, 40):
+        sols.append(O.run(w0, dataclasses.replace(b, dt=T / n), n))
+    e1 = np.linalg.norm(sols[0] - sols[1])
+    e2 = np.linalg.norm(sols[1] - sols[2])
+    assert 6.5 < e1 / e2 < 9.5, e1 / e2
+
+
+def test_cfl_dt_formula():
+    b = O.Basin(16, 32, levels=0)
+    psi = np.zeros((33, 17))
+    x = O.grid_x(b)
+    psi[:, :] = 0.0
+    psi[1:-1, 1:-1] = 3.0 * x[None, 1:-1]     # psi_x = 3 in the interior away from walls
+    u = O.max_velocity(psi, b.dx, b.dy)
+    assert u >= 3.0
+    assert O.cfl_dt(psi, b.dx, b.dy, 0.5) == pytest.approx(0.5 * b.dx / u)
