@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the CGP quasigeostrophic time step on GB300.
+
+Metric: fine-grid CGPRK3 steps per second (one step = the three TVDRK3 stages
+of Section 3.2, each restricting, solving on the elliptic grid, prolonging
+and updating the fine grid), for the one-layer double-gyre basin of
+Experiment I (Re = 200, Ro = 0.0016) on a 2048 x 4096 fine grid with two
+levels of coarsening (elliptic grid 512 x 1024), FP32 fields with FP64
+tables and reductions.  Variants (full grid, one level, FP64) are reported
+beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: W untimed steps, then K steps each bracketed by CUDA events on the
+library's stream, with a 256 MiB write between steps to flush the 129 MB
+L2 (outside the timed intervals); barrier + synchronize around the region;
+the maximum over ranks.  With N > 1 each rank advances its own basin
+(independent replicas; a basin does not shard), so the value is the sum of
+the ranks' steps over the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NX, NY, LEVELS = 2048, 4096, 2
+RE, RO, DT = 200.0, 0.0016, 2e-6
+SEED = 2
+METRIC = "fine-grid CGPRK3 steps/s, one-layer 2048x4096 basin, CGP l=2 (elliptic 512x1024), FP32"
+UNIT = "steps/s"
+WORKLOAD = ("one-layer barotropic double-gyre basin, x in [0,1], y in [-1,1], 2048x4096 "
+            "fine intervals, CGP coarsening l=2 (elliptic grid 512x1024), Experiment I "
+            "Re=200 Ro=0.0016, dt=2e-6, seeded gyre-like state")
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def n_unknowns(nx, ny):
+    return (nx - 1) * (ny - 1)
+
+
+def alg_bytes_per_launch(cls, nx, ny, levels, esz):
+    """Algorithmic bytes of one launch of each kernel class of the step: every
+    field the kernel must read or write once, halos from cache."""
+    N = n_unknowns(nx, ny)
+    Nc = n_unknowns(nx >> levels, ny >> levels)
+    if cls == "fine":      # read w^(s), psi, (w^n in stages 2, 3), write w^(s+1)
+        return esz * N * (3 + 4 + 4) / 3.0
+    if cls == "restrict":
+        return esz * (N + Nc)
+    if cls == "prolong":
+        return esz * (N + Nc)
+    if cls in ("dst_rows", "dst_cols"):
+        return esz * 2 * Nc
+    return None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(os.path.join(ROOT, "paper_1308_3290_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1308_3290_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(cls):
+    """DRAM bytes per launch of kernel class `cls` from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    ent = d.get("kernels", {}).get(cls)
+    return None if ent is None else ent.get("bytes_per_launch_full_size")
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle import qg_oracle as O
+from paper_1308_3290_gb300 import inputs
+b = O.Basin({nx}, {ny}, Re={re}, Ro={ro}, levels={lv}, dt={dt})
+w = O.embed(inputs.gyre_state({nx}, {ny}, seed={seed}))
+for _ in range({warm}):
+    w = O.cgprk3_step(w, b)
+t0 = time.perf_counter()
+n = 0
+while True:
+    w = O.cgprk3_step(w, b)
+    n += 1
+    el = time.perf_counter() - t0
+    if n >= {kmax} or el >= {budget}:
+        break
+print(json.dumps({{"steps": n, "seconds": el}}))
+"""
+
+
+def run_oracle(nx, ny, levels, warm, kmax, budget):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    code = ORACLE_SNIPPET.format(root=ROOT, nx=nx, ny=ny, re=RE, ro=RO, lv=levels, dt=DT,
+                                 seed=SEED, warm=warm, kmax=kmax, budget=budget)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle run failed: {r.stderr[-2000:]}")
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["steps"], d["seconds"]
+
+
+def reference_arm(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    kmax = max(1, args.steps)
+    steps, sec = run_oracle(NX, NY, LEVELS, warm=min(args.warmup, 1), kmax=kmax, budget=120.0)
+    v = steps / sec
+    sample = (f"{steps} of the requested {args.steps} CGPRK3 steps of the same 2048x4096 l=2 "
+              f"workload after {min(args.warmup, 1)} warm-up step(s), FP64 numpy oracle, "
+              f"1 thread (BLAS and numpy)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": steps, "warmup": min(args.warmup, 1),
+        "ms_per_step": 1e3 * sec / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "levels": LEVELS, "dt": DT},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def time_steps(torch, qg, h, stream, K, flush):
+    """K single steps, each bracketed by CUDA events, L2 flushed between."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    for k in range(K):
+        evs[k][0].record(stream)
+        qg.qg_step(h, 1)
+        evs[k][1].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def kernel_timing(torch, qg, h, stream, K, flush):
+    qg.qg_set_timing(h, True)
+    acc = {}
+    for _ in range(K):
+        qg.qg_step(h, 1)
+        t = qg.qg_read_timing(h)
+        for c, (ms, n) in t.items():
+            a = acc.setdefault(c, [0.0, 0])
+            a[0] += ms
+            a[1] += n
+        flush.zero_()
+    torch.cuda.synchronize()
+    qg.qg_set_timing(h, False)
+    return acc
+
+
+def ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1308_3290_gb300 import build, inputs, qg
+    build.build()
+    qg.load()
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    w0 = inputs.gyre_state(NX, NY, seed=SEED + rank)
+
+    def make(levels, dtype):
+        b = qg.Basin(NX, NY, Re=RE, Ro=RO, levels=levels, dt=DT, dtype=dtype, stream=stream)
+        b.set_state(w0)
+        return b
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    basin = make(LEVELS, "f32")
+    h = basin.h
+    for _ in range(args.warmup):
+        qg.qg_step(h, 1)
+        flush.zero_()
+    torch.cuda.synchronize()
+    per_step_kernels = qg.qg_step_kernel_count(h)
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.2)
+    barrier()
+    torch.cuda.synchronize()
+    times = time_steps(torch, qg, h, stream, args.steps, flush)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # per-kernel timing (graph with event nodes), for the roofline
+    ktimes = kernel_timing(torch, qg, h, stream, min(args.steps, 200), flush)
+    dom = max(ktimes, key=lambda c: ktimes[c][0])
+    avg_ms = ktimes[dom][0] / max(1, ktimes[dom][1])
+    peak, peak_kind = measured_peaks()
+    algb = alg_bytes_per_launch(dom, NX, NY, LEVELS, 4)
+    achieved = algb / (avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": ncu_traffic(dom),
+                "alg_bytes_per_launch": algb, "avg_launch_ms": avg_ms,
+                "kernels": {c: {"ms_per_step": v[0] / min(args.steps, 200),
+                                "launches_per_step": v[1] / min(args.steps, 200)}
+                            for c, v in ktimes.items()}}
+
+    # end to end through the C ABI with host buffers
+    K_e2e = min(args.steps, 100)
+    host = torch.empty((NY - 1, NX - 1), dtype=torch.float32, pin_memory=True)
+    host.copy_(torch.from_numpy(w0.astype(np.float32)))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(K_e2e):
+        qg.qg_set_state(h, host, 0)
+        qg.qg_step(h, 1)
+        qg.qg_get_state(h, host, 0)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    nbytes = 4 * (NX - 1) * (NY - 1)
+    e2e = {"value": world * K_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes,
+           "how": "per step: qg_set_state from pinned host, qg_step(1), qg_get_state to pinned host, stream sync"}
+    basin.close()
+
+    variants = {}
+    if not args.no_variants:
+        for name, lv, dt in (("cgp_l2_f32", 2, "f32"), ("cgp_l1_f32", 1, "f32"),
+                             ("full_grid_l0_f32", 0, "f32"), ("cgp_l2_f64", 2, "f64"),
+                             ("full_grid_l0_f64", 0, "f64")):
+            b = make(lv, dt)
+            for _ in range(5):
+                qg.qg_step(b.h, 1)
+            K = 200 if dt == "f32" else 20
+            ts = time_steps(torch, qg, b.h, stream, K, flush)
+            variants[name] = {"steps_per_s": K / (sum(ts) / 1e3), "ms_per_step": sum(ts) / K}
+            b.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        steps, sec = run_oracle(NX, NY, LEVELS, warm=0, kmax=2, budget=25.0)
+        cpu = {"value": steps / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{steps} CGPRK3 step(s) of the same 2048x4096 l=2 workload, "
+                         f"FP64 numpy oracle, 1 thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "levels": LEVELS,
+                       "Re": RE, "Ro": RO, "dt": DT,
+                       "l2": "256 MiB write between timed steps (outside the timed intervals)",
+                       "parallelism": f"{world} independent replica(s)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": per_step_kernels * args.steps,
+            "clocks": clocks, "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

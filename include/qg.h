@@ -1,0 +1,197 @@
+/*
+ * qg.h -- C ABI of the GB300-native coarse grid projection (CGP) time step
+ * for quasigeostrophic ocean basins (San & Staples, "An Efficient Coarse Grid
+ * Projection Method for Quasigeostrophic Models of Large-Scale Ocean
+ * Circulation", arXiv 1308.3290).
+ *
+ * Every call returns a qg_status.  No C++ exception crosses this boundary.
+ * Outputs are written only when the call returns QG_OK.  Work is enqueued on
+ * the CUDA stream given to qg_create and runs asynchronously unless a call
+ * says it synchronises; an error raised by such work is latched in the handle
+ * and returned by the next call (and by qg_last_error).
+ *
+ * Grids.  A basin has nx x ny grid INTERVALS (Section 4.3 of the paper sums
+ * over i = 1..N_x-1): nodes i = 0..nx, j = 0..ny, walls at the first and last
+ * node of each direction, unknowns at the interior nodes.  Level l of a basin
+ * is the grid with nx/2^l x ny/2^l intervals (Section 3, M = 2^-l N); level 0
+ * is the fine grid, level `coarsening_levels` the elliptic (coarse) grid.
+ *
+ * Exchange layout.  Every field passed through this ABI is the interior of a
+ * level-l grid as a dense row-major array of (ny_l - 1) rows of (nx_l - 1)
+ * values, x fastest, in the handle's dtype (float for QG_F32, double for
+ * QG_F64).  Pointers may be device pointers or host pointers (pageable host
+ * memory makes the copy synchronous; pinned host memory keeps it
+ * asynchronous).  The caller owns every pointer it passes; the handle owns
+ * its internal state and workspace (device memory allocated in qg_create).
+ *
+ * Threading.  One handle is used by one host thread at a time; calls on
+ * distinct handles are independent.
+ */
+#ifndef QG_H
+#define QG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum qg_status {
+    QG_OK = 0,
+    QG_ERR_ARG = 1,          /* NULL pointer, out-of-range scalar or level   */
+    QG_ERR_SHAPE = 2,        /* grid not a power of two, or too small/large  */
+    QG_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed  */
+    QG_ERR_OOM = 4,          /* device allocation failed                     */
+    QG_ERR_NONFINITE = 5,    /* the state holds NaN or Inf                   */
+    QG_ERR_CFL = 6,          /* CFL number above the handle's limit          */
+    QG_ERR_TIMEOUT = 7,      /* a bounded device-side wait ran out           */
+    QG_ERR_UNSUPPORTED = 8,  /* valid request this build does not provide    */
+    QG_ERR_NO_DEVICE = 9     /* no usable CUDA device                        */
+} qg_status;
+
+typedef enum qg_dtype {
+    QG_F32 = 0,  /* FP32 fields; FP64-generated twiddle/eigenvalue tables and
+                    FP64 energy/enstrophy reductions                         */
+    QG_F64 = 1   /* FP64 throughout                                          */
+} qg_dtype;
+
+/* Basin geometry and run constants.
+ * nx, ny      fine-grid intervals; powers of two, 8 <= nx, ny <= 8192.
+ * x0..y1      basin extent.  The one-layer experiments of Section 5.1 use
+ *             [0,1] x [-1,1]; the two-layer ones of Section 5.2 a square.
+ * forcing_amp amplitude a of the double-gyre wind forcing: a sin(pi y)/Ro in
+ *             the one-layer vorticity equation (Eq. ge, Section 2.1), and
+ *             a sin(2 pi y) on the upper layer of the two-layer model
+ *             (Eq. ge-non, Section 2.2).
+ * delta       H1/H of the two-layer model (Eq. pv-non); ignored for 1 layer.
+ * sigma       bottom-drag coefficient of layer 2 (Eq. ge-non).
+ * dt          fixed time step of the TVDRK3 integrator (Section 4.2).
+ * flags       reserved, must be 0.                                          */
+typedef struct qg_basin {
+    int32_t nx, ny;
+    double x0, x1, y0, y1;
+    double forcing_amp;
+    double delta;
+    double sigma;
+    double dt;
+    uint32_t flags;
+} qg_basin;
+
+typedef struct qg_ctx* qg_handle;
+
+/* qg_create -- set up a basin (Sections 2 and 3).
+ * layers            1 (barotropic vorticity equation, Section 2.1) or 2
+ *                   (two-layer QG, Section 2.2).
+ * Re, Ro            Reynolds and Rossby numbers.  One layer: the
+ *                   dissipation is (1/Re) lap(w) and the beta term
+ *                   (1/Ro) J(psi, y) (Eqs. ge, pv, Rhines, Munk).  Two
+ *                   layers: A = Ro/Re is the eddy viscosity of Eq. ge-non.
+ * Fr                Froude number of Eq. pv-non (two layers; ignored for 1).
+ * coarsening_levels l >= 0: the elliptic sub-problem is solved on level l
+ *                   (Section 3); 0 is the standard full-grid solver.  The
+ *                   coarse grid must keep at least 8 intervals per direction.
+ * dtype             QG_F32 or QG_F64.
+ * cuda_stream       cudaStream_t on which all work of this handle is
+ *                   enqueued (NULL = the legacy default stream).
+ * out               receives the handle.  The state starts at rest (w = 0).
+ * Errors: QG_ERR_ARG, QG_ERR_SHAPE, QG_ERR_OOM, QG_ERR_CUDA,
+ * QG_ERR_NO_DEVICE.  Synchronises the device once (table upload).        */
+qg_status qg_create(const qg_basin* basin, int layers, double Re, double Ro,
+                    double Fr, int coarsening_levels, qg_dtype dtype,
+                    void* cuda_stream, qg_handle* out);
+
+/* qg_destroy -- synchronise the handle's stream and free its device memory.
+ * Safe on NULL.                                                            */
+qg_status qg_destroy(qg_handle h);
+
+/* qg_set_state / qg_get_state -- copy the prognostic field of `layer`
+ * (0-based) into / out of the handle, in the exchange layout of level 0.
+ * One layer: the relative vorticity w = (q - y)/Ro (Eq. pv divided by Ro).
+ * Two layers: Q_i = q_i - y (Section 4.3).  Walls are implied zero.       */
+qg_status qg_set_state(qg_handle h, const void* field, int layer);
+qg_status qg_get_state(qg_handle h, void* field, int layer);
+
+/* qg_get_psi -- the fine-grid streamfunction of the current state: the CGP
+ * projection of steps (ii)-(iv) of Section 3 (restrict, coarse solve,
+ * prolong).  Level-0 exchange layout.                                      */
+qg_status qg_get_psi(qg_handle h, void* psi, int layer);
+
+/* qg_set_forcing -- replace the one-layer wind forcing by a fine-grid field
+ * F (level-0 exchange layout, added to the vorticity tendency as is).
+ * F == NULL restores forcing_amp sin(pi y)/Ro.                            */
+qg_status qg_set_forcing(qg_handle h, const void* forcing);
+
+/* qg_poisson_solve -- the elliptic sub-problem on level `level`
+ * (0 <= level <= coarsening_levels) with psi = 0 on the walls, by the fast
+ * sine-transform solver of Section 4.3: forward DST-I in x and y
+ * (Eq. ifft-1), division by the eigenvalues of the 5-point Laplacian
+ * (Eq. ialpha), inverse DST-I (Eq. ffft-1).
+ * One layer: solves lap_h psi = rhs.
+ * Two layers: rhs and psi hold 2 consecutive planes (Q_1, Q_2) and
+ * (psi_1, psi_2); solves the coupled system of Eq. sub-pr per mode
+ * (Eqs. isub-1/2).                                                         */
+qg_status qg_poisson_solve(qg_handle h, const void* rhs, void* psi, int level);
+
+/* qg_restrict -- full-weighting restriction (Eq. res) applied `levels`
+ * times, from level 0 to level `levels`.  qg_prolong -- bilinear
+ * prolongation (Eq. pro) applied `levels` times, from level `levels` to
+ * level 0.  1 <= levels <= coarsening_levels is not required: any level
+ * that keeps 2 intervals per direction is accepted.                        */
+qg_status qg_restrict(qg_handle h, const void* fine, void* coarse, int levels);
+qg_status qg_prolong(qg_handle h, const void* coarse, void* fine, int levels);
+
+/* qg_step -- advance n >= 0 CGPRK3 steps (Section 3.2: TVDRK3 of
+ * Section 4.2 whose every stage restricts, solves on the coarse grid,
+ * prolongs and updates the fine grid).  Asynchronous; replays a CUDA
+ * graph of the step after the first call.                                  */
+qg_status qg_step(qg_handle h, int64_t n);
+
+/* qg_diagnostics -- basin-integrated kinetic energy (Section 5.2,
+ * E = 1/2 iint |grad psi|^2, one-sided differences on grid edges), the
+ * enstrophy Z = 1/2 iint w^2 and max(|psi_x|, |psi_y|) over the interior
+ * nodes (the denominator of Eq. dt), for layer 0, accumulated in FP64 in a
+ * fixed order (bitwise reproducible).  Any output pointer may be NULL.
+ * Host pointers; synchronises the stream.  Returns QG_ERR_NONFINITE when
+ * the state holds NaN or Inf.                                              */
+qg_status qg_diagnostics(qg_handle h, double* ke, double* enstrophy,
+                         double* max_vel);
+
+/* Kernel classes of the step, for qg_read_timing.                          */
+typedef enum qg_kernel_class {
+    QG_K_RESTRICT = 0,   /* restriction (Eq. res), when not fused            */
+    QG_K_DST_ROWS = 1,   /* row sine transforms (x direction)                */
+    QG_K_DST_COLS = 2,   /* column transforms + eigenvalue division (y)      */
+    QG_K_PROLONG = 3,    /* prolongation (Eq. pro), when not fused           */
+    QG_K_FINE = 4,       /* fine-grid Arakawa / dissipation / forcing / RK   */
+    QG_K_COUNT = 5
+} qg_kernel_class;
+
+/* qg_set_timing -- enable (1) or disable (0) per-kernel timing.  When
+ * enabled, the captured step graph records a CUDA event before and after
+ * every kernel it launches; this adds event nodes to the graph, so time the
+ * whole step with timing disabled.  Re-captures the graph.                 */
+qg_status qg_set_timing(qg_handle h, int enable);
+
+/* qg_read_timing -- synchronise and return, per kernel class, the summed
+ * device time in milliseconds (ms[QG_K_COUNT]) and the number of launches
+ * (launches[QG_K_COUNT]) of the most recent step run with timing enabled.  */
+qg_status qg_read_timing(qg_handle h, double* ms, int32_t* launches);
+
+/* qg_step_kernel_count -- number of kernels one step launches.             */
+qg_status qg_step_kernel_count(qg_handle h, int64_t* count);
+
+/* qg_synchronize -- wait for the handle's work; returns any latched error. */
+qg_status qg_synchronize(qg_handle h);
+
+/* qg_status_string -- static text for a status code.                       */
+const char* qg_status_string(qg_status s);
+
+/* qg_last_error -- the latched error of the handle (QG_OK if none); reading
+ * it clears it.                                                            */
+qg_status qg_last_error(qg_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QG_H */

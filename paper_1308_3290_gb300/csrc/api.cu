@@ -1,0 +1,698 @@
+// C-ABI of libqgcgp: handle management, tables, and the CGPRK3 step.
+//
+// The step (Section 3.2) is TVDRK3 (Section 4.2) in which every stage
+//   (ii)  restricts the fine state to the elliptic grid (Eq. res, l times),
+//   (iii) solves the elliptic sub-problem there with the sine-transform
+//         solver (Eqs. ifft-1, ialpha, ffft-1; Eqs. isub-1/2 for 2 layers),
+//   (iv)  prolongs the streamfunction back (Eq. pro, l times),
+//   (i)   and updates the fine state with the stage's right-hand side.
+// The kernels of one step are captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "qg_internal.cuh"
+
+using namespace qg;
+
+namespace {
+
+struct LevelTables {
+    int mx = 0, my = 0, ldc = 0;
+    double dxc = 0, dyc = 0;
+    void* twx = nullptr;   // e^{i pi t/mx}, t < 2 mx   (Cx<T>)
+    void* twy = nullptr;   // e^{i pi t/my}, t < 2 my
+    void* lamx = nullptr;  // (2 cos(pi k/mx) - 2)/dxc^2, k = 0..mx
+    void* lamy = nullptr;  // (2 cos(pi l/my) - 2)/dyc^2, l = 0..my
+};
+
+}  // namespace
+
+struct qg_ctx {
+    int layers = 1;
+    qg_dtype dtype = QG_F32;
+    size_t esz = 4;
+    int nx = 0, ny = 0, levels = 0;
+    double x0 = 0, x1 = 1, y0 = -1, y1 = 1, dx = 0, dy = 0;
+    double Re = 0, Ro = 0, Fr = 0, delta = 0, sigma = 0, dt = 0, amp = 1;
+    int ldf = 0;
+    size_t plane_f = 0;            // elements of one fine plane
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;    // private stream used for graph capture
+    void* w[3] = {nullptr, nullptr, nullptr};  // w^n, w^(1), w^(2) (layers planes each)
+    void* psi = nullptr;           // fine psi (layers planes)
+    void* cw = nullptr;            // elliptic-grid work (layers planes)
+    void* cpsi = nullptr;          // elliptic-grid psi (layers planes)
+    size_t plane_c = 0;
+    void* frow = nullptr;          // forcing per fine row
+    void* f2d = nullptr;           // forcing field in use (padded fine) or null
+    void* f2d_buf = nullptr;       // its storage, allocated on first use
+    std::map<int, LevelTables> tables;
+    std::map<int, void*> twcache;
+    double* dpart = nullptr;
+    double* dout = nullptr;
+    double* hout = nullptr;        // pinned host copy of the 5 diagnostics
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    qg_status latched = QG_OK;
+    std::vector<void*> allocs;
+    // per-kernel timing (bench instrumentation): events recorded in the graph
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+    size_t ev_next = 0;
+    int64_t kernels_per_step = 0;
+    bool capturing = false;
+};
+
+namespace {
+
+qg_status fail(qg_ctx* h, qg_status s) {
+    if (h && h->latched == QG_OK) h->latched = s;
+    return s;
+}
+
+qg_status cuda_status(qg_ctx* h, cudaError_t e) {
+    if (e == cudaSuccess) return QG_OK;
+    if (e == cudaErrorMemoryAllocation) return fail(h, QG_ERR_OOM);
+    return fail(h, QG_ERR_CUDA);
+}
+
+#define QG_TRY(expr)                                \
+    do {                                            \
+        cudaError_t e_ = (expr);                    \
+        if (e_ != cudaSuccess) return cuda_status(h, e_); \
+    } while (0)
+
+qg_status dev_alloc(qg_ctx* h, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        (void)cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? QG_ERR_OOM : QG_ERR_CUDA;
+    }
+    h->allocs.push_back(*p);
+    e = cudaMemset(*p, 0, bytes);
+    return e == cudaSuccess ? QG_OK : QG_ERR_CUDA;
+}
+
+int padded_ld(int n) { return round_up(n + 1, 32); }
+
+// Twiddle table tw[t] = e^{i pi t / N}, t = 0..2N-1, generated in FP64.
+qg_status get_twiddles(qg_ctx* h, int N, void** out) {
+    auto it = h->twcache.find(N);
+    if (it != h->twcache.end()) {
+        *out = it->second;
+        return QG_OK;
+    }
+    const size_t n = 2 * (size_t)N;
+    void* d = nullptr;
+    qg_status s = dev_alloc(h, &d, n * 2 * h->esz);
+    if (s != QG_OK) return s;
+    const double pi = 3.14159265358979323846;
+    if (h->dtype == QG_F64) {
+        std::vector<double> t(2 * n);
+        for (size_t k = 0; k < n; ++k) {
+            t[2 * k] = std::cos(pi * (double)k / N);
+            t[2 * k + 1] = std::sin(pi * (double)k / N);
+        }
+        if (cudaMemcpy(d, t.data(), t.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+            return QG_ERR_CUDA;
+    } else {
+        std::vector<float> t(2 * n);
+        for (size_t k = 0; k < n; ++k) {
+            t[2 * k] = (float)std::cos(pi * (double)k / N);
+            t[2 * k + 1] = (float)std::sin(pi * (double)k / N);
+        }
+        if (cudaMemcpy(d, t.data(), t.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return QG_ERR_CUDA;
+    }
+    h->twcache[N] = d;
+    *out = d;
+    return QG_OK;
+}
+
+qg_status upload_real(qg_ctx* h, void** out, const std::vector<double>& v) {
+    qg_status s = dev_alloc(h, out, v.size() * h->esz);
+    if (s != QG_OK) return s;
+    cudaError_t e;
+    if (h->dtype == QG_F64) {
+        e = cudaMemcpy(*out, v.data(), v.size() * 8, cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> f(v.begin(), v.end());
+        e = cudaMemcpy(*out, f.data(), f.size() * 4, cudaMemcpyHostToDevice);
+    }
+    return e == cudaSuccess ? QG_OK : QG_ERR_CUDA;
+}
+
+// Eigenvalue and twiddle tables of grid level `lv` (Eq. ialpha without Ro).
+qg_status get_level(qg_ctx* h, int lv, const LevelTables** out) {
+    auto it = h->tables.find(lv);
+    if (it != h->tables.end()) {
+        *out = &it->second;
+        return QG_OK;
+    }
+    LevelTables t;
+    t.mx = h->nx >> lv;
+    t.my = h->ny >> lv;
+    if (dst_lane_bytes(t.mx, h->esz) > dst_max_smem() ||
+        dst_lane_bytes(t.my, h->esz) > dst_max_smem())
+        return QG_ERR_SHAPE;
+    t.ldc = padded_ld(t.mx);
+    t.dxc = h->dx * (double)(1 << lv);
+    t.dyc = h->dy * (double)(1 << lv);
+    qg_status s = get_twiddles(h, t.mx, &t.twx);
+    if (s == QG_OK) s = get_twiddles(h, t.my, &t.twy);
+    if (s != QG_OK) return s;
+    const double pi = 3.14159265358979323846;
+    std::vector<double> lx(t.mx + 1, 0.0), ly(t.my + 1, 0.0);
+    for (int k = 1; k < t.mx; ++k) lx[k] = (2.0 * std::cos(pi * k / t.mx) - 2.0) / (t.dxc * t.dxc);
+    for (int l = 1; l < t.my; ++l) ly[l] = (2.0 * std::cos(pi * l / t.my) - 2.0) / (t.dyc * t.dyc);
+    s = upload_real(h, &t.lamx, lx);
+    if (s == QG_OK) s = upload_real(h, &t.lamy, ly);
+    if (s != QG_OK) return s;
+    h->tables[lv] = t;
+    *out = &h->tables[lv];
+    return QG_OK;
+}
+
+// Bench instrumentation: when h->timing is set, each launch of the step is
+// bracketed by two externally visible events captured into the graph.
+struct KTimer {
+    qg_ctx* h;
+    cudaStream_t s;
+    int cls;
+    cudaEvent_t e1 = nullptr, e2 = nullptr;
+    KTimer(qg_ctx* h_, cudaStream_t s_, int c) : h(h_), s(s_), cls(c) {
+        if (!h->capturing) return;
+        ++h->kernels_per_step;
+        if (!h->timing) return;
+        if (h->ev_next + 2 > h->ev_pool.size()) {
+            for (int k = 0; k < 2; ++k) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) return;
+                h->ev_pool.push_back(e);
+            }
+        }
+        e1 = h->ev_pool[h->ev_next++];
+        e2 = h->ev_pool[h->ev_next++];
+        cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+    }
+    ~KTimer() {
+        if (!e1) return;
+        cudaEventRecordWithFlags(e2, s, cudaEventRecordExternal);
+        h->ev_used.push_back({cls, {e1, e2}});
+    }
+};
+
+template <typename T>
+T* plane(void* base, size_t plane_elems, int layer) {
+    return static_cast<T*>(base) + (size_t)layer * plane_elems;
+}
+
+// Elliptic solve on one level: padded in -> padded out, through `work`
+// (all three may alias).  One layer: lap_h psi = rhs.  Two layers: Eq.
+// sub-pr per mode.  `pl` is the plane size of the level's buffers.
+template <typename T>
+qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in,
+                      void* work, void* out, size_t pl, cudaStream_t s) {
+    using C = typename Cx<T>::type;
+    const DstLaunch rc = dst_rows_config(t.mx, sizeof(T));
+    const DstLaunch cc = dst_cols_config(t.my, sizeof(T));
+    const T scale = (T)((2.0 / t.mx) * (2.0 / t.my));
+    for (int L = 0; L < h->layers; ++L) {
+        KTimer kt(h, s, QG_K_DST_ROWS);
+        QG_TRY(launch_dst_rows<T>(plane<T>(const_cast<void*>(in), pl, L),
+                                  plane<T>(work, pl, L), t.ldc, t.my - 1, t.mx,
+                                  static_cast<const C*>(t.twx), rc, s));
+    }
+    {
+    KTimer ktc(h, s, QG_K_DST_COLS);
+    if (h->layers == 1) {
+        QG_TRY(launch_dst_cols_solve<T>(static_cast<T*>(work), t.ldc, t.mx - 1, t.my,
+                                        static_cast<const C*>(t.twy),
+                                        static_cast<const T*>(t.lamx),
+                                        static_cast<const T*>(t.lamy), scale, cc, s));
+    } else {
+        QG_TRY(launch_dst_cols_solve2<T>(plane<T>(work, pl, 0), plane<T>(work, pl, 1),
+                                         t.ldc, t.mx - 1, t.my,
+                                         static_cast<const C*>(t.twy),
+                                         static_cast<const T*>(t.lamx),
+                                         static_cast<const T*>(t.lamy), scale,
+                                         (T)h->Ro, (T)(h->Fr / h->delta),
+                                         (T)(h->Fr / (1.0 - h->delta)), cc, s));
+    }
+    }
+    for (int L = 0; L < h->layers; ++L) {
+        KTimer kt(h, s, QG_K_DST_ROWS);
+        QG_TRY(launch_dst_rows<T>(plane<T>(work, pl, L), plane<T>(out, pl, L), t.ldc,
+                                  t.my - 1, t.mx, static_cast<const C*>(t.twx), rc, s));
+    }
+    return QG_OK;
+}
+
+// CGP steps (ii)-(iv): fine state planes -> fine psi planes.
+template <typename T>
+qg_status project(qg_ctx* h, const void* win, cudaStream_t s) {
+    const LevelTables* t = nullptr;
+    qg_status st = get_level(h, h->levels, &t);
+    if (st != QG_OK) return fail(h, st);
+    if (h->levels == 0) {
+        return solve_level<T>(h, *t, win, h->cw, h->psi, h->plane_f, s);
+    }
+    for (int L = 0; L < h->layers; ++L) {
+        KTimer kt(h, s, QG_K_RESTRICT);
+        QG_TRY(launch_restrict<T>(plane<T>(const_cast<void*>(win), h->plane_f, L), h->ldf,
+                                  plane<T>(h->cw, h->plane_c, L), t->ldc, t->mx, t->my,
+                                  h->levels, s));
+    }
+    st = solve_level<T>(h, *t, h->cw, h->cw, h->cpsi, h->plane_c, s);
+    if (st != QG_OK) return st;
+    for (int L = 0; L < h->layers; ++L) {
+        KTimer kt(h, s, QG_K_PROLONG);
+        QG_TRY(launch_prolong<T>(plane<T>(h->cpsi, h->plane_c, L), t->ldc,
+                                 plane<T>(h->psi, h->plane_f, L), h->ldf, h->nx, h->ny,
+                                 h->levels, s));
+    }
+    return QG_OK;
+}
+
+// TVDRK3 stage s: w_out = a w^n + b (w_in + dt G(w_in)).
+template <typename T>
+qg_status stage(qg_ctx* h, int s_idx, cudaStream_t s) {
+    static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double B[3] = {1.0, 0.25, 2.0 / 3.0};
+    void* win = h->w[s_idx];
+    void* wout = h->w[(s_idx + 1) % 3];
+    qg_status st = project<T>(h, win, s);
+    if (st != QG_OK) return st;
+    KTimer kt(h, s, QG_K_FINE);
+    if (h->layers == 1) {
+        StageParams<T> p;
+        p.nx = h->nx;
+        p.ny = h->ny;
+        p.ld = h->ldf;
+        p.c_jac = (T)(1.0 / (12.0 * h->dx * h->dy));
+        p.c_beta = (T)(1.0 / (12.0 * h->Ro * h->dx));
+        p.c_lapx = (T)(1.0 / (h->Re * h->dx * h->dx));
+        p.c_lapy = (T)(1.0 / (h->Re * h->dy * h->dy));
+        p.dt = (T)h->dt;
+        p.a = (T)A[s_idx];
+        p.b = (T)B[s_idx];
+        QG_TRY(launch_fine_stage<T>(static_cast<const T*>(h->psi),
+                                    static_cast<const T*>(win),
+                                    static_cast<const T*>(h->w[0]),
+                                    static_cast<T*>(wout),
+                                    static_cast<const T*>(h->frow),
+                                    static_cast<const T*>(h->f2d), p, s));
+    } else {
+        StageParams2<T> p;
+        p.nx = h->nx;
+        p.ny = h->ny;
+        p.ld = h->ldf;
+        p.c_jac = (T)(1.0 / (12.0 * h->dx * h->dy));
+        p.c_beta = (T)(1.0 / (12.0 * h->dx));
+        p.inv_Ro = (T)(1.0 / h->Ro);
+        p.f1 = (T)(h->Fr / h->delta);
+        p.f2 = (T)(h->Fr / (1.0 - h->delta));
+        const double A2 = h->Ro / h->Re;
+        p.A_dx2 = (T)(A2 / (h->dx * h->dx));
+        p.A_dy2 = (T)(A2 / (h->dy * h->dy));
+        p.sigma = (T)h->sigma;
+        p.dt = (T)h->dt;
+        p.a = (T)A[s_idx];
+        p.b = (T)B[s_idx];
+        const size_t P = h->plane_f;
+        QG_TRY(launch_fine_stage2<T>(plane<T>(h->psi, P, 0), plane<T>(h->psi, P, 1),
+                                     plane<T>(win, P, 0), plane<T>(win, P, 1),
+                                     plane<T>(h->w[0], P, 0), plane<T>(h->w[0], P, 1),
+                                     plane<T>(wout, P, 0), plane<T>(wout, P, 1),
+                                     static_cast<const T*>(h->frow), p, s));
+    }
+    return QG_OK;
+}
+
+template <typename T>
+qg_status enqueue_step(qg_ctx* h, cudaStream_t s) {
+    for (int k = 0; k < 3; ++k) {
+        qg_status st = stage<T>(h, k, s);
+        if (st != QG_OK) return st;
+    }
+    return QG_OK;
+}
+
+qg_status enqueue_step_any(qg_ctx* h, cudaStream_t s) {
+    return h->dtype == QG_F64 ? enqueue_step<double>(h, s) : enqueue_step<float>(h, s);
+}
+
+qg_status project_any(qg_ctx* h, const void* win, cudaStream_t s) {
+    return h->dtype == QG_F64 ? project<double>(h, win, s) : project<float>(h, win, s);
+}
+
+void drop_graph(qg_ctx* h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+}
+
+qg_status build_graph(qg_ctx* h) {
+    if (h->gexec) return QG_OK;
+    h->ev_next = 0;
+    h->ev_used.clear();
+    h->kernels_per_step = 0;
+    QG_TRY(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    qg_status st = enqueue_step_any(h, h->cap);
+    h->capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    if (st != QG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_status(h, e);
+    h->graph = g;
+    QG_TRY(cudaGraphInstantiate(&h->gexec, g, 0));
+    return QG_OK;
+}
+
+bool pow2_in(int v, int lo, int hi) { return is_pow2(v) && v >= lo && v <= hi; }
+
+}  // namespace
+
+extern "C" {
+
+const char* qg_status_string(qg_status s) {
+    switch (s) {
+        case QG_OK: return "ok";
+        case QG_ERR_ARG: return "invalid argument";
+        case QG_ERR_SHAPE: return "unsupported grid shape";
+        case QG_ERR_CUDA: return "CUDA error";
+        case QG_ERR_OOM: return "device out of memory";
+        case QG_ERR_NONFINITE: return "state is not finite";
+        case QG_ERR_CFL: return "CFL limit exceeded";
+        case QG_ERR_TIMEOUT: return "device wait timed out";
+        case QG_ERR_UNSUPPORTED: return "unsupported request";
+        case QG_ERR_NO_DEVICE: return "no CUDA device";
+    }
+    return "unknown status";
+}
+
+qg_status qg_create(const qg_basin* b, int layers, double Re, double Ro, double Fr,
+                    int levels, qg_dtype dtype, void* cuda_stream, qg_handle* out) {
+    if (!b || !out) return QG_ERR_ARG;
+    *out = nullptr;
+    if (layers != 1 && layers != 2) return QG_ERR_ARG;
+    if (dtype != QG_F32 && dtype != QG_F64) return QG_ERR_ARG;
+    if (b->flags != 0) return QG_ERR_ARG;
+    if (!(Re > 0) || !(Ro > 0) || !(b->dt > 0) || !(b->x1 > b->x0) || !(b->y1 > b->y0))
+        return QG_ERR_ARG;
+    if (!std::isfinite(Re) || !std::isfinite(Ro) || !std::isfinite(b->dt)) return QG_ERR_ARG;
+    if (layers == 2 && (!(b->delta > 0) || !(b->delta < 1) || !(Fr >= 0) || !(b->sigma >= 0)))
+        return QG_ERR_ARG;
+    if (levels < 0 || levels > 10) return QG_ERR_ARG;
+    if (!pow2_in(b->nx, 8, 8192) || !pow2_in(b->ny, 8, 8192)) return QG_ERR_SHAPE;
+    if ((b->nx >> levels) < 8 || (b->ny >> levels) < 8) return QG_ERR_SHAPE;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        (void)cudaGetLastError();
+        return QG_ERR_NO_DEVICE;
+    }
+    qg_ctx* h = new (std::nothrow) qg_ctx();
+    if (!h) return QG_ERR_OOM;
+    h->layers = layers;
+    h->dtype = dtype;
+    h->esz = dtype == QG_F64 ? 8 : 4;
+    h->nx = b->nx;
+    h->ny = b->ny;
+    h->levels = levels;
+    h->x0 = b->x0; h->x1 = b->x1; h->y0 = b->y0; h->y1 = b->y1;
+    h->dx = (b->x1 - b->x0) / b->nx;
+    h->dy = (b->y1 - b->y0) / b->ny;
+    h->Re = Re; h->Ro = Ro; h->Fr = Fr;
+    h->delta = b->delta; h->sigma = b->sigma; h->dt = b->dt; h->amp = b->forcing_amp;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->ldf = padded_ld(h->nx);
+    h->plane_f = (size_t)(h->ny + 1) * h->ldf;
+    const int mx = h->nx >> levels, my = h->ny >> levels;
+    h->plane_c = (size_t)(my + 1) * padded_ld(mx);
+    qg_status s = QG_OK;
+    auto guard = [&](qg_status st) {
+        if (st != QG_OK && s == QG_OK) s = st;
+    };
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) guard(QG_ERR_CUDA);
+    if (s == QG_OK && dst_prepare_kernels() != cudaSuccess) guard(QG_ERR_CUDA);
+    const size_t fb = h->plane_f * layers * h->esz;
+    const size_t cb = h->plane_c * layers * h->esz;
+    for (int k = 0; k < 3 && s == QG_OK; ++k) guard(dev_alloc(h, &h->w[k], fb));
+    if (s == QG_OK) guard(dev_alloc(h, &h->psi, fb));
+    if (s == QG_OK) guard(dev_alloc(h, &h->cw, cb));
+    if (s == QG_OK) guard(dev_alloc(h, &h->cpsi, cb));
+    if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dpart, sizeof(double) * 5 * diag_blocks()));
+    if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dout, sizeof(double) * 8));
+    if (s == QG_OK && cudaMallocHost((void**)&h->hout, sizeof(double) * 8) != cudaSuccess) guard(QG_ERR_OOM);
+    if (s == QG_OK) {
+        const double pi = 3.14159265358979323846;
+        std::vector<double> fr(h->ny + 1, 0.0);
+        for (int j = 1; j < h->ny; ++j) {
+            const double y = h->y0 + h->dy * j;
+            fr[j] = layers == 1 ? h->amp * std::sin(pi * y) / Ro : h->amp * std::sin(2.0 * pi * y);
+        }
+        guard(upload_real(h, &h->frow, fr));
+    }
+    if (s == QG_OK) {
+        const LevelTables* t = nullptr;
+        guard(get_level(h, levels, &t));
+    }
+    if (s == QG_OK && cudaDeviceSynchronize() != cudaSuccess) guard(QG_ERR_CUDA);
+    if (s != QG_OK) {
+        qg_destroy(h);
+        (void)cudaGetLastError();
+        return s;
+    }
+    *out = h;
+    return QG_OK;
+}
+
+qg_status qg_destroy(qg_handle h) {
+    if (!h) return QG_OK;
+    cudaStreamSynchronize(h->stream);
+    drop_graph(h);
+    for (void* p : h->allocs) cudaFree(p);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->hout) cudaFreeHost(h->hout);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+    return QG_OK;
+}
+
+qg_status qg_last_error(qg_handle h) {
+    if (!h) return QG_ERR_ARG;
+    qg_status s = h->latched;
+    h->latched = QG_OK;
+    return s;
+}
+
+qg_status qg_synchronize(qg_handle h) {
+    if (!h) return QG_ERR_ARG;
+    QG_TRY(cudaStreamSynchronize(h->stream));
+    return qg_last_error(h);
+}
+
+qg_status qg_set_state(qg_handle h, const void* field, int layer) {
+    if (!h || !field || layer < 0 || layer >= h->layers) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    char* dst = static_cast<char*>(h->w[0]) + (size_t)layer * h->plane_f * h->esz;
+    QG_TRY(copy_in(dst, h->ldf, field, h->nx - 1, h->ny - 1, h->esz, h->stream));
+    return QG_OK;
+}
+
+qg_status qg_get_state(qg_handle h, void* field, int layer) {
+    if (!h || !field || layer < 0 || layer >= h->layers) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    const char* src = static_cast<const char*>(h->w[0]) + (size_t)layer * h->plane_f * h->esz;
+    QG_TRY(copy_out(field, src, h->ldf, h->nx - 1, h->ny - 1, h->esz, h->stream));
+    return QG_OK;
+}
+
+qg_status qg_get_psi(qg_handle h, void* psi, int layer) {
+    if (!h || !psi || layer < 0 || layer >= h->layers) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    qg_status s = project_any(h, h->w[0], h->stream);
+    if (s != QG_OK) return s;
+    const char* src = static_cast<const char*>(h->psi) + (size_t)layer * h->plane_f * h->esz;
+    QG_TRY(copy_out(psi, src, h->ldf, h->nx - 1, h->ny - 1, h->esz, h->stream));
+    return QG_OK;
+}
+
+qg_status qg_set_forcing(qg_handle h, const void* forcing) {
+    if (!h) return QG_ERR_ARG;
+    if (h->layers != 1) return QG_ERR_UNSUPPORTED;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    drop_graph(h);
+    if (!forcing) {
+        h->f2d = nullptr;   // f2d_buf stays allocated for reuse
+        return QG_OK;
+    }
+    if (!h->f2d_buf) {
+        // allocated on first use; listed in allocs so qg_destroy frees it
+        void* p = nullptr;
+        qg_status s = dev_alloc(h, &p, h->plane_f * h->esz);
+        if (s != QG_OK) return fail(h, s);
+        h->f2d_buf = p;
+    }
+    h->f2d = h->f2d_buf;
+    QG_TRY(copy_in(h->f2d, h->ldf, forcing, h->nx - 1, h->ny - 1, h->esz, h->stream));
+    return QG_OK;
+}
+
+qg_status qg_poisson_solve(qg_handle h, const void* rhs, void* psi, int level) {
+    if (!h || !rhs || !psi || level < 0 || level > h->levels) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    const LevelTables* t = nullptr;
+    qg_status s = get_level(h, level, &t);
+    if (s != QG_OK) return fail(h, s);
+    const size_t pl = (size_t)(t->my + 1) * t->ldc;
+    const size_t bytes = pl * h->layers * h->esz;
+    void* buf = nullptr;
+    QG_TRY(cudaMallocAsync(&buf, bytes, h->stream));
+    cudaError_t e = cudaMemsetAsync(buf, 0, bytes, h->stream);
+    const size_t dense = (size_t)(t->mx - 1) * (t->my - 1) * h->esz;
+    for (int L = 0; L < h->layers && e == cudaSuccess; ++L)
+        e = copy_in(static_cast<char*>(buf) + L * pl * h->esz, t->ldc,
+                    static_cast<const char*>(rhs) + L * dense, t->mx - 1, t->my - 1,
+                    h->esz, h->stream);
+    if (e == cudaSuccess) {
+        s = h->dtype == QG_F64 ? solve_level<double>(h, *t, buf, buf, buf, pl, h->stream)
+                               : solve_level<float>(h, *t, buf, buf, buf, pl, h->stream);
+        if (s != QG_OK) e = cudaErrorUnknown;
+    }
+    for (int L = 0; L < h->layers && e == cudaSuccess; ++L)
+        e = copy_out(static_cast<char*>(psi) + L * dense, static_cast<char*>(buf) + L * pl * h->esz,
+                     t->ldc, t->mx - 1, t->my - 1, h->esz, h->stream);
+    cudaFreeAsync(buf, h->stream);
+    if (s != QG_OK) return s;
+    QG_TRY(e);
+    return QG_OK;
+}
+
+static qg_status transfer(qg_handle h, const void* src, void* dst, int levels, bool down) {
+    if (!h || !src || !dst || levels < 1) return QG_ERR_ARG;
+    if ((h->nx >> levels) < 2 || (h->ny >> levels) < 2) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    const int mx = h->nx >> levels, my = h->ny >> levels, ldc = padded_ld(mx);
+    const size_t bf = h->plane_f * h->esz, bc = (size_t)(my + 1) * ldc * h->esz;
+    void* f = nullptr;
+    void* c = nullptr;
+    QG_TRY(cudaMallocAsync(&f, bf, h->stream));
+    cudaError_t e = cudaMallocAsync(&c, bc, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, bf, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c, 0, bc, h->stream);
+    if (down) {
+        if (e == cudaSuccess) e = copy_in(f, h->ldf, src, h->nx - 1, h->ny - 1, h->esz, h->stream);
+        if (e == cudaSuccess)
+            e = h->dtype == QG_F64
+                    ? launch_restrict<double>((const double*)f, h->ldf, (double*)c, ldc, mx, my, levels, h->stream)
+                    : launch_restrict<float>((const float*)f, h->ldf, (float*)c, ldc, mx, my, levels, h->stream);
+        if (e == cudaSuccess) e = copy_out(dst, c, ldc, mx - 1, my - 1, h->esz, h->stream);
+    } else {
+        if (e == cudaSuccess) e = copy_in(c, ldc, src, mx - 1, my - 1, h->esz, h->stream);
+        if (e == cudaSuccess)
+            e = h->dtype == QG_F64
+                    ? launch_prolong<double>((const double*)c, ldc, (double*)f, h->ldf, h->nx, h->ny, levels, h->stream)
+                    : launch_prolong<float>((const float*)c, ldc, (float*)f, h->ldf, h->nx, h->ny, levels, h->stream);
+        if (e == cudaSuccess) e = copy_out(dst, f, h->ldf, h->nx - 1, h->ny - 1, h->esz, h->stream);
+    }
+    if (c) cudaFreeAsync(c, h->stream);
+    cudaFreeAsync(f, h->stream);
+    QG_TRY(e);
+    return QG_OK;
+}
+
+qg_status qg_restrict(qg_handle h, const void* fine, void* coarse, int levels) {
+    return transfer(h, fine, coarse, levels, true);
+}
+
+qg_status qg_prolong(qg_handle h, const void* coarse, void* fine, int levels) {
+    return transfer(h, coarse, fine, levels, false);
+}
+
+qg_status qg_step(qg_handle h, int64_t n) {
+    if (!h || n < 0) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    if (n == 0) return QG_OK;
+    qg_status s = build_graph(h);
+    if (s != QG_OK) return s;
+    for (int64_t k = 0; k < n; ++k) QG_TRY(cudaGraphLaunch(h->gexec, h->stream));
+    return QG_OK;
+}
+
+qg_status qg_set_timing(qg_handle h, int enable) {
+    if (!h) return QG_ERR_ARG;
+    if ((enable != 0) != h->timing) {
+        QG_TRY(cudaStreamSynchronize(h->stream));
+        drop_graph(h);
+        h->timing = enable != 0;
+    }
+    return QG_OK;
+}
+
+qg_status qg_read_timing(qg_handle h, double* ms, int32_t* launches) {
+    if (!h || !ms || !launches) return QG_ERR_ARG;
+    if (!h->timing || !h->gexec) return QG_ERR_ARG;
+    QG_TRY(cudaStreamSynchronize(h->stream));
+    for (int c = 0; c < QG_K_COUNT; ++c) {
+        ms[c] = 0.0;
+        launches[c] = 0;
+    }
+    for (auto& u : h->ev_used) {
+        float t = 0.f;
+        QG_TRY(cudaEventElapsedTime(&t, u.second.first, u.second.second));
+        ms[u.first] += t;
+        launches[u.first] += 1;
+    }
+    return QG_OK;
+}
+
+qg_status qg_step_kernel_count(qg_handle h, int64_t* count) {
+    if (!h || !count) return QG_ERR_ARG;
+    qg_status s = build_graph(h);
+    if (s != QG_OK) return s;
+    *count = h->kernels_per_step;
+    return QG_OK;
+}
+
+qg_status qg_diagnostics(qg_handle h, double* ke, double* enstrophy, double* max_vel) {
+    if (!h) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    qg_status s = project_any(h, h->w[0], h->stream);
+    if (s != QG_OK) return s;
+    if (h->dtype == QG_F64)
+        QG_TRY(launch_diagnostics<double>((const double*)h->psi, (const double*)h->w[0], h->nx,
+                                          h->ny, h->ldf, h->dx, h->dy, h->dpart, diag_blocks(),
+                                          h->dout, h->stream));
+    else
+        QG_TRY(launch_diagnostics<float>((const float*)h->psi, (const float*)h->w[0], h->nx,
+                                         h->ny, h->ldf, h->dx, h->dy, h->dpart, diag_blocks(),
+                                         h->dout, h->stream));
+    QG_TRY(cudaMemcpyAsync(h->hout, h->dout, sizeof(double) * 5, cudaMemcpyDeviceToHost, h->stream));
+    QG_TRY(cudaStreamSynchronize(h->stream));
+    const double* r = h->hout;
+    const double dx = h->dx, dy = h->dy;
+    const double E = 0.5 * dx * dy * (r[0] / (dx * dx) + r[1] / (dy * dy));
+    const double Z = 0.5 * dx * dy * r[2];
+    const double U = std::fmax(r[3] / (2.0 * dx), r[4] / (2.0 * dy));
+    if (!std::isfinite(E) || !std::isfinite(Z)) return fail(h, QG_ERR_NONFINITE);
+    if (ke) *ke = E;
+    if (enstrophy) *enstrophy = Z;
+    if (max_vel) *max_vel = U;
+    return QG_OK;
+}
+
+}  // extern "C"

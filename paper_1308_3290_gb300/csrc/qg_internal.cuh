@@ -1,0 +1,133 @@
+// Internal declarations shared by the CUDA translation units of libqgcgp.
+//
+// Device layout of every grid of a basin ("padded node layout"): a level with
+// n_x x n_y intervals is stored as n_y + 1 rows of `ld` elements, node (i, j)
+// at [j * ld + i], i = 0..n_x, j = 0..n_y; ld = round_up(n_x + 1, 32).  The
+// wall nodes (i = 0, n_x and j = 0, n_y) always hold 0 and the columns past
+// n_x are never read.  Row j, entries 0..n_x-1, is exactly the length-n_x
+// input f_0..f_{n_x-1} (f_0 = 0) of the DST-I engine, so the solver runs on
+// the stored rows without repacking.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qg.h"
+
+namespace qg {
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+inline int ilog2(int v) { int r = 0; while ((1 << r) < v) ++r; return r; }
+inline bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Shape of one DST launch: NB butterflies per thread and pass, `lanes`
+// independent sequences per CTA.
+struct DstLaunch {
+    int nb;
+    int lanes;
+};
+
+// ---- kernels (declared here, defined in dst.cu / stencil.cu / diag.cu) ----
+
+// Unnormalised DST-I, F_k = sum_{j=1}^{N-1} f_j sin(pi j k / N), of rows
+// 1..nrows of a padded array (row length N = n_x).  in and out may alias.
+template <typename T>
+cudaError_t launch_dst_rows(const T* in, T* out, int ld, int nrows, int N,
+                            const typename Cx<T>::type* tw, DstLaunch cfg,
+                            cudaStream_t s);
+
+// Column pass of the one-layer solve on a padded level array of
+// (N_x - 1) columns: forward DST-I along y, multiplication by
+// scale / (lamx[k] + lamy[l]), inverse DST-I along y, in place.
+template <typename T>
+cudaError_t launch_dst_cols_solve(T* data, int ld, int ncols, int N,
+                                  const typename Cx<T>::type* tw,
+                                  const T* lamx, const T* lamy, T scale,
+                                  DstLaunch cfg, cudaStream_t s);
+
+// Column pass of the two-layer coupled solve (Eqs. isub-1/2): planes
+// data0 / data1 hold Q_1, Q_2 in the x-sine basis; per mode the 2x2 system
+// is solved with alpha = Ro (lamx + lamy).
+template <typename T>
+cudaError_t launch_dst_cols_solve2(T* data0, T* data1, int ld, int ncols,
+                                   int N, const typename Cx<T>::type* tw,
+                                   const T* lamx, const T* lamy, T scale,
+                                   T Ro, T f1, T f2, DstLaunch cfg,
+                                   cudaStream_t s);
+
+DstLaunch dst_rows_config(int N, size_t esz);
+size_t dst_max_smem();                       // dynamic shared memory cap per CTA
+size_t dst_lane_bytes(int N, size_t esz);    // shared memory of one sequence pair
+DstLaunch dst_cols_config(int N, size_t esz);
+cudaError_t dst_prepare_kernels();
+
+// Full-weighting restriction applied `levels` times, as one hat-weighted
+// sum (fine -> level `levels`), interior coarse nodes only.
+template <typename T>
+cudaError_t launch_restrict(const T* fine, int ldf, T* coarse, int ldc,
+                            int mx, int my, int levels, cudaStream_t s);
+
+// Bilinear prolongation applied `levels` times (level `levels` -> fine),
+// interior fine nodes only.
+template <typename T>
+cudaError_t launch_prolong(const T* coarse, int ldc, T* fine, int ldf,
+                           int nx, int ny, int levels, cudaStream_t s);
+
+// Constants of one fine-grid stage of the one-layer model.
+template <typename T>
+struct StageParams {
+    int nx, ny, ld;
+    T c_jac;      // 1 / (12 dx dy): Arakawa (J1 + J2 + J3) / 3 / (4 dx dy)
+    T c_beta;     // 1 / (12 Ro dx): closed form of (1/Ro) J(psi, y)
+    T c_lapx;     // 1 / (Re dx^2)
+    T c_lapy;     // 1 / (Re dy^2)
+    T dt;
+    T a;          // weight of w^n in the TVDRK3 combination
+    T b;          // weight of (w^(s) + dt G)
+};
+
+// One TVDRK3 stage on the fine grid: w_out = a w_n + b (w + dt G(psi, w)),
+// G = -J(psi, w) - (1/Ro) J(psi, y) + (1/Re) lap w + F.  F is the per-row
+// forcing `frow` (length ny + 1), or the padded field `f2d` when non-null.
+template <typename T>
+cudaError_t launch_fine_stage(const T* psi, const T* w, const T* wn, T* wout,
+                              const T* frow, const T* f2d,
+                              const StageParams<T>& p, cudaStream_t s);
+
+// Two-layer stage (Eq. ge-non): both layers in one pass.
+template <typename T>
+struct StageParams2 {
+    int nx, ny, ld;
+    T c_jac, c_beta;     // 1/(12 dx dy), 1/(12 dx)
+    T inv_Ro;            // 1/Ro
+    T f1, f2;            // Fr/delta, Fr/(1-delta)
+    T A_dx2, A_dy2;      // A/dx^2, A/dy^2
+    T sigma;
+    T dt, a, b;
+};
+template <typename T>
+cudaError_t launch_fine_stage2(const T* psi1, const T* psi2, const T* q1,
+                               const T* q2, const T* qn1, const T* qn2,
+                               T* out1, T* out2, const T* frow,
+                               const StageParams2<T>& p, cudaStream_t s);
+
+// Deterministic FP64 diagnostics: per-CTA partial sums of the squared edge
+// differences of psi along x and y, of w^2, and per-CTA maxima of |psi_x|,
+// |psi_y|; then one CTA folds them in a fixed order into out[0..3].
+template <typename T>
+cudaError_t launch_diagnostics(const T* psi, const T* w, int nx, int ny, int ld,
+                               double dx, double dy, double* partial,
+                               int nblocks, double* out, cudaStream_t s);
+int diag_blocks();
+
+// Copies between the dense exchange layout and the padded node layout.
+cudaError_t copy_in(void* padded, int ld, const void* dense, int nxm1,
+                    int nym1, size_t esz, cudaStream_t s);
+cudaError_t copy_out(void* dense, const void* padded, int ld, int nxm1,
+                     int nym1, size_t esz, cudaStream_t s);
+
+}  // namespace qg

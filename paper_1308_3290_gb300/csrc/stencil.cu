@@ -1,0 +1,223 @@
+// Fine-grid stage and mapping operators.
+//
+// fine_stage: one TVDRK3 stage (Section 4.2, Eq. TVDRK) of the one-layer
+// vorticity equation on the fine grid, with the Arakawa Jacobian
+// (Section 4.1, Eqs. ja1, j1-j3), the beta term J(psi, y)/Ro, the 5-point
+// dissipation (1/Re) lap w and the wind forcing (Section 2.1, Eq. ge divided
+// by Ro).  restrict / prolong: the mapping operators of Section 3.1 (Eqs. res
+// and pro), l levels at once.
+#include <cuda_runtime.h>
+
+#include "qg_internal.cuh"
+
+namespace qg {
+namespace {
+
+// The nine-point Arakawa combination J1 + J2 + J3 (without 1/(4 dx dy) and
+// the 1/3), for psi values p.. and q values q.. at offsets (di, dj), m = -1.
+template <typename T>
+__device__ __forceinline__ T arakawa_sum(T pm0, T p10, T p0m, T p01, T pmm,
+                                         T p1m, T pm1, T p11, T qm0, T q10,
+                                         T q0m, T q01, T qmm, T q1m, T qm1,
+                                         T q11) {
+    const T j1 = -(q10 - qm0) * (p01 - p0m) + (q01 - q0m) * (p10 - pm0);
+    const T j2 = -q10 * (p11 - p1m) + qm0 * (pm1 - pmm) + q01 * (p11 - pm1) -
+                 q0m * (p1m - pmm);
+    const T j3 = -q11 * (p01 - p10) + qmm * (pm0 - p0m) + qm1 * (p01 - pm0) -
+                 q1m * (p10 - p0m);
+    return j1 + j2 + j3;
+}
+
+template <typename T>
+__global__ void fine_stage_kernel(const T* __restrict__ psi,
+                                  const T* __restrict__ w, const T* wn,
+                                  T* wout, const T* __restrict__ frow,
+                                  const T* __restrict__ f2d, StageParams<T> p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    if (i >= p.nx || j >= p.ny) return;
+    const int ld = p.ld;
+    const size_t c = (size_t)j * ld + i;
+    const T* P = psi + c;
+    const T* Q = w + c;
+    const T pm0 = P[-1], p10 = P[1], p0m = P[-ld], p01 = P[ld];
+    const T pmm = P[-ld - 1], p1m = P[-ld + 1], pm1 = P[ld - 1], p11 = P[ld + 1];
+    const T q00 = Q[0];
+    const T qm0 = Q[-1], q10 = Q[1], q0m = Q[-ld], q01 = Q[ld];
+    const T qmm = Q[-ld - 1], q1m = Q[-ld + 1], qm1 = Q[ld - 1], q11 = Q[ld + 1];
+    const T jac = arakawa_sum(pm0, p10, p0m, p01, pmm, p1m, pm1, p11, qm0, q10,
+                              q0m, q01, qmm, q1m, qm1, q11) * p.c_jac;
+    // (1/Ro) J(psi, y) = (4 c_j + c_{j+1} + c_{j-1}) / (6 Ro),
+    // c = (psi_{i+1} - psi_{i-1}) / (2 dx): Arakawa's form with q = y.
+    const T beta = (T(4) * (p10 - pm0) + (p11 - pm1) + (p1m - pmm)) * p.c_beta;
+    const T lap = (q10 + qm0 - T(2) * q00) * p.c_lapx + (q01 + q0m - T(2) * q00) * p.c_lapy;
+    const T F = f2d ? f2d[c] : frow[j];
+    const T G = -jac - beta + lap + F;
+    T v = p.b * (q00 + p.dt * G);
+    if (p.a != T(0)) v += p.a * wn[c];
+    wout[c] = v;
+}
+
+// Two-layer stage (Section 2.2, Eq. ge-non with Q_i = q_i - y):
+//   G_1 = -J(psi_1, Q_1) - J(psi_1, y) + A lap w_1 + amp sin(2 pi y)
+//   G_2 = -J(psi_2, Q_2) - J(psi_2, y) + A lap w_2 - sigma w_2
+// with w_i recovered from Eq. pv-non at every node of the 5-point stencil.
+template <typename T>
+__global__ void fine_stage2_kernel(const T* __restrict__ psi1,
+                                   const T* __restrict__ psi2,
+                                   const T* __restrict__ q1,
+                                   const T* __restrict__ q2, const T* qn1,
+                                   const T* qn2, T* out1, T* out2,
+                                   const T* __restrict__ frow,
+                                   StageParams2<T> p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    if (i >= p.nx || j >= p.ny) return;
+    const int ld = p.ld;
+    const size_t c = (size_t)j * ld + i;
+    auto w1 = [&](size_t o) { return (q1[o] - p.f1 * (psi2[o] - psi1[o])) * p.inv_Ro; };
+    auto w2 = [&](size_t o) { return (q2[o] - p.f2 * (psi1[o] - psi2[o])) * p.inv_Ro; };
+#pragma unroll
+    for (int layer = 0; layer < 2; ++layer) {
+        const T* P = (layer == 0 ? psi1 : psi2) + c;
+        const T* Q = (layer == 0 ? q1 : q2) + c;
+        const T pm0 = P[-1], p10 = P[1], p0m = P[-ld], p01 = P[ld];
+        const T pmm = P[-ld - 1], p1m = P[-ld + 1], pm1 = P[ld - 1], p11 = P[ld + 1];
+        const T q00 = Q[0];
+        const T qm0 = Q[-1], q10 = Q[1], q0m = Q[-ld], q01 = Q[ld];
+        const T qmm = Q[-ld - 1], q1m = Q[-ld + 1], qm1 = Q[ld - 1], q11 = Q[ld + 1];
+        const T jac = arakawa_sum(pm0, p10, p0m, p01, pmm, p1m, pm1, p11, qm0, q10,
+                                  q0m, q01, qmm, q1m, qm1, q11) * p.c_jac;
+        const T beta = (T(4) * (p10 - pm0) + (p11 - pm1) + (p1m - pmm)) * p.c_beta;
+        T wc, wl, wr, wd, wu;
+        if (layer == 0) {
+            wc = w1(c); wl = w1(c - 1); wr = w1(c + 1); wd = w1(c - ld); wu = w1(c + ld);
+        } else {
+            wc = w2(c); wl = w2(c - 1); wr = w2(c + 1); wd = w2(c - ld); wu = w2(c + ld);
+        }
+        // walls: w = 0 (free slip); the formula gives 0 there since Q = psi = 0
+        const T lap = (wr + wl - T(2) * wc) * p.A_dx2 + (wu + wd - T(2) * wc) * p.A_dy2;
+        const T src = (layer == 0) ? frow[j] : -p.sigma * wc;
+        const T G = -jac - beta + lap + src;
+        T v = p.b * (q00 + p.dt * G);
+        if (p.a != T(0)) v += p.a * (layer == 0 ? qn1 : qn2)[c];
+        (layer == 0 ? out1 : out2)[c] = v;
+    }
+}
+
+// R^l as one hat-weighted sum: with f = 2^l, the composed full weighting has
+// separable weights (f - |d|)/f^2 per direction for |d| < f.
+template <typename T>
+__global__ void restrict_kernel(const T* __restrict__ fine, int ldf,
+                                T* __restrict__ coarse, int ldc, int mx,
+                                int my, int levels) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    if (I >= mx || J >= my) return;
+    const int f = 1 << levels;
+    const T* base = fine + (size_t)(f * J) * ldf + f * I;
+    T acc = T(0);
+    for (int dj = -(f - 1); dj <= f - 1; ++dj) {
+        const T* row = base + (ptrdiff_t)dj * ldf;
+        T racc = T(0);
+        for (int di = -(f - 1); di <= f - 1; ++di) {
+            racc += T(f - (di < 0 ? -di : di)) * row[di];
+        }
+        acc += T(f - (dj < 0 ? -dj : dj)) * racc;
+    }
+    const T inv = T(1) / (T(f) * T(f) * T(f) * T(f));
+    coarse[(size_t)J * ldc + I] = acc * inv;
+}
+
+// P^l as bilinear interpolation from the coarse nodes around each fine node.
+template <typename T>
+__global__ void prolong_kernel(const T* __restrict__ coarse, int ldc,
+                               T* __restrict__ fine, int ldf, int nx, int ny,
+                               int levels) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    if (i >= nx || j >= ny) return;
+    const int f = 1 << levels;
+    const int I = i >> levels, J = j >> levels;
+    const T a = T(i & (f - 1)) / T(f);
+    const T b = T(j & (f - 1)) / T(f);
+    const T* C = coarse + (size_t)J * ldc + I;
+    const T v = (T(1) - a) * (T(1) - b) * C[0] + a * (T(1) - b) * C[1] +
+                (T(1) - a) * b * C[ldc] + a * b * C[ldc + 1];
+    fine[(size_t)j * ldf + i] = v;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_fine_stage(const T* psi, const T* w, const T* wn, T* wout,
+                              const T* frow, const T* f2d,
+                              const StageParams<T>& p, cudaStream_t s) {
+    const dim3 block(32, 8);
+    const dim3 grid((p.nx - 1 + 31) / 32, (p.ny - 1 + 7) / 8);
+    fine_stage_kernel<T><<<grid, block, 0, s>>>(psi, w, wn, wout, frow, f2d, p);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fine_stage2(const T* psi1, const T* psi2, const T* q1,
+                               const T* q2, const T* qn1, const T* qn2,
+                               T* out1, T* out2, const T* frow,
+                               const StageParams2<T>& p, cudaStream_t s) {
+    const dim3 block(32, 8);
+    const dim3 grid((p.nx - 1 + 31) / 32, (p.ny - 1 + 7) / 8);
+    fine_stage2_kernel<T><<<grid, block, 0, s>>>(psi1, psi2, q1, q2, qn1, qn2,
+                                                  out1, out2, frow, p);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restrict(const T* fine, int ldf, T* coarse, int ldc, int mx,
+                            int my, int levels, cudaStream_t s) {
+    const dim3 block(32, 8);
+    const dim3 grid((mx - 1 + 31) / 32, (my - 1 + 7) / 8);
+    restrict_kernel<T><<<grid, block, 0, s>>>(fine, ldf, coarse, ldc, mx, my, levels);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prolong(const T* coarse, int ldc, T* fine, int ldf, int nx,
+                           int ny, int levels, cudaStream_t s) {
+    const dim3 block(32, 8);
+    const dim3 grid((nx - 1 + 31) / 32, (ny - 1 + 7) / 8);
+    prolong_kernel<T><<<grid, block, 0, s>>>(coarse, ldc, fine, ldf, nx, ny, levels);
+    return cudaGetLastError();
+}
+
+cudaError_t copy_in(void* padded, int ld, const void* dense, int nxm1, int nym1,
+                    size_t esz, cudaStream_t s) {
+    char* dst = static_cast<char*>(padded) + (size_t)(ld + 1) * esz;
+    return cudaMemcpy2DAsync(dst, (size_t)ld * esz, dense, (size_t)nxm1 * esz,
+                             (size_t)nxm1 * esz, nym1, cudaMemcpyDefault, s);
+}
+
+cudaError_t copy_out(void* dense, const void* padded, int ld, int nxm1, int nym1,
+                     size_t esz, cudaStream_t s) {
+    const char* src = static_cast<const char*>(padded) + (size_t)(ld + 1) * esz;
+    return cudaMemcpy2DAsync(dense, (size_t)nxm1 * esz, src, (size_t)ld * esz,
+                             (size_t)nxm1 * esz, nym1, cudaMemcpyDefault, s);
+}
+
+#define QG_INST(T)                                                                  \
+    template cudaError_t launch_fine_stage<T>(const T*, const T*, const T*, T*,     \
+                                              const T*, const T*,                   \
+                                              const StageParams<T>&, cudaStream_t); \
+    template cudaError_t launch_fine_stage2<T>(const T*, const T*, const T*,        \
+                                               const T*, const T*, const T*, T*,    \
+                                               T*, const T*,                        \
+                                               const StageParams2<T>&,              \
+                                               cudaStream_t);                       \
+    template cudaError_t launch_restrict<T>(const T*, int, T*, int, int, int, int,  \
+                                            cudaStream_t);                          \
+    template cudaError_t launch_prolong<T>(const T*, int, T*, int, int, int, int,   \
+                                           cudaStream_t);
+QG_INST(float)
+QG_INST(double)
+#undef QG_INST
+
+}  // namespace qg

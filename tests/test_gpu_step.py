@@ -1,0 +1,120 @@
+"""GPU parity of the CGPRK3 step (Section 3.2) with the oracle.
+
+FP64, the 64 x 128 / 32 x 64 basin of Experiment I (Re = 200, Ro = 0.0016,
+dt = 1e-4), 1000 steps from the seeded N(0, 1e-2) perturbation; FP32 after
+100 steps within the 1e-4 relative L2 bound; l = 0, 1, 2, 3; a user forcing
+field; the diagnostics; and one step of the 2048 x 4096, l = 2 workload.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import qg_oracle as O
+from paper_1308_3290_gb300 import inputs, qg
+from tests.gpu_util import rel_l2, require_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_run(nx, ny, levels, dtype, w0, nsteps, dt=1e-4, Re=200.0, Ro=0.0016, forcing=None):
+    b = qg.Basin(nx, ny, Re=Re, Ro=Ro, levels=levels, dt=dt, dtype=dtype)
+    b.set_state(w0)
+    if forcing is not None:
+        b.set_forcing(forcing)
+    b.step(nsteps)
+    out = to_np(b.state())
+    b.close()
+    return out
+
+
+def test_config1_fp64_1000_steps():
+    require_gpu()
+    nx, ny = 64, 128
+    w0 = inputs.perturbation(nx, ny, seed=1)
+    ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=1, dt=1e-4)
+    ref = O.run(w0, ob, 1000)
+    got = gpu_run(nx, ny, 1, "f64", w0, 1000)
+    assert rel_l2(got, ref) <= 1e-11
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2, 3])
+def test_fp64_100_steps(levels):
+    require_gpu()
+    nx, ny = 64, 128
+    w0 = inputs.perturbation(nx, ny, seed=3) * 50.0
+    ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=1e-4)
+    ref = O.run(w0, ob, 100)
+    got = gpu_run(nx, ny, levels, "f64", w0, 100)
+    assert rel_l2(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_fp32_100_steps(levels):
+    require_gpu()
+    nx, ny = 128, 256
+    w0 = inputs.perturbation(nx, ny, seed=4) * 50.0
+    ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=5e-5)
+    ref = O.run(w0, ob, 100)
+    got = gpu_run(nx, ny, levels, "f32", w0, 100, dt=5e-5)
+    assert rel_l2(got, ref) <= 1e-4
+
+
+def test_experiment_II_parameters():
+    require_gpu()
+    nx, ny = 64, 128
+    w0 = inputs.perturbation(nx, ny, seed=6) * 20.0
+    ob = O.Basin(nx, ny, Re=312.5, Ro=0.0025, levels=1, dt=1e-4)
+    ref = O.run(w0, ob, 200)
+    got = gpu_run(nx, ny, 1, "f64", w0, 200, Re=312.5, Ro=0.0025)
+    assert rel_l2(got, ref) <= 1e-12
+
+
+def test_user_forcing_field():
+    require_gpu()
+    nx, ny = 64, 128
+    F = inputs.perturbed_forcing_field(nx, ny, seed=5, Ro=0.0016)
+    w0 = inputs.perturbation(nx, ny, seed=7)
+    ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=1, dt=1e-4, forcing=F)
+    ref = O.run(w0, ob, 50)
+    got = gpu_run(nx, ny, 1, "f64", w0, 50, forcing=F)
+    assert rel_l2(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_diagnostics_and_psi(dtype, tol):
+    require_gpu()
+    nx, ny = 64, 128
+    w0 = inputs.smooth_field(nx, ny, seed=8, amp=100.0, noise=1.0)
+    b = qg.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=1, dt=1e-4, dtype=dtype)
+    b.set_state(w0)
+    ob = O.Basin(nx, ny, levels=1)
+    psi_ref = O.cgp_psi(O.embed(w0), ob)
+    assert rel_l2(to_np(b.psi()), O.interior(psi_ref)) <= tol
+    ke, z, u = b.diagnostics()
+    assert abs(ke - O.kinetic_energy(psi_ref, ob.dx, ob.dy)) <= tol * ke
+    assert abs(z - O.enstrophy(O.embed(w0), ob.dx, ob.dy)) <= tol * z
+    assert abs(u - O.max_velocity(psi_ref, ob.dx, ob.dy)) <= 10 * tol * u
+    b.close()
+
+
+def test_bitwise_deterministic():
+    require_gpu()
+    nx, ny = 256, 512
+    w0 = inputs.perturbation(nx, ny, seed=9) * 30.0
+    a = gpu_run(nx, ny, 2, "f32", w0, 20, dt=2e-5)
+    b = gpu_run(nx, ny, 2, "f32", w0, 20, dt=2e-5)
+    assert np.array_equal(a, b)
+
+
+def test_full_size_workload_one_step():
+    """One step of the 2048 x 4096, l = 2, FP32 workload the benchmark
+    times, against one FP64 oracle step from the same seeded state."""
+    require_gpu()
+    nx, ny = 2048, 4096
+    w0 = inputs.gyre_state(nx, ny, seed=2)
+    ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=2, dt=2e-6)
+    ref = O.run(w0, ob, 1)
+    got = gpu_run(nx, ny, 2, "f32", w0, 1, dt=2e-6)
+    assert rel_l2(got, ref) <= 1e-6
+    assert rel_l2(got - w0, ref - w0) <= 1e-3   # the increment itself

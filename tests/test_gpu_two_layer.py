@@ -1,0 +1,36 @@
+"""GPU parity of the two-layer CGPRK3 step (Section 2.2, Table 2 Experiment 1
+parameters) with the oracle."""
+import numpy as np
+import pytest
+
+from oracle import qg_oracle as O
+from paper_1308_3290_gb300 import inputs, qg
+from tests.gpu_util import rel_l2, require_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 1e-4)])
+@pytest.mark.parametrize("levels", [0, 1])
+def test_two_layer_steps(dtype, tol, levels):
+    require_gpu()
+    nx, ny = 64, 64
+    p = dict(Ro=2.49e-4, Fr=0.087, delta=0.2, sigma=1.43e-3)
+    A = 3.57e-7
+    Re = p["Ro"] / A
+    Q1 = inputs.smooth_field(nx, ny, seed=1, amp=0.05, noise=0.01)
+    Q2 = inputs.smooth_field(nx, ny, seed=2, amp=0.02, noise=0.01)
+    ob = O.TwoLayer(nx, ny, A=A, levels=levels, dt=1e-4, **p)
+    a1, a2 = O.embed(Q1), O.embed(Q2)
+    for _ in range(50):
+        a1, a2 = O.cgprk3_step_two_layer(a1, a2, ob)
+    b = qg.Basin(nx, ny, Re=Re, levels=levels, dt=1e-4, dtype=dtype, layers=2,
+                 y0=-0.5, y1=0.5, **p)
+    b.set_state(Q1, 0)
+    b.synchronize()
+    b.set_state(Q2, 1)
+    b.step(50)
+    g1, g2 = to_np(b.state(0)), to_np(b.state(1))
+    assert rel_l2(g1, O.interior(a1)) <= tol
+    assert rel_l2(g2, O.interior(a2)) <= tol
+    b.close()
