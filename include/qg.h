@@ -180,6 +180,27 @@ qg_status qg_read_timing(qg_handle h, double* ms, int32_t* launches);
 /* qg_step_kernel_count -- number of kernels one step launches.             */
 qg_status qg_step_kernel_count(qg_handle h, int64_t* count);
 
+/* qg_poisson_solve_noalloc -- the one-layer solve lap_h psi = rhs on an
+ * nx x ny-interval grid with spacings dx, dy and psi = 0 on the walls, by
+ * the same sine-transform kernels as qg_poisson_solve, for callers that must
+ * not allocate device memory (an application that hands out all device
+ * memory through its own pool or quota, or a loop where cudaMalloc/cudaFree
+ * would synchronise the device).  The paper has no counterpart to this call.
+ *
+ * It needs no handle and allocates nothing: its workspace lives in one
+ * library-owned 16 MiB device array that every GPU loading the library keeps
+ * until exit.  The padded grid plus tables must fit in it (for example up to
+ * 1024 x 2048 intervals in FP32 or 1024 x 1024 in FP64); larger requests
+ * return QG_ERR_SHAPE.  rhs and psi are DEVICE pointers in the level-0
+ * exchange layout of that grid; work is enqueued on cuda_stream on the
+ * current device.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress): make it before any stream capture starts.
+ * All calls share the array: each clears what must start at zero, and calls
+ * whose GPU work overlaps (unordered streams) race and give wrong results.  */
+qg_status qg_poisson_solve_noalloc(int32_t nx, int32_t ny, double dx, double dy,
+                                   qg_dtype dtype, const void* rhs, void* psi,
+                                   void* cuda_stream);
+
 /* qg_synchronize -- wait for the handle's work; returns any latched error. */
 qg_status qg_synchronize(qg_handle h);
 

@@ -1,0 +1,154 @@
+// qg_poisson_solve_noalloc: the sine-transform Poisson solve without any
+// device allocation.
+//
+// Some callers cannot call cudaMalloc: a host application that hands out all
+// device memory through its own pool or a hard per-tenant quota, or a
+// latency-critical loop in which cudaMalloc/cudaFree would synchronise the
+// device and stall unrelated streams.  For them this entry point keeps its
+// workspace (the padded work grid and the twiddle and eigenvalue tables) in
+// one file-scope __device__ array of fixed size, kNoAllocBytes.  Every GPU
+// that loads the library holds that array until the process exits.
+//
+// The array's name in host code is only a host-side stand-in, not a device
+// address, so the first call on each device looks up the real address with
+// cudaGetSymbolAddress while that device is current, and later calls reuse
+// it.  Make that first call on a device before any stream capture begins.
+// All calls share the one array and it keeps the contents of the last call:
+// each call clears the part that must start at zero, and two calls whose work
+// overlaps on the GPU (different streams, no ordering between them) race on
+// it.  The paper has no counterpart to this entry point.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "qg_internal.cuh"
+
+namespace qg {
+namespace {
+
+constexpr size_t kNoAllocBytes = 16u << 20;   // 16 MiB per device
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_setup_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Twiddle tables e^{i pi t/N} (t < 2N) of both directions and the 1-D
+// eigenvalues of the 5-point Laplacian, computed in FP64 on the device and
+// stored in the working precision.
+template <typename T>
+__global__ void noalloc_tables(typename Cx<T>::type* twx, int mx,
+                               typename Cx<T>::type* twy, int my, T* lamx,
+                               T* lamy, double dx, double dy) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 2 * mx) {
+        double s, c;
+        sincospi((double)i / mx, &s, &c);
+        twx[i].x = (T)c;
+        twx[i].y = (T)s;
+    }
+    if (i < 2 * my) {
+        double s, c;
+        sincospi((double)i / my, &s, &c);
+        twy[i].x = (T)c;
+        twy[i].y = (T)s;
+    }
+    if (i <= mx) lamx[i] = (i == 0 || i == mx) ? T(0) : (T)((2.0 * cospi((double)i / mx) - 2.0) / (dx * dx));
+    if (i <= my) lamy[i] = (i == 0 || i == my) ? T(0) : (T)((2.0 * cospi((double)i / my) - 2.0) / (dy * dy));
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Byte layout of the scratch for one request: padded grid, then the tables.
+struct Layout {
+    size_t grid, twx, twy, lamx, lamy, total;
+};
+
+Layout layout(int nx, int ny, size_t esz) {
+    Layout L;
+    const int ld = round_up(nx + 1, 32);
+    L.grid = 0;
+    L.twx = align256((size_t)(ny + 1) * ld * esz);
+    L.twy = L.twx + align256((size_t)4 * nx * esz);
+    L.lamx = L.twy + align256((size_t)4 * ny * esz);
+    L.lamy = L.lamx + align256((size_t)(nx + 1) * esz);
+    L.total = L.lamy + align256((size_t)(ny + 1) * esz);
+    return L;
+}
+
+template <typename T>
+qg_status solve(unsigned char* base, const Layout& Lo, int nx, int ny, double dx,
+                double dy, const void* rhs, void* psi, cudaStream_t s) {
+    using C = typename Cx<T>::type;
+    const int ld = round_up(nx + 1, 32);
+    T* grid = reinterpret_cast<T*>(base + Lo.grid);
+    C* twx = reinterpret_cast<C*>(base + Lo.twx);
+    C* twy = reinterpret_cast<C*>(base + Lo.twy);
+    T* lamx = reinterpret_cast<T*>(base + Lo.lamx);
+    T* lamy = reinterpret_cast<T*>(base + Lo.lamy);
+    const size_t esz = sizeof(T);
+    // the walls of the padded grid must be zero: clear the whole grid
+    if (cudaMemsetAsync(grid, 0, (size_t)(ny + 1) * ld * esz, s) != cudaSuccess) return QG_ERR_CUDA;
+    const int n = 2 * (nx > ny ? nx : ny) + 1;
+    noalloc_tables<T><<<(n + 255) / 256, 256, 0, s>>>(twx, nx, twy, ny, lamx, lamy, dx, dy);
+    if (cudaGetLastError() != cudaSuccess) return QG_ERR_CUDA;
+    if (copy_in(grid, ld, rhs, nx - 1, ny - 1, esz, s) != cudaSuccess) return QG_ERR_CUDA;
+    const T scale = (T)((2.0 / nx) * (2.0 / ny));
+    if (launch_dst_rows<T>(grid, grid, ld, ny - 1, nx, twx, dst_rows_config(nx, esz), s) != cudaSuccess)
+        return QG_ERR_CUDA;
+    if (launch_dst_cols_solve<T>(grid, ld, nx - 1, ny, twy, lamx, lamy, scale,
+                                 dst_cols_config(ny, esz), s) != cudaSuccess)
+        return QG_ERR_CUDA;
+    if (launch_dst_rows<T>(grid, grid, ld, ny - 1, nx, twx, dst_rows_config(nx, esz), s) != cudaSuccess)
+        return QG_ERR_CUDA;
+    if (copy_out(psi, grid, ld, nx - 1, ny - 1, esz, s) != cudaSuccess) return QG_ERR_CUDA;
+    return QG_OK;
+}
+
+}  // namespace
+}  // namespace qg
+
+using namespace qg;
+
+extern "C" qg_status qg_poisson_solve_noalloc(int32_t nx, int32_t ny, double dx,
+                                              double dy, qg_dtype dtype,
+                                              const void* rhs, void* psi,
+                                              void* cuda_stream) {
+    if (!rhs || !psi) return QG_ERR_ARG;
+    if (dtype != QG_F32 && dtype != QG_F64) return QG_ERR_ARG;
+    if (!(dx > 0) || !(dy > 0)) return QG_ERR_ARG;
+    if (!is_pow2(nx) || !is_pow2(ny) || nx < 8 || ny < 8 || nx > 8192 || ny > 8192)
+        return QG_ERR_SHAPE;
+    const size_t esz = dtype == QG_F64 ? 8 : 4;
+    if (layout(nx, ny, esz).total > kNoAllocBytes) return QG_ERR_SHAPE;
+    if (dst_lane_bytes(nx, esz) > dst_max_smem() || dst_lane_bytes(ny, esz) > dst_max_smem())
+        return QG_ERR_SHAPE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return QG_ERR_NO_DEVICE;
+    }
+    if (dev < 0 || dev >= kMaxDevices) return QG_ERR_UNSUPPORTED;
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (!g_scratch_addr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+                (void)cudaGetLastError();
+                return QG_ERR_CUDA;
+            }
+            if (dst_prepare_kernels() != cudaSuccess) {
+                (void)cudaGetLastError();
+                return QG_ERR_CUDA;
+            }
+            g_scratch_addr[dev] = p;
+        }
+        base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    }
+    const Layout Lo = layout(nx, ny, esz);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    return dtype == QG_F64 ? solve<double>(base, Lo, nx, ny, dx, dy, rhs, psi, s)
+                           : solve<float>(base, Lo, nx, ny, dx, dy, rhs, psi, s);
+}

@@ -34,7 +34,7 @@ EXPORTS = [
     "qg_set_forcing", "qg_poisson_solve", "qg_restrict", "qg_prolong",
     "qg_step", "qg_diagnostics", "qg_set_timing", "qg_read_timing",
     "qg_step_kernel_count", "qg_synchronize", "qg_status_string",
-    "qg_last_error",
+    "qg_last_error", "qg_poisson_solve_noalloc",
 ]
 
 KERNEL_CLASSES = ["restrict", "dst_rows", "dst_cols", "prolong", "fine"]
@@ -85,6 +85,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "qg_read_timing": [vp, ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_int32)],
         "qg_step_kernel_count": [vp, ctypes.POINTER(i64)],
         "qg_synchronize": [vp],
+        "qg_poisson_solve_noalloc": [i32, i32, dbl, dbl, i32, vp, vp, vp],
         "qg_last_error": [vp],
     }
     for name, args in sig.items():
@@ -187,6 +188,15 @@ def qg_step_kernel_count(h: int) -> int:
     c = ctypes.c_int64()
     _check(load().qg_step_kernel_count(h, ctypes.byref(c)), "qg_step_kernel_count")
     return c.value
+
+
+def qg_poisson_solve_noalloc(nx: int, ny: int, dx: float, dy: float, dtype: int,
+                             rhs, psi, stream: int | None = None) -> None:
+    """Handle-free Poisson solve that allocates no device memory (its
+    workspace is a fixed library-owned device array); rhs and psi are device
+    buffers of shape (ny-1, nx-1)."""
+    _check(load().qg_poisson_solve_noalloc(nx, ny, dx, dy, dtype, _ptr(rhs), _ptr(psi),
+                                           stream or None), "qg_poisson_solve_noalloc")
 
 
 def qg_synchronize(h: int) -> None:
