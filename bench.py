@@ -72,8 +72,12 @@ def alg_bytes_per_launch(cls, nx, ny, levels, esz):
     field the kernel must read or write once, halos from cache."""
     N = n_unknowns(nx, ny)
     Nc = n_unknowns(nx >> levels, ny >> levels)
-    if cls == "fine":      # read w^(s), psi, (w^n in stages 2, 3), write w^(s+1)
-        return esz * N * (3 + 4 + 4) / 3.0
+    if cls == "fine":
+        # fused stage: read w^(s), write w^(s+1), read w^n in stages 2 and 3;
+        # l >= 1: read the elliptic-grid psi, write the restricted field;
+        # l = 0: read the fine psi
+        fine = esz * N * (2 + 3 + 3) / 3.0
+        return fine + (esz * N if levels == 0 else 2 * esz * Nc)
     if cls == "restrict":
         return esz * (N + Nc)
     if cls == "prolong":

@@ -87,9 +87,10 @@ typedef struct qg_ctx* qg_handle;
  *                   (1/Ro) J(psi, y) (Eqs. ge, pv, Rhines, Munk).  Two
  *                   layers: A = Ro/Re is the eddy viscosity of Eq. ge-non.
  * Fr                Froude number of Eq. pv-non (two layers; ignored for 1).
- * coarsening_levels l >= 0: the elliptic sub-problem is solved on level l
- *                   (Section 3); 0 is the standard full-grid solver.  The
- *                   coarse grid must keep at least 8 intervals per direction.
+ * coarsening_levels 0 <= l <= 4: the elliptic sub-problem is solved on
+ *                   level l (Section 3); 0 is the standard full-grid solver.
+ *                   The coarse grid must keep at least 8 intervals per
+ *                   direction.
  * dtype             QG_F32 or QG_F64.
  * cuda_stream       cudaStream_t on which all work of this handle is
  *                   enqueued (NULL = the legacy default stream).

@@ -7,6 +7,8 @@
 //   (iv)  prolongs the streamfunction back (Eq. pro, l times),
 //   (i)   and updates the fine state with the stage's right-hand side.
 // The kernels of one step are captured once into a CUDA graph and replayed.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -49,6 +51,8 @@ struct qg_ctx {
     void* cw = nullptr;            // elliptic-grid work (layers planes)
     void* cpsi = nullptr;          // elliptic-grid psi (layers planes)
     size_t plane_c = 0;
+    void* part = nullptr;          // 4 restriction partial-sum planes (one layer, l >= 1)
+    bool part_valid = false;       // part holds R^l w^n of the current state
     void* frow = nullptr;          // forcing per fine row
     void* f2d = nullptr;           // forcing field in use (padded fine) or null
     void* f2d_buf = nullptr;       // its storage, allocated on first use
@@ -68,7 +72,42 @@ struct qg_ctx {
     size_t ev_next = 0;
     int64_t kernels_per_step = 0;
     bool capturing = false;
+    // TMA tensor maps of the fine buffers (halo and interior boxes)
+    CUtensorMap tm_halo[3], tm_int[3], tm_psi, tm_f;
+    int* derr = nullptr;           // device error flag of bounded waits
 };
+
+namespace qg {
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+cudaError_t make_tensor_map(CUtensorMap* m, const void* base, int nx, int ny, int ld,
+                            size_t esz, int bw, int bh) {
+    auto fn = tensor_map_encoder();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)nx + 1, (cuuint64_t)ny + 1};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * esz};
+    const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = fn(m, esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                          2, const_cast<void*>(base), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace qg
 
 namespace {
 
@@ -220,15 +259,18 @@ T* plane(void* base, size_t plane_elems, int layer) {
 // sub-pr per mode.  `pl` is the plane size of the level's buffers.
 template <typename T>
 qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in,
-                      void* work, void* out, size_t pl, cudaStream_t s) {
+                      void* work, void* out, size_t pl, cudaStream_t s,
+                      int nparts = 1) {
     using C = typename Cx<T>::type;
     const DstLaunch rc = dst_rows_config(t.mx, sizeof(T));
     const DstLaunch cc = dst_cols_config(t.my, sizeof(T));
     const T scale = (T)((2.0 / t.mx) * (2.0 / t.my));
     for (int L = 0; L < h->layers; ++L) {
         KTimer kt(h, s, QG_K_DST_ROWS);
-        QG_TRY(launch_dst_rows<T>(plane<T>(const_cast<void*>(in), pl, L),
-                                  plane<T>(work, pl, L), t.ldc, t.my - 1, t.mx,
+        RowInput<T> ri{{nullptr, nullptr, nullptr, nullptr}, nparts};
+        for (int q = 0; q < nparts; ++q)
+            ri.p[q] = plane<T>(const_cast<void*>(in), pl, L * nparts + q);
+        QG_TRY(launch_dst_rows<T>(ri, plane<T>(work, pl, L), t.ldc, t.my - 1, t.mx,
                                   static_cast<const C*>(t.twx), rc, s));
     }
     {
@@ -250,7 +292,8 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in,
     }
     for (int L = 0; L < h->layers; ++L) {
         KTimer kt(h, s, QG_K_DST_ROWS);
-        QG_TRY(launch_dst_rows<T>(plane<T>(work, pl, L), plane<T>(out, pl, L), t.ldc,
+        RowInput<T> ri{{plane<T>(work, pl, L), nullptr, nullptr, nullptr}, 1};
+        QG_TRY(launch_dst_rows<T>(ri, plane<T>(out, pl, L), t.ldc,
                                   t.my - 1, t.mx, static_cast<const C*>(t.twx), rc, s));
     }
     return QG_OK;
@@ -337,10 +380,76 @@ qg_status stage(qg_ctx* h, int s_idx, cudaStream_t s) {
     return QG_OK;
 }
 
+// One-layer stage with the fused fine kernel.  On entry the restriction of
+// w^(s) is in the partial planes (l >= 1) or w^(s) itself is the elliptic
+// right-hand side (l = 0); the stage solves for psibar^(s), then the fused
+// kernel prolongs it, updates the fine state and leaves R^l w^(s+1) in the
+// partial planes for the next stage.
+template <typename T>
+qg_status stage_fused(qg_ctx* h, int s_idx, cudaStream_t s) {
+    static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double B[3] = {1.0, 0.25, 2.0 / 3.0};
+    void* win = h->w[s_idx];
+    void* wout = h->w[(s_idx + 1) % 3];
+    const LevelTables* t = nullptr;
+    qg_status st = get_level(h, h->levels, &t);
+    if (st != QG_OK) return fail(h, st);
+    if (h->levels == 0) {
+        st = solve_level<T>(h, *t, win, h->cw, h->psi, h->plane_f, s);
+    } else {
+        st = solve_level<T>(h, *t, h->part, h->cw, h->cpsi, h->plane_c, s, 4);
+    }
+    if (st != QG_OK) return st;
+    FusedParams<T> p;
+    p.nx = h->nx;
+    p.ny = h->ny;
+    p.ld = h->ldf;
+    p.psi = static_cast<const T*>(h->levels == 0 ? h->psi : h->cpsi);
+    p.ldp = h->levels == 0 ? h->ldf : t->ldc;
+    p.w = static_cast<const T*>(win);
+    p.wn = static_cast<const T*>(h->w[0]);
+    p.wout = static_cast<T*>(wout);
+    p.frow = static_cast<const T*>(h->frow);
+    p.f2d = static_cast<const T*>(h->f2d);
+    for (int q = 0; q < 4; ++q)
+        p.part[q] = h->part ? plane<T>(h->part, h->plane_c, q) : nullptr;
+    p.ldc = t->ldc;
+    p.err = h->derr;
+    p.c_jac = (T)(1.0 / (12.0 * h->dx * h->dy));
+    p.c_beta = (T)(1.0 / (12.0 * h->Ro * h->dx));
+    p.c_lapx = (T)(1.0 / (h->Re * h->dx * h->dx));
+    p.c_lapy = (T)(1.0 / (h->Re * h->dy * h->dy));
+    p.dt = (T)h->dt;
+    p.a = (T)A[s_idx];
+    p.b = (T)B[s_idx];
+    FineMaps m;
+    m.w = h->tm_halo[s_idx];
+    m.wn = h->tm_int[0];
+    m.psi = h->tm_psi;
+    m.f = h->tm_f;
+    KTimer kt(h, s, QG_K_FINE);
+    QG_TRY(launch_fine_fused<T>(p, m, h->levels, s));
+    return QG_OK;
+}
+
+// Restriction of the current state into the partial planes (plane 0 holds
+// the complete values, planes 1-3 zero), needed once after qg_set_state.
+template <typename T>
+qg_status init_partials(qg_ctx* h, cudaStream_t s) {
+    const LevelTables* t = nullptr;
+    qg_status st = get_level(h, h->levels, &t);
+    if (st != QG_OK) return fail(h, st);
+    QG_TRY(cudaMemsetAsync(h->part, 0, 4 * h->plane_c * sizeof(T), s));
+    QG_TRY(launch_restrict<T>(static_cast<const T*>(h->w[0]), h->ldf,
+                              static_cast<T*>(h->part), t->ldc, t->mx, t->my,
+                              h->levels, s));
+    return QG_OK;
+}
+
 template <typename T>
 qg_status enqueue_step(qg_ctx* h, cudaStream_t s) {
     for (int k = 0; k < 3; ++k) {
-        qg_status st = stage<T>(h, k, s);
+        qg_status st = (h->layers == 1) ? stage_fused<T>(h, k, s) : stage<T>(h, k, s);
         if (st != QG_OK) return st;
     }
     return QG_OK;
@@ -416,7 +525,7 @@ qg_status qg_create(const qg_basin* b, int layers, double Re, double Ro, double 
     if (!std::isfinite(Re) || !std::isfinite(Ro) || !std::isfinite(b->dt)) return QG_ERR_ARG;
     if (layers == 2 && (!(b->delta > 0) || !(b->delta < 1) || !(Fr >= 0) || !(b->sigma >= 0)))
         return QG_ERR_ARG;
-    if (levels < 0 || levels > 10) return QG_ERR_ARG;
+    if (levels < 0 || levels > 4) return QG_ERR_ARG;
     if (!pow2_in(b->nx, 8, 8192) || !pow2_in(b->ny, 8, 8192)) return QG_ERR_SHAPE;
     if ((b->nx >> levels) < 8 || (b->ny >> levels) < 8) return QG_ERR_SHAPE;
     int ndev = 0;
@@ -454,6 +563,22 @@ qg_status qg_create(const qg_basin* b, int layers, double Re, double Ro, double 
     if (s == QG_OK) guard(dev_alloc(h, &h->psi, fb));
     if (s == QG_OK) guard(dev_alloc(h, &h->cw, cb));
     if (s == QG_OK) guard(dev_alloc(h, &h->cpsi, cb));
+    if (s == QG_OK && layers == 1 && levels >= 1) guard(dev_alloc(h, &h->part, 4 * h->plane_c * h->esz));
+    if (s == QG_OK) guard(dev_alloc(h, (void**)&h->derr, sizeof(int) * 4));
+    if (s == QG_OK && layers == 1) {
+        const int rows = (int)fine_tile_rows(h->esz);
+        for (int k = 0; k < 3 && s == QG_OK; ++k) {
+            if (make_tensor_map(&h->tm_halo[k], h->w[k], h->nx, h->ny, h->ldf, h->esz,
+                                fine_halo_cols(), rows + 2) != cudaSuccess ||
+                make_tensor_map(&h->tm_int[k], h->w[k], h->nx, h->ny, h->ldf, h->esz,
+                                fine_block_cols(), rows) != cudaSuccess)
+                guard(QG_ERR_CUDA);
+        }
+        if (s == QG_OK && make_tensor_map(&h->tm_psi, h->psi, h->nx, h->ny, h->ldf, h->esz,
+                                          fine_halo_cols(), rows + 2) != cudaSuccess)
+            guard(QG_ERR_CUDA);
+        h->tm_f = h->tm_int[0];
+    }
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dpart, sizeof(double) * 5 * diag_blocks()));
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dout, sizeof(double) * 8));
     if (s == QG_OK && cudaMallocHost((void**)&h->hout, sizeof(double) * 8) != cudaSuccess) guard(QG_ERR_OOM);
@@ -499,9 +624,26 @@ qg_status qg_last_error(qg_handle h) {
     return s;
 }
 
+// Reads and clears the device error flag of the bounded waits.
+static qg_status check_device_flag(qg_ctx* h) {
+    int flag = 0;
+    QG_TRY(cudaMemcpyAsync(&flag, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    QG_TRY(cudaStreamSynchronize(h->stream));
+    if (flag) {
+        QG_TRY(cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream));
+        return fail(h, QG_ERR_TIMEOUT);
+    }
+    return QG_OK;
+}
+
 qg_status qg_synchronize(qg_handle h) {
     if (!h) return QG_ERR_ARG;
     QG_TRY(cudaStreamSynchronize(h->stream));
+    qg_status s = check_device_flag(h);
+    if (s != QG_OK) {
+        qg_last_error(h);
+        return s;
+    }
     return qg_last_error(h);
 }
 
@@ -510,6 +652,7 @@ qg_status qg_set_state(qg_handle h, const void* field, int layer) {
     if (h->latched != QG_OK) return qg_last_error(h);
     char* dst = static_cast<char*>(h->w[0]) + (size_t)layer * h->plane_f * h->esz;
     QG_TRY(copy_in(dst, h->ldf, field, h->nx - 1, h->ny - 1, h->esz, h->stream));
+    h->part_valid = false;
     return QG_OK;
 }
 
@@ -548,6 +691,9 @@ qg_status qg_set_forcing(qg_handle h, const void* forcing) {
         h->f2d_buf = p;
     }
     h->f2d = h->f2d_buf;
+    if (make_tensor_map(&h->tm_f, h->f2d, h->nx, h->ny, h->ldf, h->esz, fine_block_cols(),
+                        (int)fine_tile_rows(h->esz)) != cudaSuccess)
+        return fail(h, QG_ERR_CUDA);
     QG_TRY(copy_in(h->f2d, h->ldf, forcing, h->nx - 1, h->ny - 1, h->esz, h->stream));
     return QG_OK;
 }
@@ -629,6 +775,11 @@ qg_status qg_step(qg_handle h, int64_t n) {
     if (n == 0) return QG_OK;
     qg_status s = build_graph(h);
     if (s != QG_OK) return s;
+    if (h->part && !h->part_valid) {
+        s = h->dtype == QG_F64 ? init_partials<double>(h, h->stream) : init_partials<float>(h, h->stream);
+        if (s != QG_OK) return s;
+        h->part_valid = true;
+    }
     for (int64_t k = 0; k < n; ++k) QG_TRY(cudaGraphLaunch(h->gexec, h->stream));
     return QG_OK;
 }
@@ -683,6 +834,10 @@ qg_status qg_diagnostics(qg_handle h, double* ke, double* enstrophy, double* max
                                          h->dout, h->stream));
     QG_TRY(cudaMemcpyAsync(h->hout, h->dout, sizeof(double) * 5, cudaMemcpyDeviceToHost, h->stream));
     QG_TRY(cudaStreamSynchronize(h->stream));
+    {
+        const qg_status fs = check_device_flag(h);
+        if (fs != QG_OK) return fs;
+    }
     const double* r = h->hout;
     const double dx = h->dx, dy = h->dy;
     const double E = 0.5 * dx * dy * (r[0] / (dx * dx) + r[1] / (dy * dy));

@@ -173,7 +173,7 @@ __device__ __forceinline__ void put_pair(T* buf, int N, int j, T a, T b) {
 // Rows kernel: each lane transforms rows r0 = 1 + 2p and r1 = r0 + 1.
 template <typename T, int NB>
 __global__ void __launch_bounds__(512)
-dst_rows_kernel(const T* in, T* out, int ld, int nrows, int N,
+dst_rows_kernel(RowInput<T> in, T* out, int ld, int nrows, int N,
                 const typename Cx<T>::type* __restrict__ tw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geo g = make_geo(N, NB);
@@ -182,11 +182,15 @@ dst_rows_kernel(const T* in, T* out, int ld, int nrows, int N,
     const int r0 = 1 + 2 * (blockIdx.x * lanes + g.lane);
     const int r1 = r0 + 1;
     const bool v0 = r0 <= nrows, v1 = r1 <= nrows;
-    const T* s0 = in + (size_t)r0 * ld;
-    const T* s1 = in + (size_t)r1 * ld;
+    const size_t o0 = (size_t)r0 * ld, o1 = (size_t)r1 * ld;
     for (int j = g.t; j < N; j += g.TPR) {
-        const T a = (v0 && j > 0) ? s0[j] : T(0);
-        const T b = (v1 && j > 0) ? s1[j] : T(0);
+        T a = T(0), b = T(0);
+        if (j > 0) {
+            for (int q = 0; q < in.n; ++q) {
+                if (v0) a += in.p[q][o0 + j];
+                if (v1) b += in.p[q][o1 + j];
+            }
+        }
         put_pair(buf, N, j, a, b);
     }
     __syncthreads();
@@ -383,7 +387,7 @@ cudaError_t dst_prepare_kernels() {
 }
 
 template <typename T>
-cudaError_t launch_dst_rows(const T* in, T* out, int ld, int nrows, int N,
+cudaError_t launch_dst_rows(RowInput<T> in, T* out, int ld, int nrows, int N,
                             const typename Cx<T>::type* tw, DstLaunch cfg,
                             cudaStream_t s) {
     const int tpr = (2 * N) / (4 * cfg.nb);
@@ -442,7 +446,7 @@ cudaError_t launch_dst_cols_solve2(T* d0, T* d1, int ld, int ncols, int N,
 }
 
 #define QG_INST(T)                                                               \
-    template cudaError_t launch_dst_rows<T>(const T*, T*, int, int, int,          \
+    template cudaError_t launch_dst_rows<T>(RowInput<T>, T*, int, int, int,       \
                                             const Cx<T>::type*, DstLaunch,        \
                                             cudaStream_t);                        \
     template cudaError_t launch_dst_cols_solve<T>(T*, int, int, int,              \

@@ -1,0 +1,459 @@
+// Fused fine-grid stage of the one-layer model: prolongation on load,
+// Arakawa / beta / dissipation / forcing and the TVDRK3 combination, and
+// restriction on store, in one pass over the fine grid.
+//
+// A CTA covers a 64-node-wide column block over RC = GROUPS x 16 rows.  One
+// elected thread stages its inputs into shared memory with 2-D TMA tensor
+// copies (w^(s) with a halo, w^n, the fine psi for l = 0, a forcing field),
+// all issued at once and completed on one mbarrier, so a CTA keeps its whole
+// working set (~70 KB) in flight; the wait is bounded and a timeout sets an
+// error flag instead of hanging.  Meanwhile the other threads stage the
+// elliptic-grid streamfunction patch.  Then each group of 16 threads (half a
+// warp) owns the block's columns,
+// x in [x0, x0 + 64), 4 x-consecutive nodes per thread, and sweeps the 16
+// fine rows y in [ys, ys + 16), ys a multiple of 16, keeping the three rows
+// of w^(s) and psi its stencil needs in registers.  x-halos come from the
+// neighbouring threads by shuffles (the group's first and last thread read
+// the block's edge columns).  Per row it
+//   1. loads w^(s) of the next row, and builds psi of that row either by
+//      bilinear interpolation from the elliptic-grid streamfunction held in
+//      registers (Eq. pro applied l times is bilinear interpolation at
+//      2^-l spacing) or, for l = 0, by loading the fine psi;
+//   2. computes w^(s+1) = a w^n + b (w^(s) + dt G) with
+//      G = -J(psi, w) - (1/Ro) J(psi, y) + (1/Re) lap w + F (Eqs. ja1, j1-j3,
+//      Eq. ge divided by Ro) and stores it;
+//   3. for l >= 1 adds the row's share to the restriction of w^(s+1):
+//      Eq. res applied l times has the separable hat weights (f-|d|)/f^2,
+//      f = 2^l, so a node at distance d in [0, f) past coarse line N gives
+//      (f-d)/f^2 of itself to N and d/f^2 to N+1 in each direction; the x
+//      shares are combined across threads by shuffles and the y shares
+//      accumulate in registers over the sweep.
+// A coarse node whose support straddles the block's right edge line or the
+// group's last row receives the rest from the neighbouring block or group,
+// so each group writes its sums into one of four planes by the node's
+// position (q = 0: the node lies in the group's block and rows; bit 0: on
+// the block's right edge line; bit 1: on the row after the group's last).
+// Every (node, plane) has one writer, planes 1-3 stay zero off those lines,
+// and the row sine transform adds P0 + P1 + P2 + P3 in that order.
+#include <cuda_runtime.h>
+
+#include "qg_internal.cuh"
+
+namespace qg {
+namespace {
+
+constexpr int TX = 64;      // nodes per column block (16 threads x 4)
+constexpr int SWX = TX + 8; // halo tile row: fine x in [x0 - 4, x0 + 68)
+// rows swept by one group: 8, or 2^l when that is larger (a group must
+// cover whole coarse cells for the partial-sum planes)
+template <int LV> struct Sweep { static constexpr int RY = (1 << LV) > 8 ? (1 << LV) : 8; };
+
+// fine rows per CTA
+template <typename T> struct Rows { static constexpr int value = 128; };
+template <> struct Rows<double> { static constexpr int value = 64; };
+
+template <typename T>
+__device__ __forceinline__ void lds4(const T* p, T v[4]) {
+    v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[3];
+}
+__device__ __forceinline__ void lds4(const float* p, float v[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double v[4]) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void stg4(float* p, const float v[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void stg4(double* p, const double v[4]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *(reinterpret_cast<double2*>(p) + 1) = make_double2(v[2], v[3]);
+}
+
+// ---- mbarrier / TMA (inline PTX) --------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+// Bounded wait for phase `parity` of the barrier: true when it completed.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+    for (int i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+constexpr int kWaitLimit = 1 << 22;
+
+// Shared-memory plan of one CTA (byte offsets, 128-byte aligned).
+template <typename T, int LV>
+struct Plan {
+    static constexpr int RC = Rows<T>::value;
+    static constexpr int RY = Sweep<LV>::RY;
+    static constexpr int G = RC / RY;               // groups per CTA
+    static constexpr int THREADS = 16 * G;
+    static constexpr int F = 1 << LV;
+    static constexpr int CPX = TX / F + 4;
+    static constexpr int CPY = RC / F + 3;
+    static constexpr size_t al(size_t v) { return (v + 127) / 128 * 128; }
+    static constexpr size_t W = 0;                                             // (RC+2) x SWX
+    static constexpr size_t WN = al(W + sizeof(T) * (RC + 2) * SWX);          // RC x TX
+    static constexpr size_t P = al(WN + sizeof(T) * RC * TX);                 // (RC+2) x SWX (l = 0)
+    static constexpr size_t CP = al(P + (LV == 0 ? sizeof(T) * (RC + 2) * SWX : 0));  // l >= 1
+    static constexpr size_t FF = al(CP + (LV > 0 ? sizeof(T) * CPY * CPX : 0));       // RC x TX
+    static constexpr size_t END_NOF = FF;                 // without a forcing field
+    static constexpr size_t END = al(FF + sizeof(T) * RC * TX);
+};
+
+template <typename T, int LV>
+__global__ void __launch_bounds__(Plan<T, LV>::THREADS, sizeof(T) == 4 ? 3 : 2)
+fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
+                  const __grid_constant__ CUtensorMap tm_wn,
+                  const __grid_constant__ CUtensorMap tm_p,
+                  const __grid_constant__ CUtensorMap tm_f, FusedParams<T> p) {
+    using PL = Plan<T, LV>;
+    constexpr int F = 1 << LV;
+    constexpr int RC = PL::RC;
+    constexpr int RY = PL::RY;
+    constexpr int NM = RY / F + 1;                  // node rows a group touches
+    constexpr int G = (F >= 4) ? F / 4 : 1;          // threads per coarse cell
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    T* sw = reinterpret_cast<T*>(smem + PL::W);
+    T* swn = reinterpret_cast<T*>(smem + PL::WN);
+    T* sp = reinterpret_cast<T*>(smem + PL::P);
+    T* sf = reinterpret_cast<T*>(smem + PL::FF);
+    T* cp = reinterpret_cast<T*>(smem + PL::CP);
+
+    const int nx = p.nx, ny = p.ny, ld = p.ld;
+    const int x0 = blockIdx.x * TX;
+    const int yc = blockIdx.y * RC;
+    const bool use_wn = p.a != T(0);
+    const bool use_f = p.f2d != nullptr;
+    const uint32_t bar = smem_u32(&mbar);
+
+    // ---- stage the inputs ------------------------------------------------
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t bytes = sizeof(T) * (RC + 2) * SWX;
+        if (use_wn) bytes += sizeof(T) * RC * TX;
+        if (LV == 0) bytes += sizeof(T) * (RC + 2) * SWX;
+        if (use_f) bytes += sizeof(T) * RC * TX;
+        mbar_expect_tx(bar, bytes);
+        tma_load_2d(smem_u32(sw), &tm_w, x0 - 4, yc - 1, bar);
+        if (use_wn) tma_load_2d(smem_u32(swn), &tm_wn, x0, yc, bar);
+        if (LV == 0) tma_load_2d(smem_u32(sp), &tm_p, x0 - 4, yc - 1, bar);
+        if (use_f) tma_load_2d(smem_u32(sf), &tm_f, x0, yc, bar);
+    }
+    const int mx = nx >> LV, my = ny >> LV;
+    const int I_lo = (x0 - 1) >> LV;      // may be -1
+    const int J_lo = (yc - 1) >> LV;      // may be -1
+    if (LV > 0) {
+        for (int e = threadIdx.x; e < PL::CPX * PL::CPY; e += blockDim.x) {
+            const int ii = e % PL::CPX, jj = e / PL::CPX;
+            const int I = I_lo + ii, J = J_lo + jj;
+            cp[e] = (I >= 0 && I <= mx && J >= 0 && J <= my)
+                        ? __ldg(p.psi + (size_t)J * p.ldp + I) : T(0);
+        }
+    }
+    const bool arrived = mbar_wait(bar, 0, kWaitLimit);
+    __syncthreads();
+    if (!arrived) {
+        if (threadIdx.x == 0) atomicExch(p.err, 1);
+        (void)mbar_wait(bar, 0, kWaitLimit);     // let copies in flight land
+        return;
+    }
+
+    // ---- sweep -----------------------------------------------------------
+    const int lane = threadIdx.x & 15;
+    const int grp = threadIdx.x >> 4;
+    const unsigned gm = 0xFFFFu << (16 * (grp & 1));
+    const int ys = yc + grp * RY;
+    if (ys >= ny) return;                            // whole group
+    const int xq = x0 + 4 * lane;
+
+    // row y of a halo tile (w^(s) or the fine psi): own quad + shuffled halos
+    auto row_halo = [&](const T* tile, int y, T v[6]) {
+        const T* r = tile + (y - yc + 1) * SWX;
+        T c[4];
+        lds4(r + 4 * lane + 4, c);
+        T left = __shfl_up_sync(gm, c[3], 1, 16);
+        T right = __shfl_down_sync(gm, c[0], 1, 16);
+        if (lane == 0) left = r[3];
+        if (lane == 15) right = r[TX + 4];
+        v[0] = left; v[1] = c[0]; v[2] = c[1]; v[3] = c[2]; v[4] = c[3]; v[5] = right;
+    };
+    const int Ib = (xq - 1) >> LV;
+    T c0[4], c1[4];
+    auto coarse_row = [&](int J, T c[4]) {
+        const T* r = cp + (J - J_lo) * PL::CPX + (Ib - I_lo);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] = r[k];
+    };
+    auto psi_row = [&](int y, T v[6]) {
+        if (y < 0 || y >= ny) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) v[k] = T(0);
+            return;
+        }
+        const T b = T(y & (F - 1)) * (T(1) / T(F));
+        T cv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cv[k] = (T(1) - b) * c0[k] + b * c1[k];
+        if (LV == 1) {
+            v[0] = T(0.5) * (cv[0] + cv[1]); v[1] = cv[1];
+            v[2] = T(0.5) * (cv[1] + cv[2]); v[3] = cv[2];
+            v[4] = T(0.5) * (cv[2] + cv[3]); v[5] = cv[3];
+        } else if (LV == 2) {
+            v[0] = T(0.25) * cv[0] + T(0.75) * cv[1]; v[1] = cv[1];
+            v[2] = T(0.75) * cv[1] + T(0.25) * cv[2];
+            v[3] = T(0.5) * (cv[1] + cv[2]);
+            v[4] = T(0.25) * cv[1] + T(0.75) * cv[2]; v[5] = cv[2];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const int x = xq - 1 + k;
+                const int cell = (x >> LV) - Ib;
+                const T a = T(x & (F - 1)) * (T(1) / T(F));
+                const T lo = cell == 0 ? cv[0] : (cell == 1 ? cv[1] : cv[2]);
+                const T hi = cell == 0 ? cv[1] : (cell == 1 ? cv[2] : cv[3]);
+                v[k] = (T(1) - a) * lo + a * hi;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (xq - 1 + k > nx || xq - 1 + k < 0) v[k] = T(0);
+    };
+    // psi of sweep row rr (fine row y = ys - 1 + rr)
+    auto load_psi = [&](int rr, int y, T v[6]) {
+        if (LV == 0) {
+            row_halo(sp, y, v);
+        } else {
+            if (rr <= 1) {
+                coarse_row(y >> LV, c0);
+                coarse_row((y >> LV) + 1, c1);
+            } else if (((rr - 1) & (F - 1)) == 0) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) c0[k] = c1[k];
+                coarse_row((y >> LV) + 1, c1);
+            }
+            psi_row(y, v);
+        }
+    };
+
+    T W[3][6], P[3][6];
+    row_halo(sw, ys - 1, W[0]);
+    load_psi(0, ys - 1, P[0]);
+    row_halo(sw, ys, W[1]);
+    load_psi(1, ys, P[1]);
+
+    T accA[NM], accB[NM], accE[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) accA[m] = accB[m] = accE[m] = T(0);
+
+#pragma unroll
+    for (int o = 0; o < RY; ++o) {
+        const int y = ys + o;
+        const int sb = o % 3, sc = (o + 1) % 3, sa = (o + 2) % 3;
+        row_halo(sw, y + 1, W[sa]);
+        load_psi(o + 2, y + 1, P[sa]);
+        const bool row_ok = y >= 1 && y <= ny - 1;
+        const size_t ro = (size_t)y * ld;
+        T wn[4] = {T(0), T(0), T(0), T(0)};
+        if (use_wn) lds4(swn + (y - yc) * TX + 4 * lane, wn);
+        T fv[4];
+        if (use_f) {
+            lds4(sf + (y - yc) * TX + 4 * lane, fv);
+        } else {
+            const T fr = __ldg(p.frow + (y <= ny ? y : ny));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) fv[q] = fr;
+        }
+        // differences shared by the four nodes: vertical psi differences per
+        // column, horizontal psi differences per row
+        T V[6], Hb[4], Hc[4], Ha[4];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) V[c] = P[sa][c] - P[sb][c];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            Hb[q] = P[sb][q + 2] - P[sb][q];
+            Hc[q] = P[sc][q + 2] - P[sc][q];
+            Ha[q] = P[sa][q + 2] - P[sa][q];
+        }
+        T out[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = q + 1;
+            const T pm0 = P[sc][i - 1], p10 = P[sc][i + 1], p0m = P[sb][i], p01 = P[sa][i];
+            const T q00 = W[sc][i];
+            const T qm0 = W[sc][i - 1], q10 = W[sc][i + 1], q0m = W[sb][i], q01 = W[sa][i];
+            const T qmm = W[sb][i - 1], q1m = W[sb][i + 1], qm1 = W[sa][i - 1], q11 = W[sa][i + 1];
+            // Arakawa J1 + J2 + J3 (Eqs. j1-j3) with
+            //   J1 = -(q10 - qm0) V_i + (q01 - q0m) Hc_i
+            //   J2 = -q10 V_{i+1} + qm0 V_{i-1} + q01 Ha_i - q0m Hb_i
+            //   J3 = -q11 (p01 - p10) + qmm (pm0 - p0m) + qm1 (p01 - pm0) - q1m (p10 - p0m)
+            T jac = -(q10 - qm0) * V[i];
+            jac = fma(q01 - q0m, Hc[q], jac);
+            jac = fma(-q10, V[i + 1], jac);
+            jac = fma(qm0, V[i - 1], jac);
+            jac = fma(q01, Ha[q], jac);
+            jac = fma(-q0m, Hb[q], jac);
+            jac = fma(-q11, p01 - p10, jac);
+            jac = fma(qmm, pm0 - p0m, jac);
+            jac = fma(qm1, p01 - pm0, jac);
+            jac = fma(-q1m, p10 - p0m, jac);
+            // (1/Ro) J(psi, y) in Arakawa's form: (4 c_j + c_{j+1} + c_{j-1})/(6 Ro)
+            const T beta = fma(T(4), Hc[q], Ha[q] + Hb[q]);
+            const T lap = (q10 + qm0 - T(2) * q00) * p.c_lapx + (q01 + q0m - T(2) * q00) * p.c_lapy;
+            T Gv = fma(-p.c_jac, jac, fv[q] + lap);
+            Gv = fma(-p.c_beta, beta, Gv);
+            out[q] = fma(p.a, wn[q], p.b * fma(p.dt, Gv, q00));
+        }
+        const bool quad_ok = row_ok && xq >= 1 && xq + 3 <= nx - 1;
+        if (quad_ok) {
+            stg4(p.wout + ro + xq, out);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int x = xq + q;
+                if (row_ok && x >= 1 && x <= nx - 1) p.wout[ro + x] = out[q];
+                else out[q] = T(0);
+            }
+        }
+        if (LV > 0) {
+            // x shares of this row
+            T xa, xb = T(0), xe;
+            if (LV == 1) {
+                const T A = T(0.5) * out[0] + T(0.25) * out[1];
+                const T C = T(0.25) * out[3];
+                xb = T(0.25) * out[1] + T(0.5) * out[2] + T(0.25) * out[3];
+                const T Cp = __shfl_up_sync(gm, C, 1, 16);
+                xa = A + (lane > 0 ? Cp : T(0));
+                xe = C;
+            } else {
+                T Va = T(0), Vb = T(0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int d = (xq + q) & (F - 1);
+                    Va += T(F - d) * (T(1) / T(F * F)) * out[q];
+                    Vb += T(d) * (T(1) / T(F * F)) * out[q];
+                }
+#pragma unroll
+                for (int off = 1; off < G; off <<= 1) {
+                    Va += __shfl_xor_sync(gm, Va, off, 16);
+                    Vb += __shfl_xor_sync(gm, Vb, off, 16);
+                }
+                const T Vbp = __shfl_up_sync(gm, Vb, G, 16);
+                xa = Va + (lane >= G ? Vbp : T(0));
+                xe = Vb;
+            }
+            const int dy = o & (F - 1);
+            const int mlo = o >> LV;
+            const T wlo = T(F - dy) * (T(1) / T(F * F));
+            const T whi = T(dy) * (T(1) / T(F * F));
+            accA[mlo] += wlo * xa;
+            accE[mlo] += wlo * xe;
+            if (LV == 1) accB[mlo] += wlo * xb;
+            if (dy != 0) {
+                accA[mlo + 1] += whi * xa;
+                accE[mlo + 1] += whi * xe;
+                if (LV == 1) accB[mlo + 1] += whi * xb;
+            }
+        }
+    }
+
+    // ---- restriction partial sums ---------------------------------------
+    if (LV > 0) {
+        const int Ix0 = x0 >> LV;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            const int J = (ys >> LV) + m;
+            if (J < 1 || J > my - 1) continue;
+            const int qy = (m == NM - 1) ? 2 : 0;
+            T* rowA = p.part[qy] + (size_t)J * p.ldc;
+            if (LV == 1) {
+                const int I = Ix0 + 2 * lane;
+                if (I >= 1 && I <= mx - 1) rowA[I] = accA[m];
+                if (I + 1 >= 1 && I + 1 <= mx - 1) rowA[I + 1] = accB[m];
+            } else if (lane % G == 0) {
+                const int I = Ix0 + lane / G;
+                if (I >= 1 && I <= mx - 1) rowA[I] = accA[m];
+            }
+            if (lane == 15) {
+                const int I = Ix0 + TX / F;
+                if (I >= 1 && I <= mx - 1) p.part[qy + 1][(size_t)J * p.ldc + I] = accE[m];
+            }
+        }
+    }
+}
+
+template <typename T, int LV>
+cudaError_t launch_sweep(const FusedParams<T>& p, const FineMaps& m, cudaStream_t s) {
+    using PL = Plan<T, LV>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(fine_sweep_kernel<T, LV>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)PL::END);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const dim3 block(PL::THREADS);
+    const dim3 grid((p.nx + TX - 1) / TX, (p.ny + PL::RC - 1) / PL::RC);
+    const size_t sm = p.f2d ? PL::END : PL::END_NOF;
+    fine_sweep_kernel<T, LV><<<grid, block, sm, s>>>(m.w, m.wn, m.psi, m.f, p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int levels,
+                              cudaStream_t s) {
+    switch (levels) {
+        case 0: return launch_sweep<T, 0>(p, m, s);
+        case 1: return launch_sweep<T, 1>(p, m, s);
+        case 2: return launch_sweep<T, 2>(p, m, s);
+        case 3: return launch_sweep<T, 3>(p, m, s);
+        case 4: return launch_sweep<T, 4>(p, m, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t fine_tile_rows(size_t esz) { return esz == 8 ? Rows<double>::value : Rows<float>::value; }
+int fine_halo_cols() { return SWX; }
+int fine_block_cols() { return TX; }
+
+template cudaError_t launch_fine_fused<float>(const FusedParams<float>&, const FineMaps&, int,
+                                              cudaStream_t);
+template cudaError_t launch_fine_fused<double>(const FusedParams<double>&, const FineMaps&, int,
+                                               cudaStream_t);
+
+}  // namespace qg

@@ -95,12 +95,13 @@ qg_status solve(unsigned char* base, const Layout& Lo, int nx, int ny, double dx
     if (cudaGetLastError() != cudaSuccess) return QG_ERR_CUDA;
     if (copy_in(grid, ld, rhs, nx - 1, ny - 1, esz, s) != cudaSuccess) return QG_ERR_CUDA;
     const T scale = (T)((2.0 / nx) * (2.0 / ny));
-    if (launch_dst_rows<T>(grid, grid, ld, ny - 1, nx, twx, dst_rows_config(nx, esz), s) != cudaSuccess)
+    const RowInput<T> in{{grid, nullptr, nullptr, nullptr}, 1};
+    if (launch_dst_rows<T>(in, grid, ld, ny - 1, nx, twx, dst_rows_config(nx, esz), s) != cudaSuccess)
         return QG_ERR_CUDA;
     if (launch_dst_cols_solve<T>(grid, ld, nx - 1, ny, twy, lamx, lamy, scale,
                                  dst_cols_config(ny, esz), s) != cudaSuccess)
         return QG_ERR_CUDA;
-    if (launch_dst_rows<T>(grid, grid, ld, ny - 1, nx, twx, dst_rows_config(nx, esz), s) != cudaSuccess)
+    if (launch_dst_rows<T>(in, grid, ld, ny - 1, nx, twx, dst_rows_config(nx, esz), s) != cudaSuccess)
         return QG_ERR_CUDA;
     if (copy_out(psi, grid, ld, nx - 1, ny - 1, esz, s) != cudaSuccess) return QG_ERR_CUDA;
     return QG_OK;

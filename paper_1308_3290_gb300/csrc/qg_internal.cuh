@@ -9,6 +9,7 @@
 // the stored rows without repacking.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,10 +34,18 @@ struct DstLaunch {
 
 // ---- kernels (declared here, defined in dst.cu / stencil.cu / diag.cu) ----
 
+// Input of a row transform: the sum of n (1..4) padded planes, added in
+// index order (the restriction arrives as four partial-sum planes).
+template <typename T>
+struct RowInput {
+    const T* p[4];
+    int n;
+};
+
 // Unnormalised DST-I, F_k = sum_{j=1}^{N-1} f_j sin(pi j k / N), of rows
 // 1..nrows of a padded array (row length N = n_x).  in and out may alias.
 template <typename T>
-cudaError_t launch_dst_rows(const T* in, T* out, int ld, int nrows, int N,
+cudaError_t launch_dst_rows(RowInput<T> in, T* out, int ld, int nrows, int N,
                             const typename Cx<T>::type* tw, DstLaunch cfg,
                             cudaStream_t s);
 
@@ -97,6 +106,42 @@ template <typename T>
 cudaError_t launch_fine_stage(const T* psi, const T* w, const T* wn, T* wout,
                               const T* frow, const T* f2d,
                               const StageParams<T>& p, cudaStream_t s);
+
+// Fused one-layer stage (fused.cu): prolongation of psi on load, the stage
+// update, and restriction of the result into four partial-sum planes.
+template <typename T>
+struct FusedParams {
+    int nx, ny, ld;        // fine grid intervals and pitch
+    const T* psi;          // l = 0: fine psi; l >= 1: elliptic-grid psi
+    int ldp;               // pitch of psi
+    const T* w;            // w^(s)
+    const T* wn;           // w^n (read only when a != 0; may alias wout)
+    T* wout;               // w^(s+1)
+    const T* frow;         // forcing per fine row
+    const T* f2d;          // forcing field or null
+    T* part[4];            // restriction partial planes (l >= 1)
+    int ldc;               // their pitch
+    int* err;              // set to 1 when a bounded wait runs out
+    T c_jac, c_beta, c_lapx, c_lapy, dt, a, b;
+};
+
+// TMA tensor maps of the inputs of one fused launch: w^(s) and the fine psi
+// with halo boxes, w^n and the forcing field with interior boxes.  Unused
+// maps may hold anything (they are not dereferenced).
+struct FineMaps {
+    CUtensorMap w, wn, psi, f;
+};
+template <typename T>
+cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int levels,
+                              cudaStream_t s);
+size_t fine_tile_rows(size_t esz);   // fine rows per CTA
+int fine_halo_cols();                // columns of a halo box
+int fine_block_cols();               // columns of an interior box
+
+// 2-D tensor map over a padded level array (x = 0..n_x, y = 0..n_y), box
+// bw x bh, zero fill outside.
+cudaError_t make_tensor_map(CUtensorMap* m, const void* base, int nx, int ny, int ld,
+                            size_t esz, int bw, int bh);
 
 // Two-layer stage (Eq. ge-non): both layers in one pass.
 template <typename T>
