@@ -56,7 +56,29 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="run W + K steps of the workload and exit (for ncu captures)")
+    ap.add_argument("--nx", type=int, default=NX)
+    ap.add_argument("--ny", type=int, default=NY)
+    ap.add_argument("--levels", type=int, default=LEVELS)
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     return ap.parse_args()
+
+
+def profile_only(args):
+    """W + K plain steps of one basin, for profiler captures."""
+    import torch
+    from paper_1308_3290_gb300 import build, inputs, qg
+    build.build()
+    qg.load()
+    b = qg.Basin(args.nx, args.ny, Re=RE, Ro=RO, levels=args.levels, dt=DT, dtype=args.dtype)
+    b.set_state(inputs.gyre_state(args.nx, args.ny, seed=SEED))
+    b.step(args.warmup + args.steps)
+    b.synchronize()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_only": True, "nx": args.nx, "ny": args.ny,
+                      "levels": args.levels, "dtype": args.dtype,
+                      "steps": args.warmup + args.steps}))
 
 
 # ---------------------------------------------------------------------------
@@ -402,7 +424,9 @@ def ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_only:
+        profile_only(args)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         ours(args)

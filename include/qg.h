@@ -189,10 +189,10 @@ qg_status qg_step_kernel_count(qg_handle h, int64_t* count);
  * would synchronise the device).  The paper has no counterpart to this call.
  *
  * It needs no handle and allocates nothing: its workspace lives in one
- * library-owned 16 MiB device array that every GPU loading the library keeps
- * until exit.  The padded grid plus tables must fit in it (for example up to
- * 1024 x 2048 intervals in FP32 or 1024 x 1024 in FP64); larger requests
- * return QG_ERR_SHAPE.  rhs and psi are DEVICE pointers in the level-0
+ * library-owned 32 MiB device array that every GPU loading the library keeps
+ * until exit.  The padded grid, its transposed spectrum and the tables must
+ * fit in it (for example up to 1024 x 2048 intervals in FP32 or 1024 x 1024
+ * in FP64); larger requests return QG_ERR_SHAPE.  rhs and psi are DEVICE pointers in the level-0
  * exchange layout of that grid; work is enqueued on cuda_stream on the
  * current device.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress): make it before any stream capture starts.

@@ -51,6 +51,9 @@ struct qg_ctx {
     void* cw = nullptr;            // elliptic-grid work (layers planes)
     void* cpsi = nullptr;          // elliptic-grid psi (layers planes)
     size_t plane_c = 0;
+    void* ct = nullptr;            // transposed x-spectrum of the elliptic grid (layers planes)
+    int ld_t = 0;                  // its pitch (round_up(my + 1, 32))
+    size_t plane_t = 0;            // its plane size ((mx + 1) rows)
     void* part = nullptr;          // 4 restriction partial-sum planes (one layer, l >= 1)
     bool part_valid = false;       // part holds R^l w^n of the current state
     void* frow = nullptr;          // forcing per fine row
@@ -254,47 +257,82 @@ T* plane(void* base, size_t plane_elems, int layer) {
     return static_cast<T*>(base) + (size_t)layer * plane_elems;
 }
 
-// Elliptic solve on one level: padded in -> padded out, through `work`
-// (all three may alias).  One layer: lap_h psi = rhs.  Two layers: Eq.
-// sub-pr per mode.  `pl` is the plane size of the level's buffers.
+// Elliptic solve on one level: the x pass of `in` (the sum of `nparts`
+// planes per layer) into the transposed buffer `tr` (pitch ld_tr), the y pass
+// with the eigenvalue division (or the coupled two-layer system) back into
+// `work`, and the inverse x pass into `out`.  in, work and out have the
+// level's padded layout and plane size pl; work and out may alias, in may
+// alias either.
 template <typename T>
-qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in,
-                      void* work, void* out, size_t pl, cudaStream_t s,
-                      int nparts = 1) {
+qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr, int ld_tr,
+                      size_t pl_tr, void* work, void* out, size_t pl, cudaStream_t s,
+                      int nparts = 1, bool pdl = false) {
     using C = typename Cx<T>::type;
-    const DstLaunch rc = dst_rows_config(t.mx, sizeof(T));
-    const DstLaunch cc = dst_cols_config(t.my, sizeof(T));
+    const DstLaunch cx = dst_config(t.mx, sizeof(T), false);
     const T scale = (T)((2.0 / t.mx) * (2.0 / t.my));
     for (int L = 0; L < h->layers; ++L) {
         KTimer kt(h, s, QG_K_DST_ROWS);
-        RowInput<T> ri{{nullptr, nullptr, nullptr, nullptr}, nparts};
+        DstPass<T> d = {};
+        d.N = t.mx;
+        d.nrows = t.my - 1;
         for (int q = 0; q < nparts; ++q)
-            ri.p[q] = plane<T>(const_cast<void*>(in), pl, L * nparts + q);
-        QG_TRY(launch_dst_rows<T>(ri, plane<T>(work, pl, L), t.ldc, t.my - 1, t.mx,
-                                  static_cast<const C*>(t.twx), rc, s));
+            d.in[0][q] = plane<T>(const_cast<void*>(in), pl, L * nparts + q);
+        d.nin = nparts;
+        if (nparts > 1) {
+            d.part_px = fine_part_period_x(h->levels);
+            d.part_py = fine_part_period_y(h->levels, sizeof(T));
+        }
+        d.ld_in = t.ldc;
+        d.out[0] = plane<T>(tr, pl_tr, L);
+        d.ld_out = ld_tr;
+        d.transpose_out = 1;
+        d.tw = static_cast<const C*>(t.twx);
+        d.err = h->derr;
+        QG_TRY(launch_dst_pass<T>(d, 0, cx, s, pdl));
     }
     {
-    KTimer ktc(h, s, QG_K_DST_COLS);
-    if (h->layers == 1) {
-        QG_TRY(launch_dst_cols_solve<T>(static_cast<T*>(work), t.ldc, t.mx - 1, t.my,
-                                        static_cast<const C*>(t.twy),
-                                        static_cast<const T*>(t.lamx),
-                                        static_cast<const T*>(t.lamy), scale, cc, s));
-    } else {
-        QG_TRY(launch_dst_cols_solve2<T>(plane<T>(work, pl, 0), plane<T>(work, pl, 1),
-                                         t.ldc, t.mx - 1, t.my,
-                                         static_cast<const C*>(t.twy),
-                                         static_cast<const T*>(t.lamx),
-                                         static_cast<const T*>(t.lamy), scale,
-                                         (T)h->Ro, (T)(h->Fr / h->delta),
-                                         (T)(h->Fr / (1.0 - h->delta)), cc, s));
-    }
+        KTimer ktc(h, s, QG_K_DST_COLS);
+        DstPass<T> d = {};
+        d.N = t.my;
+        d.nrows = t.mx - 1;
+        d.nin = 1;
+        d.ld_in = ld_tr;
+        d.ld_out = t.ldc;
+        d.transpose_out = 1;
+        d.tw = static_cast<const C*>(t.twy);
+        d.lamx = static_cast<const T*>(t.lamx);
+        d.lamy = static_cast<const T*>(t.lamy);
+        d.scale = scale;
+        d.err = h->derr;
+        if (h->layers == 1) {
+            d.in[0][0] = static_cast<const T*>(tr);
+            d.out[0] = static_cast<T*>(work);
+            QG_TRY(launch_dst_pass<T>(d, 1, dst_config(t.my, sizeof(T), false), s, pdl));
+        } else {
+            d.pair_planes = 1;
+            d.in[0][0] = plane<T>(tr, pl_tr, 0);
+            d.in[1][0] = plane<T>(tr, pl_tr, 1);
+            d.out[0] = plane<T>(work, pl, 0);
+            d.out[1] = plane<T>(work, pl, 1);
+            d.Ro = (T)h->Ro;
+            d.f1 = (T)(h->Fr / h->delta);
+            d.f2 = (T)(h->Fr / (1.0 - h->delta));
+            QG_TRY(launch_dst_pass<T>(d, 2, dst_config(t.my, sizeof(T), true), s, pdl));
+        }
     }
     for (int L = 0; L < h->layers; ++L) {
         KTimer kt(h, s, QG_K_DST_ROWS);
-        RowInput<T> ri{{plane<T>(work, pl, L), nullptr, nullptr, nullptr}, 1};
-        QG_TRY(launch_dst_rows<T>(ri, plane<T>(out, pl, L), t.ldc,
-                                  t.my - 1, t.mx, static_cast<const C*>(t.twx), rc, s));
+        DstPass<T> d = {};
+        d.N = t.mx;
+        d.nrows = t.my - 1;
+        d.in[0][0] = plane<T>(work, pl, L);
+        d.nin = 1;
+        d.ld_in = t.ldc;
+        d.out[0] = plane<T>(out, pl, L);
+        d.ld_out = t.ldc;
+        d.tw = static_cast<const C*>(t.twx);
+        d.err = h->derr;
+        QG_TRY(launch_dst_pass<T>(d, 0, cx, s, pdl));
     }
     return QG_OK;
 }
@@ -306,7 +344,8 @@ qg_status project(qg_ctx* h, const void* win, cudaStream_t s) {
     qg_status st = get_level(h, h->levels, &t);
     if (st != QG_OK) return fail(h, st);
     if (h->levels == 0) {
-        return solve_level<T>(h, *t, win, h->cw, h->psi, h->plane_f, s);
+        return solve_level<T>(h, *t, win, h->ct, h->ld_t, h->plane_t, h->cw, h->psi,
+                              h->plane_f, s);
     }
     for (int L = 0; L < h->layers; ++L) {
         KTimer kt(h, s, QG_K_RESTRICT);
@@ -314,7 +353,8 @@ qg_status project(qg_ctx* h, const void* win, cudaStream_t s) {
                                   plane<T>(h->cw, h->plane_c, L), t->ldc, t->mx, t->my,
                                   h->levels, s));
     }
-    st = solve_level<T>(h, *t, h->cw, h->cw, h->cpsi, h->plane_c, s);
+    st = solve_level<T>(h, *t, h->cw, h->ct, h->ld_t, h->plane_t, h->cw, h->cpsi,
+                        h->plane_c, s);
     if (st != QG_OK) return st;
     for (int L = 0; L < h->layers; ++L) {
         KTimer kt(h, s, QG_K_PROLONG);
@@ -395,9 +435,11 @@ qg_status stage_fused(qg_ctx* h, int s_idx, cudaStream_t s) {
     qg_status st = get_level(h, h->levels, &t);
     if (st != QG_OK) return fail(h, st);
     if (h->levels == 0) {
-        st = solve_level<T>(h, *t, win, h->cw, h->psi, h->plane_f, s);
+        st = solve_level<T>(h, *t, win, h->ct, h->ld_t, h->plane_t, h->cw, h->psi,
+                            h->plane_f, s, 1, true);
     } else {
-        st = solve_level<T>(h, *t, h->part, h->cw, h->cpsi, h->plane_c, s, 4);
+        st = solve_level<T>(h, *t, h->part, h->ct, h->ld_t, h->plane_t, h->cw, h->cpsi,
+                            h->plane_c, s, 4, true);
     }
     if (st != QG_OK) return st;
     FusedParams<T> p;
@@ -563,6 +605,9 @@ qg_status qg_create(const qg_basin* b, int layers, double Re, double Ro, double 
     if (s == QG_OK) guard(dev_alloc(h, &h->psi, fb));
     if (s == QG_OK) guard(dev_alloc(h, &h->cw, cb));
     if (s == QG_OK) guard(dev_alloc(h, &h->cpsi, cb));
+    h->ld_t = padded_ld(my);
+    h->plane_t = (size_t)(mx + 1) * h->ld_t;
+    if (s == QG_OK) guard(dev_alloc(h, &h->ct, h->plane_t * layers * h->esz));
     if (s == QG_OK && layers == 1 && levels >= 1) guard(dev_alloc(h, &h->part, 4 * h->plane_c * h->esz));
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->derr, sizeof(int) * 4));
     if (s == QG_OK && layers == 1) {
@@ -705,9 +750,12 @@ qg_status qg_poisson_solve(qg_handle h, const void* rhs, void* psi, int level) {
     qg_status s = get_level(h, level, &t);
     if (s != QG_OK) return fail(h, s);
     const size_t pl = (size_t)(t->my + 1) * t->ldc;
-    const size_t bytes = pl * h->layers * h->esz;
+    const int ld_tr = padded_ld(t->my);
+    const size_t pl_tr = (size_t)(t->mx + 1) * ld_tr;
+    const size_t bytes = (pl + pl_tr) * h->layers * h->esz;
     void* buf = nullptr;
     QG_TRY(cudaMallocAsync(&buf, bytes, h->stream));
+    void* tbuf = static_cast<char*>(buf) + pl * h->layers * h->esz;
     cudaError_t e = cudaMemsetAsync(buf, 0, bytes, h->stream);
     const size_t dense = (size_t)(t->mx - 1) * (t->my - 1) * h->esz;
     for (int L = 0; L < h->layers && e == cudaSuccess; ++L)
@@ -715,8 +763,9 @@ qg_status qg_poisson_solve(qg_handle h, const void* rhs, void* psi, int level) {
                     static_cast<const char*>(rhs) + L * dense, t->mx - 1, t->my - 1,
                     h->esz, h->stream);
     if (e == cudaSuccess) {
-        s = h->dtype == QG_F64 ? solve_level<double>(h, *t, buf, buf, buf, pl, h->stream)
-                               : solve_level<float>(h, *t, buf, buf, buf, pl, h->stream);
+        s = h->dtype == QG_F64
+                ? solve_level<double>(h, *t, buf, tbuf, ld_tr, pl_tr, buf, buf, pl, h->stream)
+                : solve_level<float>(h, *t, buf, tbuf, ld_tr, pl_tr, buf, buf, pl, h->stream);
         if (s != QG_OK) e = cudaErrorUnknown;
     }
     for (int L = 0; L < h->layers && e == cudaSuccess; ++L)

@@ -16,12 +16,22 @@
 // accuracy like sqrt N and missed the FP32 tolerance at N >= 1024).
 //
 // Twiddles come from one FP64-generated table per N, tw[t] = e^{i pi t/N},
-// t = 0..2N-1, stored in the working precision.  A CTA holds `lanes`
-// complex sequences of length 2N in shared memory (stride 4N + 2 reals,
-// which keeps the transposing column loads free of bank conflicts); each is
-// worked on by TPR = 2N/(4 NB) threads doing NB radix-4 butterflies per
-// pass.  Every pass reads its operands into registers, synchronises and
-// writes in place, so one buffer per sequence suffices.
+// t = 0..2N-1, stored in the working precision and staged in shared memory
+// when it is small.  A CTA holds `lanes` complex sequences of length 2N in
+// shared memory (stride 4N + 2 reals); each is worked on by TPR = 2N/(4 NB)
+// threads doing NB radix-4 butterflies per pass.  Every pass reads its
+// operands into registers, synchronises and writes in place.
+//
+// The 2-D solve is three launches of one kernel:
+//   x pass   rows of the elliptic-grid field (the restriction arrives as the
+//            sum of up to four partial planes) -> x-spectrum written
+//            transposed, so the y pass reads contiguous rows;
+//   y pass   rows of the transposed array: forward DST over y, division by
+//            the eigenvalues of Eq. ialpha (or the 2x2 system of Eqs.
+//            isub-1/2 for two layers, the two layers of a mode forming one
+//            sequence pair), inverse DST, written back untransposed;
+//   x pass   inverse transform of the rows -> streamfunction.
+// All reads are contiguous; only the stores are strided.
 #include <cuda_runtime.h>
 
 #include "qg_internal.cuh"
@@ -49,7 +59,6 @@ __device__ __forceinline__ Cplx<T> cmul_conj(Cplx<T> a, W w) {
     return Cplx<T>{a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y};
 }
 
-// Per-sequence thread geometry inside a CTA.
 struct Geo {
     int N;      // DST length parameter (N - 1 unknowns)
     int L;      // complex FFT length, 2N
@@ -72,7 +81,6 @@ __device__ __forceinline__ Geo make_geo(int N, int NB) {
 
 __host__ __device__ constexpr int lane_stride(int N) { return 4 * N + 2; }
 
-// First pass when log2 L is odd: radix 2 with Ns = 1 (no twiddles).
 template <typename T, int NB>
 __device__ __forceinline__ void fft_pass2_first(T* buf, const Geo& g) {
     constexpr int B = 2 * NB;
@@ -98,9 +106,8 @@ __device__ __forceinline__ void fft_pass2_first(T* buf, const Geo& g) {
 
 // One radix-4 Stockham pass with sub-transform size Ns (forward, e^{-i}).
 // The twiddle of input r is e^{-2 pi i r k/(4 Ns)} = conj(tw[r k N/(2 Ns)]).
-template <typename T, int NB>
-__device__ __forceinline__ void fft_pass4(T* buf, const Geo& g, int Ns,
-                                          const typename Cx<T>::type* tw) {
+template <typename T, int NB, typename TW>
+__device__ __forceinline__ void fft_pass4(T* buf, const Geo& g, int Ns, const TW* tw) {
     const int quarter = g.L >> 2;
     const int tstep = g.N / (2 * Ns);
     Cplx<T> o[NB][4];
@@ -140,11 +147,8 @@ __device__ __forceinline__ void fft_pass4(T* buf, const Geo& g, int Ns,
     __syncthreads();
 }
 
-// Forward complex FFT of length L in place (buf holds L interleaved complex
-// values).  Must be reached by every thread of the CTA.
-template <typename T, int NB>
-__device__ __forceinline__ void fft_inplace(T* buf, const Geo& g,
-                                            const typename Cx<T>::type* tw) {
+template <typename T, int NB, typename TW>
+__device__ __forceinline__ void fft_inplace(T* buf, const Geo& g, const TW* tw) {
     int Ns = 1;
     if (g.logL & 1) {
         fft_pass2_first<T, NB>(buf, g);
@@ -153,8 +157,8 @@ __device__ __forceinline__ void fft_inplace(T* buf, const Geo& g,
     for (; Ns < g.L; Ns <<= 2) fft_pass4<T, NB>(buf, g, Ns, tw);
 }
 
-// Write z_j = (a_j, b_j) and its odd extension z_{2N-j} = -z_j (j >= 1);
-// j = 0 also clears z_N.
+// z_j = (a_j, b_j) and its odd extension z_{2N-j} = -z_j (j >= 1); j = 0
+// also clears z_N.
 template <typename T>
 __device__ __forceinline__ void put_pair(T* buf, int N, int j, T a, T b) {
     if (j == 0) {
@@ -170,197 +174,210 @@ __device__ __forceinline__ void put_pair(T* buf, int N, int j, T a, T b) {
     }
 }
 
-// Rows kernel: each lane transforms rows r0 = 1 + 2p and r1 = r0 + 1.
-template <typename T, int NB>
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// 1-D bulk copies of the constant tables into shared memory on an mbarrier.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+    for (int i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Byte offsets of the shared-memory regions of one dst_pass CTA.
+__host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) / 16 * 16; }
+__host__ __device__ inline size_t lamy_offset(int N, int lanes, size_t esz) {
+    return al16((size_t)lanes * lane_stride(N) * esz);
+}
+__host__ __device__ inline size_t tw_offset(int N, int lanes, size_t esz, bool lamy) {
+    return al16(lamy_offset(N, lanes, esz) + (lamy ? (size_t)N * esz : 0));
+}
+
+// One DST pass over sequence pairs; see DstPass in qg_internal.cuh.
+template <typename T, int NB, int OP>
 __global__ void __launch_bounds__(512)
-dst_rows_kernel(RowInput<T> in, T* out, int ld, int nrows, int N,
-                const typename Cx<T>::type* __restrict__ tw) {
+dst_pass_kernel(DstPass<T> d) {
+    using C = typename Cx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Geo g = make_geo(N, NB);
+    const Geo g = make_geo(d.N, NB);
     const int lanes = blockDim.x / g.TPR;
-    T* buf = reinterpret_cast<T*>(smem_raw) + g.lane * lane_stride(N);
-    const int r0 = 1 + 2 * (blockIdx.x * lanes + g.lane);
-    const int r1 = r0 + 1;
-    const bool v0 = r0 <= nrows, v1 = r1 <= nrows;
-    const size_t o0 = (size_t)r0 * ld, o1 = (size_t)r1 * ld;
-    for (int j = g.t; j < N; j += g.TPR) {
+    const int N = d.N;
+    T* base = reinterpret_cast<T*>(smem_raw);
+    T* buf = base + g.lane * lane_stride(N);
+    // constant tables (twiddles, lamy) go to shared memory by bulk copies
+    // issued before waiting on the previous kernel
+    __shared__ __align__(8) uint64_t mbar;
+    const uint32_t bar = smem_u32(&mbar);
+    T* slamy = reinterpret_cast<T*>(smem_raw + lamy_offset(N, lanes, sizeof(T)));
+    C* stw = reinterpret_cast<C*>(smem_raw + tw_offset(N, lanes, sizeof(T), OP != 0));
+    const bool staged = (OP != 0) || d.tw_in_smem;
+    if (staged) {
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint32_t tb = d.tw_in_smem ? (uint32_t)(2 * N * sizeof(C)) : 0u;
+            const uint32_t lb = OP != 0 ? (uint32_t)(N * sizeof(T)) : 0u;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         ::"r"(bar), "r"(tb + lb) : "memory");
+            if (tb) bulk_copy(smem_u32(stw), d.tw, tb, bar);
+            if (lb) bulk_copy(smem_u32(slamy), d.lamy, lb, bar);
+        }
+    }
+    const C* tw = d.tw_in_smem ? stw : d.tw;
+    pdl_wait();
+
+    // sequence pair of this lane: rows ra / rb of planes pa / pb
+    const int pair = blockIdx.x * lanes + g.lane;
+    int ra, rb, pa, pb;
+    if (d.pair_planes) {
+        ra = rb = 1 + pair;
+        pa = 0;
+        pb = 1;
+    } else {
+        ra = 1 + 2 * pair;
+        rb = ra + 1;
+        pa = pb = 0;
+    }
+    const bool va = ra <= d.nrows, vb = rb <= d.nrows;
+    // all input loads first (2 NB elements of each sequence per thread)
+    constexpr int JPT = 2 * NB;
+    T av[JPT], bv[JPT];
+    const bool rpa = d.nin > 1 && (ra % d.part_py) == 0;
+    const bool rpb = d.nin > 1 && (rb % d.part_py) == 0;
+    const size_t oa = (size_t)ra * d.ld_in, ob = (size_t)rb * d.ld_in;
+#pragma unroll
+    for (int it = 0; it < JPT; ++it) {
+        const int j = g.t + it * g.TPR;
         T a = T(0), b = T(0);
         if (j > 0) {
-            for (int q = 0; q < in.n; ++q) {
-                if (v0) a += in.p[q][o0 + j];
-                if (v1) b += in.p[q][o1 + j];
+            if (va) a = __ldg(d.in[pa][0] + oa + j);
+            if (vb) b = __ldg(d.in[pb][0] + ob + j);
+            if (d.nin > 1) {
+                const bool cx = (j % d.part_px) == 0;
+                if (va) {
+                    if (cx) a += __ldg(d.in[pa][1] + oa + j);
+                    if (rpa) a += __ldg(d.in[pa][2] + oa + j);
+                    if (cx && rpa) a += __ldg(d.in[pa][3] + oa + j);
+                }
+                if (vb) {
+                    if (cx) b += __ldg(d.in[pb][1] + ob + j);
+                    if (rpb) b += __ldg(d.in[pb][2] + ob + j);
+                    if (cx && rpb) b += __ldg(d.in[pb][3] + ob + j);
+                }
             }
         }
-        put_pair(buf, N, j, a, b);
+        av[it] = a;
+        bv[it] = b;
     }
+#pragma unroll
+    for (int it = 0; it < JPT; ++it) put_pair(buf, N, g.t + it * g.TPR, av[it], bv[it]);
+    bool ok = true;
+    if (staged) ok = mbar_wait(bar, 0, 1 << 22);
     __syncthreads();
-    fft_inplace<T, NB>(buf, g, tw);
-    T* d0 = out + (size_t)r0 * ld;
-    T* d1 = out + (size_t)r1 * ld;
-    for (int k = g.t; k < N; k += g.TPR) {
-        if (v0) d0[k] = (k == 0) ? T(0) : T(-0.5) * buf[2 * k + 1];
-        if (v1) d1[k] = (k == 0) ? T(0) : T(0.5) * buf[2 * k];
+    if (!__syncthreads_and(ok)) {
+        if (threadIdx.x == 0 && d.err) atomicExch(d.err, 1);
+        return;
     }
-}
+    fft_inplace<T, NB>(buf, g, tw);
 
-// Column panel load: c = 2p + part enumerates the 2*lanes sequences of the
-// CTA; sequence c comes from plane `src(c)` column `col(c)`.
-template <typename T, typename Src>
-__device__ __forceinline__ void load_panel(T* base, int N, int lanes, int ld,
-                                           Src src) {
-    const int nseq = 2 * lanes;
-    for (int idx = threadIdx.x; idx < N * nseq; idx += blockDim.x) {
-        const int c = idx % nseq, j = idx / nseq;
-        const int p = c >> 1, part = c & 1;
-        T* buf = base + p * lane_stride(N);
-        const T* s = src(c);
-        const T v = (j > 0 && s) ? s[(size_t)j * ld] : T(0);
-        if (j == 0) {
-            buf[part] = T(0);
-            buf[2 * N + part] = T(0);
-        } else {
-            buf[2 * j + part] = v;
-            buf[2 * (2 * N - j) + part] = -v;
+    if (OP != 0) {
+        // mode space: F_l(a) = -Im Z_l / 2, F_l(b) = Re Z_l / 2
+        for (int l = g.t; l < N; l += g.TPR) {
+            T a = T(0), b = T(0);
+            if (l > 0) {
+                const T Fa = T(-0.5) * buf[2 * l + 1];
+                const T Fb = T(0.5) * buf[2 * l];
+                const T ly = slamy[l];
+                if (OP == 1) {
+                    // one layer: psihat = scale Qhat / (lamx[k] + lamy[l])
+                    if (va) a = Fa * (d.scale / (d.lamx[ra] + ly));
+                    if (vb) b = Fb * (d.scale / (d.lamx[rb] + ly));
+                } else if (va) {
+                    // two layers, Eqs. isub-1/2 with alpha = Ro (lamx + lamy)
+                    const T q1 = d.scale * Fa, q2 = d.scale * Fb;
+                    const T al = d.Ro * (d.lamx[ra] + ly);
+                    const T den = al * (al - d.f1 - d.f2);
+                    a = (al * q1 - d.f2 * q1 - d.f1 * q2) / den;
+                    b = (al * q2 - d.f2 * q1 - d.f1 * q2) / den;
+                }
+            }
+            put_pair(buf, N, l, a, b);
+        }
+        __syncthreads();
+        fft_inplace<T, NB>(buf, g, tw);
+    }
+    pdl_trigger();
+
+    // outputs: F_k(a) -> (plane pa, row ra), F_k(b) -> (plane pb, row rb)
+    if (!d.transpose_out) {
+        T* oa = d.out[pa] + (size_t)ra * d.ld_out;
+        T* ob = d.out[pb] + (size_t)rb * d.ld_out;
+        for (int k = g.t; k < N; k += g.TPR) {
+            if (va) oa[k] = (k == 0) ? T(0) : T(-0.5) * buf[2 * k + 1];
+            if (vb) ob[k] = (k == 0) ? T(0) : T(0.5) * buf[2 * k];
+        }
+    } else {
+        // element k of row r goes to out[k][r]: consecutive threads take
+        // consecutive rows of one k
+        const int nseq = 2 * lanes;
+        for (int idx = threadIdx.x; idx < (N - 1) * nseq; idx += blockDim.x) {
+            const int c = idx % nseq, k = 1 + idx / nseq;
+            const int ln = c >> 1, part = c & 1;
+            const int pr = blockIdx.x * lanes + ln;
+            int r, pl;
+            if (d.pair_planes) {
+                r = 1 + pr;
+                pl = part;
+            } else {
+                r = 1 + 2 * pr + part;
+                pl = 0;
+            }
+            if (r > d.nrows) continue;
+            const T* bl = base + ln * lane_stride(N);
+            d.out[pl][(size_t)k * d.ld_out + r] =
+                part ? T(0.5) * bl[2 * k] : T(-0.5) * bl[2 * k + 1];
         }
     }
-}
-
-template <typename T, typename Dst>
-__device__ __forceinline__ void store_panel(const T* base, int N, int lanes,
-                                            int ld, Dst dst) {
-    const int nseq = 2 * lanes;
-    for (int idx = threadIdx.x; idx < N * nseq; idx += blockDim.x) {
-        const int c = idx % nseq, j = idx / nseq;
-        if (j == 0) continue;
-        T* d = dst(c);
-        if (!d) continue;
-        const T* buf = base + (c >> 1) * lane_stride(N);
-        d[(size_t)j * ld] = (c & 1) ? T(0.5) * buf[2 * j] : T(-0.5) * buf[2 * j + 1];
-    }
-}
-
-// One-layer column pass: forward DST-I along y of columns col_a = col0+2p
-// and col_b = col_a+1, psihat = scale Qhat/(lamx[k] + lamy[l]), inverse.
-template <typename T, int NB>
-__global__ void __launch_bounds__(512)
-dst_cols_solve_kernel(T* __restrict__ data, int ld, int ncols, int N,
-                      const typename Cx<T>::type* __restrict__ tw,
-                      const T* __restrict__ lamx, const T* __restrict__ lamy,
-                      T scale) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Geo g = make_geo(N, NB);
-    const int lanes = blockDim.x / g.TPR;
-    T* base = reinterpret_cast<T*>(smem_raw);
-    T* buf = base + g.lane * lane_stride(N);
-    const int col0 = 1 + blockIdx.x * 2 * lanes;
-    load_panel<T>(base, N, lanes, ld, [&](int c) -> const T* {
-        const int col = col0 + c;
-        return col <= ncols ? data + col : nullptr;
-    });
-    __syncthreads();
-    fft_inplace<T, NB>(buf, g, tw);
-    const int ca = col0 + 2 * g.lane, cb = ca + 1;
-    const T lxa = ca <= ncols ? lamx[ca] : T(0);
-    const T lxb = cb <= ncols ? lamx[cb] : T(0);
-    for (int l = g.t; l < N; l += g.TPR) {
-        T a = T(0), b = T(0);
-        if (l > 0) {
-            const T Fa = T(-0.5) * buf[2 * l + 1];
-            const T Fb = T(0.5) * buf[2 * l];
-            const T ly = lamy[l];
-            a = ca <= ncols ? Fa * (scale / (lxa + ly)) : T(0);
-            b = cb <= ncols ? Fb * (scale / (lxb + ly)) : T(0);
-        }
-        put_pair(buf, N, l, a, b);
-    }
-    __syncthreads();
-    fft_inplace<T, NB>(buf, g, tw);
-    store_panel<T>(base, N, lanes, ld, [&](int c) -> T* {
-        const int col = col0 + c;
-        return col <= ncols ? data + col : nullptr;
-    });
-}
-
-// Two-layer column pass: lane p holds column col0+p of both planes (layer 1
-// as the real part, layer 2 as the imaginary part), so the coupled 2x2
-// system of Eqs. isub-1/2 is solved mode by mode inside the lane.
-template <typename T, int NB>
-__global__ void __launch_bounds__(512)
-dst_cols_solve2_kernel(T* __restrict__ d0, T* __restrict__ d1, int ld,
-                       int ncols, int N,
-                       const typename Cx<T>::type* __restrict__ tw,
-                       const T* __restrict__ lamx, const T* __restrict__ lamy,
-                       T scale, T Ro, T f1, T f2) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Geo g = make_geo(N, NB);
-    const int lanes = blockDim.x / g.TPR;
-    T* base = reinterpret_cast<T*>(smem_raw);
-    T* buf = base + g.lane * lane_stride(N);
-    const int col0 = 1 + blockIdx.x * lanes;
-    load_panel<T>(base, N, lanes, ld, [&](int c) -> const T* {
-        const int col = col0 + (c >> 1);
-        return col <= ncols ? ((c & 1) ? d1 : d0) + col : nullptr;
-    });
-    __syncthreads();
-    fft_inplace<T, NB>(buf, g, tw);
-    const int col = col0 + g.lane;
-    const T lx = col <= ncols ? lamx[col] : T(0);
-    for (int l = g.t; l < N; l += g.TPR) {
-        T p1 = T(0), p2 = T(0);
-        if (l > 0 && col <= ncols) {
-            const T q1 = T(-0.5) * scale * buf[2 * l + 1];
-            const T q2 = T(0.5) * scale * buf[2 * l];
-            const T a = Ro * (lx + lamy[l]);
-            const T den = a * (a - f1 - f2);
-            p1 = (a * q1 - f2 * q1 - f1 * q2) / den;
-            p2 = (a * q2 - f2 * q1 - f1 * q2) / den;
-        }
-        put_pair(buf, N, l, p1, p2);
-    }
-    __syncthreads();
-    fft_inplace<T, NB>(buf, g, tw);
-    store_panel<T>(base, N, lanes, ld, [&](int c) -> T* {
-        const int cc = col0 + (c >> 1);
-        return cc <= ncols ? ((c & 1) ? d1 : d0) + cc : nullptr;
-    });
-}
-
-template <typename T>
-size_t dst_smem(int N, int lanes) {
-    return sizeof(T) * (size_t)lanes * lane_stride(N);
 }
 
 }  // namespace
 
-// Launch shapes: NB grows until a sequence has at most 256 threads.
+// one radix-4 butterfly per thread and pass, up to 512 threads per pair
 static int pick_nb(int N) {
     const int L = 2 * N;
-    int nb = 1;
-    while (L / (4 * nb) > 256 && nb < 8) nb <<= 1;
+    int nb = L / 2048;
+    if (nb < 1) nb = 1;
+    if (nb > 8) nb = 8;
     return nb;
 }
 
 static constexpr size_t kSmemCap = 200 * 1024;
+static constexpr size_t kTwiddleSmemCap = 32 * 1024;
 
-DstLaunch dst_rows_config(int N, size_t esz) {
+DstLaunch dst_config(int N, size_t esz, bool pair_planes) {
+    (void)pair_planes;
     DstLaunch c;
     c.nb = pick_nb(N);
     const int tpr = (2 * N) / (4 * c.nb);
-    int lanes = 256 / tpr;
-    if (lanes < 1) lanes = 1;
-    while (lanes > 1 && esz * (size_t)lanes * lane_stride(N) > 64 * 1024) lanes >>= 1;
-    c.lanes = lanes;
-    return c;
-}
+    int lanes = 1;
 
-DstLaunch dst_cols_config(int N, size_t esz) {
-    DstLaunch c;
-    c.nb = pick_nb(N);
-    const int tpr = (2 * N) / (4 * c.nb);
-    int lanes = 512 / tpr;
-    if (lanes < 1) lanes = 1;
-    if (lanes > 8) lanes = 8;
-    while (lanes > 1 && esz * (size_t)lanes * lane_stride(N) > kSmemCap) lanes >>= 1;
     c.lanes = lanes;
     return c;
 }
@@ -370,95 +387,65 @@ size_t dst_lane_bytes(int N, size_t esz) { return esz * (size_t)lane_stride(N); 
 
 template <typename K>
 static cudaError_t allow_smem(K k) {
-    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kSmemCap);
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
 }
 
 cudaError_t dst_prepare_kernels() {
     cudaError_t e = cudaSuccess;
-#define QG_ALLOW(T, NB)                                                        \
-    if (e == cudaSuccess) e = allow_smem(dst_rows_kernel<T, NB>);            \
-    if (e == cudaSuccess) e = allow_smem(dst_cols_solve_kernel<T, NB>);      \
-    if (e == cudaSuccess) e = allow_smem(dst_cols_solve2_kernel<T, NB>);
+#define QG_ALLOW(T, NB)                                                         \
+    if (e == cudaSuccess) e = allow_smem(dst_pass_kernel<T, NB, 0>);          \
+    if (e == cudaSuccess) e = allow_smem(dst_pass_kernel<T, NB, 1>);          \
+    if (e == cudaSuccess) e = allow_smem(dst_pass_kernel<T, NB, 2>);
     QG_ALLOW(float, 1) QG_ALLOW(float, 2) QG_ALLOW(float, 4) QG_ALLOW(float, 8)
     QG_ALLOW(double, 1) QG_ALLOW(double, 2) QG_ALLOW(double, 4) QG_ALLOW(double, 8)
 #undef QG_ALLOW
     return e;
 }
 
+template <typename T, int NB, int OP>
+static cudaError_t launch_nb(const DstPass<T>& d, dim3 grid, dim3 block, size_t sm,
+                             cudaStream_t s, bool pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, dst_pass_kernel<T, NB, OP>, d);
+}
+
 template <typename T>
-cudaError_t launch_dst_rows(RowInput<T> in, T* out, int ld, int nrows, int N,
-                            const typename Cx<T>::type* tw, DstLaunch cfg,
-                            cudaStream_t s) {
-    const int tpr = (2 * N) / (4 * cfg.nb);
+cudaError_t launch_dst_pass(DstPass<T> d, int op, DstLaunch cfg, cudaStream_t s, bool pdl) {
+    using C = typename Cx<T>::type;
+    const int tpr = (2 * d.N) / (4 * cfg.nb);
     const dim3 block(tpr * cfg.lanes);
-    const int pairs = (nrows + 1) / 2;
+    const int pairs = d.pair_planes ? d.nrows : (d.nrows + 1) / 2;
     const dim3 grid((pairs + cfg.lanes - 1) / cfg.lanes);
-    const size_t sm = dst_smem<T>(N, cfg.lanes);
+    // smem: sequence buffers, lamy (op != 0), twiddles (16-byte aligned)
+    const size_t twb = sizeof(C) * 2 * (size_t)d.N;
+    d.tw_in_smem = twb <= kTwiddleSmemCap ? 1 : 0;
+    const size_t sm = tw_offset(d.N, cfg.lanes, sizeof(T), op != 0) + (d.tw_in_smem ? twb : 0);
+    if (d.nin > 1 && (d.part_px <= 0 || d.part_py <= 0)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaErrorInvalidValue;
+#define QG_CASE(NB)                                                                  \
+    case NB:                                                                         \
+        e = op == 0 ? launch_nb<T, NB, 0>(d, grid, block, sm, s, pdl)               \
+          : op == 1 ? launch_nb<T, NB, 1>(d, grid, block, sm, s, pdl)               \
+                    : launch_nb<T, NB, 2>(d, grid, block, sm, s, pdl);              \
+        break;
     switch (cfg.nb) {
-        case 1: dst_rows_kernel<T, 1><<<grid, block, sm, s>>>(in, out, ld, nrows, N, tw); break;
-        case 2: dst_rows_kernel<T, 2><<<grid, block, sm, s>>>(in, out, ld, nrows, N, tw); break;
-        case 4: dst_rows_kernel<T, 4><<<grid, block, sm, s>>>(in, out, ld, nrows, N, tw); break;
-        case 8: dst_rows_kernel<T, 8><<<grid, block, sm, s>>>(in, out, ld, nrows, N, tw); break;
-        default: return cudaErrorInvalidValue;
+        QG_CASE(1) QG_CASE(2) QG_CASE(4) QG_CASE(8)
+        default: break;
     }
-    return cudaGetLastError();
+#undef QG_CASE
+    return e;
 }
 
-template <typename T>
-cudaError_t launch_dst_cols_solve(T* data, int ld, int ncols, int N,
-                                  const typename Cx<T>::type* tw,
-                                  const T* lamx, const T* lamy, T scale,
-                                  DstLaunch cfg, cudaStream_t s) {
-    const int tpr = (2 * N) / (4 * cfg.nb);
-    const dim3 block(tpr * cfg.lanes);
-    const int per = 2 * cfg.lanes;
-    const dim3 grid((ncols + per - 1) / per);
-    const size_t sm = dst_smem<T>(N, cfg.lanes);
-    switch (cfg.nb) {
-        case 1: dst_cols_solve_kernel<T, 1><<<grid, block, sm, s>>>(data, ld, ncols, N, tw, lamx, lamy, scale); break;
-        case 2: dst_cols_solve_kernel<T, 2><<<grid, block, sm, s>>>(data, ld, ncols, N, tw, lamx, lamy, scale); break;
-        case 4: dst_cols_solve_kernel<T, 4><<<grid, block, sm, s>>>(data, ld, ncols, N, tw, lamx, lamy, scale); break;
-        case 8: dst_cols_solve_kernel<T, 8><<<grid, block, sm, s>>>(data, ld, ncols, N, tw, lamx, lamy, scale); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_dst_cols_solve2(T* d0, T* d1, int ld, int ncols, int N,
-                                   const typename Cx<T>::type* tw,
-                                   const T* lamx, const T* lamy, T scale,
-                                   T Ro, T f1, T f2, DstLaunch cfg,
-                                   cudaStream_t s) {
-    const int tpr = (2 * N) / (4 * cfg.nb);
-    const dim3 block(tpr * cfg.lanes);
-    const dim3 grid((ncols + cfg.lanes - 1) / cfg.lanes);
-    const size_t sm = dst_smem<T>(N, cfg.lanes);
-    switch (cfg.nb) {
-        case 1: dst_cols_solve2_kernel<T, 1><<<grid, block, sm, s>>>(d0, d1, ld, ncols, N, tw, lamx, lamy, scale, Ro, f1, f2); break;
-        case 2: dst_cols_solve2_kernel<T, 2><<<grid, block, sm, s>>>(d0, d1, ld, ncols, N, tw, lamx, lamy, scale, Ro, f1, f2); break;
-        case 4: dst_cols_solve2_kernel<T, 4><<<grid, block, sm, s>>>(d0, d1, ld, ncols, N, tw, lamx, lamy, scale, Ro, f1, f2); break;
-        case 8: dst_cols_solve2_kernel<T, 8><<<grid, block, sm, s>>>(d0, d1, ld, ncols, N, tw, lamx, lamy, scale, Ro, f1, f2); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-#define QG_INST(T)                                                               \
-    template cudaError_t launch_dst_rows<T>(RowInput<T>, T*, int, int, int,       \
-                                            const Cx<T>::type*, DstLaunch,        \
-                                            cudaStream_t);                        \
-    template cudaError_t launch_dst_cols_solve<T>(T*, int, int, int,              \
-                                                  const Cx<T>::type*, const T*,   \
-                                                  const T*, T, DstLaunch,         \
-                                                  cudaStream_t);                  \
-    template cudaError_t launch_dst_cols_solve2<T>(T*, T*, int, int, int,         \
-                                                   const Cx<T>::type*, const T*,  \
-                                                   const T*, T, T, T, T,          \
-                                                   DstLaunch, cudaStream_t);
-QG_INST(float)
-QG_INST(double)
-#undef QG_INST
+template cudaError_t launch_dst_pass<float>(DstPass<float>, int, DstLaunch, cudaStream_t, bool);
+template cudaError_t launch_dst_pass<double>(DstPass<double>, int, DstLaunch, cudaStream_t, bool);
 
 }  // namespace qg

@@ -108,6 +108,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int lim
 }
 constexpr int kWaitLimit = 1 << 22;
 
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Shared-memory plan of one CTA (byte offsets, 128-byte aligned).
 template <typename T, int LV>
 struct Plan {
@@ -142,6 +145,8 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
     constexpr int G = (F >= 4) ? F / 4 : 1;          // threads per coarse cell
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
+    // restriction partial sums of node rows on the seam between two groups
+    __shared__ T seam[(LV > 0) ? PL::G : 1][(LV > 0) ? TX / (1 << LV) + 1 : 1];
     T* sw = reinterpret_cast<T*>(smem + PL::W);
     T* swn = reinterpret_cast<T*>(smem + PL::WN);
     T* sp = reinterpret_cast<T*>(smem + PL::P);
@@ -161,6 +166,7 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_wait();      // inputs come from the previous kernel of the step
     if (threadIdx.x == 0) {
         uint32_t bytes = sizeof(T) * (RC + 2) * SWX;
         if (use_wn) bytes += sizeof(T) * RC * TX;
@@ -196,7 +202,7 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
     const int grp = threadIdx.x >> 4;
     const unsigned gm = 0xFFFFu << (16 * (grp & 1));
     const int ys = yc + grp * RY;
-    if (ys >= ny) return;                            // whole group
+    const bool active = ys < ny;                     // uniform in the group
     const int xq = x0 + 4 * lane;
 
     // row y of a halo tile (w^(s) or the fine psi): own quad + shuffled halos
@@ -268,147 +274,175 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
         }
     };
 
-    T W[3][6], P[3][6];
-    row_halo(sw, ys - 1, W[0]);
-    load_psi(0, ys - 1, P[0]);
-    row_halo(sw, ys, W[1]);
-    load_psi(1, ys, P[1]);
-
     T accA[NM], accB[NM], accE[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) accA[m] = accB[m] = accE[m] = T(0);
+    if (active) {
+        T W[3][6], P[3][6];
+        row_halo(sw, ys - 1, W[0]);
+        load_psi(0, ys - 1, P[0]);
+        row_halo(sw, ys, W[1]);
+        load_psi(1, ys, P[1]);
 
-#pragma unroll
-    for (int o = 0; o < RY; ++o) {
-        const int y = ys + o;
-        const int sb = o % 3, sc = (o + 1) % 3, sa = (o + 2) % 3;
-        row_halo(sw, y + 1, W[sa]);
-        load_psi(o + 2, y + 1, P[sa]);
-        const bool row_ok = y >= 1 && y <= ny - 1;
-        const size_t ro = (size_t)y * ld;
-        T wn[4] = {T(0), T(0), T(0), T(0)};
-        if (use_wn) lds4(swn + (y - yc) * TX + 4 * lane, wn);
-        T fv[4];
-        if (use_f) {
-            lds4(sf + (y - yc) * TX + 4 * lane, fv);
-        } else {
-            const T fr = __ldg(p.frow + (y <= ny ? y : ny));
-#pragma unroll
-            for (int q = 0; q < 4; ++q) fv[q] = fr;
-        }
-        // differences shared by the four nodes: vertical psi differences per
-        // column, horizontal psi differences per row
-        T V[6], Hb[4], Hc[4], Ha[4];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) V[c] = P[sa][c] - P[sb][c];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            Hb[q] = P[sb][q + 2] - P[sb][q];
-            Hc[q] = P[sc][q + 2] - P[sc][q];
-            Ha[q] = P[sa][q + 2] - P[sa][q];
-        }
-        T out[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = q + 1;
-            const T pm0 = P[sc][i - 1], p10 = P[sc][i + 1], p0m = P[sb][i], p01 = P[sa][i];
-            const T q00 = W[sc][i];
-            const T qm0 = W[sc][i - 1], q10 = W[sc][i + 1], q0m = W[sb][i], q01 = W[sa][i];
-            const T qmm = W[sb][i - 1], q1m = W[sb][i + 1], qm1 = W[sa][i - 1], q11 = W[sa][i + 1];
-            // Arakawa J1 + J2 + J3 (Eqs. j1-j3) with
-            //   J1 = -(q10 - qm0) V_i + (q01 - q0m) Hc_i
-            //   J2 = -q10 V_{i+1} + qm0 V_{i-1} + q01 Ha_i - q0m Hb_i
-            //   J3 = -q11 (p01 - p10) + qmm (pm0 - p0m) + qm1 (p01 - pm0) - q1m (p10 - p0m)
-            T jac = -(q10 - qm0) * V[i];
-            jac = fma(q01 - q0m, Hc[q], jac);
-            jac = fma(-q10, V[i + 1], jac);
-            jac = fma(qm0, V[i - 1], jac);
-            jac = fma(q01, Ha[q], jac);
-            jac = fma(-q0m, Hb[q], jac);
-            jac = fma(-q11, p01 - p10, jac);
-            jac = fma(qmm, pm0 - p0m, jac);
-            jac = fma(qm1, p01 - pm0, jac);
-            jac = fma(-q1m, p10 - p0m, jac);
-            // (1/Ro) J(psi, y) in Arakawa's form: (4 c_j + c_{j+1} + c_{j-1})/(6 Ro)
-            const T beta = fma(T(4), Hc[q], Ha[q] + Hb[q]);
-            const T lap = (q10 + qm0 - T(2) * q00) * p.c_lapx + (q01 + q0m - T(2) * q00) * p.c_lapy;
-            T Gv = fma(-p.c_jac, jac, fv[q] + lap);
-            Gv = fma(-p.c_beta, beta, Gv);
-            out[q] = fma(p.a, wn[q], p.b * fma(p.dt, Gv, q00));
-        }
-        const bool quad_ok = row_ok && xq >= 1 && xq + 3 <= nx - 1;
-        if (quad_ok) {
-            stg4(p.wout + ro + xq, out);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int x = xq + q;
-                if (row_ok && x >= 1 && x <= nx - 1) p.wout[ro + x] = out[q];
-                else out[q] = T(0);
-            }
-        }
-        if (LV > 0) {
-            // x shares of this row
-            T xa, xb = T(0), xe;
-            if (LV == 1) {
-                const T A = T(0.5) * out[0] + T(0.25) * out[1];
-                const T C = T(0.25) * out[3];
-                xb = T(0.25) * out[1] + T(0.5) * out[2] + T(0.25) * out[3];
-                const T Cp = __shfl_up_sync(gm, C, 1, 16);
-                xa = A + (lane > 0 ? Cp : T(0));
-                xe = C;
+
+    #pragma unroll
+        for (int o = 0; o < RY; ++o) {
+            const int y = ys + o;
+            const int sb = o % 3, sc = (o + 1) % 3, sa = (o + 2) % 3;
+            row_halo(sw, y + 1, W[sa]);
+            load_psi(o + 2, y + 1, P[sa]);
+            const bool row_ok = y >= 1 && y <= ny - 1;
+            const size_t ro = (size_t)y * ld;
+            T wn[4] = {T(0), T(0), T(0), T(0)};
+            if (use_wn) lds4(swn + (y - yc) * TX + 4 * lane, wn);
+            T fv[4];
+            if (use_f) {
+                lds4(sf + (y - yc) * TX + 4 * lane, fv);
             } else {
-                T Va = T(0), Vb = T(0);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int d = (xq + q) & (F - 1);
-                    Va += T(F - d) * (T(1) / T(F * F)) * out[q];
-                    Vb += T(d) * (T(1) / T(F * F)) * out[q];
-                }
-#pragma unroll
-                for (int off = 1; off < G; off <<= 1) {
-                    Va += __shfl_xor_sync(gm, Va, off, 16);
-                    Vb += __shfl_xor_sync(gm, Vb, off, 16);
-                }
-                const T Vbp = __shfl_up_sync(gm, Vb, G, 16);
-                xa = Va + (lane >= G ? Vbp : T(0));
-                xe = Vb;
+                const T fr = __ldg(p.frow + (y <= ny ? y : ny));
+    #pragma unroll
+                for (int q = 0; q < 4; ++q) fv[q] = fr;
             }
-            const int dy = o & (F - 1);
-            const int mlo = o >> LV;
-            const T wlo = T(F - dy) * (T(1) / T(F * F));
-            const T whi = T(dy) * (T(1) / T(F * F));
-            accA[mlo] += wlo * xa;
-            accE[mlo] += wlo * xe;
-            if (LV == 1) accB[mlo] += wlo * xb;
-            if (dy != 0) {
-                accA[mlo + 1] += whi * xa;
-                accE[mlo + 1] += whi * xe;
-                if (LV == 1) accB[mlo + 1] += whi * xb;
+            // differences shared by the four nodes: vertical psi differences per
+            // column, horizontal psi differences per row
+            T V[6], Hb[4], Hc[4], Ha[4];
+    #pragma unroll
+            for (int c = 0; c < 6; ++c) V[c] = P[sa][c] - P[sb][c];
+    #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                Hb[q] = P[sb][q + 2] - P[sb][q];
+                Hc[q] = P[sc][q + 2] - P[sc][q];
+                Ha[q] = P[sa][q + 2] - P[sa][q];
+            }
+            T out[4];
+    #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = q + 1;
+                const T pm0 = P[sc][i - 1], p10 = P[sc][i + 1], p0m = P[sb][i], p01 = P[sa][i];
+                const T q00 = W[sc][i];
+                const T qm0 = W[sc][i - 1], q10 = W[sc][i + 1], q0m = W[sb][i], q01 = W[sa][i];
+                const T qmm = W[sb][i - 1], q1m = W[sb][i + 1], qm1 = W[sa][i - 1], q11 = W[sa][i + 1];
+                // Arakawa J1 + J2 + J3 (Eqs. j1-j3) with
+                //   J1 = -(q10 - qm0) V_i + (q01 - q0m) Hc_i
+                //   J2 = -q10 V_{i+1} + qm0 V_{i-1} + q01 Ha_i - q0m Hb_i
+                //   J3 = -q11 (p01 - p10) + qmm (pm0 - p0m) + qm1 (p01 - pm0) - q1m (p10 - p0m)
+                T jac = -(q10 - qm0) * V[i];
+                jac = fma(q01 - q0m, Hc[q], jac);
+                jac = fma(-q10, V[i + 1], jac);
+                jac = fma(qm0, V[i - 1], jac);
+                jac = fma(q01, Ha[q], jac);
+                jac = fma(-q0m, Hb[q], jac);
+                jac = fma(-q11, p01 - p10, jac);
+                jac = fma(qmm, pm0 - p0m, jac);
+                jac = fma(qm1, p01 - pm0, jac);
+                jac = fma(-q1m, p10 - p0m, jac);
+                // (1/Ro) J(psi, y) in Arakawa's form: (4 c_j + c_{j+1} + c_{j-1})/(6 Ro)
+                const T beta = fma(T(4), Hc[q], Ha[q] + Hb[q]);
+                const T lap = (q10 + qm0 - T(2) * q00) * p.c_lapx + (q01 + q0m - T(2) * q00) * p.c_lapy;
+                T Gv = fma(-p.c_jac, jac, fv[q] + lap);
+                Gv = fma(-p.c_beta, beta, Gv);
+                out[q] = fma(p.a, wn[q], p.b * fma(p.dt, Gv, q00));
+            }
+            const bool quad_ok = row_ok && xq >= 1 && xq + 3 <= nx - 1;
+            if (quad_ok) {
+                stg4(p.wout + ro + xq, out);
+            } else {
+    #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int x = xq + q;
+                    if (row_ok && x >= 1 && x <= nx - 1) p.wout[ro + x] = out[q];
+                    else out[q] = T(0);
+                }
+            }
+            if (LV > 0) {
+                // x shares of this row
+                T xa, xb = T(0), xe;
+                if (LV == 1) {
+                    const T A = T(0.5) * out[0] + T(0.25) * out[1];
+                    const T C = T(0.25) * out[3];
+                    xb = T(0.25) * out[1] + T(0.5) * out[2] + T(0.25) * out[3];
+                    const T Cp = __shfl_up_sync(gm, C, 1, 16);
+                    xa = A + (lane > 0 ? Cp : T(0));
+                    xe = C;
+                } else {
+                    T Va = T(0), Vb = T(0);
+    #pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int d = (xq + q) & (F - 1);
+                        Va += T(F - d) * (T(1) / T(F * F)) * out[q];
+                        Vb += T(d) * (T(1) / T(F * F)) * out[q];
+                    }
+    #pragma unroll
+                    for (int off = 1; off < G; off <<= 1) {
+                        Va += __shfl_xor_sync(gm, Va, off, 16);
+                        Vb += __shfl_xor_sync(gm, Vb, off, 16);
+                    }
+                    const T Vbp = __shfl_up_sync(gm, Vb, G, 16);
+                    xa = Va + (lane >= G ? Vbp : T(0));
+                    xe = Vb;
+                }
+                const int dy = o & (F - 1);
+                const int mlo = o >> LV;
+                const T wlo = T(F - dy) * (T(1) / T(F * F));
+                const T whi = T(dy) * (T(1) / T(F * F));
+                accA[mlo] += wlo * xa;
+                accE[mlo] += wlo * xe;
+                if (LV == 1) accB[mlo] += wlo * xb;
+                if (dy != 0) {
+                    accA[mlo + 1] += whi * xa;
+                    accE[mlo + 1] += whi * xe;
+                    if (LV == 1) accB[mlo + 1] += whi * xb;
+                }
             }
         }
     }
-
+    pdl_trigger();
     // ---- restriction partial sums ---------------------------------------
+    // The node row on the seam between group g and g+1 of this CTA gets its
+    // two shares added here (lower group's share first); only the last
+    // group's top row, on the CTA's seam, goes to a seam plane.
     if (LV > 0) {
-        const int Ix0 = x0 >> LV;
-#pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            const int J = (ys >> LV) + m;
-            if (J < 1 || J > my - 1) continue;
-            const int qy = (m == NM - 1) ? 2 : 0;
-            T* rowA = p.part[qy] + (size_t)J * p.ldc;
+        if (active) {
             if (LV == 1) {
-                const int I = Ix0 + 2 * lane;
-                if (I >= 1 && I <= mx - 1) rowA[I] = accA[m];
-                if (I + 1 >= 1 && I + 1 <= mx - 1) rowA[I + 1] = accB[m];
+                seam[grp][2 * lane] = accA[NM - 1];
+                seam[grp][2 * lane + 1] = accB[NM - 1];
             } else if (lane % G == 0) {
-                const int I = Ix0 + lane / G;
-                if (I >= 1 && I <= mx - 1) rowA[I] = accA[m];
+                seam[grp][lane / G] = accA[NM - 1];
             }
-            if (lane == 15) {
-                const int I = Ix0 + TX / F;
-                if (I >= 1 && I <= mx - 1) p.part[qy + 1][(size_t)J * p.ldc + I] = accE[m];
+            if (lane == 15) seam[grp][TX / F] = accE[NM - 1];
+        }
+        __syncthreads();
+        if (active && grp > 0) {
+            if (LV == 1) {
+                accA[0] = seam[grp - 1][2 * lane] + accA[0];
+                accB[0] = seam[grp - 1][2 * lane + 1] + accB[0];
+            } else if (lane % G == 0) {
+                accA[0] = seam[grp - 1][lane / G] + accA[0];
+            }
+            if (lane == 15) accE[0] = seam[grp - 1][TX / F] + accE[0];
+        }
+        if (active) {
+            const int Ix0 = x0 >> LV;
+            const int mlast = (grp == PL::G - 1) ? NM : NM - 1;
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                if (m >= mlast) break;
+                const int J = (ys >> LV) + m;
+                if (J < 1 || J > my - 1) continue;
+                const int qy = (m == NM - 1) ? 2 : 0;
+                T* rowA = p.part[qy] + (size_t)J * p.ldc;
+                if (LV == 1) {
+                    const int I = Ix0 + 2 * lane;
+                    if (I >= 1 && I <= mx - 1) rowA[I] = accA[m];
+                    if (I + 1 >= 1 && I + 1 <= mx - 1) rowA[I + 1] = accB[m];
+                } else if (lane % G == 0) {
+                    const int I = Ix0 + lane / G;
+                    if (I >= 1 && I <= mx - 1) rowA[I] = accA[m];
+                }
+                if (lane == 15) {
+                    const int I = Ix0 + TX / F;
+                    if (I >= 1 && I <= mx - 1) p.part[qy + 1][(size_t)J * p.ldc + I] = accE[m];
+                }
             }
         }
     }
@@ -427,9 +461,17 @@ cudaError_t launch_sweep(const FusedParams<T>& p, const FineMaps& m, cudaStream_
     }
     const dim3 block(PL::THREADS);
     const dim3 grid((p.nx + TX - 1) / TX, (p.ny + PL::RC - 1) / PL::RC);
-    const size_t sm = p.f2d ? PL::END : PL::END_NOF;
-    fine_sweep_kernel<T, LV><<<grid, block, sm, s>>>(m.w, m.wn, m.psi, m.f, p);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = p.f2d ? PL::END : PL::END_NOF;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fine_sweep_kernel<T, LV>, m.w, m.wn, m.psi, m.f, p);
 }
 
 }  // namespace
@@ -448,6 +490,8 @@ cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int le
 }
 
 size_t fine_tile_rows(size_t esz) { return esz == 8 ? Rows<double>::value : Rows<float>::value; }
+int fine_part_period_x(int levels) { return TX >> levels; }
+int fine_part_period_y(int levels, size_t esz) { return (int)fine_tile_rows(esz) >> levels; }
 int fine_halo_cols() { return SWX; }
 int fine_block_cols() { return TX; }
 

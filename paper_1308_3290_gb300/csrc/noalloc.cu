@@ -5,7 +5,8 @@
 // device memory through its own pool or a hard per-tenant quota, or a
 // latency-critical loop in which cudaMalloc/cudaFree would synchronise the
 // device and stall unrelated streams.  For them this entry point keeps its
-// workspace (the padded work grid and the twiddle and eigenvalue tables) in
+// workspace (the padded work grid, its transposed spectrum, and the twiddle
+// and eigenvalue tables) in
 // one file-scope __device__ array of fixed size, kNoAllocBytes.  Every GPU
 // that loads the library holds that array until the process exits.
 //
@@ -26,7 +27,7 @@
 namespace qg {
 namespace {
 
-constexpr size_t kNoAllocBytes = 16u << 20;   // 16 MiB per device
+constexpr size_t kNoAllocBytes = 32u << 20;   // 32 MiB per device
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -62,14 +63,16 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Byte layout of the scratch for one request: padded grid, then the tables.
 struct Layout {
-    size_t grid, twx, twy, lamx, lamy, total;
+    size_t grid, tr, twx, twy, lamx, lamy, total;
 };
 
 Layout layout(int nx, int ny, size_t esz) {
     Layout L;
     const int ld = round_up(nx + 1, 32);
+    const int ldt = round_up(ny + 1, 32);
     L.grid = 0;
-    L.twx = align256((size_t)(ny + 1) * ld * esz);
+    L.tr = align256((size_t)(ny + 1) * ld * esz);
+    L.twx = L.tr + align256((size_t)(nx + 1) * ldt * esz);
     L.twy = L.twx + align256((size_t)4 * nx * esz);
     L.lamx = L.twy + align256((size_t)4 * ny * esz);
     L.lamy = L.lamx + align256((size_t)(nx + 1) * esz);
@@ -95,14 +98,43 @@ qg_status solve(unsigned char* base, const Layout& Lo, int nx, int ny, double dx
     if (cudaGetLastError() != cudaSuccess) return QG_ERR_CUDA;
     if (copy_in(grid, ld, rhs, nx - 1, ny - 1, esz, s) != cudaSuccess) return QG_ERR_CUDA;
     const T scale = (T)((2.0 / nx) * (2.0 / ny));
-    const RowInput<T> in{{grid, nullptr, nullptr, nullptr}, 1};
-    if (launch_dst_rows<T>(in, grid, ld, ny - 1, nx, twx, dst_rows_config(nx, esz), s) != cudaSuccess)
-        return QG_ERR_CUDA;
-    if (launch_dst_cols_solve<T>(grid, ld, nx - 1, ny, twy, lamx, lamy, scale,
-                                 dst_cols_config(ny, esz), s) != cudaSuccess)
-        return QG_ERR_CUDA;
-    if (launch_dst_rows<T>(in, grid, ld, ny - 1, nx, twx, dst_rows_config(nx, esz), s) != cudaSuccess)
-        return QG_ERR_CUDA;
+    const int ldt = round_up(ny + 1, 32);
+    T* tr = reinterpret_cast<T*>(base + Lo.tr);
+    DstPass<T> d = {};
+    d.N = nx;                     // x pass, transposed into tr
+    d.nrows = ny - 1;
+    d.in[0][0] = grid;
+    d.nin = 1;
+    d.ld_in = ld;
+    d.out[0] = tr;
+    d.ld_out = ldt;
+    d.transpose_out = 1;
+    d.tw = twx;
+    if (launch_dst_pass<T>(d, 0, dst_config(nx, esz, false), s, false) != cudaSuccess) return QG_ERR_CUDA;
+    d = DstPass<T>{};            // y pass with the eigenvalue division, back into grid
+    d.N = ny;
+    d.nrows = nx - 1;
+    d.in[0][0] = tr;
+    d.nin = 1;
+    d.ld_in = ldt;
+    d.out[0] = grid;
+    d.ld_out = ld;
+    d.transpose_out = 1;
+    d.tw = twy;
+    d.lamx = lamx;
+    d.lamy = lamy;
+    d.scale = scale;
+    if (launch_dst_pass<T>(d, 1, dst_config(ny, esz, false), s, false) != cudaSuccess) return QG_ERR_CUDA;
+    d = DstPass<T>{};            // inverse x pass, in place
+    d.N = nx;
+    d.nrows = ny - 1;
+    d.in[0][0] = grid;
+    d.nin = 1;
+    d.ld_in = ld;
+    d.out[0] = grid;
+    d.ld_out = ld;
+    d.tw = twx;
+    if (launch_dst_pass<T>(d, 0, dst_config(nx, esz, false), s, false) != cudaSuccess) return QG_ERR_CUDA;
     if (copy_out(psi, grid, ld, nx - 1, ny - 1, esz, s) != cudaSuccess) return QG_ERR_CUDA;
     return QG_OK;
 }

@@ -34,44 +34,44 @@ struct DstLaunch {
 
 // ---- kernels (declared here, defined in dst.cu / stencil.cu / diag.cu) ----
 
-// Input of a row transform: the sum of n (1..4) padded planes, added in
-// index order (the restriction arrives as four partial-sum planes).
+// One launch of the sine-transform engine (dst.cu) over sequence pairs.
+// Sequences are rows 1..nrows of padded planes; row r holds f_0..f_{N-1}
+// (f_0 forced to 0).  A pair is rows (r, r+1) of plane 0, or with
+// pair_planes row r of planes 0 and 1.  The input of a sequence is the sum of
+// nin planes in[plane][0..nin-1] (all of pitch ld_in), added in index order.
+// op 0: unnormalised DST-I.  op 1: DST-I, multiplication of mode l of row r
+// by scale / (lamx[r] + lamy[l]), DST-I.  op 2 (pair_planes): DST-I, the
+// coupled two-layer solve of Eqs. isub-1/2 per mode with
+// alpha = Ro (lamx[r] + lamy[l]), DST-I.  Output element k of row r goes to
+// out[plane][r * ld_out + k], or to out[plane][k * ld_out + r] with
+// transpose_out.
 template <typename T>
-struct RowInput {
-    const T* p[4];
-    int n;
+struct DstPass {
+    int N;
+    int nrows;
+    const T* in[2][4];
+    int nin;               // 1, or 4 for the restriction partial planes
+    int part_px, part_py;  // with nin == 4: plane 1 is read only at columns
+                           // k % part_px == 0, plane 2 at rows r % part_py == 0,
+                           // plane 3 at both (elsewhere they hold zeros)
+    int ld_in;
+    T* out[2];
+    int ld_out;
+    int transpose_out;
+    int pair_planes;
+    const typename Cx<T>::type* tw;   // e^{i pi t/N}, t < 2N
+    int tw_in_smem;                    // set by the launcher
+    const T* lamx;
+    const T* lamy;
+    T scale, Ro, f1, f2;
+    int* err;                          // set to 1 when a bounded wait runs out
 };
 
-// Unnormalised DST-I, F_k = sum_{j=1}^{N-1} f_j sin(pi j k / N), of rows
-// 1..nrows of a padded array (row length N = n_x).  in and out may alias.
 template <typename T>
-cudaError_t launch_dst_rows(RowInput<T> in, T* out, int ld, int nrows, int N,
-                            const typename Cx<T>::type* tw, DstLaunch cfg,
-                            cudaStream_t s);
-
-// Column pass of the one-layer solve on a padded level array of
-// (N_x - 1) columns: forward DST-I along y, multiplication by
-// scale / (lamx[k] + lamy[l]), inverse DST-I along y, in place.
-template <typename T>
-cudaError_t launch_dst_cols_solve(T* data, int ld, int ncols, int N,
-                                  const typename Cx<T>::type* tw,
-                                  const T* lamx, const T* lamy, T scale,
-                                  DstLaunch cfg, cudaStream_t s);
-
-// Column pass of the two-layer coupled solve (Eqs. isub-1/2): planes
-// data0 / data1 hold Q_1, Q_2 in the x-sine basis; per mode the 2x2 system
-// is solved with alpha = Ro (lamx + lamy).
-template <typename T>
-cudaError_t launch_dst_cols_solve2(T* data0, T* data1, int ld, int ncols,
-                                   int N, const typename Cx<T>::type* tw,
-                                   const T* lamx, const T* lamy, T scale,
-                                   T Ro, T f1, T f2, DstLaunch cfg,
-                                   cudaStream_t s);
-
-DstLaunch dst_rows_config(int N, size_t esz);
+cudaError_t launch_dst_pass(DstPass<T> d, int op, DstLaunch cfg, cudaStream_t s, bool pdl);
+DstLaunch dst_config(int N, size_t esz, bool pair_planes);
 size_t dst_max_smem();                       // dynamic shared memory cap per CTA
 size_t dst_lane_bytes(int N, size_t esz);    // shared memory of one sequence pair
-DstLaunch dst_cols_config(int N, size_t esz);
 cudaError_t dst_prepare_kernels();
 
 // Full-weighting restriction applied `levels` times, as one hat-weighted
@@ -135,6 +135,8 @@ template <typename T>
 cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int levels,
                               cudaStream_t s);
 size_t fine_tile_rows(size_t esz);   // fine rows per CTA
+int fine_part_period_x(int levels);  // coarse columns between tile edges
+int fine_part_period_y(int levels, size_t esz);  // coarse rows between CTA edges
 int fine_halo_cols();                // columns of a halo box
 int fine_block_cols();               // columns of an interior box
 
