@@ -160,11 +160,10 @@ qg_status qg_diagnostics(qg_handle h, double* ke, double* enstrophy,
 /* Kernel classes of the step, for qg_read_timing.                          */
 typedef enum qg_kernel_class {
     QG_K_RESTRICT = 0,   /* restriction (Eq. res), when not fused            */
-    QG_K_DST_ROWS = 1,   /* row sine transforms (x direction)                */
-    QG_K_DST_COLS = 2,   /* column transforms + eigenvalue division (y)      */
-    QG_K_PROLONG = 3,    /* prolongation (Eq. pro), when not fused           */
-    QG_K_FINE = 4,       /* fine-grid Arakawa / dissipation / forcing / RK   */
-    QG_K_COUNT = 5
+    QG_K_SOLVE = 1,      /* elliptic solve: sine transforms + eigenvalues    */
+    QG_K_PROLONG = 2,    /* prolongation (Eq. pro), when not fused           */
+    QG_K_FINE = 3,       /* fine-grid Arakawa / dissipation / forcing / RK   */
+    QG_K_COUNT = 4
 } qg_kernel_class;
 
 /* qg_set_timing -- enable (1) or disable (0) per-kernel timing.  When

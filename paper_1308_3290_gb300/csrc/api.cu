@@ -12,10 +12,13 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "qg_internal.cuh"
@@ -77,7 +80,9 @@ struct qg_ctx {
     bool capturing = false;
     // TMA tensor maps of the fine buffers (halo and interior boxes)
     CUtensorMap tm_halo[3], tm_int[3], tm_psi, tm_f;
+    int solve_engine = 4;          // FFT base radix of the step's solve (autotuned)
     int* derr = nullptr;           // device error flag of bounded waits
+    unsigned* dbar = nullptr;      // grid-barrier counters of the solve kernel
 };
 
 namespace qg {
@@ -202,8 +207,8 @@ qg_status get_level(qg_ctx* h, int lv, const LevelTables** out) {
     LevelTables t;
     t.mx = h->nx >> lv;
     t.my = h->ny >> lv;
-    if (dst_lane_bytes(t.mx, h->esz) > dst_max_smem() ||
-        dst_lane_bytes(t.my, h->esz) > dst_max_smem())
+    if (solve_smem_bytes(t.mx, t.my, h->esz, 4) > 200 * 1024 &&
+        solve_smem_bytes(t.mx, t.my, h->esz, 16) > 200 * 1024)
         return QG_ERR_SHAPE;
     t.ldc = padded_ld(t.mx);
     t.dxc = h->dx * (double)(1 << lv);
@@ -257,83 +262,181 @@ T* plane(void* base, size_t plane_elems, int layer) {
     return static_cast<T*>(base) + (size_t)layer * plane_elems;
 }
 
-// Elliptic solve on one level: the x pass of `in` (the sum of `nparts`
-// planes per layer) into the transposed buffer `tr` (pitch ld_tr), the y pass
-// with the eigenvalue division (or the coupled two-layer system) back into
-// `work`, and the inverse x pass into `out`.  in, work and out have the
-// level's padded layout and plane size pl; work and out may alias, in may
-// alias either.
+// Elliptic solve on one level (one cooperative launch): `in` holds
+// `nparts` planes per layer (the restriction's partial sums when 4), tr is
+// the transposed scratch (pitch ld_tr, plane pl_tr), work the y-pass output;
+// in, work and out have the level's padded layout and plane size pl.  work
+// and out may alias; in may alias either.
+int engine_rule(int mx, int my);
+int engine_for(qg_ctx* h, int mx, int my);
+
 template <typename T>
 qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr, int ld_tr,
                       size_t pl_tr, void* work, void* out, size_t pl, cudaStream_t s,
-                      int nparts = 1, bool pdl = false) {
+                      int nparts = 1, int engine = 0) {
     using C = typename Cx<T>::type;
-    const DstLaunch cx = dst_config(t.mx, sizeof(T), false);
-    const T scale = (T)((2.0 / t.mx) * (2.0 / t.my));
+    SolveParams<T> P = {};
+    P.mx = t.mx;
+    P.my = t.my;
+    P.layers = h->layers;
     for (int L = 0; L < h->layers; ++L) {
-        KTimer kt(h, s, QG_K_DST_ROWS);
-        DstPass<T> d = {};
-        d.N = t.mx;
-        d.nrows = t.my - 1;
         for (int q = 0; q < nparts; ++q)
-            d.in[0][q] = plane<T>(const_cast<void*>(in), pl, L * nparts + q);
-        d.nin = nparts;
-        if (nparts > 1) {
-            d.part_px = fine_part_period_x(h->levels);
-            d.part_py = fine_part_period_y(h->levels, sizeof(T));
-        }
-        d.ld_in = t.ldc;
-        d.out[0] = plane<T>(tr, pl_tr, L);
-        d.ld_out = ld_tr;
-        d.transpose_out = 1;
-        d.tw = static_cast<const C*>(t.twx);
-        d.err = h->derr;
-        QG_TRY(launch_dst_pass<T>(d, 0, cx, s, pdl));
+            P.in[L][q] = plane<T>(const_cast<void*>(in), pl, L * nparts + q);
+        P.tr[L] = plane<T>(tr, pl_tr, L);
+        P.work[L] = plane<T>(work, pl, L);
+        P.out[L] = plane<T>(out, pl, L);
     }
+    P.nin = nparts;
+    P.part_px = P.part_py = 1;
+    if (nparts > 1) {
+        P.part_px = fine_part_period_x(h->levels);
+        P.part_py = fine_part_period_y(h->levels, sizeof(T));
+    }
+    P.ld = t.ldc;
+    P.ld_tr = ld_tr;
+    P.twx = static_cast<const C*>(t.twx);
+    P.twy = static_cast<const C*>(t.twy);
+    P.lamx = static_cast<const T*>(t.lamx);
+    P.lamy = static_cast<const T*>(t.lamy);
+    P.scale = (T)((2.0 / t.mx) * (2.0 / t.my));
+    P.Ro = (T)h->Ro;
+    if (h->layers == 2) {
+        P.f1 = (T)(h->Fr / h->delta);
+        P.f2 = (T)(h->Fr / (1.0 - h->delta));
+    }
+    P.bar = h->dbar;
+    P.err = h->derr;
+    KTimer kt(h, s, QG_K_SOLVE);
+    QG_TRY(launch_solve<T>(P, engine ? engine : engine_for(h, t.mx, t.my), s));
+    return QG_OK;
+}
+
+// ---- solve-engine autotuner ---------------------------------------------
+// The FFT base radix of the solve (4: many threads per sequence pair; 16:
+// fewer passes and instructions) is timed on the handle's own elliptic grid
+// when the handle is created by timing a few whole steps with each (the
+// solve alone, timed back to back, ranks them differently: in a step the
+// fine sweep has just streamed its fields through L2), and the faster one is
+// kept.  Results are cached per (nx, ny, levels, layers, dtype) for the
+// process and, when the environment variable QG_TUNE_CACHE names a file, in
+// that file (one line "nx ny levels layers esz engine" per entry).
+// QG_SOLVE_ENGINE=4|16 forces a choice.  Other grids use the size rule.
+
+int engine_rule(int mx, int my) { return (long)mx * my >= (1L << 21) ? 16 : 4; }
+
+int engine_for(qg_ctx* h, int mx, int my) {
+    const LevelTables* t = nullptr;
+    if (get_level(h, h->levels, &t) == QG_OK && t->mx == mx && t->my == my) return h->solve_engine;
+    return engine_rule(mx, my);
+}
+
+using TuneKey = std::tuple<int, int, int, int, int>;
+std::mutex g_tune_mutex;
+std::map<TuneKey, int> g_tune_cache;
+bool g_tune_file_read = false;
+
+void tune_file_load() {
+    if (g_tune_file_read) return;
+    g_tune_file_read = true;
+    const char* path = std::getenv("QG_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    int a, b, c, d, x, e;
+    while (std::fscanf(f, "%d %d %d %d %d %d", &a, &b, &c, &d, &x, &e) == 6)
+        if (e == 4 || e == 16) g_tune_cache[TuneKey(a, b, c, d, x)] = e;
+    std::fclose(f);
+}
+
+void tune_file_store(const TuneKey& k, int e) {
+    const char* path = std::getenv("QG_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+                 std::get<3>(k), std::get<4>(k), e);
+    std::fclose(f);
+}
+
+qg_status build_graph(qg_ctx* h);
+void drop_graph(qg_ctx* h);
+template <typename T>
+qg_status init_partials(qg_ctx* h, cudaStream_t s);
+
+// Milliseconds of 5 captured steps with solve engine `engine` (after 3
+// untimed ones), run on the handle's own buffers.
+template <typename T>
+float time_steps(qg_ctx* h, int engine) {
+    const LevelTables* t = nullptr;
+    if (get_level(h, h->levels, &t) != QG_OK) return 1e30f;
+    if (solve_smem_bytes(t->mx, t->my, sizeof(T), engine) > 200 * 1024) return 1e30f;
+    h->solve_engine = engine;
+    drop_graph(h);
+    if (build_graph(h) != QG_OK) return 1e30f;
+    if (h->part && init_partials<T>(h, h->stream) != QG_OK) return 1e30f;
+    for (int k = 0; k < 3; ++k)
+        if (cudaGraphLaunch(h->gexec, h->stream) != cudaSuccess) return 1e30f;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return 1e30f;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return 1e30f;
+    }
+    float ms = 1e30f;
+    bool ok = cudaEventRecord(e0, h->stream) == cudaSuccess;
+    for (int k = 0; k < 5 && ok; ++k) ok = cudaGraphLaunch(h->gexec, h->stream) == cudaSuccess;
+    ok = ok && cudaEventRecord(e1, h->stream) == cudaSuccess;
+    if (ok && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+template <typename T>
+qg_status autotune_solve(qg_ctx* h) {
+    const LevelTables* t = nullptr;
+    qg_status st = get_level(h, h->levels, &t);
+    if (st != QG_OK) return st;
+    if (const char* force = std::getenv("QG_SOLVE_ENGINE")) {
+        const int e = std::atoi(force);
+        if (e == 4 || e == 16) {
+            h->solve_engine = e;
+            return QG_OK;
+        }
+    }
+    const TuneKey key(h->nx, h->ny, h->levels, h->layers, (int)h->esz);
     {
-        KTimer ktc(h, s, QG_K_DST_COLS);
-        DstPass<T> d = {};
-        d.N = t.my;
-        d.nrows = t.mx - 1;
-        d.nin = 1;
-        d.ld_in = ld_tr;
-        d.ld_out = t.ldc;
-        d.transpose_out = 1;
-        d.tw = static_cast<const C*>(t.twy);
-        d.lamx = static_cast<const T*>(t.lamx);
-        d.lamy = static_cast<const T*>(t.lamy);
-        d.scale = scale;
-        d.err = h->derr;
-        if (h->layers == 1) {
-            d.in[0][0] = static_cast<const T*>(tr);
-            d.out[0] = static_cast<T*>(work);
-            QG_TRY(launch_dst_pass<T>(d, 1, dst_config(t.my, sizeof(T), false), s, pdl));
-        } else {
-            d.pair_planes = 1;
-            d.in[0][0] = plane<T>(tr, pl_tr, 0);
-            d.in[1][0] = plane<T>(tr, pl_tr, 1);
-            d.out[0] = plane<T>(work, pl, 0);
-            d.out[1] = plane<T>(work, pl, 1);
-            d.Ro = (T)h->Ro;
-            d.f1 = (T)(h->Fr / h->delta);
-            d.f2 = (T)(h->Fr / (1.0 - h->delta));
-            QG_TRY(launch_dst_pass<T>(d, 2, dst_config(t.my, sizeof(T), true), s, pdl));
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        tune_file_load();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            h->solve_engine = it->second;
+            return QG_OK;
         }
     }
-    for (int L = 0; L < h->layers; ++L) {
-        KTimer kt(h, s, QG_K_DST_ROWS);
-        DstPass<T> d = {};
-        d.N = t.mx;
-        d.nrows = t.my - 1;
-        d.in[0][0] = plane<T>(work, pl, L);
-        d.nin = 1;
-        d.ld_in = t.ldc;
-        d.out[0] = plane<T>(out, pl, L);
-        d.ld_out = t.ldc;
-        d.tw = static_cast<const C*>(t.twx);
-        d.err = h->derr;
-        QG_TRY(launch_dst_pass<T>(d, 0, cx, s, pdl));
+    const float t4 = time_steps<T>(h, 4);
+    const float t16 = time_steps<T>(h, 16);
+    // a candidate that cannot run on this grid is a tuning result, not an error
+    h->latched = QG_OK;
+    (void)cudaGetLastError();
+    drop_graph(h);
+    if (t4 >= 1e29f && t16 >= 1e29f) return fail(h, QG_ERR_CUDA);
+    h->solve_engine = t16 < t4 ? 16 : 4;
+    // the timing steps ran on the handle's buffers: return them to rest
+    cudaStreamSynchronize(h->stream);
+    for (void* p : {h->w[0], h->w[1], h->w[2], h->psi}) {
+        if (p) QG_TRY(cudaMemsetAsync(p, 0, h->plane_f * h->layers * h->esz, h->stream));
     }
+    for (void* p : {h->cw, h->cpsi}) {
+        if (p) QG_TRY(cudaMemsetAsync(p, 0, h->plane_c * h->layers * h->esz, h->stream));
+    }
+    if (h->ct) QG_TRY(cudaMemsetAsync(h->ct, 0, h->plane_t * h->layers * h->esz, h->stream));
+    if (h->part) QG_TRY(cudaMemsetAsync(h->part, 0, 4 * h->plane_c * h->esz, h->stream));
+    h->part_valid = false;
+    QG_TRY(cudaStreamSynchronize(h->stream));
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = h->solve_engine;
+    tune_file_store(key, h->solve_engine);
     return QG_OK;
 }
 
@@ -436,10 +539,10 @@ qg_status stage_fused(qg_ctx* h, int s_idx, cudaStream_t s) {
     if (st != QG_OK) return fail(h, st);
     if (h->levels == 0) {
         st = solve_level<T>(h, *t, win, h->ct, h->ld_t, h->plane_t, h->cw, h->psi,
-                            h->plane_f, s, 1, true);
+                            h->plane_f, s, 1);
     } else {
         st = solve_level<T>(h, *t, h->part, h->ct, h->ld_t, h->plane_t, h->cw, h->cpsi,
-                            h->plane_c, s, 4, true);
+                            h->plane_c, s, 4);
     }
     if (st != QG_OK) return st;
     FusedParams<T> p;
@@ -598,7 +701,7 @@ qg_status qg_create(const qg_basin* b, int layers, double Re, double Ro, double 
         if (st != QG_OK && s == QG_OK) s = st;
     };
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) guard(QG_ERR_CUDA);
-    if (s == QG_OK && dst_prepare_kernels() != cudaSuccess) guard(QG_ERR_CUDA);
+
     const size_t fb = h->plane_f * layers * h->esz;
     const size_t cb = h->plane_c * layers * h->esz;
     for (int k = 0; k < 3 && s == QG_OK; ++k) guard(dev_alloc(h, &h->w[k], fb));
@@ -610,6 +713,7 @@ qg_status qg_create(const qg_basin* b, int layers, double Re, double Ro, double 
     if (s == QG_OK) guard(dev_alloc(h, &h->ct, h->plane_t * layers * h->esz));
     if (s == QG_OK && layers == 1 && levels >= 1) guard(dev_alloc(h, &h->part, 4 * h->plane_c * h->esz));
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->derr, sizeof(int) * 4));
+    if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dbar, sizeof(unsigned) * 4));
     if (s == QG_OK && layers == 1) {
         const int rows = (int)fine_tile_rows(h->esz);
         for (int k = 0; k < 3 && s == QG_OK; ++k) {
@@ -641,6 +745,8 @@ qg_status qg_create(const qg_basin* b, int layers, double Re, double Ro, double 
         guard(get_level(h, levels, &t));
     }
     if (s == QG_OK && cudaDeviceSynchronize() != cudaSuccess) guard(QG_ERR_CUDA);
+    if (s == QG_OK)
+        guard(h->dtype == QG_F64 ? autotune_solve<double>(h) : autotune_solve<float>(h));
     if (s != QG_OK) {
         qg_destroy(h);
         (void)cudaGetLastError();
@@ -676,6 +782,7 @@ static qg_status check_device_flag(qg_ctx* h) {
     QG_TRY(cudaStreamSynchronize(h->stream));
     if (flag) {
         QG_TRY(cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream));
+        QG_TRY(cudaMemsetAsync(h->dbar, 0, sizeof(unsigned) * 2, h->stream));
         return fail(h, QG_ERR_TIMEOUT);
     }
     return QG_OK;

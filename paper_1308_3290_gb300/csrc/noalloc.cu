@@ -63,7 +63,7 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Byte layout of the scratch for one request: padded grid, then the tables.
 struct Layout {
-    size_t grid, tr, twx, twy, lamx, lamy, total;
+    size_t grid, tr, twx, twy, lamx, lamy, bar, total;
 };
 
 Layout layout(int nx, int ny, size_t esz) {
@@ -76,7 +76,8 @@ Layout layout(int nx, int ny, size_t esz) {
     L.twy = L.twx + align256((size_t)4 * nx * esz);
     L.lamx = L.twy + align256((size_t)4 * ny * esz);
     L.lamy = L.lamx + align256((size_t)(nx + 1) * esz);
-    L.total = L.lamy + align256((size_t)(ny + 1) * esz);
+    L.bar = L.lamy + align256((size_t)(ny + 1) * esz);   // 2 barrier counters + error word
+    L.total = L.bar + 256;
     return L;
 }
 
@@ -97,44 +98,29 @@ qg_status solve(unsigned char* base, const Layout& Lo, int nx, int ny, double dx
     noalloc_tables<T><<<(n + 255) / 256, 256, 0, s>>>(twx, nx, twy, ny, lamx, lamy, dx, dy);
     if (cudaGetLastError() != cudaSuccess) return QG_ERR_CUDA;
     if (copy_in(grid, ld, rhs, nx - 1, ny - 1, esz, s) != cudaSuccess) return QG_ERR_CUDA;
-    const T scale = (T)((2.0 / nx) * (2.0 / ny));
-    const int ldt = round_up(ny + 1, 32);
-    T* tr = reinterpret_cast<T*>(base + Lo.tr);
-    DstPass<T> d = {};
-    d.N = nx;                     // x pass, transposed into tr
-    d.nrows = ny - 1;
-    d.in[0][0] = grid;
-    d.nin = 1;
-    d.ld_in = ld;
-    d.out[0] = tr;
-    d.ld_out = ldt;
-    d.transpose_out = 1;
-    d.tw = twx;
-    if (launch_dst_pass<T>(d, 0, dst_config(nx, esz, false), s, false) != cudaSuccess) return QG_ERR_CUDA;
-    d = DstPass<T>{};            // y pass with the eigenvalue division, back into grid
-    d.N = ny;
-    d.nrows = nx - 1;
-    d.in[0][0] = tr;
-    d.nin = 1;
-    d.ld_in = ldt;
-    d.out[0] = grid;
-    d.ld_out = ld;
-    d.transpose_out = 1;
-    d.tw = twy;
-    d.lamx = lamx;
-    d.lamy = lamy;
-    d.scale = scale;
-    if (launch_dst_pass<T>(d, 1, dst_config(ny, esz, false), s, false) != cudaSuccess) return QG_ERR_CUDA;
-    d = DstPass<T>{};            // inverse x pass, in place
-    d.N = nx;
-    d.nrows = ny - 1;
-    d.in[0][0] = grid;
-    d.nin = 1;
-    d.ld_in = ld;
-    d.out[0] = grid;
-    d.ld_out = ld;
-    d.tw = twx;
-    if (launch_dst_pass<T>(d, 0, dst_config(nx, esz, false), s, false) != cudaSuccess) return QG_ERR_CUDA;
+    unsigned* bar = reinterpret_cast<unsigned*>(base + Lo.bar);
+    if (cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return QG_ERR_CUDA;
+    SolveParams<T> P = {};
+    P.mx = nx;
+    P.my = ny;
+    P.layers = 1;
+    P.in[0][0] = grid;
+    P.nin = 1;
+    P.part_px = P.part_py = 1;
+    P.ld = ld;
+    P.tr[0] = reinterpret_cast<T*>(base + Lo.tr);
+    P.ld_tr = round_up(ny + 1, 32);
+    P.work[0] = grid;
+    P.out[0] = grid;
+    P.twx = twx;
+    P.twy = twy;
+    P.lamx = lamx;
+    P.lamy = lamy;
+    P.scale = (T)((2.0 / nx) * (2.0 / ny));
+    P.bar = bar;
+    P.err = reinterpret_cast<int*>(bar + 2);
+    const int engine = (long)nx * ny >= (1L << 21) ? 16 : 4;
+    if (launch_solve<T>(P, engine, s) != cudaSuccess) return QG_ERR_CUDA;
     if (copy_out(psi, grid, ld, nx - 1, ny - 1, esz, s) != cudaSuccess) return QG_ERR_CUDA;
     return QG_OK;
 }
@@ -155,7 +141,7 @@ extern "C" qg_status qg_poisson_solve_noalloc(int32_t nx, int32_t ny, double dx,
         return QG_ERR_SHAPE;
     const size_t esz = dtype == QG_F64 ? 8 : 4;
     if (layout(nx, ny, esz).total > kNoAllocBytes) return QG_ERR_SHAPE;
-    if (dst_lane_bytes(nx, esz) > dst_max_smem() || dst_lane_bytes(ny, esz) > dst_max_smem())
+    if (solve_smem_bytes(nx, ny, esz, (long)nx * ny >= (1L << 21) ? 16 : 4) > 200 * 1024)
         return QG_ERR_SHAPE;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -169,10 +155,6 @@ extern "C" qg_status qg_poisson_solve_noalloc(int32_t nx, int32_t ny, double dx,
         if (!g_scratch_addr[dev]) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-                (void)cudaGetLastError();
-                return QG_ERR_CUDA;
-            }
-            if (dst_prepare_kernels() != cudaSuccess) {
                 (void)cudaGetLastError();
                 return QG_ERR_CUDA;
             }

@@ -34,45 +34,36 @@ struct DstLaunch {
 
 // ---- kernels (declared here, defined in dst.cu / stencil.cu / diag.cu) ----
 
-// One launch of the sine-transform engine (dst.cu) over sequence pairs.
-// Sequences are rows 1..nrows of padded planes; row r holds f_0..f_{N-1}
-// (f_0 forced to 0).  A pair is rows (r, r+1) of plane 0, or with
-// pair_planes row r of planes 0 and 1.  The input of a sequence is the sum of
-// nin planes in[plane][0..nin-1] (all of pitch ld_in), added in index order.
-// op 0: unnormalised DST-I.  op 1: DST-I, multiplication of mode l of row r
-// by scale / (lamx[r] + lamy[l]), DST-I.  op 2 (pair_planes): DST-I, the
-// coupled two-layer solve of Eqs. isub-1/2 per mode with
-// alpha = Ro (lamx[r] + lamy[l]), DST-I.  Output element k of row r goes to
-// out[plane][r * ld_out + k], or to out[plane][k * ld_out + r] with
-// transpose_out.
+// The elliptic solve of one level (solve.cu): x pass of `in` (the sum of
+// nin planes per layer; with nin == 4 plane 1 is read only at columns
+// k % part_px == 0, plane 2 at rows r % part_py == 0, plane 3 at both), the
+// y pass with the eigenvalue division (one layer: lap_h psi = rhs) or the
+// coupled solve of Eqs. isub-1/2 (two layers), the inverse x pass into
+// `out`.  in / work / out have the level's padded layout (pitch ld), tr the
+// transposed layout (mx + 1 rows of pitch ld_tr).  bar: two zero-initialised
+// counters of the grid barrier.  One cooperative launch.
 template <typename T>
-struct DstPass {
-    int N;
-    int nrows;
+struct SolveParams {
+    int mx, my, layers;
     const T* in[2][4];
-    int nin;               // 1, or 4 for the restriction partial planes
-    int part_px, part_py;  // with nin == 4: plane 1 is read only at columns
-                           // k % part_px == 0, plane 2 at rows r % part_py == 0,
-                           // plane 3 at both (elsewhere they hold zeros)
-    int ld_in;
+    int nin, part_px, part_py;
+    int ld;
+    T* tr[2];
+    int ld_tr;
+    T* work[2];
     T* out[2];
-    int ld_out;
-    int transpose_out;
-    int pair_planes;
-    const typename Cx<T>::type* tw;   // e^{i pi t/N}, t < 2N
-    int tw_in_smem;                    // set by the launcher
-    const T* lamx;
-    const T* lamy;
+    const typename Cx<T>::type* twx;   // e^{i pi t/mx}, t < 2 mx
+    const typename Cx<T>::type* twy;   // e^{i pi t/my}, t < 2 my
+    const T* lamx;                      // (2 cos(pi k/mx) - 2)/dx^2, k = 0..mx
+    const T* lamy;                      // (2 cos(pi l/my) - 2)/dy^2, l = 0..my
     T scale, Ro, f1, f2;
-    int* err;                          // set to 1 when a bounded wait runs out
+    unsigned* bar;
+    int* err;
 };
-
+// engine: base radix of the FFT passes, 4 or 16 (see dst_engine.cuh)
 template <typename T>
-cudaError_t launch_dst_pass(DstPass<T> d, int op, DstLaunch cfg, cudaStream_t s, bool pdl);
-DstLaunch dst_config(int N, size_t esz, bool pair_planes);
-size_t dst_max_smem();                       // dynamic shared memory cap per CTA
-size_t dst_lane_bytes(int N, size_t esz);    // shared memory of one sequence pair
-cudaError_t dst_prepare_kernels();
+cudaError_t launch_solve(const SolveParams<T>& P, int engine, cudaStream_t s);
+size_t solve_smem_bytes(int mx, int my, size_t esz, int engine);
 
 // Full-weighting restriction applied `levels` times, as one hat-weighted
 // sum (fine -> level `levels`), interior coarse nodes only.

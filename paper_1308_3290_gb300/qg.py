@@ -37,7 +37,7 @@ EXPORTS = [
     "qg_last_error", "qg_poisson_solve_noalloc",
 ]
 
-KERNEL_CLASSES = ["restrict", "dst_rows", "dst_cols", "prolong", "fine"]
+KERNEL_CLASSES = ["restrict", "solve", "prolong", "fine"]
 
 
 class QGError(RuntimeError):

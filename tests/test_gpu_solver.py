@@ -80,3 +80,19 @@ def test_two_layer_solve_parity():
         assert rel_l2(got[0], r1) <= TOL[dtype] * 5
         assert rel_l2(got[1], r2) <= TOL[dtype] * 5
         b.close()
+
+
+@pytest.mark.parametrize("engine", ["4", "16"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_both_fft_engines(engine, dtype, monkeypatch):
+    """The solve has two FFT schedules (base radix 4 and 16) chosen by the
+    autotuner; each must meet the same tolerance."""
+    require_gpu()
+    monkeypatch.setenv("QG_SOLVE_ENGINE", engine)
+    for nx, ny in ((64, 128), (512, 1024), (2048, 256)):
+        b = qg.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=0, dt=1e-4, dtype=dtype)
+        rhs = inputs.smooth_field(nx, ny, seed=nx, noise=0.3)
+        got = to_np(b.poisson_solve(rhs))
+        ref = O.poisson_solve(rhs, nx, ny, 1.0 / nx, 2.0 / ny)
+        assert rel_l2(got, ref) <= TOL[dtype], (nx, ny, rel_l2(got, ref))
+        b.close()
