@@ -407,6 +407,19 @@ def ours(args):
                 variants[name]["rooflines"] = {
                     c: kernel_roofline(c, kt, 0, 50) for c in kt if kt[c][1] > 0}
             b.close()
+        # two-layer basin of Table 2 Experiment 1 (Section 2.2): square
+        # basin, 1024x2048 intervals per layer, l = 1, FP32
+        tl = dict(Ro=2.49e-4, Fr=0.087, delta=0.2, sigma=1.43e-3)
+        b = qg.Basin(1024, 2048, Re=tl["Ro"] / 3.57e-7, levels=1, dt=1e-5, dtype="f32",
+                     layers=2, y0=-0.5, y1=0.5, stream=stream, **tl)
+        b.set_state(inputs.smooth_field(1024, 2048, seed=3, amp=0.05, noise=0.01), 0)
+        b.set_state(inputs.smooth_field(1024, 2048, seed=4, amp=0.02, noise=0.01), 1)
+        for _ in range(5):
+            qg.qg_step(b.h, 1)
+        ts = time_steps(torch, qg, b.h, stream, 100, flush)
+        variants["two_layer_1024x2048_l1_f32"] = {"steps_per_s": 100 / (sum(ts) / 1e3),
+                                                  "ms_per_step": sum(ts) / 100}
+        b.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -12,9 +12,10 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 1e-4)])
 @pytest.mark.parametrize("levels", [0, 1])
-def test_two_layer_steps(dtype, tol, levels):
+@pytest.mark.parametrize("nx,ny", [(64, 64), (64, 128)])
+def test_two_layer_steps(dtype, tol, levels, nx, ny):
+    """The square basin on N x N and on N x 2N intervals (dy = dx/2)."""
     require_gpu()
-    nx, ny = 64, 64
     p = dict(Ro=2.49e-4, Fr=0.087, delta=0.2, sigma=1.43e-3)
     A = 3.57e-7
     Re = p["Ro"] / A
