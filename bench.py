@@ -198,6 +198,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def slowest_rank_ms(total_ms, world, device):
+    """The job's time: the largest timed total over all ranks."""
+    if world == 1:
+        return float(total_ms)
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, job_ms):
+    """Whole-job steps/s: every rank advances its own basin by `steps`."""
+    return world * steps / (job_ms / 1e3)
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -342,12 +357,8 @@ def ours(args):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop() if sampler else None
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = slowest_rank_ms(sum(times), world, "cuda")
+    value = job_throughput(world, args.steps, total_ms)
     ms_per_step = total_ms / args.steps
 
     # per-kernel timing (graph with event nodes), for the roofline

@@ -201,6 +201,22 @@ qg_status qg_poisson_solve_noalloc(int32_t nx, int32_t ny, double dx, double dy,
                                    qg_dtype dtype, const void* rhs, void* psi,
                                    void* cuda_stream);
 
+/* qg_inject_fault -- failure-detection test switch (the paper has no
+ * counterpart).  kind = QG_FAULT_BARRIER_STALL makes every later elliptic
+ * solve of the handle wait at its first grid barrier for one arrival more
+ * than the grid has, so the wait runs out of its bound (about a second),
+ * the kernel sets the handle's error flag and returns; the next
+ * qg_synchronize or qg_diagnostics returns QG_ERR_TIMEOUT and clears the
+ * flag.  Results computed meanwhile are garbage.  QG_FAULT_NONE restores
+ * normal operation.  No memory outside the handle's buffers is touched and
+ * the CUDA context stays usable.  Re-captures the step graph.
+ * Errors: QG_ERR_ARG for a NULL handle or an unknown kind.                 */
+typedef enum qg_fault {
+    QG_FAULT_NONE = 0,
+    QG_FAULT_BARRIER_STALL = 1
+} qg_fault;
+qg_status qg_inject_fault(qg_handle h, int kind);
+
 /* qg_synchronize -- wait for the handle's work; returns any latched error. */
 qg_status qg_synchronize(qg_handle h);
 

@@ -73,6 +73,7 @@ struct qg_ctx {
     std::vector<void*> allocs;
     // per-kernel timing (bench instrumentation): events recorded in the graph
     bool timing = false;
+    int fault = QG_FAULT_NONE;     // failure-detection test switch
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     size_t ev_next = 0;
@@ -305,6 +306,7 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
         P.f2 = (T)(h->Fr / (1.0 - h->delta));
     }
     P.bar = h->dbar;
+    P.bar_extra = h->fault == QG_FAULT_BARRIER_STALL ? 1u : 0u;
     P.err = h->derr;
     KTimer kt(h, s, QG_K_SOLVE);
     QG_TRY(launch_solve<T>(P, engine ? engine : engine_for(h, t.mx, t.my), s));
@@ -946,6 +948,16 @@ qg_status qg_set_timing(qg_handle h, int enable) {
         QG_TRY(cudaStreamSynchronize(h->stream));
         drop_graph(h);
         h->timing = enable != 0;
+    }
+    return QG_OK;
+}
+
+qg_status qg_inject_fault(qg_handle h, int kind) {
+    if (!h || kind < QG_FAULT_NONE || kind > QG_FAULT_BARRIER_STALL) return QG_ERR_ARG;
+    if (kind != h->fault) {
+        QG_TRY(cudaStreamSynchronize(h->stream));
+        drop_graph(h);
+        h->fault = kind;
     }
     return QG_OK;
 }

@@ -58,6 +58,8 @@ struct SolveParams {
     const T* lamy;                      // (2 cos(pi l/my) - 2)/dy^2, l = 0..my
     T scale, Ro, f1, f2;
     unsigned* bar;
+    unsigned bar_extra;  // arrivals the grid barrier waits for beyond the grid
+                         // (0; 1 only under fault injection: never released)
     int* err;
 };
 // engine: base radix of the FFT passes, 4 or 16 (see dst_engine.cuh)

@@ -70,15 +70,16 @@ __host__ __device__ inline Layout layout(int mx, int my, size_t esz, int E) {
 }
 
 // Grid-wide barrier with a bounded wait.  bar[0] counts arrivals, bar[1] is
-// the generation.  Returns false (on every thread) when the wait ran out.
-__device__ bool grid_sync(unsigned* bar, int limit) {
+// the generation; the last of gridDim.x + extra arrivals releases it.
+// Returns false (on every thread) when the wait ran out.
+__device__ bool grid_sync(unsigned* bar, unsigned extra, int limit) {
     __syncthreads();
     int ok = 1;
     if (threadIdx.x == 0) {
         volatile unsigned* gen = bar + 1;
         const unsigned g0 = *gen;
         __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+        if (atomicAdd(bar, 1u) == gridDim.x - 1 + extra) {
             bar[0] = 0;
             __threadfence();
             atomicAdd(bar + 1, 1u);
@@ -262,6 +263,7 @@ solve_kernel(SolveParams<T> P) {
     const bool ok = mbar_wait(bar, 0, kSpinLimit);
     if (!__syncthreads_and(ok)) {
         if (threadIdx.x == 0) atomicExch(P.err, 1);
+        (void)mbar_wait(bar, 0, kSpinLimit);     // let copies in flight land
         return;
     }
     const C* twx = Lo.twx_smem ? stwx : P.twx;
@@ -284,7 +286,7 @@ solve_kernel(SolveParams<T> P) {
         io.transpose = true;
         run_phase<T, NBM, E>(io, 0, bufs, twx, P.lamx, slamy, P.scale, P.Ro, P.f1, P.f2);
     }
-    if (!grid_sync(P.bar, kSpinLimit)) {
+    if (!grid_sync(P.bar, P.bar_extra, kSpinLimit)) {
         if (threadIdx.x == 0) atomicExch(P.err, 1);
         return;
     }
@@ -305,7 +307,7 @@ solve_kernel(SolveParams<T> P) {
         io.transpose = true;
         run_phase<T, NBM, E>(io, OPY, bufs, twy, P.lamx, slamy, P.scale, P.Ro, P.f1, P.f2);
     }
-    if (!grid_sync(P.bar, kSpinLimit)) {
+    if (!grid_sync(P.bar, P.bar_extra, kSpinLimit)) {
         if (threadIdx.x == 0) atomicExch(P.err, 1);
         return;
     }

@@ -21,6 +21,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libqgcgp.so")
 
 QG_F32, QG_F64 = 0, 1
+QG_FAULT_NONE, QG_FAULT_BARRIER_STALL = 0, 1
+QG_ERR_TIMEOUT = 7
 
 STATUS = {
     0: "QG_OK", 1: "QG_ERR_ARG", 2: "QG_ERR_SHAPE", 3: "QG_ERR_CUDA",
@@ -34,7 +36,7 @@ EXPORTS = [
     "qg_set_forcing", "qg_poisson_solve", "qg_restrict", "qg_prolong",
     "qg_step", "qg_diagnostics", "qg_set_timing", "qg_read_timing",
     "qg_step_kernel_count", "qg_synchronize", "qg_status_string",
-    "qg_last_error", "qg_poisson_solve_noalloc",
+    "qg_last_error", "qg_poisson_solve_noalloc", "qg_inject_fault",
 ]
 
 KERNEL_CLASSES = ["restrict", "solve", "prolong", "fine"]
@@ -87,6 +89,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "qg_synchronize": [vp],
         "qg_poisson_solve_noalloc": [i32, i32, dbl, dbl, i32, vp, vp, vp],
         "qg_last_error": [vp],
+        "qg_inject_fault": [vp, i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -197,6 +200,14 @@ def qg_poisson_solve_noalloc(nx: int, ny: int, dx: float, dy: float, dtype: int,
     buffers of shape (ny-1, nx-1)."""
     _check(load().qg_poisson_solve_noalloc(nx, ny, dx, dy, dtype, _ptr(rhs), _ptr(psi),
                                            stream or None), "qg_poisson_solve_noalloc")
+
+
+def qg_inject_fault(h: int, kind: int) -> None:
+    """Failure-detection test switch: QG_FAULT_BARRIER_STALL makes the
+    handle's solves run out of their bounded grid-barrier wait (the next
+    synchronisation raises QGError with QG_ERR_TIMEOUT); QG_FAULT_NONE
+    restores normal operation."""
+    _check(load().qg_inject_fault(h, kind), "qg_inject_fault")
 
 
 def qg_synchronize(h: int) -> None:

@@ -70,6 +70,7 @@ def test_calls_on_null_handle(lib):
     assert lib.qg_step(None, 1) == 1
     assert lib.qg_set_state(None, None, 0) == 1
     assert lib.qg_synchronize(None) == 1
+    assert lib.qg_inject_fault(None, 1) == 1
 
 
 def test_no_device_is_reported():
