@@ -313,6 +313,47 @@ def kernel_timing(torch, qg, h, stream, K, flush):
     return acc
 
 
+def ensemble_members(count=96, seed=4):
+    """Independent one-layer basins of four sizes, Re ~ U[200, 1000], forcing
+    amplitude ~ U[0.5, 1.5], Ro = 0.0016, CGP level 1 or 2, seeded."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes = [(128, 256), (256, 512), (512, 1024), (1024, 2048)]
+    out = []
+    for _ in range(count):
+        nx, ny = sizes[rng.integers(0, 4)]
+        out.append(dict(nx=int(nx), ny=int(ny), Re=float(rng.uniform(200, 1000)), Ro=RO,
+                        levels=int(rng.integers(1, 3)), dt=1e-5,
+                        amp=float(rng.uniform(0.5, 1.5))))
+    return out
+
+
+def ensemble_variant(torch, qg, inputs, stream, flush, K=50):
+    members = ensemble_members()
+    ens = qg.Ensemble(members, dtype="f32", stream=stream)
+    for i, m in enumerate(members):
+        ens.member(i).set_state(inputs.perturbation(m["nx"], m["ny"], seed=1000 + i) * 50.0)
+    ens.step(3)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    for k in range(K):
+        evs[k][0].record(stream)
+        ens.step(1)
+        evs[k][1].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    ens.synchronize()
+    points = sum((m["nx"] - 1) * (m["ny"] - 1) for m in members)
+    out = {"basins": len(members), "steps_per_s": K / (ms / 1e3), "ms_per_step": ms / K,
+           "basin_steps_per_s": len(members) * K / (ms / 1e3),
+           "fine_point_steps_per_s": points * K / (ms / 1e3),
+           "kernels_per_step": ens.kernel_count()}
+    ens.close()
+    return out
+
+
 def ours(args):
     import numpy as np
     import torch
@@ -431,6 +472,7 @@ def ours(args):
         variants["two_layer_1024x2048_l1_f32"] = {"steps_per_s": 100 / (sum(ts) / 1e3),
                                                   "ms_per_step": sum(ts) / 100}
         b.close()
+        variants["ensemble_96_f32"] = ensemble_variant(torch, qg, inputs, stream, flush)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

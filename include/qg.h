@@ -217,6 +217,47 @@ typedef enum qg_fault {
 } qg_fault;
 qg_status qg_inject_fault(qg_handle h, int kind);
 
+/* ---- ensembles of basins --------------------------------------------------
+ * Many independent one-layer basins (Section 2.1), each with its own grid,
+ * Re, Ro, forcing amplitude, dt and CGP level (Section 3), stepped together:
+ * one CUDA graph per ensemble step holds every member's CGPRK3 step on up to
+ * 8 concurrent branches, members placed largest first on the least-loaded
+ * branch.  Each member runs the kernels a handle of its own would, except
+ * that its solves run as three plain launches instead of one cooperative
+ * launch, so that members can share the GPU; with the same FFT schedule the
+ * results are bitwise those of a stand-alone handle.  The paper runs one basin at a time; the
+ * ensemble is this library's way of filling a GPU with small basins.     */
+typedef struct qg_ensemble_s* qg_ensemble;
+
+/* qg_ensemble_create -- `count` (1..4096) members; basins[i], Re[i], Ro[i],
+ * levels[i] as for qg_create with layers = 1 and Fr = 0.  All members share
+ * `dtype` and `cuda_stream`.  Member states start at zero.
+ * Errors: as qg_create for the first failing member (nothing is kept),
+ * QG_ERR_ARG for NULL arrays or a bad count.                               */
+qg_status qg_ensemble_create(const qg_basin* basins, const double* Re, const double* Ro,
+                             const int* levels, int count, qg_dtype dtype,
+                             void* cuda_stream, qg_ensemble* out);
+
+/* qg_ensemble_member -- the handle of member `index`, for qg_set_state,
+ * qg_get_state, qg_get_psi, qg_set_forcing, qg_diagnostics and
+ * qg_synchronize.  The ensemble owns it: do not qg_destroy it.  qg_step on a
+ * member steps that member alone.                                          */
+qg_status qg_ensemble_member(qg_ensemble e, int index, qg_handle* out);
+
+/* qg_ensemble_step -- n steps of every member, asynchronous on the
+ * ensemble's stream (one graph launch per step).                           */
+qg_status qg_ensemble_step(qg_ensemble e, int64_t n);
+
+/* qg_ensemble_kernel_count -- kernels one ensemble step launches.          */
+qg_status qg_ensemble_kernel_count(qg_ensemble e, int64_t* count);
+
+/* qg_ensemble_synchronize -- wait for the ensemble's work; returns the
+ * first error of any member (bounded-wait timeouts included).              */
+qg_status qg_ensemble_synchronize(qg_ensemble e);
+
+/* qg_ensemble_destroy -- frees the members and the graph; safe on NULL.    */
+qg_status qg_ensemble_destroy(qg_ensemble e);
+
 /* qg_synchronize -- wait for the handle's work; returns any latched error. */
 qg_status qg_synchronize(qg_handle h);
 

@@ -11,6 +11,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -74,6 +75,9 @@ struct qg_ctx {
     // per-kernel timing (bench instrumentation): events recorded in the graph
     bool timing = false;
     int fault = QG_FAULT_NONE;     // failure-detection test switch
+    uint64_t graph_gen = 0;        // bumped whenever the captured step is invalidated
+    bool split_solve = false;      // solve as three plain launches (ensemble
+                                   // members: no cooperative grids side by side)
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     size_t ev_next = 0;
@@ -238,7 +242,7 @@ struct KTimer {
     cudaEvent_t e1 = nullptr, e2 = nullptr;
     KTimer(qg_ctx* h_, cudaStream_t s_, int c) : h(h_), s(s_), cls(c) {
         if (!h->capturing) return;
-        ++h->kernels_per_step;
+        h->kernels_per_step += (c == QG_K_SOLVE && h->split_solve) ? 3 : 1;
         if (!h->timing) return;
         if (h->ev_next + 2 > h->ev_pool.size()) {
             for (int k = 0; k < 2; ++k) {
@@ -308,6 +312,7 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
     P.bar = h->dbar;
     P.bar_extra = h->fault == QG_FAULT_BARRIER_STALL ? 1u : 0u;
     P.err = h->derr;
+    P.split = h->split_solve ? 1 : 0;
     KTimer kt(h, s, QG_K_SOLVE);
     QG_TRY(launch_solve<T>(P, engine ? engine : engine_for(h, t.mx, t.my), s));
     return QG_OK;
@@ -611,6 +616,7 @@ qg_status project_any(qg_ctx* h, const void* win, cudaStream_t s) {
 }
 
 void drop_graph(qg_ctx* h) {
+    ++h->graph_gen;
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     h->gexec = nullptr;
@@ -660,8 +666,18 @@ const char* qg_status_string(qg_status s) {
     return "unknown status";
 }
 
+static qg_status create_ctx(const qg_basin* b, int layers, double Re, double Ro, double Fr,
+                            int levels, qg_dtype dtype, void* cuda_stream, bool split,
+                            qg_handle* out);
+
 qg_status qg_create(const qg_basin* b, int layers, double Re, double Ro, double Fr,
                     int levels, qg_dtype dtype, void* cuda_stream, qg_handle* out) {
+    return create_ctx(b, layers, Re, Ro, Fr, levels, dtype, cuda_stream, false, out);
+}
+
+static qg_status create_ctx(const qg_basin* b, int layers, double Re, double Ro, double Fr,
+                            int levels, qg_dtype dtype, void* cuda_stream, bool split,
+                            qg_handle* out) {
     if (!b || !out) return QG_ERR_ARG;
     *out = nullptr;
     if (layers != 1 && layers != 2) return QG_ERR_ARG;
@@ -694,6 +710,7 @@ qg_status qg_create(const qg_basin* b, int layers, double Re, double Ro, double 
     h->Re = Re; h->Ro = Ro; h->Fr = Fr;
     h->delta = b->delta; h->sigma = b->sigma; h->dt = b->dt; h->amp = b->forcing_amp;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->split_solve = split;
     h->ldf = padded_ld(h->nx);
     h->plane_f = (size_t)(h->ny + 1) * h->ldf;
     const int mx = h->nx >> levels, my = h->ny >> levels;
@@ -1015,6 +1032,209 @@ qg_status qg_diagnostics(qg_handle h, double* ke, double* enstrophy, double* max
     if (ke) *ke = E;
     if (enstrophy) *enstrophy = Z;
     if (max_vel) *max_vel = U;
+    return QG_OK;
+}
+
+}  // extern "C"
+
+// ---- ensembles -------------------------------------------------------------
+
+struct qg_ensemble_s {
+    std::vector<qg_ctx*> m;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;             // capture origin
+    std::vector<cudaStream_t> lanes;        // concurrent branches of the step graph
+    std::vector<cudaEvent_t> ev;            // fork event, then one join event per lane
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<uint64_t> gen;              // members' graph_gen when it was captured
+    int64_t kernels = 0;
+};
+
+namespace {
+
+constexpr int kEnsembleLanes = 8;
+
+void ensemble_free(qg_ensemble e) {
+    if (!e) return;
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    if (e->gexec) cudaGraphExecDestroy(e->gexec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    for (qg_ctx* h : e->m) qg_destroy(h);
+    for (cudaEvent_t v : e->ev) cudaEventDestroy(v);
+    for (cudaStream_t s : e->lanes) cudaStreamDestroy(s);
+    if (e->cap) cudaStreamDestroy(e->cap);
+    delete e;
+}
+
+// Members sorted by fine nodes, largest first, each on the lane with the
+// least work so far: the branches of the graph end at about the same time.
+std::vector<int> ensemble_placement(const qg_ensemble e) {
+    const int n = (int)e->m.size(), L = (int)e->lanes.size();
+    std::vector<int> order(n), lane(n, 0);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    auto work = [&](int i) { return (double)e->m[i]->nx * e->m[i]->ny; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+    std::vector<double> load(L, 0.0);
+    for (int i : order) {
+        int best = 0;
+        for (int k = 1; k < L; ++k)
+            if (load[k] < load[best]) best = k;
+        lane[i] = best;
+        load[best] += work(i);
+    }
+    return lane;
+}
+
+qg_status ensemble_build(qg_ensemble e) {
+    // a member whose own step graph was invalidated (new forcing field,
+    // timing, fault switch) invalidates the ensemble's too
+    bool stale = e->gen.size() != e->m.size();
+    for (size_t i = 0; i < e->m.size() && !stale; ++i) stale = e->gen[i] != e->m[i]->graph_gen;
+    if (e->gexec && !stale) return QG_OK;
+    if (e->gexec) {
+        cudaStreamSynchronize(e->stream);
+        cudaGraphExecDestroy(e->gexec);
+        e->gexec = nullptr;
+    }
+    if (e->graph) {
+        cudaGraphDestroy(e->graph);
+        e->graph = nullptr;
+    }
+    const std::vector<int> lane = ensemble_placement(e);
+    if (cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return QG_ERR_CUDA;
+    qg_status st = QG_OK;
+    bool ok = cudaEventRecord(e->ev[0], e->cap) == cudaSuccess;
+    for (size_t k = 0; k < e->lanes.size() && ok; ++k)
+        ok = cudaStreamWaitEvent(e->lanes[k], e->ev[0], 0) == cudaSuccess;
+    e->kernels = 0;
+    for (size_t i = 0; i < e->m.size() && ok && st == QG_OK; ++i) {
+        qg_ctx* h = e->m[i];
+        h->kernels_per_step = 0;
+        h->capturing = true;
+        st = enqueue_step_any(h, e->lanes[lane[i]]);
+        h->capturing = false;
+        e->kernels += h->kernels_per_step;
+    }
+    for (size_t k = 0; k < e->lanes.size() && ok; ++k) {
+        ok = cudaEventRecord(e->ev[1 + k], e->lanes[k]) == cudaSuccess &&
+             cudaStreamWaitEvent(e->cap, e->ev[1 + k], 0) == cudaSuccess;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(e->cap, &g);
+    if (st != QG_OK || !ok || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        return st != QG_OK ? st : QG_ERR_CUDA;
+    }
+    e->graph = g;
+    if (cudaGraphInstantiate(&e->gexec, g, 0) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return QG_ERR_CUDA;
+    }
+    e->gen.clear();
+    for (qg_ctx* h : e->m) e->gen.push_back(h->graph_gen);
+    return QG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qg_status qg_ensemble_create(const qg_basin* basins, const double* Re, const double* Ro,
+                             const int* levels, int count, qg_dtype dtype,
+                             void* cuda_stream, qg_ensemble* out) {
+    if (!basins || !Re || !Ro || !levels || !out || count < 1 || count > 4096) return QG_ERR_ARG;
+    *out = nullptr;
+    qg_ensemble e = new (std::nothrow) qg_ensemble_s();
+    if (!e) return QG_ERR_OOM;
+    e->stream = static_cast<cudaStream_t>(cuda_stream);
+    for (int i = 0; i < count; ++i) {
+        qg_handle h = nullptr;
+        const qg_status s = create_ctx(&basins[i], 1, Re[i], Ro[i], 0.0, levels[i], dtype,
+                                       cuda_stream, true, &h);
+        if (s != QG_OK) {
+            ensemble_free(e);
+            return s;
+        }
+        e->m.push_back(h);
+    }
+    const int L = count < kEnsembleLanes ? count : kEnsembleLanes;
+    bool ok = cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < L && ok; ++k) {
+        cudaStream_t s = nullptr;
+        ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) e->lanes.push_back(s);
+    }
+    for (int k = 0; k <= L && ok; ++k) {
+        cudaEvent_t v = nullptr;
+        ok = cudaEventCreateWithFlags(&v, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) e->ev.push_back(v);
+    }
+    if (!ok) {
+        ensemble_free(e);
+        (void)cudaGetLastError();
+        return QG_ERR_CUDA;
+    }
+    *out = e;
+    return QG_OK;
+}
+
+qg_status qg_ensemble_member(qg_ensemble e, int index, qg_handle* out) {
+    if (!e || !out || index < 0 || index >= (int)e->m.size()) return QG_ERR_ARG;
+    *out = e->m[index];
+    return QG_OK;
+}
+
+qg_status qg_ensemble_step(qg_ensemble e, int64_t n) {
+    if (!e || n < 0) return QG_ERR_ARG;
+    for (qg_ctx* h : e->m)
+        if (h->latched != QG_OK) return qg_last_error(h);
+    if (n == 0) return QG_OK;
+    // the members' partial sums of R^l w^n are made on the ensemble stream
+    for (qg_ctx* h : e->m) {
+        if (h->part && !h->part_valid) {
+            const qg_status s = h->dtype == QG_F64 ? init_partials<double>(h, h->stream)
+                                                   : init_partials<float>(h, h->stream);
+            if (s != QG_OK) return s;
+            h->part_valid = true;
+        }
+    }
+    qg_status s = ensemble_build(e);
+    if (s != QG_OK) return s;
+    for (int64_t k = 0; k < n; ++k)
+        if (cudaGraphLaunch(e->gexec, e->stream) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return QG_ERR_CUDA;
+        }
+    return QG_OK;
+}
+
+qg_status qg_ensemble_kernel_count(qg_ensemble e, int64_t* count) {
+    if (!e || !count) return QG_ERR_ARG;
+    const qg_status s = ensemble_build(e);
+    if (s != QG_OK) return s;
+    *count = e->kernels;
+    return QG_OK;
+}
+
+qg_status qg_ensemble_synchronize(qg_ensemble e) {
+    if (!e) return QG_ERR_ARG;
+    if (cudaStreamSynchronize(e->stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return QG_ERR_CUDA;
+    }
+    qg_status first = QG_OK;
+    for (qg_ctx* h : e->m) {
+        const qg_status s = qg_synchronize(h);
+        if (first == QG_OK) first = s;
+    }
+    return first;
+}
+
+qg_status qg_ensemble_destroy(qg_ensemble e) {
+    ensemble_free(e);
     return QG_OK;
 }
 

@@ -41,7 +41,8 @@ struct DstLaunch {
 // coupled solve of Eqs. isub-1/2 (two layers), the inverse x pass into
 // `out`.  in / work / out have the level's padded layout (pitch ld), tr the
 // transposed layout (mx + 1 rows of pitch ld_tr).  bar: two zero-initialised
-// counters of the grid barrier.  One cooperative launch.
+// counters of the grid barrier.  One cooperative launch, or (split) one
+// plain launch per pass.
 template <typename T>
 struct SolveParams {
     int mx, my, layers;
@@ -61,6 +62,9 @@ struct SolveParams {
     unsigned bar_extra;  // arrivals the grid barrier waits for beyond the grid
                          // (0; 1 only under fault injection: never released)
     int* err;
+    int split;           // 0: the three passes in one cooperative launch with
+                         // grid barriers; 1: three plain launches, one per pass
+    int phase;           // the pass a split launch runs (set by launch_solve)
 };
 // engine: base radix of the FFT passes, 4 or 16 (see dst_engine.cuh)
 template <typename T>

@@ -268,9 +268,10 @@ solve_kernel(SolveParams<T> P) {
     }
     const C* twx = Lo.twx_smem ? stwx : P.twx;
     const C* twy = Lo.twy_smem ? stwy : P.twy;
+    const bool all = P.split == 0;
 
     // 1. x pass of the right-hand side, transposed into tr
-    {
+    if (all || P.phase == 0) {
         PairIO<T> io;
         io.N = P.mx;
         io.nrows = P.my - 1;
@@ -286,12 +287,12 @@ solve_kernel(SolveParams<T> P) {
         io.transpose = true;
         run_phase<T, NBM, E>(io, 0, bufs, twx, P.lamx, slamy, P.scale, P.Ro, P.f1, P.f2);
     }
-    if (!grid_sync(P.bar, P.bar_extra, kSpinLimit)) {
+    if (all && !grid_sync(P.bar, P.bar_extra, kSpinLimit)) {
         if (threadIdx.x == 0) atomicExch(P.err, 1);
         return;
     }
     // 2. y pass with the mode-space solve, transposed back into work
-    {
+    if (all || P.phase == 1) {
         const T* trin[8] = {P.tr[0], nullptr, nullptr, nullptr, P.tr[1], nullptr, nullptr, nullptr};
         PairIO<T> io;
         io.N = P.my;
@@ -307,12 +308,12 @@ solve_kernel(SolveParams<T> P) {
         io.transpose = true;
         run_phase<T, NBM, E>(io, OPY, bufs, twy, P.lamx, slamy, P.scale, P.Ro, P.f1, P.f2);
     }
-    if (!grid_sync(P.bar, P.bar_extra, kSpinLimit)) {
+    if (all && !grid_sync(P.bar, P.bar_extra, kSpinLimit)) {
         if (threadIdx.x == 0) atomicExch(P.err, 1);
         return;
     }
     // 3. inverse x pass into out
-    {
+    if (all || P.phase == 2) {
         const T* win[8] = {P.work[0], nullptr, nullptr, nullptr, P.work[1], nullptr, nullptr, nullptr};
         PairIO<T> io;
         io.N = P.mx;
@@ -358,11 +359,20 @@ cudaError_t launch_one(const SolveParams<T>& P, size_t sm, cudaStream_t s) {
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, P);
+    if (!P.split) {
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k, P);
+    }
+    // one plain launch per pass; stream order separates the passes
+    SolveParams<T> Q = P;
+    for (int ph = 0; ph < 3; ++ph) {
+        Q.phase = ph;
+        if ((e = cudaLaunchKernelEx(&cfg, k, Q)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace

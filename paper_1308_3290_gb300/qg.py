@@ -37,6 +37,8 @@ EXPORTS = [
     "qg_step", "qg_diagnostics", "qg_set_timing", "qg_read_timing",
     "qg_step_kernel_count", "qg_synchronize", "qg_status_string",
     "qg_last_error", "qg_poisson_solve_noalloc", "qg_inject_fault",
+    "qg_ensemble_create", "qg_ensemble_member", "qg_ensemble_step",
+    "qg_ensemble_kernel_count", "qg_ensemble_synchronize", "qg_ensemble_destroy",
 ]
 
 KERNEL_CLASSES = ["restrict", "solve", "prolong", "fine"]
@@ -90,6 +92,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "qg_poisson_solve_noalloc": [i32, i32, dbl, dbl, i32, vp, vp, vp],
         "qg_last_error": [vp],
         "qg_inject_fault": [vp, i32],
+        "qg_ensemble_create": [ctypes.POINTER(qg_basin), ctypes.POINTER(dbl),
+                               ctypes.POINTER(dbl), ctypes.POINTER(i32), i32, i32, vp,
+                               ctypes.POINTER(vp)],
+        "qg_ensemble_member": [vp, i32, ctypes.POINTER(vp)],
+        "qg_ensemble_step": [vp, i64],
+        "qg_ensemble_kernel_count": [vp, ctypes.POINTER(i64)],
+        "qg_ensemble_synchronize": [vp],
+        "qg_ensemble_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -312,8 +322,83 @@ class Basin:
 
     def close(self):
         if getattr(self, "h", None):
-            qg_destroy(self.h)
+            if getattr(self, "_owned", True):   # ensemble members are not
+                qg_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ensemble:
+    """Independent one-layer basins stepped together (one graph launch per
+    step).  ``members`` is a list of dicts with the keys of ``Basin``'s
+    constructor (nx, ny, Re, Ro, levels, dt and optionally amp, x0, x1, y0,
+    y1).  ``member(i)`` returns a ``Basin`` view of member i for state I/O
+    and diagnostics (owned by the ensemble)."""
+
+    def __init__(self, members, *, dtype: str = "f32", stream=None):
+        import torch
+        self.torch = torch
+        n = len(members)
+        bs = (qg_basin * n)()
+        Re = (ctypes.c_double * n)()
+        Ro = (ctypes.c_double * n)()
+        lv = (ctypes.c_int * n)()
+        for i, m in enumerate(members):
+            bs[i] = qg_basin(m["nx"], m["ny"], m.get("x0", 0.0), m.get("x1", 1.0),
+                             m.get("y0", -1.0), m.get("y1", 1.0), m.get("amp", 1.0),
+                             0.5, 0.0, m["dt"], 0)
+            Re[i], Ro[i], lv[i] = m["Re"], m["Ro"], m["levels"]
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        e = ctypes.c_void_p()
+        _check(load().qg_ensemble_create(bs, Re, Ro, lv, n,
+                                         QG_F32 if dtype == "f32" else QG_F64,
+                                         s.cuda_stream, ctypes.byref(e)), "qg_ensemble_create")
+        self.e = e.value
+        self.views = []
+        for i, m in enumerate(members):
+            h = ctypes.c_void_p()
+            _check(load().qg_ensemble_member(self.e, i, ctypes.byref(h)), "qg_ensemble_member")
+            v = Basin.__new__(Basin)
+            v.torch = torch
+            v.nx, v.ny, v.levels, v.layers = m["nx"], m["ny"], m["levels"], 1
+            v.tdtype = torch.float32 if dtype == "f32" else torch.float64
+            v.stream = s
+            v._keep = {}
+            v.h = h.value
+            v._owned = False
+            self.views.append(v)
+
+    def __len__(self):
+        return len(self.views)
+
+    def member(self, i: int) -> "Basin":
+        return self.views[i]
+
+    def step(self, n: int = 1):
+        _check(load().qg_ensemble_step(self.e, n), "qg_ensemble_step")
+        return self
+
+    def kernel_count(self) -> int:
+        c = ctypes.c_int64()
+        _check(load().qg_ensemble_kernel_count(self.e, ctypes.byref(c)),
+               "qg_ensemble_kernel_count")
+        return c.value
+
+    def synchronize(self):
+        _check(load().qg_ensemble_synchronize(self.e), "qg_ensemble_synchronize")
+
+    def close(self):
+        if getattr(self, "e", None):
+            for v in self.views:
+                v.h = None
+            load().qg_ensemble_destroy(self.e)
+            self.e = None
 
     def __del__(self):
         try:

@@ -1,0 +1,96 @@
+"""GPU parity of the ensemble: independent one-layer basins of different
+sizes, Reynolds and Rossby numbers, forcing amplitudes, time steps and CGP
+levels (Sections 2.1 and 3) stepped together by one graph per step."""
+import numpy as np
+import pytest
+
+from oracle import qg_oracle as O
+from paper_1308_3290_gb300 import inputs, qg
+from tests.gpu_util import rel_l2, require_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+MEMBERS = [
+    dict(nx=32, ny=64, Re=200.0, Ro=0.0016, levels=0, dt=1e-4, amp=1.0),
+    dict(nx=32, ny=64, Re=450.0, Ro=0.0036, levels=1, dt=1e-4, amp=0.7),
+    dict(nx=64, ny=128, Re=312.5, Ro=0.0025, levels=1, dt=1e-4, amp=1.3),
+    dict(nx=64, ny=128, Re=200.0, Ro=0.0016, levels=2, dt=5e-5, amp=1.0),
+    dict(nx=128, ny=256, Re=800.0, Ro=0.0016, levels=2, dt=5e-5, amp=0.5),
+    dict(nx=64, ny=64, Re=200.0, Ro=0.0016, levels=1, dt=1e-4, amp=1.5),
+    dict(nx=256, ny=128, Re=200.0, Ro=0.0016, levels=3, dt=2e-5, amp=1.0),
+]
+
+
+def oracle_basin(m, forcing=None):
+    return O.Basin(m["nx"], m["ny"], Re=m["Re"], Ro=m["Ro"], levels=m["levels"],
+                   dt=m["dt"], amp=m["amp"], forcing=forcing)
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-4)])
+def test_ensemble_matches_oracle(dtype, tol):
+    require_gpu()
+    ens = qg.Ensemble(MEMBERS, dtype=dtype)
+    w0 = [inputs.perturbation(m["nx"], m["ny"], seed=20 + i) * 50.0
+          for i, m in enumerate(MEMBERS)]
+    for i, w in enumerate(w0):
+        ens.member(i).set_state(w)
+    # one member with a forcing field (its captured step changes)
+    f = inputs.perturbed_forcing_field(64, 128, seed=5, Ro=0.0016)
+    ens.member(3).set_forcing(f)
+    ens.step(20)
+    ens.synchronize()
+    for i, m in enumerate(MEMBERS):
+        ref = O.run(w0[i], oracle_basin(m, forcing=f if i == 3 else None), 20)
+        got = to_np(ens.member(i).state())
+        assert rel_l2(got, ref) <= tol, (i, rel_l2(got, ref))
+    ens.close()
+
+
+def test_ensemble_equals_standalone_handles(monkeypatch):
+    """With the same FFT schedule the ensemble's results are bitwise those
+    of stand-alone handles (the split solve does the same arithmetic)."""
+    require_gpu()
+    monkeypatch.setenv("QG_SOLVE_ENGINE", "4")
+    ens = qg.Ensemble(MEMBERS, dtype="f32")
+    solo = [qg.Basin(m["nx"], m["ny"], Re=m["Re"], Ro=m["Ro"], levels=m["levels"], dt=m["dt"],
+                     amp=m["amp"], dtype="f32") for m in MEMBERS]
+    for i, m in enumerate(MEMBERS):
+        w = inputs.perturbation(m["nx"], m["ny"], seed=40 + i) * 50.0
+        ens.member(i).set_state(w)
+        solo[i].set_state(w)
+    ens.step(7)
+    for b in solo:
+        b.step(7)
+    ens.synchronize()
+    for i, b in enumerate(solo):
+        b.synchronize()
+        assert np.array_equal(to_np(ens.member(i).state()), to_np(b.state())), i
+        b.close()
+    counts = sum(qg.qg_step_kernel_count(b.h) for b in solo)
+    # each member's solve is three launches instead of one
+    n_solves = 3 * len(MEMBERS)      # one per TVDRK3 stage
+    assert ens.kernel_count() == counts + 2 * n_solves
+    ens.close()
+
+
+def test_ensemble_of_96_basins_steps():
+    """The ensemble workload's shape (96 basins of four sizes, l in {1, 2}):
+    every member advances and stays finite."""
+    require_gpu()
+    rng = np.random.default_rng(4)
+    sizes = [(128, 256), (256, 512), (512, 1024), (1024, 2048)]
+    members = []
+    for _ in range(96):
+        nx, ny = sizes[rng.integers(0, 4)]
+        members.append(dict(nx=nx, ny=ny, Re=float(rng.uniform(200, 1000)), Ro=0.0016,
+                            levels=int(rng.integers(1, 3)), dt=1e-5,
+                            amp=float(rng.uniform(0.5, 1.5))))
+    ens = qg.Ensemble(members, dtype="f32")
+    for i, m in enumerate(members):
+        ens.member(i).set_state(inputs.perturbation(m["nx"], m["ny"], seed=1000 + i))
+    ens.step(5)
+    ens.synchronize()
+    for i in (0, 17, 95):
+        ke, z, u = ens.member(i).diagnostics()
+        assert np.isfinite(ke) and ke > 0 and np.isfinite(z)
+    ens.close()
