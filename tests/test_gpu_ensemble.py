@@ -65,8 +65,9 @@ def test_ensemble_equals_standalone_handles(monkeypatch):
     for i, b in enumerate(solo):
         b.synchronize()
         assert np.array_equal(to_np(ens.member(i).state()), to_np(b.state())), i
-        b.close()
     counts = sum(qg.qg_step_kernel_count(b.h) for b in solo)
+    for b in solo:
+        b.close()
     # each member's solve is three launches instead of one
     n_solves = 3 * len(MEMBERS)      # one per TVDRK3 stage
     assert ens.kernel_count() == counts + 2 * n_solves
