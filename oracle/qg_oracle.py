@@ -16,7 +16,7 @@ first and last node of each direction and the unknowns are the interior nodes
 i = 1..nx-1, j = 1..ny-1.  A "node array" has shape (ny+1, nx+1) and is
 indexed [j, i]; an "interior array" has shape (ny-1, nx-1).
 
-Readings of points the paper leaves open (all listed in the design doc):
+Readings of points the paper leaves open:
   * The one-layer state is the relative vorticity w = (q - y)/Ro rather than
     q itself (the two are equal in exact arithmetic, see ``rhs_q_form``).
   * Dissipation is (1/Re) times the 5-point Laplacian of the fine-grid w,

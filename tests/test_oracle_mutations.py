@@ -124,3 +124,42 @@ def test_time_pins_reject_mistakes():
     want = 1 + z + z * z / 2 + z ** 3 / 6
     assert abs(amp(O.tvdrk3, z) - want) < 1e-14
     assert abs(amp(wrong_stage2, z) - want) > 1e-4
+
+
+def test_adjoint_pins_reject_mistakes():
+    """The forward-difference pin of rhs_adjoint rejects a flipped beta term,
+    a missing projection and transposed Jacobian operands."""
+    from oracle import qg_adjoint as AD
+
+    b = O.Basin(16, 32, levels=1)
+    rng = np.random.default_rng(21)
+    w = O.embed(20.0 * rng.normal(size=(31, 15)))
+    dw = O.embed(rng.normal(size=(31, 15)))
+    lam = O.embed(rng.normal(size=(31, 15)))
+    eps = 1e-3
+    dG = (O.cgp_rhs(w + eps * dw, b) - O.cgp_rhs(w - eps * dw, b)) / (2 * eps)
+    lhs = np.sum(dG * O.interior(lam))
+    psi = O.cgp_psi(w, b)
+
+    def ok(adj):
+        rhs = np.sum(O.interior(dw) * adj(lam, w, psi, b))
+        return abs(lhs - rhs) <= 1e-9 * np.sqrt(np.sum(dG ** 2) * np.sum(lam ** 2))
+
+    def flipped_beta(la, wv, ps, bb):
+        t = O.arakawa(wv, la, bb.dx, bb.dy) + AD.beta_jacobian(la, bb) / bb.Ro
+        return (O.arakawa(ps, la, bb.dx, bb.dy) + O.laplacian5(la, bb.dx, bb.dy) / bb.Re
+                - O.interior(O.cgp_psi(O.embed(t), bb)))
+
+    def no_projection(la, wv, ps, bb):
+        t = O.arakawa(wv, la, bb.dx, bb.dy) - AD.beta_jacobian(la, bb) / bb.Ro
+        return (O.arakawa(ps, la, bb.dx, bb.dy) + O.laplacian5(la, bb.dx, bb.dy) / bb.Re - t)
+
+    def transposed_operands(la, wv, ps, bb):
+        t = O.arakawa(wv, la, bb.dx, bb.dy) - AD.beta_jacobian(la, bb) / bb.Ro
+        return (O.arakawa(la, ps, bb.dx, bb.dy) + O.laplacian5(la, bb.dx, bb.dy) / bb.Re
+                - O.interior(O.cgp_psi(O.embed(t), bb)))
+
+    assert ok(AD.rhs_adjoint)
+    assert not ok(flipped_beta)
+    assert not ok(no_projection)
+    assert not ok(transposed_operands)
