@@ -217,6 +217,49 @@ typedef enum qg_fault {
 } qg_fault;
 qg_status qg_inject_fault(qg_handle h, int kind);
 
+/* ---- discrete adjoint (one layer) ------------------------------------------
+ * The paper has no adjoint.  These calls give the exact transpose of the
+ * Jacobian of the discrete CGPRK3 step of Section 3.2 (restriction Eq. res,
+ * Poisson solve Section 4.3, prolongation Eq. pro, Arakawa Jacobian
+ * Eq. ja1, TVDRK3 Eq. TVDRK), for gradients of functionals of the
+ * trajectory, such as a time-mean kinetic energy (Section 5.2), with
+ * respect to the state and to the wind-forcing field F.  With psi = A w,
+ * A = P^l S R^l (symmetric), the transposed right-hand side is
+ *   G_w^T lam = J(psi, lam) + (1/Re) lap lam - A[J(w, lam) - (1/Ro) J(lam, y)],
+ * using that J(p, .) and J(., y) are skew-symmetric with zero walls.
+ *
+ * Usage: qg_tape_begin records the current state as tape time 0; every
+ * later qg_step(h, n) appends n steps (at most max_steps in all).  The
+ * reverse cursor starts at the last recorded time t; qg_adjoint_step moves
+ * it back, qg_energy_gradient reads the state at it.  The forward states
+ * are stored every `every` steps (every = 1 keeps all of them; a 256 x 512
+ * FP32 state is 0.6 MB, a 2048 x 4096 one 34 MB) and the others are
+ * recomputed per segment with the handle's own step graph.  While a tape
+ * is being reversed with every > 1 the handle's state serves as scratch;
+ * qg_tape_end puts back the state the handle had when the reversal began.
+ * One-layer handles only (QG_ERR_UNSUPPORTED for two layers).            */
+
+/* qg_tape_begin -- start recording.  every >= 1, max_steps >= 1.
+ * Errors: QG_ERR_ARG, QG_ERR_OOM, QG_ERR_UNSUPPORTED.                      */
+qg_status qg_tape_begin(qg_handle h, int64_t every, int64_t max_steps);
+
+/* qg_tape_end -- stop recording, free the tape, restore the state (see
+ * above).  Safe without a tape.                                            */
+qg_status qg_tape_end(qg_handle h);
+
+/* qg_adjoint_step -- reverse n steps from the cursor t (n <= t): on entry
+ * lambda holds dJ/dw at time t, on return dJ/dw at time t - n through those
+ * steps; dJdF += dJ/dF through them.  lambda and dJdF are caller device
+ * buffers in the exchange layout and the handle's dtype.  Objective terms at
+ * intermediate times are added between calls (qg_energy_gradient).
+ * Errors: QG_ERR_ARG (no tape, n out of range, NULL buffers).              */
+qg_status qg_adjoint_step(qg_handle h, int64_t n, void* lambda, void* dJdF);
+
+/* qg_energy_gradient -- g += scale * dE/dw at the state of tape time t (the
+ * cursor), E the kinetic energy of psi = A w (as qg_diagnostics reports it):
+ * dE/dw = A(-dx dy lap psi).  g: caller device buffer, exchange layout.    */
+qg_status qg_energy_gradient(qg_handle h, double scale, void* g);
+
 /* ---- ensembles of basins --------------------------------------------------
  * Many independent one-layer basins (Section 2.1), each with its own grid,
  * Re, Ro, forcing amplitude, dt and CGP level (Section 3), stepped together:

@@ -39,6 +39,21 @@ struct LevelTables {
 
 }  // namespace
 
+// Forward states kept for the adjoint (one layer): the state at every
+// `every`-th step, the states of the segment being reversed (every > 1), the
+// handle's state when the reversal began, and the adjoint's work fields.
+struct Tape {
+    int64_t every = 1, max_steps = 0, recorded = 0, cursor = 0;
+    bool reversing = false;
+    std::vector<void*> ckpt;
+    std::vector<void*> seg;
+    int64_t seg_start = -1;
+    void* live = nullptr;
+    enum { W1, W2, P0, P1, P2, U, PHI, L0, L1, ACC, GF, NBUF };
+    void* buf[NBUF] = {};
+    std::vector<void*> allocs;
+};
+
 struct qg_ctx {
     int layers = 1;
     qg_dtype dtype = QG_F32;
@@ -88,6 +103,7 @@ struct qg_ctx {
     int solve_engine = 4;          // FFT base radix of the step's solve (autotuned)
     int* derr = nullptr;           // device error flag of bounded waits
     unsigned* dbar = nullptr;      // grid-barrier counters of the solve kernel
+    Tape* tape = nullptr;          // adjoint tape (qg_tape_begin .. qg_tape_end)
 };
 
 namespace qg {
@@ -447,14 +463,14 @@ qg_status autotune_solve(qg_ctx* h) {
     return QG_OK;
 }
 
-// CGP steps (ii)-(iv): fine state planes -> fine psi planes.
+// CGP steps (ii)-(iv): fine state planes -> fine psi planes (into `out`).
 template <typename T>
-qg_status project(qg_ctx* h, const void* win, cudaStream_t s) {
+qg_status project_to(qg_ctx* h, const void* win, void* out, cudaStream_t s) {
     const LevelTables* t = nullptr;
     qg_status st = get_level(h, h->levels, &t);
     if (st != QG_OK) return fail(h, st);
     if (h->levels == 0) {
-        return solve_level<T>(h, *t, win, h->ct, h->ld_t, h->plane_t, h->cw, h->psi,
+        return solve_level<T>(h, *t, win, h->ct, h->ld_t, h->plane_t, h->cw, out,
                               h->plane_f, s);
     }
     for (int L = 0; L < h->layers; ++L) {
@@ -469,10 +485,15 @@ qg_status project(qg_ctx* h, const void* win, cudaStream_t s) {
     for (int L = 0; L < h->layers; ++L) {
         KTimer kt(h, s, QG_K_PROLONG);
         QG_TRY(launch_prolong<T>(plane<T>(h->cpsi, h->plane_c, L), t->ldc,
-                                 plane<T>(h->psi, h->plane_f, L), h->ldf, h->nx, h->ny,
+                                 plane<T>(out, h->plane_f, L), h->ldf, h->nx, h->ny,
                                  h->levels, s));
     }
     return QG_OK;
+}
+
+template <typename T>
+qg_status project(qg_ctx* h, const void* win, cudaStream_t s) {
+    return project_to<T>(h, win, h->psi, s);
 }
 
 // TVDRK3 stage s: w_out = a w^n + b (w_in + dt G(w_in)).
@@ -775,9 +796,12 @@ static qg_status create_ctx(const qg_basin* b, int layers, double Re, double Ro,
     return QG_OK;
 }
 
+static void tape_release(qg_ctx* h);
+
 qg_status qg_destroy(qg_handle h) {
     if (!h) return QG_OK;
     cudaStreamSynchronize(h->stream);
+    tape_release(h);
     drop_graph(h);
     for (void* p : h->allocs) cudaFree(p);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -955,7 +979,19 @@ qg_status qg_step(qg_handle h, int64_t n) {
         if (s != QG_OK) return s;
         h->part_valid = true;
     }
-    for (int64_t k = 0; k < n; ++k) QG_TRY(cudaGraphLaunch(h->gexec, h->stream));
+    Tape* tp = h->tape;
+    if (tp && (tp->reversing || tp->recorded + n > tp->max_steps)) return QG_ERR_ARG;
+    const size_t bytes = h->plane_f * h->esz;
+    for (int64_t k = 0; k < n; ++k) {
+        QG_TRY(cudaGraphLaunch(h->gexec, h->stream));
+        if (tp) {
+            ++tp->recorded;
+            tp->cursor = tp->recorded;
+            if (tp->recorded % tp->every == 0)
+                QG_TRY(cudaMemcpyAsync(tp->ckpt[tp->recorded / tp->every], h->w[0], bytes,
+                                       cudaMemcpyDeviceToDevice, h->stream));
+        }
+    }
     return QG_OK;
 }
 
@@ -1033,6 +1069,247 @@ qg_status qg_diagnostics(qg_handle h, double* ke, double* enstrophy, double* max
     if (enstrophy) *enstrophy = Z;
     if (max_vel) *max_vel = U;
     return QG_OK;
+}
+
+}  // extern "C"
+
+// ---- adjoint ---------------------------------------------------------------
+
+namespace {
+
+void tape_free_all(Tape* tp) {
+    for (void* p : tp->allocs) cudaFree(p);
+    delete tp;
+}
+
+template <typename T>
+StageParams<T> stage_params(const qg_ctx* h, double a, double b) {
+    StageParams<T> p;
+    p.nx = h->nx;
+    p.ny = h->ny;
+    p.ld = h->ldf;
+    p.c_jac = (T)(1.0 / (12.0 * h->dx * h->dy));
+    p.c_beta = (T)(1.0 / (12.0 * h->Ro * h->dx));
+    p.c_lapx = (T)(1.0 / (h->Re * h->dx * h->dx));
+    p.c_lapy = (T)(1.0 / (h->Re * h->dy * h->dy));
+    p.dt = (T)h->dt;
+    p.a = (T)a;
+    p.b = (T)b;
+    return p;
+}
+
+template <typename T>
+AdjParams<T> adj_params(const qg_ctx* h, double a, double b) {
+    AdjParams<T> p;
+    p.nx = h->nx;
+    p.ny = h->ny;
+    p.ld = h->ldf;
+    p.c_jac = (T)(1.0 / (12.0 * h->dx * h->dy));
+    p.c_beta = (T)(1.0 / (12.0 * h->Ro * h->dx));
+    p.c_lapx = (T)(1.0 / (h->Re * h->dx * h->dx));
+    p.c_lapy = (T)(1.0 / (h->Re * h->dy * h->dy));
+    p.dt = (T)h->dt;
+    p.a = (T)a;
+    p.b = (T)b;
+    p.inv_dx2 = (T)(1.0 / (h->dx * h->dx));
+    p.inv_dy2 = (T)(1.0 / (h->dy * h->dy));
+    p.dxdy = (T)(h->dx * h->dy);
+    return p;
+}
+
+// The forward state at tape time t (t <= recorded).
+template <typename T>
+qg_status tape_state(qg_ctx* h, int64_t t, const void** out) {
+    Tape* tp = h->tape;
+    const size_t bytes = h->plane_f * h->esz;
+    if (tp->every == 1) {
+        *out = tp->ckpt[t];
+        return QG_OK;
+    }
+    const int64_t start = t / tp->every * tp->every;
+    if (tp->seg_start != start) {
+        if (!tp->live) {
+            QG_TRY(cudaMalloc(&tp->live, bytes));
+            tp->allocs.push_back(tp->live);
+            QG_TRY(cudaMemcpyAsync(tp->live, h->w[0], bytes, cudaMemcpyDeviceToDevice, h->stream));
+        }
+        void* c = tp->ckpt[start / tp->every];
+        QG_TRY(cudaMemcpyAsync(tp->seg[0], c, bytes, cudaMemcpyDeviceToDevice, h->stream));
+        QG_TRY(cudaMemcpyAsync(h->w[0], c, bytes, cudaMemcpyDeviceToDevice, h->stream));
+        qg_status s = build_graph(h);
+        if (s != QG_OK) return s;
+        if (h->part) {
+            s = init_partials<T>(h, h->stream);
+            if (s != QG_OK) return s;
+        }
+        const int64_t end = std::min(start + tp->every, tp->recorded);
+        for (int64_t k = 1; k <= end - start; ++k) {
+            QG_TRY(cudaGraphLaunch(h->gexec, h->stream));
+            QG_TRY(cudaMemcpyAsync(tp->seg[k], h->w[0], bytes, cudaMemcpyDeviceToDevice, h->stream));
+        }
+        h->part_valid = false;
+        tp->seg_start = start;
+    }
+    *out = tp->seg[t - start];
+    return QG_OK;
+}
+
+// lam(t) -> lam(t - 1) through the step from w^n = w (tape time t - 1): the
+// three stages are recomputed (w^(1), w^(2), psi^(0..2)), then reversed.
+template <typename T>
+qg_status adjoint_one(qg_ctx* h, const void* w) {
+    Tape* tp = h->tape;
+    cudaStream_t s = h->stream;
+    T* B[Tape::NBUF];
+    for (int k = 0; k < Tape::NBUF; ++k) B[k] = static_cast<T*>(tp->buf[k]);
+    const T* wn = static_cast<const T*>(w);
+    const T* frow = static_cast<const T*>(h->frow);
+    const T* f2d = static_cast<const T*>(h->f2d);
+    static const double RA[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double RB[3] = {1.0, 0.25, 2.0 / 3.0};
+    // forward stages
+    qg_status st = project_to<T>(h, wn, B[Tape::P0], s);
+    if (st != QG_OK) return st;
+    QG_TRY(launch_fine_stage<T>(B[Tape::P0], wn, wn, B[Tape::W1], frow, f2d,
+                                stage_params<T>(h, RA[0], RB[0]), s));
+    if ((st = project_to<T>(h, B[Tape::W1], B[Tape::P1], s)) != QG_OK) return st;
+    QG_TRY(launch_fine_stage<T>(B[Tape::P1], B[Tape::W1], wn, B[Tape::W2], frow, f2d,
+                                stage_params<T>(h, RA[1], RB[1]), s));
+    if ((st = project_to<T>(h, B[Tape::W2], B[Tape::P2], s)) != QG_OK) return st;
+    // reverse: lam in L0, result in ACC
+    QG_TRY(cudaMemsetAsync(B[Tape::ACC], 0, h->plane_f * h->esz, s));
+    const T* ws[3] = {wn, B[Tape::W1], B[Tape::W2]};
+    const T* ps[3] = {B[Tape::P0], B[Tape::P1], B[Tape::P2]};
+    T* lam = B[Tape::L0];
+    T* nxt = B[Tape::L1];
+    for (int k = 2; k >= 0; --k) {
+        const AdjParams<T> p = adj_params<T>(h, RA[k], RB[k]);
+        QG_TRY(launch_adj_source<T>(ws[k], lam, B[Tape::U], p, s));
+        if ((st = project_to<T>(h, B[Tape::U], B[Tape::PHI], s)) != QG_OK) return st;
+        T* out = k == 0 ? B[Tape::ACC] : nxt;
+        QG_TRY(launch_adj_stage<T>(ps[k], lam, B[Tape::PHI], out, B[Tape::ACC], B[Tape::GF], p,
+                                   k == 0, s));
+        if (k > 0) std::swap(lam, nxt);
+    }
+    std::swap(tp->buf[Tape::L0], tp->buf[Tape::ACC]);
+    return QG_OK;
+}
+
+template <typename T>
+qg_status adjoint_steps(qg_ctx* h, int64_t n, void* lambda, void* dJdF) {
+    Tape* tp = h->tape;
+    cudaStream_t s = h->stream;
+    const size_t bytes = h->plane_f * h->esz;
+    tp->reversing = true;
+    QG_TRY(copy_in(tp->buf[Tape::L0], h->ldf, lambda, h->nx - 1, h->ny - 1, h->esz, s));
+    QG_TRY(cudaMemsetAsync(tp->buf[Tape::GF], 0, bytes, s));
+    for (int64_t k = 0; k < n; ++k) {
+        const void* w = nullptr;
+        qg_status st = tape_state<T>(h, tp->cursor - 1, &w);
+        if (st != QG_OK) return st;
+        if ((st = adjoint_one<T>(h, w)) != QG_OK) return st;
+        --tp->cursor;
+    }
+    QG_TRY(copy_out(lambda, tp->buf[Tape::L0], h->ldf, h->nx - 1, h->ny - 1, h->esz, s));
+    QG_TRY(launch_add_to_dense<T>(static_cast<T*>(dJdF), static_cast<const T*>(tp->buf[Tape::GF]),
+                                  1.0, h->nx, h->ny, h->ldf, s));
+    return QG_OK;
+}
+
+template <typename T>
+qg_status energy_gradient(qg_ctx* h, double scale, void* g) {
+    Tape* tp = h->tape;
+    cudaStream_t s = h->stream;
+    const void* w = nullptr;
+    qg_status st = tape_state<T>(h, tp->cursor, &w);
+    if (st != QG_OK) return st;
+    T* P = static_cast<T*>(tp->buf[Tape::P0]);
+    T* U = static_cast<T*>(tp->buf[Tape::U]);
+    T* PHI = static_cast<T*>(tp->buf[Tape::PHI]);
+    if ((st = project_to<T>(h, w, P, s)) != QG_OK) return st;
+    QG_TRY(launch_energy_source<T>(P, U, adj_params<T>(h, 0.0, 0.0), s));
+    if ((st = project_to<T>(h, U, PHI, s)) != QG_OK) return st;
+    QG_TRY(launch_add_to_dense<T>(static_cast<T*>(g), PHI, scale, h->nx, h->ny, h->ldf, s));
+    return QG_OK;
+}
+
+}  // namespace
+
+static void tape_release(qg_ctx* h) {
+    if (!h->tape) return;
+    cudaStreamSynchronize(h->stream);
+    tape_free_all(h->tape);
+    h->tape = nullptr;
+}
+
+extern "C" {
+
+qg_status qg_tape_begin(qg_handle h, int64_t every, int64_t max_steps) {
+    if (!h || every < 1 || max_steps < 1) return QG_ERR_ARG;
+    if (h->layers != 1) return QG_ERR_UNSUPPORTED;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    tape_release(h);
+    Tape* tp = new (std::nothrow) Tape();
+    if (!tp) return QG_ERR_OOM;
+    tp->every = every;
+    tp->max_steps = max_steps;
+    const size_t bytes = h->plane_f * h->esz;
+    auto alloc = [&](void** p) {
+        if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+        tp->allocs.push_back(*p);
+        return cudaMemsetAsync(*p, 0, bytes, h->stream) == cudaSuccess;
+    };
+    bool ok = true;
+    const int64_t nck = max_steps / every + 1;
+    for (int64_t k = 0; k < nck && ok; ++k) {
+        void* p = nullptr;
+        ok = alloc(&p);
+        if (ok) tp->ckpt.push_back(p);
+    }
+    for (int64_t k = 0; every > 1 && k <= every && ok; ++k) {
+        void* p = nullptr;
+        ok = alloc(&p);
+        if (ok) tp->seg.push_back(p);
+    }
+    for (int k = 0; k < Tape::NBUF && ok; ++k) ok = alloc(&tp->buf[k]);
+    if (ok) ok = cudaMemcpyAsync(tp->ckpt[0], h->w[0], bytes, cudaMemcpyDeviceToDevice,
+                                 h->stream) == cudaSuccess;
+    if (!ok) {
+        cudaStreamSynchronize(h->stream);
+        tape_free_all(tp);
+        (void)cudaGetLastError();
+        return QG_ERR_OOM;
+    }
+    h->tape = tp;
+    return QG_OK;
+}
+
+qg_status qg_tape_end(qg_handle h) {
+    if (!h) return QG_ERR_ARG;
+    Tape* tp = h->tape;
+    if (!tp) return QG_OK;
+    if (tp->live) {
+        QG_TRY(cudaMemcpyAsync(h->w[0], tp->live, h->plane_f * h->esz, cudaMemcpyDeviceToDevice,
+                               h->stream));
+        h->part_valid = false;
+    }
+    tape_release(h);
+    return QG_OK;
+}
+
+qg_status qg_adjoint_step(qg_handle h, int64_t n, void* lambda, void* dJdF) {
+    if (!h || !lambda || !dJdF || !h->tape || n < 0 || n > h->tape->cursor) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    if (n == 0) return QG_OK;
+    return h->dtype == QG_F64 ? adjoint_steps<double>(h, n, lambda, dJdF)
+                              : adjoint_steps<float>(h, n, lambda, dJdF);
+}
+
+qg_status qg_energy_gradient(qg_handle h, double scale, void* g) {
+    if (!h || !g || !h->tape) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    return h->dtype == QG_F64 ? energy_gradient<double>(h, scale, g)
+                              : energy_gradient<float>(h, scale, g);
 }
 
 }  // extern "C"

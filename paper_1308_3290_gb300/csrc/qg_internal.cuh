@@ -104,6 +104,32 @@ cudaError_t launch_fine_stage(const T* psi, const T* w, const T* wn, T* wout,
                               const T* frow, const T* f2d,
                               const StageParams<T>& p, cudaStream_t s);
 
+// Adjoint kernels (adjoint.cu) of the one-layer step.
+template <typename T>
+struct AdjParams {
+    int nx, ny, ld;
+    T c_jac, c_beta;      // 1/(12 dx dy), 1/(12 Ro dx)
+    T c_lapx, c_lapy;     // 1/(Re dx^2), 1/(Re dy^2)
+    T dt, a, b;           // time step and the stage's TVDRK3 weights
+    T inv_dx2, inv_dy2, dxdy;
+};
+// out = J(w, lam) - (1/Ro) J(lam, y)
+template <typename T>
+cudaError_t launch_adj_source(const T* w, const T* lam, T* out, const AdjParams<T>& p,
+                              cudaStream_t s);
+// next = [next +] b lam + b dt (J(psi, lam) + (1/Re) lap lam - phi);
+// acc += a lam; g += b dt lam
+template <typename T>
+cudaError_t launch_adj_stage(const T* psi, const T* lam, const T* phi, T* next, T* acc, T* g,
+                             const AdjParams<T>& p, bool accumulate, cudaStream_t s);
+// out = -dx dy lap psi
+template <typename T>
+cudaError_t launch_energy_source(const T* psi, T* out, const AdjParams<T>& p, cudaStream_t s);
+// dense (exchange layout) += scale * padded (interior)
+template <typename T>
+cudaError_t launch_add_to_dense(T* dense, const T* padded, double scale, int nx, int ny, int ld,
+                                cudaStream_t s);
+
 // Fused one-layer stage (fused.cu): prolongation of psi on load, the stage
 // update, and restriction of the result into four partial-sum planes.
 template <typename T>

@@ -39,6 +39,7 @@ EXPORTS = [
     "qg_last_error", "qg_poisson_solve_noalloc", "qg_inject_fault",
     "qg_ensemble_create", "qg_ensemble_member", "qg_ensemble_step",
     "qg_ensemble_kernel_count", "qg_ensemble_synchronize", "qg_ensemble_destroy",
+    "qg_tape_begin", "qg_tape_end", "qg_adjoint_step", "qg_energy_gradient",
 ]
 
 KERNEL_CLASSES = ["restrict", "solve", "prolong", "fine"]
@@ -100,6 +101,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "qg_ensemble_kernel_count": [vp, ctypes.POINTER(i64)],
         "qg_ensemble_synchronize": [vp],
         "qg_ensemble_destroy": [vp],
+        "qg_tape_begin": [vp, i64, i64],
+        "qg_tape_end": [vp],
+        "qg_adjoint_step": [vp, i64, vp, vp],
+        "qg_energy_gradient": [vp, dbl, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -218,6 +223,22 @@ def qg_inject_fault(h: int, kind: int) -> None:
     synchronisation raises QGError with QG_ERR_TIMEOUT); QG_FAULT_NONE
     restores normal operation."""
     _check(load().qg_inject_fault(h, kind), "qg_inject_fault")
+
+
+def qg_tape_begin(h: int, every: int, max_steps: int) -> None:
+    _check(load().qg_tape_begin(h, every, max_steps), "qg_tape_begin")
+
+
+def qg_tape_end(h: int) -> None:
+    _check(load().qg_tape_end(h), "qg_tape_end")
+
+
+def qg_adjoint_step(h: int, n: int, lam, dJdF) -> None:
+    _check(load().qg_adjoint_step(h, n, _ptr(lam), _ptr(dJdF)), "qg_adjoint_step")
+
+
+def qg_energy_gradient(h: int, scale: float, g) -> None:
+    _check(load().qg_energy_gradient(h, scale, _ptr(g)), "qg_energy_gradient")
 
 
 def qg_synchronize(h: int) -> None:
