@@ -354,6 +354,30 @@ def ensemble_variant(torch, qg, inputs, stream, flush, K=50):
     return out
 
 
+def adjoint_variant(torch, qg, inputs, stream, N=2000, first=1500):
+    """Gradient of the kinetic energy averaged over steps 1500..2000 with
+    respect to the forcing field, 256x512 basin, l = 1, FP32: forward sweep
+    with every state kept, then the reverse sweep (wall-clock seconds)."""
+    from paper_1308_3290_gb300 import adjoint
+    nx, ny = 256, 512
+    b = qg.Basin(nx, ny, Re=RE, Ro=RO, levels=1, dt=5e-5, dtype="f32", stream=stream)
+    F = torch.as_tensor(inputs.perturbed_forcing_field(nx, ny, seed=5, Ro=RO),
+                        dtype=torch.float32, device="cuda").contiguous().requires_grad_(True)
+    w0 = torch.as_tensor(inputs.perturbation(nx, ny, seed=5), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = adjoint.mean_kinetic_energy(F, b, w0, N, first, 1)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    out = {"steps": N, "window": [first, N], "J": float(J), "forward_s": t1 - t0,
+           "backward_s": t2 - t1, "grad_norm": float(F.grad.norm())}
+    b.close()
+    return out
+
+
 def ours(args):
     import numpy as np
     import torch
@@ -473,6 +497,7 @@ def ours(args):
                                                   "ms_per_step": sum(ts) / 100}
         b.close()
         variants["ensemble_96_f32"] = ensemble_variant(torch, qg, inputs, stream, flush)
+        variants["adjoint_256x512_l1_f32"] = adjoint_variant(torch, qg, inputs, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
