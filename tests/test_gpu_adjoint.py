@@ -63,7 +63,7 @@ def test_energy_gradient_matches_oracle(dtype, tol):
 def test_mean_energy_gradient_matches_oracle(dtype, tol):
     """The autograd wrapper's dJ/dF of the time-mean kinetic energy against
     the oracle's; checkpointing every 16 steps gives the result of keeping
-    every state."""
+    every state to rounding."""
     torch = require_gpu()
     nx, ny, N, first = 64, 128, 60, 40
     w0 = inputs.perturbation(nx, ny, seed=34) * 50.0
@@ -78,11 +78,10 @@ def test_mean_energy_gradient_matches_oracle(dtype, tol):
         J = adjoint.mean_kinetic_energy(F, b, torch.as_tensor(w0, dtype=td, device="cuda"),
                                         N, first, every)
         J.backward()
-        assert float(J) == pytest.approx(J_ref, rel=1e-10 if dtype == "f64" else 1e-5)
+        assert float(J.detach()) == pytest.approx(J_ref, rel=1e-10 if dtype == "f64" else 1e-5)
         grads.append(to_np(F.grad))
         b.close()
     assert rel_l2(grads[0], g_ref) <= tol
-    if dtype == "f64":
-        assert np.array_equal(grads[0], grads[1])
-    else:
-        assert rel_l2(grads[1], grads[0]) <= 1e-5
+    # the recomputed segments start from a fresh restriction of the
+    # checkpoint instead of the previous step's partial sums: equal to rounding
+    assert rel_l2(grads[1], grads[0]) <= (1e-11 if dtype == "f64" else 1e-5)
