@@ -35,6 +35,8 @@ struct LevelTables {
     void* twy = nullptr;   // e^{i pi t/my}, t < 2 my
     void* lamx = nullptr;  // (2 cos(pi k/mx) - 2)/dxc^2, k = 0..mx
     void* lamy = nullptr;  // (2 cos(pi l/my) - 2)/dyc^2, l = 0..my
+    void* ptx = nullptr;   // radix-32 engine pass twiddles for L = 2 mx (Cx<T>)
+    void* pty = nullptr;   //   and for L = 2 my
 };
 
 }  // namespace
@@ -218,6 +220,29 @@ qg_status upload_real(qg_ctx* h, void** out, const std::vector<double>& v) {
     return e == cudaSuccess ? QG_OK : QG_ERR_CUDA;
 }
 
+// Per-pass twiddles of the radix-32 engine for FFT length L (cached).
+qg_status get_pass_table(qg_ctx* h, int L, void** out) {
+    const int key = -L;   // shares the twiddle cache; negative keys
+    auto it = h->twcache.find(key);
+    if (it != h->twcache.end()) {
+        *out = it->second;
+        return QG_OK;
+    }
+    const size_t n = pass_table_size(L);
+    std::vector<double> re(n + 1), im(n + 1), v(2 * (n + 1));
+    pass_table(L, re.data(), im.data());
+    for (size_t k = 0; k <= n; ++k) {
+        v[2 * k] = re[k];
+        v[2 * k + 1] = im[k];
+    }
+    void* d = nullptr;
+    qg_status s = upload_real(h, &d, v);
+    if (s != QG_OK) return s;
+    h->twcache[key] = d;
+    *out = d;
+    return QG_OK;
+}
+
 // Eigenvalue and twiddle tables of grid level `lv` (Eq. ialpha without Ro).
 qg_status get_level(qg_ctx* h, int lv, const LevelTables** out) {
     auto it = h->tables.find(lv);
@@ -236,6 +261,10 @@ qg_status get_level(qg_ctx* h, int lv, const LevelTables** out) {
     t.dyc = h->dy * (double)(1 << lv);
     qg_status s = get_twiddles(h, t.mx, &t.twx);
     if (s == QG_OK) s = get_twiddles(h, t.my, &t.twy);
+    if (s == QG_OK && solve32_supports(t.mx, t.my)) {
+        s = get_pass_table(h, 2 * t.mx, &t.ptx);
+        if (s == QG_OK) s = get_pass_table(h, 2 * t.my, &t.pty);
+    }
     if (s != QG_OK) return s;
     const double pi = 3.14159265358979323846;
     std::vector<double> lx(t.mx + 1, 0.0), ly(t.my + 1, 0.0);
@@ -317,6 +346,8 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
     P.ld_tr = ld_tr;
     P.twx = static_cast<const C*>(t.twx);
     P.twy = static_cast<const C*>(t.twy);
+    P.ptx = static_cast<const C*>(t.ptx);
+    P.pty = static_cast<const C*>(t.pty);
     P.lamx = static_cast<const T*>(t.lamx);
     P.lamy = static_cast<const T*>(t.lamy);
     P.scale = (T)((2.0 / t.mx) * (2.0 / t.my));
@@ -367,7 +398,7 @@ void tune_file_load() {
     if (!f) return;
     int a, b, c, d, x, e;
     while (std::fscanf(f, "%d %d %d %d %d %d", &a, &b, &c, &d, &x, &e) == 6)
-        if (e == 4 || e == 16) g_tune_cache[TuneKey(a, b, c, d, x)] = e;
+        if (e == 4 || e == 16 || e == 32) g_tune_cache[TuneKey(a, b, c, d, x)] = e;
     std::fclose(f);
 }
 
@@ -392,7 +423,11 @@ template <typename T>
 float time_steps(qg_ctx* h, int engine) {
     const LevelTables* t = nullptr;
     if (get_level(h, h->levels, &t) != QG_OK) return 1e30f;
-    if (solve_smem_bytes(t->mx, t->my, sizeof(T), engine) > 200 * 1024) return 1e30f;
+    if (engine == 32) {
+        if (!t->ptx || solve32_smem_bytes(t->mx, t->my, sizeof(T)) > 200 * 1024) return 1e30f;
+    } else if (solve_smem_bytes(t->mx, t->my, sizeof(T), engine) > 200 * 1024) {
+        return 1e30f;
+    }
     h->solve_engine = engine;
     drop_graph(h);
     if (build_graph(h) != QG_OK) return 1e30f;
@@ -422,7 +457,7 @@ qg_status autotune_solve(qg_ctx* h) {
     if (st != QG_OK) return st;
     if (const char* force = std::getenv("QG_SOLVE_ENGINE")) {
         const int e = std::atoi(force);
-        if (e == 4 || e == 16) {
+        if (e == 4 || e == 16 || (e == 32 && t->ptx)) {
             h->solve_engine = e;
             return QG_OK;
         }
@@ -438,13 +473,15 @@ qg_status autotune_solve(qg_ctx* h) {
         }
     }
     const float t4 = time_steps<T>(h, 4);
+    const float t32 = time_steps<T>(h, 32);
     const float t16 = time_steps<T>(h, 16);
     // a candidate that cannot run on this grid is a tuning result, not an error
     h->latched = QG_OK;
     (void)cudaGetLastError();
     drop_graph(h);
-    if (t4 >= 1e29f && t16 >= 1e29f) return fail(h, QG_ERR_CUDA);
+    if (t4 >= 1e29f && t16 >= 1e29f && t32 >= 1e29f) return fail(h, QG_ERR_CUDA);
     h->solve_engine = t16 < t4 ? 16 : 4;
+    if (t32 < (t16 < t4 ? t16 : t4)) h->solve_engine = 32;
     // the timing steps ran on the handle's buffers: return them to rest
     cudaStreamSynchronize(h->stream);
     for (void* p : {h->w[0], h->w[1], h->w[2], h->psi}) {

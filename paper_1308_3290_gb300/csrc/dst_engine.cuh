@@ -263,5 +263,34 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int lim
     return false;
 }
 
+// Grid-wide barrier with a bounded wait.  bar[0] counts arrivals, bar[1] is
+// the generation; the last of gridDim.x + extra arrivals releases it.
+// Returns false (on every thread) when the wait ran out.
+__device__ inline bool grid_sync(unsigned* bar, unsigned extra, int limit) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1 + extra) {
+            bar[0] = 0;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            int i = 0;
+            while (*gen == g0) {
+                if (++i > limit) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
 }  // namespace eng
 }  // namespace qg

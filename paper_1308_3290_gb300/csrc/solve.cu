@@ -69,35 +69,6 @@ __host__ __device__ inline Layout layout(int mx, int my, size_t esz, int E) {
     return L;
 }
 
-// Grid-wide barrier with a bounded wait.  bar[0] counts arrivals, bar[1] is
-// the generation; the last of gridDim.x + extra arrivals releases it.
-// Returns false (on every thread) when the wait ran out.
-__device__ bool grid_sync(unsigned* bar, unsigned extra, int limit) {
-    __syncthreads();
-    int ok = 1;
-    if (threadIdx.x == 0) {
-        volatile unsigned* gen = bar + 1;
-        const unsigned g0 = *gen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1 + extra) {
-            bar[0] = 0;
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            int i = 0;
-            while (*gen == g0) {
-                if (++i > limit) {
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    return __syncthreads_and(ok) != 0;
-}
-
 // Where the values of a phase's sequence pair come from and go to.
 template <typename T>
 struct PairIO {
@@ -394,6 +365,7 @@ static cudaError_t launch_engine(const SolveParams<T>& P, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_solve(const SolveParams<T>& P, int engine, cudaStream_t s) {
+    if (engine == 32) return launch_solve32<T>(P, s);
     return engine == 4 ? launch_engine<T, 4>(P, s) : launch_engine<T, 16>(P, s);
 }
 

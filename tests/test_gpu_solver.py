@@ -82,17 +82,54 @@ def test_two_layer_solve_parity():
         b.close()
 
 
-@pytest.mark.parametrize("engine", ["4", "16"])
+@pytest.mark.parametrize("engine", ["4", "16", "32"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_both_fft_engines(engine, dtype, monkeypatch):
-    """The solve has two FFT schedules (base radix 4 and 16) chosen by the
-    autotuner; each must meet the same tolerance."""
+    """The solve has three FFT schedules (shared-memory engine with base
+    radix 4 or 16, warp-group engine with radix 32) chosen by the autotuner;
+    each must meet the same tolerance."""
     require_gpu()
     monkeypatch.setenv("QG_SOLVE_ENGINE", engine)
-    for nx, ny in ((64, 128), (512, 1024), (2048, 256)):
+    shapes = [(64, 128), (512, 1024), (2048, 256)]
+    if engine == "32":
+        shapes += [(16, 16), (32, 64), (256, 32), (4096, 64), (1024, 2048)]
+    for nx, ny in shapes:
         b = qg.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=0, dt=1e-4, dtype=dtype)
         rhs = inputs.smooth_field(nx, ny, seed=nx, noise=0.3)
         got = to_np(b.poisson_solve(rhs))
         ref = O.poisson_solve(rhs, nx, ny, 1.0 / nx, 2.0 / ny)
         assert rel_l2(got, ref) <= TOL[dtype], (nx, ny, rel_l2(got, ref))
         b.close()
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_radix32_engine_in_the_step(levels, monkeypatch):
+    """100 FP64 steps with the warp-group engine forced, one layer and two."""
+    require_gpu()
+    monkeypatch.setenv("QG_SOLVE_ENGINE", "32")
+    nx, ny = 64, 128
+    w0 = inputs.perturbation(nx, ny, seed=3) * 50.0
+    ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=1e-4)
+    ref = O.run(w0, ob, 100)
+    b = qg.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=1e-4, dtype="f64")
+    b.set_state(w0)
+    b.step(100)
+    assert rel_l2(to_np(b.state()), ref) <= 1e-12
+    b.close()
+    if levels <= 1:
+        p = dict(Ro=2.49e-4, Fr=0.087, delta=0.2, sigma=1.43e-3)
+        A = 3.57e-7
+        Q1 = inputs.smooth_field(64, 64, seed=1, amp=0.05, noise=0.01)
+        Q2 = inputs.smooth_field(64, 64, seed=2, amp=0.02, noise=0.01)
+        ob2 = O.TwoLayer(64, 64, A=A, levels=levels, dt=1e-4, **p)
+        a1, a2 = O.embed(Q1), O.embed(Q2)
+        for _ in range(20):
+            a1, a2 = O.cgprk3_step_two_layer(a1, a2, ob2)
+        b2 = qg.Basin(64, 64, Re=p["Ro"] / A, levels=levels, dt=1e-4, dtype="f64", layers=2,
+                      y0=-0.5, y1=0.5, **p)
+        b2.set_state(Q1, 0)
+        b2.set_state(Q2, 1)
+        b2.step(20)
+        assert rel_l2(to_np(b2.state(0)), O.interior(a1)) <= 1e-11
+        assert rel_l2(to_np(b2.state(1)), O.interior(a2)) <= 1e-11
+        b2.close()
