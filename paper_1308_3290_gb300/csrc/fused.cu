@@ -166,7 +166,9 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
         fence_mbar_init();
     }
     __syncthreads();
-    pdl_wait();      // inputs come from the previous kernel of the step
+    // w^(s), w^n and the forcing were written before the solve this kernel
+    // follows began (the solve is launched in stream order), so their copies
+    // start before the programmatic wait; psi comes from the solve itself.
     if (threadIdx.x == 0) {
         uint32_t bytes = sizeof(T) * (RC + 2) * SWX;
         if (use_wn) bytes += sizeof(T) * RC * TX;
@@ -175,9 +177,10 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
         mbar_expect_tx(bar, bytes);
         tma_load_2d(smem_u32(sw), &tm_w, x0 - 4, yc - 1, bar);
         if (use_wn) tma_load_2d(smem_u32(swn), &tm_wn, x0, yc, bar);
-        if (LV == 0) tma_load_2d(smem_u32(sp), &tm_p, x0 - 4, yc - 1, bar);
         if (use_f) tma_load_2d(smem_u32(sf), &tm_f, x0, yc, bar);
     }
+    pdl_wait();
+    if (LV == 0 && threadIdx.x == 0) tma_load_2d(smem_u32(sp), &tm_p, x0 - 4, yc - 1, bar);
     const int mx = nx >> LV, my = ny >> LV;
     const int I_lo = (x0 - 1) >> LV;      // may be -1
     const int J_lo = (yc - 1) >> LV;      // may be -1

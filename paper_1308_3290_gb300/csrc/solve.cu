@@ -231,6 +231,7 @@ solve_kernel(SolveParams<T> P) {
         bulk_copy(smem_u32(slamy), P.lamy, bl, bar);
     }
     pdl_wait();
+    pdl_trigger();   // the next fine stage may start staging its own inputs
     const bool ok = mbar_wait(bar, 0, kSpinLimit);
     if (!__syncthreads_and(ok)) {
         if (threadIdx.x == 0) atomicExch(P.err, 1);

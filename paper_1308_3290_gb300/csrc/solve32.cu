@@ -64,7 +64,7 @@ namespace {
 
 using namespace eng;
 
-constexpr int kT = 256;                 // threads per CTA
+constexpr int kT = 256;                 // most threads per CTA
 constexpr int kSpin = 1 << 22;
 constexpr int kMinLog = 5, kMaxLog = 13;   // L = 32 .. 8192
 
@@ -75,11 +75,16 @@ struct Pl {
     static constexpr int L = 1 << LOG, N = L / 2, G = L / 32;
     static constexpr int NP = LOG / 5, REM = LOG % 5;
     static constexpr int BUF = px(L) + 2;        // padded complex per pair
-    static constexpr int PAIRS = kT / G;         // pairs per CTA
 };
 
-__host__ __device__ constexpr int buf_cplx(int lg) {
-    return (kT / ((1 << lg) / 32)) * (px(1 << lg) + 2);
+// CTA size: one pair of the longer direction (at least a warp), so that the
+// few pairs of a small elliptic grid spread over many SMs.
+__host__ __device__ constexpr int cta_threads(int lgx, int lgy) {
+    const int g = ((1 << (lgx > lgy ? lgx : lgy)) / 32);
+    return g < 32 ? 32 : g;
+}
+__host__ __device__ constexpr int buf_cplx(int lg, int threads) {
+    return (threads / ((1 << lg) / 32)) * (px(1 << lg) + 2);
 }
 
 // Group barrier: the G threads of one pair.
@@ -300,9 +305,10 @@ __device__ void rows_fwd(const SolveParams<T>& P, CT<T>* bufs) {
     const int nrows = P.my - 1;
     const int ppl = (nrows + 1) / 2;
     const int npairs = ppl * P.layers;
-    const int nslots = (npairs + Q::PAIRS - 1) / Q::PAIRS;
+    const int per = blockDim.x / Q::G;
+    const int nslots = (npairs + per - 1) / per;
     for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
-        const int pair = slot * Q::PAIRS + grp;
+        const int pair = slot * per + grp;
         const bool pv = pair < npairs;
         const int layer = pv ? pair / ppl : 0;
         const int ra = 1 + 2 * (pv ? pair % ppl : 0), rb = ra + 1;
@@ -344,9 +350,10 @@ __device__ void cols_solve(const SolveParams<T>& P, CT<T>* bufs) {
     const Sync sy{1 + grp, Q::G};
     const int ncols = P.mx - 1;
     const int npairs = OPY == 2 ? ncols : (ncols + 1) / 2;
-    const int nslots = (npairs + Q::PAIRS - 1) / Q::PAIRS;
+    const int per = blockDim.x / Q::G;
+    const int nslots = (npairs + per - 1) / per;
     for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
-        const int pair = slot * Q::PAIRS + grp;
+        const int pair = slot * per + grp;
         const bool pv = pair < npairs;
         int ka, kb;
         const T *sa, *sb;
@@ -427,9 +434,10 @@ __device__ void rows_inv(const SolveParams<T>& P, CT<T>* bufs) {
     const int nrows = P.my - 1;
     const int ppl = (nrows + 1) / 2;
     const int npairs = ppl * P.layers;
-    const int nslots = (npairs + Q::PAIRS - 1) / Q::PAIRS;
+    const int per = blockDim.x / Q::G;
+    const int nslots = (npairs + per - 1) / per;
     for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
-        const int pair = slot * Q::PAIRS + grp;
+        const int pair = slot * per + grp;
         const bool pv = pair < npairs;
         const int layer = pv ? pair / ppl : 0;
         const int ra = 1 + 2 * (pv ? pair % ppl : 0), rb = ra + 1;
@@ -482,6 +490,7 @@ __global__ void __launch_bounds__(kT, sizeof(T) == 4 ? 2 : 1) solve32_kernel(Sol
     extern __shared__ __align__(16) unsigned char smem[];
     CT<T>* bufs = reinterpret_cast<CT<T>*>(smem);
     pdl_wait();
+    pdl_trigger();   // the next fine stage may start staging its own inputs
     const bool all = P.split == 0;
     if (all || P.phase == 0) {
         const int lg = lgx;
@@ -515,16 +524,18 @@ template <typename T, int OPY>
 cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
     auto k = solve32_kernel<T, OPY>;
     const size_t sm = solve32_smem_bytes(P.mx, P.my, sizeof(T));
+    const int lgx = log2i(2 * P.mx), lgy = log2i(2 * P.my);
+    const int threads = cta_threads(lgx, lgy);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, per = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kT, sm)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, sm)) != cudaSuccess)
+        return e;
     if (per < 1) return cudaErrorInvalidConfiguration;
-    const int lgx = log2i(2 * P.mx), lgy = log2i(2 * P.my);
-    auto slots = [](int lg, int npairs) {
-        const int pairs = kT / ((1 << lg) / 32);
+    auto slots = [threads](int lg, int npairs) {
+        const int pairs = threads / ((1 << lg) / 32);
         return (npairs + pairs - 1) / pairs;
     };
     const int rows = (P.my / 2) * P.layers;
@@ -535,7 +546,7 @@ cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
     if (want < grid) grid = want;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kT);
+    cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -563,7 +574,8 @@ bool solve32_supports(int mx, int my) {
 }
 
 size_t solve32_smem_bytes(int mx, int my, size_t esz) {
-    const int a = buf_cplx(log2i(2 * mx)), b = buf_cplx(log2i(2 * my));
+    const int lx = log2i(2 * mx), ly = log2i(2 * my), th = cta_threads(lx, ly);
+    const int a = buf_cplx(lx, th), b = buf_cplx(ly, th);
     return (size_t)(a > b ? a : b) * 2 * esz;
 }
 
