@@ -209,7 +209,9 @@ qg_status qg_poisson_solve_noalloc(int32_t nx, int32_t ny, double dx, double dy,
  * qg_synchronize or qg_diagnostics returns QG_ERR_TIMEOUT and clears the
  * flag.  Results computed meanwhile are garbage.  QG_FAULT_NONE restores
  * normal operation.  No memory outside the handle's buffers is touched and
- * the CUDA context stays usable.  Re-captures the step graph.
+ * the CUDA context stays usable.  Re-captures the step graph.  Ensemble
+ * members solve with three plain launches and no grid barrier: there the
+ * switch has no effect.
  * Errors: QG_ERR_ARG for a NULL handle or an unknown kind.                 */
 typedef enum qg_fault {
     QG_FAULT_NONE = 0,

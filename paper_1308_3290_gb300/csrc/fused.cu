@@ -256,9 +256,8 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                 v[k] = (T(1) - a) * lo + a * hi;
             }
         }
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-            if (xq - 1 + k > nx || xq - 1 + k < 0) v[k] = T(0);
+        // columns at or beyond a wall interpolate between the zero wall
+        // values and the zero fill of the patch, so they come out zero
     };
     // psi of sweep row rr (fine row y = ys - 1 + rr)
     auto load_psi = [&](int rr, int y, T v[6]) {
@@ -371,7 +370,8 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                     T Va = T(0), Vb = T(0);
     #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int d = (xq + q) & (F - 1);
+                        // x0 is a multiple of 64 and xq of 4
+                        const int d = F <= 4 ? (q & (F - 1)) : ((4 * lane + q) & (F - 1));
                         Va += T(F - d) * (T(1) / T(F * F)) * out[q];
                         Vb += T(d) * (T(1) / T(F * F)) * out[q];
                     }
