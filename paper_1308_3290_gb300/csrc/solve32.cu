@@ -24,6 +24,9 @@
 // column k - 1 likewise, and the inverse x pass reads that shift back.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <cstdlib>
+
 #include "dst_engine.cuh"
 #include "qg_internal.cuh"
 
@@ -70,21 +73,30 @@ constexpr int kMinLog = 5, kMaxLog = 13;   // L = 32 .. 8192
 
 __host__ __device__ constexpr int px(int m) { return m + (m >> 5); }
 
-template <int LOG>
-struct Pl {
-    static constexpr int L = 1 << LOG, N = L / 2, G = L / 32;
-    static constexpr int NP = LOG / 5, REM = LOG % 5;
-    static constexpr int BUF = px(L) + 2;        // padded complex per pair
+// Geometry of one FFT length L = 2^lg: N = L/2, G = L/32 threads per pair,
+// np radix-32 passes and a remainder pass of radix 2^rem (rem = 0: none).
+struct Geo32 {
+    int L, N, G, np, rem, buf;
 };
-
-// CTA size: one pair of the longer direction (at least a warp), so that the
-// few pairs of a small elliptic grid spread over many SMs.
-__host__ __device__ constexpr int cta_threads(int lgx, int lgy) {
-    const int g = ((1 << (lgx > lgy ? lgx : lgy)) / 32);
-    return g < 32 ? 32 : g;
+__host__ __device__ inline Geo32 geo32(int lg) {
+    Geo32 g;
+    g.L = 1 << lg;
+    g.N = g.L / 2;
+    g.G = g.L / 32;
+    g.np = lg / 5;
+    g.rem = lg % 5;
+    g.buf = px(g.L) + 2;    // padded complex per pair
+    return g;
 }
-__host__ __device__ constexpr int buf_cplx(int lg, int threads) {
-    return (threads / ((1 << lg) / 32)) * (px(1 << lg) + 2);
+
+// CTA size: at least one pair group of the longer direction.
+__host__ __device__ inline int cta_threads(int lgx, int lgy, int least) {
+    const int g = (1 << (lgx > lgy ? lgx : lgy)) / 32;
+    return g < least ? least : g;
+}
+__host__ __device__ inline int buf_cplx(int lg, int threads) {
+    const Geo32 g = geo32(lg);
+    return (threads / g.G) * g.buf;
 }
 
 // Group barrier: the G threads of one pair.
@@ -181,73 +193,94 @@ __device__ __forceinline__ void dft32(Cplx<T> (&v)[32]) {
     }
 }
 
-// Element m = t + r G of the odd extension of z (stored at 0..N-1, z_0 = 0).
-template <typename T, int LOG>
-__device__ __forceinline__ Cplx<T> first_read(const CT<T>* cb, int t, int r) {
-    using P = Pl<LOG>;
-    if (r < 16) return ldp<T>(cb, t + r * P::G);
-    if (r == 16) {
-        if (t == 0) return Cplx<T>{T(0), T(0)};
-        const Cplx<T> z = ldp<T>(cb, P::N - t);
-        return Cplx<T>{-z.x, -z.y};
+// One radix-32 Stockham pass (one 32-point DFT per thread, butterfly j = t):
+// input j + r G, twiddle table entry r NS + k (k = j mod NS), output
+// (j - k) 32 + k + r NS.  The first pass (NS = 1) reads the odd extension of
+// the stored z_0..z_{N-1}: element m = t + r G is z_m (r < 16), 0 (m = N),
+// or -z_{L-m}.
+template <typename T>
+__device__ __forceinline__ void pass32(CT<T>* cb, int t, const Geo32& g, int NS, bool first,
+                                       const CT<T>* __restrict__ tw, const Sync& sy) {
+    const int k = t & (NS - 1);
+    Cplx<T> v[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        if (!first) {
+            v[r] = ldp<T>(cb, t + r * g.G);
+        } else if (r < 16) {
+            v[r] = ldp<T>(cb, t + r * g.G);
+        } else {
+            const int m = r == 16 ? g.N - t : (32 - r) * g.G - t;
+            const Cplx<T> z = (r == 16 && t == 0) ? Cplx<T>{T(0), T(0)} : ldp<T>(cb, m);
+            v[r] = Cplx<T>{-z.x, -z.y};
+        }
     }
-    const Cplx<T> z = ldp<T>(cb, (32 - r) * P::G - t);
-    return Cplx<T>{-z.x, -z.y};
+    if (!first) {
+#pragma unroll
+        for (int r = 1; r < 32; ++r) {
+            const CT<T> w = __ldg(tw + r * NS + k);
+            v[r] = cmul(v[r], w.x, w.y);
+        }
+    }
+    dft32<T>(v);
+    sy.sync();
+    const int d = (t - k) * 32 + k;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) stp<T>(cb, d + r * NS, v[r]);
+    sy.sync();
 }
 
-// One Stockham pass of radix R with sub-transform size NS: every thread does
-// 32/R butterflies j = t + b G; input j + r L/R, output (j - k) R + k + r NS.
-template <typename T, int LOG, int R, int NS, bool FIRST>
-__device__ __forceinline__ void pass(CT<T>* cb, int t, const CT<T>* __restrict__ tw,
-                                     const Sync& sy) {
-    using P = Pl<LOG>;
-    constexpr int B = 32 / R, STRIDE = P::L / R;
+// The remainder pass, radix R < 32: 32/R butterflies j = t + b G per thread.
+// Out of line: inlined next to the radix-32 pass its registers spill.
+template <typename T, int R>
+__device__ __noinline__ void passR(CT<T>* cb, int t, Geo32 g, int NS,
+                                   const CT<T>* __restrict__ tw, Sync sy) {
+    constexpr int B = 32 / R;
+    const int stride = g.L / R;
     Cplx<T> v[B][R];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        const int j = t + b * P::G;
+        const int j = t + b * g.G;
         const int k = j & (NS - 1);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if constexpr (FIRST) v[b][r] = first_read<T, LOG>(cb, t, r);
-            else v[b][r] = ldp<T>(cb, j + r * STRIDE);
-        }
-        if constexpr (NS > 1) {
+        for (int r = 0; r < R; ++r) v[b][r] = ldp<T>(cb, j + r * stride);
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const CT<T> w = __ldg(tw + r * NS + k);
-                v[b][r] = cmul(v[b][r], w.x, w.y);
-            }
+        for (int r = 1; r < R; ++r) {
+            const CT<T> w = __ldg(tw + r * NS + k);
+            v[b][r] = cmul(v[b][r], w.x, w.y);
         }
-        if constexpr (R == 32) dft32<T>(v[b]);
-        else dft<T, R>(v[b]);
+        dft<T, R>(v[b]);
     }
     sy.sync();
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        const int j = t + b * P::G;
+        const int j = t + b * g.G;
         const int k = j & (NS - 1);
         const int d = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if constexpr (R == 32) stp<T>(cb, d + r * NS, v[b][r]);
-            else stp<T>(cb, d + r * NS, v[b][out_slot<R>(r)]);
-        }
+        for (int r = 0; r < R; ++r) stp<T>(cb, d + r * NS, v[b][out_slot<R>(r)]);
     }
     sy.sync();
 }
 
 // Forward FFT of length L of the odd extension of cb[0..N) in place; the
 // result Z_k is at cb[px(k)], k = 0..L-1.  Starts and ends with a group sync.
-template <typename T, int LOG>
-__device__ __forceinline__ void fft(CT<T>* cb, int t, const CT<T>* tw, const Sync& sy) {
-    using P = Pl<LOG>;
+template <typename T>
+__device__ __forceinline__ void fft_rt(CT<T>* cb, int t, const Geo32& g, const CT<T>* tw,
+                                       const Sync& sy) {
     sy.sync();
-    pass<T, LOG, 32, 1, true>(cb, t, tw, sy);
-    if constexpr (P::NP >= 2) pass<T, LOG, 32, 32, false>(cb, t, tw, sy);
-    if constexpr (P::REM > 0)
-        pass<T, LOG, (1 << P::REM), (P::NP >= 2 ? 1024 : 32), false>(
-            cb, t, tw + (P::NP >= 2 ? 1024 : 0), sy);
+#pragma unroll 1
+    for (int p = 0; p < g.np; ++p) pass32<T>(cb, t, g, p == 0 ? 1 : 32, p == 0, tw, sy);
+    if (g.rem > 0) {
+        const int ns = g.np >= 2 ? 1024 : 32;
+        const CT<T>* tr = tw + (g.np >= 2 ? 1024 : 0);
+        switch (g.rem) {
+            case 1: passR<T, 2>(cb, t, g, ns, tr, sy); break;
+            case 2: passR<T, 4>(cb, t, g, ns, tr, sy); break;
+            case 3: passR<T, 8>(cb, t, g, ns, tr, sy); break;
+            default: passR<T, 16>(cb, t, g, ns, tr, sy); break;
+        }
+    }
 }
 
 template <typename T>
@@ -295,223 +328,184 @@ __device__ __forceinline__ void rhs4(const SolveParams<T>& P, int layer, int r, 
     }
 }
 
-// Phase 1: pairs of rows (ra, ra + 1) -> DST over x -> tr[k][ra - 1 .. ra].
-template <typename T, int LOG>
-__device__ void rows_fwd(const SolveParams<T>& P, CT<T>* bufs) {
-    using Q = Pl<LOG>;
-    const int grp = threadIdx.x / Q::G, t = threadIdx.x % Q::G;
-    CT<T>* cb = bufs + grp * Q::BUF;
-    const Sync sy{1 + grp, Q::G};
-    const int nrows = P.my - 1;
-    const int ppl = (nrows + 1) / 2;
-    const int npairs = ppl * P.layers;
-    const int per = blockDim.x / Q::G;
-    const int nslots = (npairs + per - 1) / per;
-    for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
-        const int pair = slot * per + grp;
-        const bool pv = pair < npairs;
-        const int layer = pv ? pair / ppl : 0;
-        const int ra = 1 + 2 * (pv ? pair % ppl : 0), rb = ra + 1;
-        const bool vb = pv && rb <= nrows;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int c0 = 4 * (t + i * Q::G);
-            T a[4] = {T(0), T(0), T(0), T(0)}, b[4] = {T(0), T(0), T(0), T(0)};
-            if (pv) rhs4<T>(P, layer, ra, c0, a);
-            if (vb) rhs4<T>(P, layer, rb, c0, b);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) stp<T>(cb, c0 + q, Cplx<T>{a[q], b[q]});
-        }
-        if (t == 0) stp<T>(cb, 0, Cplx<T>{T(0), T(0)});
-        fft<T, LOG>(cb, t, P.ptx, sy);
-        if (pv) {
-            T* tr = P.tr[layer] + (ra - 1);
-#pragma unroll 4
-            for (int i = 0; i < 16; ++i) {
-                const int k = t + i * Q::G;
-                if (k == 0) continue;
-                const CT<T> z = cb[px(k)];
-                if (vb) st2<T>(tr + (size_t)k * P.ld_tr, T(-0.5) * z.y, T(0.5) * z.x);
-                else tr[(size_t)k * P.ld_tr] = T(-0.5) * z.y;
-            }
-        }
-        sy.sync();
-    }
-}
-
-// Phase 2: pairs of x-modes -> DST over y, mode-space solve, DST over y ->
-// work[j][k - 1].  OPY 1: modes (ka, ka + 1) of one layer; OPY 2: mode k of
-// both layers (the coupled 2x2 solve).
-template <typename T, int LOG, int OPY>
-__device__ void cols_solve(const SolveParams<T>& P, CT<T>* bufs) {
-    using Q = Pl<LOG>;
-    const int grp = threadIdx.x / Q::G, t = threadIdx.x % Q::G;
-    CT<T>* cb = bufs + grp * Q::BUF;
-    const Sync sy{1 + grp, Q::G};
-    const int ncols = P.mx - 1;
-    const int npairs = OPY == 2 ? ncols : (ncols + 1) / 2;
-    const int per = blockDim.x / Q::G;
-    const int nslots = (npairs + per - 1) / per;
-    for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
-        const int pair = slot * per + grp;
-        const bool pv = pair < npairs;
-        int ka, kb;
-        const T *sa, *sb;
-        if (OPY == 2) {
-            ka = kb = 1 + (pv ? pair : 0);
-            sa = P.tr[0] + (size_t)ka * P.ld_tr;
-            sb = P.tr[1] + (size_t)kb * P.ld_tr;
-        } else {
-            ka = 1 + 2 * (pv ? pair : 0);
-            kb = ka + 1;
-            sa = P.tr[0] + (size_t)ka * P.ld_tr;
-            sb = P.tr[0] + (size_t)kb * P.ld_tr;
-        }
-        const bool va = pv, vb = pv && (OPY == 2 || kb <= ncols);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int c0 = 4 * (t + i * Q::G);
-            T a[4] = {T(0), T(0), T(0), T(0)}, b[4] = {T(0), T(0), T(0), T(0)};
-            if (va) ld4<T>(sa + c0, a);
-            if (vb) ld4<T>(sb + c0, b);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) stp<T>(cb, c0 + 1 + q, Cplx<T>{a[q], b[q]});
-        }
-        if (t == 0) stp<T>(cb, 0, Cplx<T>{T(0), T(0)});
-        fft<T, LOG>(cb, t, P.pty, sy);
-        const T lxa = __ldg(P.lamx + ka), lxb = __ldg(P.lamx + kb);
-#pragma unroll 4
-        for (int i = 0; i < 16; ++i) {
-            const int l = t + i * Q::G;
-            const Cplx<T> z = ldp<T>(cb, l);
-            const T Fa = T(-0.5) * z.y, Fb = T(0.5) * z.x;
-            T a = T(0), b = T(0);
-            if (l > 0 && pv) {
-                const T ly = __ldg(P.lamy + l);
-                if (OPY == 1) {
-                    a = Fa * (P.scale / (lxa + ly));
-                    if (vb) b = Fb * (P.scale / (lxb + ly));
-                } else {
-                    const T q1 = P.scale * Fa, q2 = P.scale * Fb;
-                    const T al = P.Ro * (lxa + ly);
-                    const T den = al * (al - P.f1 - P.f2);
-                    a = (al * q1 - P.f2 * q1 - P.f1 * q2) / den;
-                    b = (al * q2 - P.f2 * q1 - P.f1 * q2) / den;
-                }
-            }
-            stp<T>(cb, l, Cplx<T>{a, b});
-        }
-        fft<T, LOG>(cb, t, P.pty, sy);
-        if (pv) {
-#pragma unroll 4
-            for (int i = 0; i < 16; ++i) {
-                const int j = t + i * Q::G;
-                if (j == 0) continue;
-                const CT<T> z = cb[px(j)];
-                const T ga = T(-0.5) * z.y, gb = T(0.5) * z.x;
-                if (OPY == 2) {
-                    P.work[0][(size_t)j * P.ld + ka - 1] = ga;
-                    P.work[1][(size_t)j * P.ld + kb - 1] = gb;
-                } else if (vb) {
-                    st2<T>(P.work[0] + (size_t)j * P.ld + ka - 1, ga, gb);
-                } else {
-                    P.work[0][(size_t)j * P.ld + ka - 1] = ga;
-                }
-            }
-        }
-        sy.sync();
-    }
-}
-
-// Phase 3: pairs of rows of work (element k at column k - 1) -> DST over x
-// -> out[r][k], k = 0..mx-1 (k = 0 is the wall).
-template <typename T, int LOG>
-__device__ void rows_inv(const SolveParams<T>& P, CT<T>* bufs) {
-    using Q = Pl<LOG>;
-    const int grp = threadIdx.x / Q::G, t = threadIdx.x % Q::G;
-    CT<T>* cb = bufs + grp * Q::BUF;
-    const Sync sy{1 + grp, Q::G};
-    const int nrows = P.my - 1;
-    const int ppl = (nrows + 1) / 2;
-    const int npairs = ppl * P.layers;
-    const int per = blockDim.x / Q::G;
-    const int nslots = (npairs + per - 1) / per;
-    for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
-        const int pair = slot * per + grp;
-        const bool pv = pair < npairs;
-        const int layer = pv ? pair / ppl : 0;
-        const int ra = 1 + 2 * (pv ? pair % ppl : 0), rb = ra + 1;
-        const bool vb = pv && rb <= nrows;
-        const T* wa = P.work[layer] + (size_t)ra * P.ld;
-        const T* wb = P.work[layer] + (size_t)rb * P.ld;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int c0 = 4 * (t + i * Q::G);
-            T a[4] = {T(0), T(0), T(0), T(0)}, b[4] = {T(0), T(0), T(0), T(0)};
-            if (pv) ld4<T>(wa + c0, a);
-            if (vb) ld4<T>(wb + c0, b);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) stp<T>(cb, c0 + 1 + q, Cplx<T>{a[q], b[q]});
-        }
-        if (t == 0) stp<T>(cb, 0, Cplx<T>{T(0), T(0)});
-        fft<T, LOG>(cb, t, P.ptx, sy);
-        if (pv) {
-            T* oa = P.out[layer] + (size_t)ra * P.ld;
-            T* ob = P.out[layer] + (size_t)rb * P.ld;
-#pragma unroll 4
-            for (int i = 0; i < 16; ++i) {
-                const int k = t + i * Q::G;
-                const CT<T> z = cb[px(k)];
-                oa[k] = k == 0 ? T(0) : T(-0.5) * z.y;
-                if (vb) ob[k] = k == 0 ? T(0) : T(0.5) * z.x;
-            }
-        }
-        sy.sync();
-    }
-}
-
-// Run phase F for the FFT length 2^lg (5 <= lg <= 13).
-#define QG_CASES(F, ...)                                  \
-    switch (lg) {                                         \
-        case 5: F<T, 5, ##__VA_ARGS__>(P, bufs); break;   \
-        case 6: F<T, 6, ##__VA_ARGS__>(P, bufs); break;   \
-        case 7: F<T, 7, ##__VA_ARGS__>(P, bufs); break;   \
-        case 8: F<T, 8, ##__VA_ARGS__>(P, bufs); break;   \
-        case 9: F<T, 9, ##__VA_ARGS__>(P, bufs); break;   \
-        case 10: F<T, 10, ##__VA_ARGS__>(P, bufs); break; \
-        case 11: F<T, 11, ##__VA_ARGS__>(P, bufs); break; \
-        case 12: F<T, 12, ##__VA_ARGS__>(P, bufs); break; \
-        case 13: F<T, 13, ##__VA_ARGS__>(P, bufs); break; \
-        default: break;                                   \
-    }
+// The sequence pair `pair` of phase ph (0: rows of the right-hand side,
+// 1: x-modes, 2: rows of work) and where its two sequences live.
+struct PairAt {
+    bool va, vb;
+    int layer;    // phases 0, 2
+    int ra, rb;   // rows (phases 0, 2) or x-modes (phase 1)
+};
 
 template <typename T, int OPY>
-__global__ void __launch_bounds__(kT, sizeof(T) == 4 ? 2 : 1) solve32_kernel(SolveParams<T> P, int lgx, int lgy) {
+__device__ __forceinline__ PairAt pair_at(const SolveParams<T>& P, int ph, int pair, int npairs) {
+    PairAt a;
+    const bool pv = pair < npairs;
+    if (ph == 1) {
+        const int ncols = P.mx - 1;
+        a.layer = 0;
+        if (OPY == 2) {
+            a.ra = a.rb = 1 + (pv ? pair : 0);
+        } else {
+            a.ra = 1 + 2 * (pv ? pair : 0);
+            a.rb = a.ra + 1;
+        }
+        a.va = pv;
+        a.vb = pv && (OPY == 2 || a.rb <= ncols);
+    } else {
+        const int nrows = P.my - 1, ppl = (nrows + 1) / 2;
+        a.layer = pv ? pair / ppl : 0;
+        a.ra = 1 + 2 * (pv ? pair % ppl : 0);
+        a.rb = a.ra + 1;
+        a.va = pv;
+        a.vb = pv && a.rb <= nrows;
+    }
+    return a;
+}
+
+// Stage the pair's input z_j = (a_j, b_j), j = 0..N-1, into cb (z_0 = 0).
+//   phase 0: rows of the right-hand side (sum of the partial planes);
+//   phase 1: rows ka, kb of tr (element j at column j - 1);
+//   phase 2: rows of work (element j at column j - 1).
+template <typename T, int OPY>
+__device__ __forceinline__ void load_pair(const SolveParams<T>& P, int ph, const PairAt& a,
+                                          const Geo32& g, CT<T>* cb, int t) {
+    const T *sa = nullptr, *sb = nullptr;
+    if (ph == 1) {
+        sa = P.tr[0] + (size_t)a.ra * P.ld_tr;
+        sb = P.tr[OPY == 2 ? 1 : 0] + (size_t)a.rb * P.ld_tr;
+    } else if (ph == 2) {
+        sa = P.work[a.layer] + (size_t)a.ra * P.ld;
+        sb = P.work[a.layer] + (size_t)a.rb * P.ld;
+    }
+    const int shift = ph == 0 ? 0 : 1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int c0 = 4 * (t + i * g.G);
+        T x[4] = {T(0), T(0), T(0), T(0)}, y[4] = {T(0), T(0), T(0), T(0)};
+        if (ph == 0) {
+            if (a.va) rhs4<T>(P, a.layer, a.ra, c0, x);
+            if (a.vb) rhs4<T>(P, a.layer, a.rb, c0, y);
+        } else {
+            if (a.va) ld4<T>(sa + c0, x);
+            if (a.vb) ld4<T>(sb + c0, y);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) stp<T>(cb, c0 + shift + q, Cplx<T>{x[q], y[q]});
+    }
+    if (t == 0) stp<T>(cb, 0, Cplx<T>{T(0), T(0)});
+}
+
+// Between the two y transforms of phase 1: the mode-space solve, Eq. ialpha
+// (OPY 1) or Eqs. isub-1/2 (OPY 2), written back as the next input.
+template <typename T, int OPY>
+__device__ __forceinline__ void mode_solve(const SolveParams<T>& P, const PairAt& a,
+                                           const Geo32& g, CT<T>* cb, int t) {
+    const T lxa = __ldg(P.lamx + a.ra), lxb = __ldg(P.lamx + a.rb);
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i) {
+        const int l = t + i * g.G;
+        const Cplx<T> z = ldp<T>(cb, l);
+        const T Fa = T(-0.5) * z.y, Fb = T(0.5) * z.x;
+        T x = T(0), y = T(0);
+        if (l > 0 && a.va) {
+            const T ly = __ldg(P.lamy + l);
+            if (OPY == 1) {
+                x = Fa * (P.scale / (lxa + ly));
+                if (a.vb) y = Fb * (P.scale / (lxb + ly));
+            } else {
+                const T q1 = P.scale * Fa, q2 = P.scale * Fb;
+                const T al = P.Ro * (lxa + ly);
+                const T den = al * (al - P.f1 - P.f2);
+                x = (al * q1 - P.f2 * q1 - P.f1 * q2) / den;
+                y = (al * q2 - P.f2 * q1 - P.f1 * q2) / den;
+            }
+        }
+        stp<T>(cb, l, Cplx<T>{x, y});
+    }
+}
+
+// Write the transformed pair: F(a)_k = -Im Z_k / 2, F(b)_k = Re Z_k / 2.
+//   phase 0: tr[k][ra - 1], tr[k][rb - 1] (k >= 1);
+//   phase 1: work[j][ka - 1], work[j][kb - 1] (j >= 1);
+//   phase 2: out[ra][k], out[rb][k], k = 0..N-1 (k = 0 is the wall).
+template <typename T, int OPY>
+__device__ __forceinline__ void store_pair(const SolveParams<T>& P, int ph, const PairAt& a,
+                                           const Geo32& g, const CT<T>* cb, int t) {
+    if (!a.va) return;
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i) {
+        const int k = t + i * g.G;
+        const CT<T> z = cb[px(k)];
+        const T fa = T(-0.5) * z.y, fb = T(0.5) * z.x;
+        if (ph == 2) {
+            P.out[a.layer][(size_t)a.ra * P.ld + k] = k == 0 ? T(0) : fa;
+            if (a.vb) P.out[a.layer][(size_t)a.rb * P.ld + k] = k == 0 ? T(0) : fb;
+            continue;
+        }
+        if (k == 0) continue;
+        if (ph == 0) {
+            T* d = P.tr[a.layer] + (size_t)k * P.ld_tr + (a.ra - 1);
+            if (a.vb) st2<T>(d, fa, fb);
+            else d[0] = fa;
+        } else if (OPY == 2) {
+            P.work[0][(size_t)k * P.ld + a.ra - 1] = fa;
+            P.work[1][(size_t)k * P.ld + a.rb - 1] = fb;
+        } else if (a.vb) {
+            st2<T>(P.work[0] + (size_t)k * P.ld + a.ra - 1, fa, fb);
+        } else {
+            P.work[0][(size_t)k * P.ld + a.ra - 1] = fa;
+        }
+    }
+}
+
+template <typename T, int OPY>
+__global__ void __launch_bounds__(kT, 1)
+solve32_kernel(SolveParams<T> P, int lgx, int lgy) {
     extern __shared__ __align__(16) unsigned char smem[];
     CT<T>* bufs = reinterpret_cast<CT<T>*>(smem);
     pdl_wait();
     pdl_trigger();   // the next fine stage may start staging its own inputs
-    const bool all = P.split == 0;
-    if (all || P.phase == 0) {
-        const int lg = lgx;
-        QG_CASES(rows_fwd)
+    const int ph0 = P.split ? P.phase : 0, ph1 = P.split ? P.phase + 1 : 3;
+    for (int ph = ph0; ph < ph1; ++ph) {
+        if (ph > ph0 && !grid_sync(P.bar, P.bar_extra, kSpin)) {
+            if (threadIdx.x == 0) atomicExch(P.err, 1);
+            return;
+        }
+        const Geo32 g = geo32(ph == 1 ? lgy : lgx);
+        const CT<T>* tw = ph == 1 ? P.pty : P.ptx;
+        const int grp = threadIdx.x / g.G, t = threadIdx.x % g.G;
+        CT<T>* cb = bufs + grp * g.buf;
+        const Sync sy{1 + grp, g.G};
+        int npairs;
+        if (ph == 1) npairs = OPY == 2 ? P.mx - 1 : P.mx / 2;
+        else npairs = (P.my / 2) * P.layers;
+        const int per = blockDim.x / g.G;
+        const int nslots = (npairs + per - 1) / per;
+        for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
+            const PairAt a = pair_at<T, OPY>(P, ph, slot * per + grp, npairs);
+            load_pair<T, OPY>(P, ph, a, g, cb, t);
+            const int nfft = ph == 1 ? 2 : 1;
+#pragma unroll 1
+            for (int f = 0; f < nfft; ++f) {
+                if (f == 1) mode_solve<T, OPY>(P, a, g, cb, t);
+                fft_rt<T>(cb, t, g, tw, sy);
+            }
+            store_pair<T, OPY>(P, ph, a, g, cb, t);
+            sy.sync();
+        }
     }
-    if (all && !grid_sync(P.bar, P.bar_extra, kSpin)) {
-        if (threadIdx.x == 0) atomicExch(P.err, 1);
-        return;
+}
+
+int least_threads() {
+    static int v = 0;
+    if (!v) {
+        v = 256;
+        if (const char* e = std::getenv("QG_SOLVE32_THREADS")) {
+            const int t = std::atoi(e);
+            if (t >= 32 && t <= 256 && (t & (t - 1)) == 0) v = t;
+        }
     }
-    if (all || P.phase == 1) {
-        const int lg = lgy;
-        QG_CASES(cols_solve, OPY)
-    }
-    if (all && !grid_sync(P.bar, P.bar_extra, kSpin)) {
-        if (threadIdx.x == 0) atomicExch(P.err, 1);
-        return;
-    }
-    if (all || P.phase == 2) {
-        const int lg = lgx;
-        QG_CASES(rows_inv)
-    }
+    return v;
 }
 
 int log2i(int v) {
@@ -525,7 +519,7 @@ cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
     auto k = solve32_kernel<T, OPY>;
     const size_t sm = solve32_smem_bytes(P.mx, P.my, sizeof(T));
     const int lgx = log2i(2 * P.mx), lgy = log2i(2 * P.my);
-    const int threads = cta_threads(lgx, lgy);
+    const int threads = cta_threads(lgx, lgy, least_threads());
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, per = 0;
@@ -574,7 +568,7 @@ bool solve32_supports(int mx, int my) {
 }
 
 size_t solve32_smem_bytes(int mx, int my, size_t esz) {
-    const int lx = log2i(2 * mx), ly = log2i(2 * my), th = cta_threads(lx, ly);
+    const int lx = log2i(2 * mx), ly = log2i(2 * my), th = cta_threads(lx, ly, least_threads());
     const int a = buf_cplx(lx, th), b = buf_cplx(ly, th);
     return (size_t)(a > b ? a : b) * 2 * esz;
 }
