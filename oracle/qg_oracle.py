@@ -39,7 +39,8 @@ __all__ = [
     "prolong_levels", "arakawa", "arakawa_terms", "laplacian5",
     "forcing_one_layer", "rhs_omega", "cgp_psi", "cgp_rhs", "tvdrk3",
     "cgprk3_step", "run", "rhs_q_form", "cgprk3_step_q_form",
-    "kinetic_energy", "enstrophy", "max_velocity", "cfl_dt",
+    "kinetic_energy", "enstrophy", "max_velocity", "cfl_dt", "adaptive_dt",
+    "cgprk3_step_adaptive", "run_adaptive",
     "two_layer_cgp_psi", "two_layer_rhs", "cgprk3_step_two_layer",
     "interior", "embed",
 ]
@@ -459,6 +460,32 @@ def max_velocity(psi: np.ndarray, dx: float, dy: float) -> float:
 def cfl_dt(psi: np.ndarray, dx: float, dy: float, c: float) -> float:
     """Eq. dt: dt = c min(dx, dy) / max(|psi_x|, |psi_y|)."""
     return c * min(dx, dy) / max_velocity(psi, dx, dy)
+
+
+def adaptive_dt(psi: np.ndarray, b: Basin, c: float) -> float:
+    """The step size of Eq. dt for the current streamfunction, capped by the
+    basin's dt (the flow may start from rest, where Eq. dt has no bound):
+    dt = min(b.dt, c min(dx, dy) / max(|psi_x|, |psi_y|))."""
+    u = max_velocity(psi, b.dx, b.dy)
+    return b.dt if u <= 0.0 else min(b.dt, c * min(b.dx, b.dy) / u)
+
+
+def cgprk3_step_adaptive(omega: np.ndarray, b: Basin, c: float):
+    """One CGPRK3 step whose dt follows Eq. dt from psi^n, the streamfunction
+    of the step's first stage (CGP steps (ii)-(iv) applied to w^n).
+    Returns (w^(n+1), dt)."""
+    dt = adaptive_dt(cgp_psi(omega, b), b, c)
+    return tvdrk3(omega, lambda w: cgp_rhs(w, b), dt), dt
+
+
+def run_adaptive(omega0_int: np.ndarray, b: Basin, nsteps: int, c: float):
+    """``nsteps`` adaptive CGPRK3 steps; returns (interior w, list of dt)."""
+    w = embed(np.asarray(omega0_int, dtype=np.float64))
+    dts = []
+    for _ in range(nsteps):
+        w, dt = cgprk3_step_adaptive(w, b, c)
+        dts.append(dt)
+    return interior(w), dts
 
 
 # ---------------------------------------------------------------------------

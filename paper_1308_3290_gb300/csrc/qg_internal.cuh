@@ -73,6 +73,7 @@ struct SolveParams {
 template <typename T>
 cudaError_t launch_solve(const SolveParams<T>& P, int engine, cudaStream_t s);
 size_t solve_smem_bytes(int mx, int my, size_t esz, int engine);
+bool solve_engine_supports(int mx, int my, size_t esz, int engine);
 // The radix-32 engine's twiddle table for an FFT of length L = 2N: for each
 // pass p >= 1 (radix R_p, sub-transform size Ns_p), R_p x Ns_p entries
 // e^{-2 pi i r k / (R_p Ns_p)} at [r Ns_p + k], passes in order.

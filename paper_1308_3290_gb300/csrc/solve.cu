@@ -353,6 +353,13 @@ size_t solve_smem_bytes(int mx, int my, size_t esz, int engine) {
     return layout(mx, my, esz, engine).end;
 }
 
+bool solve_engine_supports(int mx, int my, size_t esz, int engine) {
+    if (engine == 32) return solve32_supports(mx, my) && solve32_smem_bytes(mx, my, esz) <= 200 * 1024;
+    if (engine != 4 && engine != 16) return false;
+    const int nbm = nb_for(mx, engine) > nb_for(my, engine) ? nb_for(mx, engine) : nb_for(my, engine);
+    return nbm <= 2 && layout(mx, my, esz, engine).end <= 200 * 1024;
+}
+
 template <typename T, int E>
 static cudaError_t launch_engine(const SolveParams<T>& P, cudaStream_t s) {
     const size_t sm = layout(P.mx, P.my, sizeof(T), E).end;

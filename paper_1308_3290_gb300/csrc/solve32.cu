@@ -499,7 +499,7 @@ solve32_kernel(SolveParams<T> P, int lgx, int lgy) {
 int least_threads() {
     static int v = 0;
     if (!v) {
-        v = 256;
+        v = 128;
         if (const char* e = std::getenv("QG_SOLVE32_THREADS")) {
             const int t = std::atoi(e);
             if (t >= 32 && t <= 256 && (t & (t - 1)) == 0) v = t;

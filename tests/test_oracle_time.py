@@ -101,3 +101,26 @@ def test_cfl_dt_formula():
     u = O.max_velocity(psi, b.dx, b.dy)
     assert u >= 3.0
     assert O.cfl_dt(psi, b.dx, b.dy, 0.5) == pytest.approx(0.5 * b.dx / u)
+
+
+def test_adaptive_dt_rules():
+    """Eq. dt with the cap: from rest the basin's dt; a capped step is the
+    fixed step; otherwise c min(dx, dy) / max|grad psi| and the step is
+    TVDRK3 with that dt."""
+    b = O.Basin(32, 64, levels=1, dt=1e-3)
+    w0 = O.embed(np.zeros((63, 31)))
+    assert O.adaptive_dt(O.cgp_psi(w0, b), b, 0.5) == b.dt
+    w = O.embed(inputs.perturbation(32, 64, seed=9) * 50.0)
+    psi = O.cgp_psi(w, b)
+    u = O.max_velocity(psi, b.dx, b.dy)
+    c_small = 0.1 * b.dt * u / min(b.dx, b.dy)           # Eq. dt below the cap
+    dt = O.adaptive_dt(psi, b, c_small)
+    assert dt == pytest.approx(c_small * min(b.dx, b.dy) / u, rel=1e-15)
+    assert dt < b.dt
+    w1, dt1 = O.cgprk3_step_adaptive(w, b, c_small)
+    assert dt1 == dt
+    ref = O.tvdrk3(w, lambda s: O.cgp_rhs(s, b), dt)
+    assert np.array_equal(w1, ref)
+    w2, dt2 = O.cgprk3_step_adaptive(w, b, 1e9)             # capped
+    assert dt2 == b.dt
+    assert np.array_equal(w2, O.cgprk3_step(w, b))
