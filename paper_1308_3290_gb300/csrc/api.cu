@@ -379,65 +379,6 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
 // forces a choice where that engine supports the grid.  Other grids use the
 // size rule.
 
-int engine_rule(int mx, int my);
-int engine_for(qg_ctx* h, int mx, int my);
-
-template <typename T>
-qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr, int ld_tr,
-                      size_t pl_tr, void* work, void* out, size_t pl, cudaStream_t s,
-                      int nparts = 1, int engine = 0) {
-    using C = typename Cx<T>::type;
-    SolveParams<T> P = {};
-    P.mx = t.mx;
-    P.my = t.my;
-    P.layers = h->layers;
-    for (int L = 0; L < h->layers; ++L) {
-        for (int q = 0; q < nparts; ++q)
-            P.in[L][q] = plane<T>(const_cast<void*>(in), pl, L * nparts + q);
-        P.tr[L] = plane<T>(tr, pl_tr, L);
-        P.work[L] = plane<T>(work, pl, L);
-        P.out[L] = plane<T>(out, pl, L);
-    }
-    P.nin = nparts;
-    P.part_px = P.part_py = 1;
-    if (nparts > 1) {
-        P.part_px = fine_part_period_x(h->levels);
-        P.part_py = fine_part_period_y(h->levels, sizeof(T));
-    }
-    P.ld = t.ldc;
-    P.ld_tr = ld_tr;
-    P.twx = static_cast<const C*>(t.twx);
-    P.twy = static_cast<const C*>(t.twy);
-    P.ptx = static_cast<const C*>(t.ptx);
-    P.pty = static_cast<const C*>(t.pty);
-    P.lamx = static_cast<const T*>(t.lamx);
-    P.lamy = static_cast<const T*>(t.lamy);
-    P.scale = (T)((2.0 / t.mx) * (2.0 / t.my));
-    P.Ro = (T)h->Ro;
-    if (h->layers == 2) {
-        P.f1 = (T)(h->Fr / h->delta);
-        P.f2 = (T)(h->Fr / (1.0 - h->delta));
-    }
-    P.bar = h->dbar;
-    P.bar_extra = h->fault == QG_FAULT_BARRIER_STALL ? 1u : 0u;
-    P.err = h->derr;
-    P.split = h->split_solve ? 1 : 0;
-    KTimer kt(h, s, QG_K_SOLVE);
-    QG_TRY(launch_solve<T>(P, engine ? engine : engine_for(h, t.mx, t.my), s));
-    return QG_OK;
-}
-
-// ---- solve-engine autotuner ---------------------------------------------
-// The FFT base radix of the solve (4: many threads per sequence pair; 16:
-// fewer passes and instructions) is timed on the handle's own elliptic grid
-// when the handle is created by timing a few whole steps with each (the
-// solve alone, timed back to back, ranks them differently: in a step the
-// fine sweep has just streamed its fields through L2), and the faster one is
-// kept.  Results are cached per (nx, ny, levels, layers, dtype) for the
-// process and, when the environment variable QG_TUNE_CACHE names a file, in
-// that file (one line "nx ny levels layers esz engine" per entry).
-// QG_SOLVE_ENGINE=4|16 forces a choice.  Other grids use the size rule.
-
 int engine_rule(int mx, int my) { return (long)mx * my >= (1L << 21) ? 16 : 4; }
 
 int engine_for(qg_ctx* h, int mx, int my) {
