@@ -108,6 +108,9 @@ def alg_bytes_per_launch(cls, nx, ny, levels, esz):
         # x pass (read rhs, write transposed), y pass (read, write), inverse
         # x pass (read, write): six passes over the elliptic grid
         return esz * 6 * Nc
+    if cls == "cfl":
+        # the adaptive step's reduction reads the step's first streamfunction
+        return esz * (N if levels == 0 else Nc)
     return None
 
 

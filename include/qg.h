@@ -163,7 +163,8 @@ typedef enum qg_kernel_class {
     QG_K_SOLVE = 1,      /* elliptic solve: sine transforms + eigenvalues    */
     QG_K_PROLONG = 2,    /* prolongation (Eq. pro), when not fused           */
     QG_K_FINE = 3,       /* fine-grid Arakawa / dissipation / forcing / RK   */
-    QG_K_COUNT = 4
+    QG_K_CFL = 4,        /* max |grad psi| of the adaptive step (Eq. dt)     */
+    QG_K_COUNT = 5
 } qg_kernel_class;
 
 /* qg_set_timing -- enable (1) or disable (0) per-kernel timing.  When
@@ -200,6 +201,21 @@ qg_status qg_step_kernel_count(qg_handle h, int64_t* count);
 qg_status qg_poisson_solve_noalloc(int32_t nx, int32_t ny, double dx, double dy,
                                    qg_dtype dtype, const void* rhs, void* psi,
                                    void* cuda_stream);
+
+/* qg_set_cfl -- adaptive time step (Section 4.2, Eq. dt).  c > 0: every
+ * later step uses dt = min(basin.dt, c min(dx, dy) / max|grad psi^n|), the
+ * maximum of |psi_x| and |psi_y| (central differences) over the interior
+ * fine nodes of the streamfunction of the step's first stage (reduced on the
+ * device; the paper states c <= 1); basin.dt caps the step (a flow at rest
+ * has no Eq. dt bound).  c = 0: the fixed basin.dt again.  One-layer
+ * handles only (QG_ERR_UNSUPPORTED otherwise, or while an adjoint tape is
+ * open).  Re-captures the step graph.  Errors: QG_ERR_ARG for c < 0.     */
+qg_status qg_set_cfl(qg_handle h, double c);
+
+/* qg_get_time -- model time since creation or the last qg_set_state, and
+ * the size of the last step (host pointers; either may be NULL).
+ * Synchronises the handle's stream.                                        */
+qg_status qg_get_time(qg_handle h, double* t, double* dt_last);
 
 /* qg_inject_fault -- failure-detection test switch (the paper has no
  * counterpart).  kind = QG_FAULT_BARRIER_STALL makes every later elliptic

@@ -106,6 +106,9 @@ struct qg_ctx {
     int* derr = nullptr;           // device error flag of bounded waits
     unsigned* dbar = nullptr;      // grid-barrier counters of the solve kernel
     Tape* tape = nullptr;          // adjoint tape (qg_tape_begin .. qg_tape_end)
+    double cfl = 0.0;              // > 0: adaptive step (Eq. dt) with this CFL number
+    double time_host = 0.0;        // model time of two-layer handles (fixed dt)
+    double* dclock = nullptr;      // device {umax bits, time, last dt, spare}
 };
 
 namespace qg {
@@ -492,6 +495,7 @@ qg_status autotune_solve(qg_ctx* h) {
     }
     if (h->ct) QG_TRY(cudaMemsetAsync(h->ct, 0, h->plane_t * h->layers * h->esz, h->stream));
     if (h->part) QG_TRY(cudaMemsetAsync(h->part, 0, 4 * h->plane_c * h->esz, h->stream));
+    QG_TRY(cudaMemsetAsync(h->dclock, 0, sizeof(double) * 4, h->stream));
     h->part_valid = false;
     QG_TRY(cudaStreamSynchronize(h->stream));
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -632,6 +636,22 @@ qg_status stage_fused(qg_ctx* h, int s_idx, cudaStream_t s) {
     p.dt = (T)h->dt;
     p.a = (T)A[s_idx];
     p.b = (T)B[s_idx];
+    p.umax = nullptr;
+    p.cfl_h = h->cfl * std::fmin(h->dx, h->dy);
+    p.dt_cap = h->dt;
+    p.clock = h->dclock + 1;
+    p.last_stage = s_idx == 2;
+    if (h->cfl > 0.0) {
+        p.umax = reinterpret_cast<const unsigned long long*>(h->dclock);
+        if (s_idx == 0) {
+            // Eq. dt from psi^n, the streamfunction of this first stage
+            QG_TRY(cudaMemsetAsync(h->dclock, 0, sizeof(double), s));
+            KTimer kc(h, s, QG_K_CFL);
+            QG_TRY(launch_cfl_max<T>(static_cast<const T*>(p.psi), p.ldp, h->nx, h->ny,
+                                     h->levels, h->dx, h->dy,
+                                     reinterpret_cast<unsigned long long*>(h->dclock), s));
+        }
+    }
     FineMaps m;
     m.w = h->tm_halo[s_idx];
     m.wn = h->tm_int[0];
@@ -791,6 +811,7 @@ static qg_status create_ctx(const qg_basin* b, int layers, double Re, double Ro,
     if (s == QG_OK && layers == 1 && levels >= 1) guard(dev_alloc(h, &h->part, 4 * h->plane_c * h->esz));
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->derr, sizeof(int) * 4));
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dbar, sizeof(unsigned) * 4));
+    if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dclock, sizeof(double) * 4));
     if (s == QG_OK && layers == 1) {
         const int rows = (int)fine_tile_rows(h->esz);
         for (int k = 0; k < 3 && s == QG_OK; ++k) {
@@ -885,6 +906,8 @@ qg_status qg_set_state(qg_handle h, const void* field, int layer) {
     char* dst = static_cast<char*>(h->w[0]) + (size_t)layer * h->plane_f * h->esz;
     QG_TRY(copy_in(dst, h->ldf, field, h->nx - 1, h->ny - 1, h->esz, h->stream));
     h->part_valid = false;
+    h->time_host = 0.0;
+    QG_TRY(cudaMemsetAsync(h->dclock, 0, sizeof(double) * 4, h->stream));
     return QG_OK;
 }
 
@@ -1018,6 +1041,7 @@ qg_status qg_step(qg_handle h, int64_t n) {
     }
     Tape* tp = h->tape;
     if (tp && (tp->reversing || tp->recorded + n > tp->max_steps)) return QG_ERR_ARG;
+    if (h->layers == 2) h->time_host += (double)n * h->dt;
     const size_t bytes = h->plane_f * h->esz;
     for (int64_t k = 0; k < n; ++k) {
         QG_TRY(cudaGraphLaunch(h->gexec, h->stream));
@@ -1039,6 +1063,34 @@ qg_status qg_set_timing(qg_handle h, int enable) {
         drop_graph(h);
         h->timing = enable != 0;
     }
+    return QG_OK;
+}
+
+qg_status qg_set_cfl(qg_handle h, double c) {
+    if (!h || !(c >= 0.0) || !std::isfinite(c)) return QG_ERR_ARG;
+    if (c > 0.0 && (h->layers != 1 || h->tape)) return QG_ERR_UNSUPPORTED;
+    if (c != h->cfl) {
+        QG_TRY(cudaStreamSynchronize(h->stream));
+        drop_graph(h);
+        h->cfl = c;
+    }
+    return QG_OK;
+}
+
+qg_status qg_get_time(qg_handle h, double* t, double* dt_last) {
+    if (!h) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    double v[4] = {0, 0, 0, 0};
+    if (h->layers == 1) {
+        QG_TRY(cudaMemcpyAsync(v, h->dclock, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+        QG_TRY(cudaStreamSynchronize(h->stream));
+    } else {
+        QG_TRY(cudaStreamSynchronize(h->stream));
+        v[1] = h->time_host;
+        v[2] = h->dt;
+    }
+    if (t) *t = v[1];
+    if (dt_last) *dt_last = v[2];
     return QG_OK;
 }
 
@@ -1166,9 +1218,11 @@ qg_status tape_state(qg_ctx* h, int64_t t, const void** out) {
     const int64_t start = t / tp->every * tp->every;
     if (tp->seg_start != start) {
         if (!tp->live) {
-            QG_TRY(cudaMalloc(&tp->live, bytes));
+            QG_TRY(cudaMalloc(&tp->live, bytes + 4 * sizeof(double)));
             tp->allocs.push_back(tp->live);
             QG_TRY(cudaMemcpyAsync(tp->live, h->w[0], bytes, cudaMemcpyDeviceToDevice, h->stream));
+            QG_TRY(cudaMemcpyAsync(static_cast<char*>(tp->live) + bytes, h->dclock,
+                                   4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         }
         void* c = tp->ckpt[start / tp->every];
         QG_TRY(cudaMemcpyAsync(tp->seg[0], c, bytes, cudaMemcpyDeviceToDevice, h->stream));
@@ -1283,7 +1337,7 @@ extern "C" {
 
 qg_status qg_tape_begin(qg_handle h, int64_t every, int64_t max_steps) {
     if (!h || every < 1 || max_steps < 1) return QG_ERR_ARG;
-    if (h->layers != 1) return QG_ERR_UNSUPPORTED;
+    if (h->layers != 1 || h->cfl > 0.0) return QG_ERR_UNSUPPORTED;
     if (h->latched != QG_OK) return qg_last_error(h);
     tape_release(h);
     Tape* tp = new (std::nothrow) Tape();
@@ -1326,8 +1380,10 @@ qg_status qg_tape_end(qg_handle h) {
     Tape* tp = h->tape;
     if (!tp) return QG_OK;
     if (tp->live) {
-        QG_TRY(cudaMemcpyAsync(h->w[0], tp->live, h->plane_f * h->esz, cudaMemcpyDeviceToDevice,
-                               h->stream));
+        const size_t bytes = h->plane_f * h->esz;
+        QG_TRY(cudaMemcpyAsync(h->w[0], tp->live, bytes, cudaMemcpyDeviceToDevice, h->stream));
+        QG_TRY(cudaMemcpyAsync(h->dclock, static_cast<const char*>(tp->live) + bytes,
+                               4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         h->part_valid = false;
     }
     tape_release(h);

@@ -181,6 +181,17 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
     }
     pdl_wait();
     if (LV == 0 && threadIdx.x == 0) tma_load_2d(smem_u32(sp), &tm_p, x0 - 4, yc - 1, bar);
+    // the step size: fixed, or Eq. dt from this step's first streamfunction
+    double dtd = (double)p.dt;
+    if (p.umax) {
+        const double u = __longlong_as_double((long long)*p.umax);
+        dtd = u > 0.0 ? fmin(p.dt_cap, p.cfl_h / u) : p.dt_cap;
+    }
+    const T dt = (T)dtd;
+    if (p.last_stage && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        p.clock[0] += dtd;
+        p.clock[1] = dtd;
+    }
     const int mx = nx >> LV, my = ny >> LV;
     const int I_lo = (x0 - 1) >> LV;      // may be -1
     const int J_lo = (yc - 1) >> LV;      // may be -1
@@ -343,7 +354,7 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                 const T lap = (q10 + qm0 - T(2) * q00) * p.c_lapx + (q01 + q0m - T(2) * q00) * p.c_lapy;
                 T Gv = fma(-p.c_jac, jac, fv[q] + lap);
                 Gv = fma(-p.c_beta, beta, Gv);
-                out[q] = fma(p.a, wn[q], p.b * fma(p.dt, Gv, q00));
+                out[q] = fma(p.a, wn[q], p.b * fma(dt, Gv, q00));
             }
             const bool quad_ok = row_ok && xq >= 1 && xq + 3 <= nx - 1;
             if (quad_ok) {

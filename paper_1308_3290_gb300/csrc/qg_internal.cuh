@@ -159,7 +159,20 @@ struct FusedParams {
     int ldc;               // their pitch
     int* err;              // set to 1 when a bounded wait runs out
     T c_jac, c_beta, c_lapx, c_lapy, dt, a, b;
+    // Adaptive step (Eq. dt): when umax is non-null, dt = min(dt_cap,
+    // cfl_h / u) with u the double whose bits *umax holds (u = 0: dt_cap).
+    const unsigned long long* umax;
+    double cfl_h, dt_cap;
+    double* clock;         // {time, last dt}: the last stage adds its dt
+    int last_stage;
 };
+
+// u = max over interior fine nodes of |psi_x| and |psi_y| (central
+// differences, Eq. dt) of psi prolonged `levels` times from `psi` (pitch
+// ldp); atomically max-ed into *umax as the bits of a non-negative double.
+template <typename T>
+cudaError_t launch_cfl_max(const T* psi, int ldp, int nx, int ny, int levels, double dx,
+                           double dy, unsigned long long* umax, cudaStream_t s);
 
 // TMA tensor maps of the inputs of one fused launch: w^(s) and the fine psi
 // with halo boxes, w^n and the forcing field with interior boxes.  Unused

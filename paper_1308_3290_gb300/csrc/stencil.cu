@@ -175,6 +175,67 @@ cudaError_t launch_prolong(const T* coarse, int ldc, T* fine, int ldf, int nx,
     return cudaGetLastError();
 }
 
+// psi at fine node (i, j) prolonged `levels` times from the elliptic grid c:
+// bilinear interpolation at spacing 2^-levels (Eq. pro applied l times).
+template <typename T>
+__device__ __forceinline__ T prolonged_at(const T* __restrict__ c, int ldc, int i, int j,
+                                          int levels) {
+    if (levels == 0) return c[(size_t)j * ldc + i];
+    const int f = 1 << levels;
+    const int I = i >> levels, J = j >> levels;
+    const int di = i & (f - 1), dj = j & (f - 1);
+    const T a = T(di) / T(f), b = T(dj) / T(f);
+    const T* r0 = c + (size_t)J * ldc + I;
+    const T v00 = r0[0];
+    const T v10 = di ? r0[1] : T(0);
+    const T v01 = dj ? r0[ldc] : T(0);
+    const T v11 = (di && dj) ? r0[ldc + 1] : T(0);
+    return (T(1) - b) * ((T(1) - a) * v00 + a * v10) + b * ((T(1) - a) * v01 + a * v11);
+}
+
+// Eq. dt's denominator: max over interior fine nodes of |psi_x| and |psi_y|
+// (central differences); the block maximum is max-ed into *umax as the bits
+// of a non-negative double (bit order = value order), so the result does not
+// depend on the order of the blocks.
+template <typename T>
+__global__ void cfl_max_kernel(const T* __restrict__ psi, int ldp, int nx, int ny, int levels,
+                               double inv2dx, double inv2dy, unsigned long long* umax) {
+    __shared__ double red[32];
+    double m = 0.0;
+    const long n = (long)(nx - 1) * (ny - 1);
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        const int i = 1 + (int)(e % (nx - 1)), j = 1 + (int)(e / (nx - 1));
+        const T gx = prolonged_at(psi, ldp, i + 1, j, levels) - prolonged_at(psi, ldp, i - 1, j, levels);
+        const T gy = prolonged_at(psi, ldp, i, j + 1, levels) - prolonged_at(psi, ldp, i, j - 1, levels);
+        m = fmax(m, fmax(fabs((double)gx) * inv2dx, fabs((double)gy) * inv2dy));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) atomicMax(umax, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+template <typename T>
+cudaError_t launch_cfl_max(const T* psi, int ldp, int nx, int ny, int levels, double dx,
+                           double dy, unsigned long long* umax, cudaStream_t s) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long n = (long)(nx - 1) * (ny - 1);
+    long blocks = (n + 255) / 256;
+    if (blocks > 8L * nsm) blocks = 8L * nsm;
+    cfl_max_kernel<T><<<(int)blocks, 256, 0, s>>>(psi, ldp, nx, ny, levels, 0.5 / dx, 0.5 / dy,
+                                                  umax);
+    return cudaGetLastError();
+}
+
 cudaError_t copy_in(void* padded, int ld, const void* dense, int nxm1, int nym1,
                     size_t esz, cudaStream_t s) {
     char* dst = static_cast<char*>(padded) + (size_t)(ld + 1) * esz;
@@ -201,7 +262,9 @@ cudaError_t copy_out(void* dense, const void* padded, int ld, int nxm1, int nym1
     template cudaError_t launch_restrict<T>(const T*, int, T*, int, int, int, int,  \
                                             cudaStream_t);                          \
     template cudaError_t launch_prolong<T>(const T*, int, T*, int, int, int, int,   \
-                                           cudaStream_t);
+                                           cudaStream_t);                            \
+    template cudaError_t launch_cfl_max<T>(const T*, int, int, int, int, double,     \
+                                           double, unsigned long long*, cudaStream_t);
 QG_INST(float)
 QG_INST(double)
 #undef QG_INST

@@ -40,9 +40,10 @@ EXPORTS = [
     "qg_ensemble_create", "qg_ensemble_member", "qg_ensemble_step",
     "qg_ensemble_kernel_count", "qg_ensemble_synchronize", "qg_ensemble_destroy",
     "qg_tape_begin", "qg_tape_end", "qg_adjoint_step", "qg_energy_gradient",
+    "qg_set_cfl", "qg_get_time",
 ]
 
-KERNEL_CLASSES = ["restrict", "solve", "prolong", "fine"]
+KERNEL_CLASSES = ["restrict", "solve", "prolong", "fine", "cfl"]
 
 
 class QGError(RuntimeError):
@@ -105,6 +106,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "qg_tape_end": [vp],
         "qg_adjoint_step": [vp, i64, vp, vp],
         "qg_energy_gradient": [vp, dbl, vp],
+        "qg_set_cfl": [vp, dbl],
+        "qg_get_time": [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -239,6 +242,17 @@ def qg_adjoint_step(h: int, n: int, lam, dJdF) -> None:
 
 def qg_energy_gradient(h: int, scale: float, g) -> None:
     _check(load().qg_energy_gradient(h, scale, _ptr(g)), "qg_energy_gradient")
+
+
+def qg_set_cfl(h: int, c: float) -> None:
+    _check(load().qg_set_cfl(h, c), "qg_set_cfl")
+
+
+def qg_get_time(h: int) -> tuple[float, float]:
+    """(model time, last step size)."""
+    t, dt = ctypes.c_double(), ctypes.c_double()
+    _check(load().qg_get_time(h, ctypes.byref(t), ctypes.byref(dt)), "qg_get_time")
+    return t.value, dt.value
 
 
 def qg_synchronize(h: int) -> None:

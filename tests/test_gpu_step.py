@@ -118,3 +118,32 @@ def test_full_size_workload_one_step():
     got = gpu_run(nx, ny, 2, "f32", w0, 1, dt=2e-6)
     assert rel_l2(got, ref) <= 1e-6
     assert rel_l2(got - w0, ref - w0) <= 1e-3   # the increment itself
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 1e-4)])
+def test_adaptive_step_matches_oracle(levels, dtype, tol):
+    """Eq. dt with a device-side max |grad psi|: the state, the model time and
+    the last step size follow the oracle; the step starts at the cap and
+    drops below it as the forcing spins the flow up."""
+    require_gpu()
+    nx, ny, n, c = 64, 128, 30, 0.3
+    w0 = inputs.perturbation(nx, ny, seed=3) * 50.0
+    ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=1e-3)
+    ref, dts = O.run_adaptive(w0, ob, n, c)
+    assert max(dts) == ob.dt and min(dts) < 0.7 * ob.dt
+    b = qg.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=1e-3, dtype=dtype)
+    qg.qg_set_cfl(b.h, c)
+    b.set_state(w0)
+    b.step(n)
+    assert rel_l2(to_np(b.state()), ref) <= tol
+    t, dt_last = qg.qg_get_time(b.h)
+    rt = 1e-12 if dtype == "f64" else 1e-5
+    assert t == pytest.approx(sum(dts), rel=rt)
+    assert dt_last == pytest.approx(dts[-1], rel=rt)
+    qg.qg_set_cfl(b.h, 0.0)             # back to the fixed step
+    b.set_state(w0)
+    b.step(3)
+    t, dt_last = qg.qg_get_time(b.h)
+    assert dt_last == pytest.approx(1e-3, rel=1e-6) and t == pytest.approx(3e-3, rel=1e-6)
+    b.close()
