@@ -270,7 +270,8 @@ qg_status get_level(qg_ctx* h, int lv, const LevelTables** out) {
     }
     if (s != QG_OK) return s;
     const double pi = 3.14159265358979323846;
-    std::vector<double> lx(t.mx + 1, 0.0), ly(t.my + 1, 0.0);
+    // padded to a multiple of 4 entries: the solve copies them in 16-byte units
+    std::vector<double> lx((t.mx + 1 + 3) / 4 * 4, 0.0), ly((t.my + 1 + 3) / 4 * 4, 0.0);
     for (int k = 1; k < t.mx; ++k) lx[k] = (2.0 * std::cos(pi * k / t.mx) - 2.0) / (t.dxc * t.dxc);
     for (int l = 1; l < t.my; ++l) ly[l] = (2.0 * std::cos(pi * l / t.my) - 2.0) / (t.dyc * t.dyc);
     s = upload_real(h, &t.lamx, lx);

@@ -399,7 +399,8 @@ __device__ __forceinline__ void load_pair(const SolveParams<T>& P, int ph, const
 // (OPY 1) or Eqs. isub-1/2 (OPY 2), written back as the next input.
 template <typename T, int OPY>
 __device__ __forceinline__ void mode_solve(const SolveParams<T>& P, const PairAt& a,
-                                           const Geo32& g, CT<T>* cb, int t) {
+                                           const Geo32& g, CT<T>* cb, int t,
+                                           const T* __restrict__ lamy) {
     const T lxa = __ldg(P.lamx + a.ra), lxb = __ldg(P.lamx + a.rb);
 #pragma unroll 4
     for (int i = 0; i < 16; ++i) {
@@ -408,7 +409,7 @@ __device__ __forceinline__ void mode_solve(const SolveParams<T>& P, const PairAt
         const T Fa = T(-0.5) * z.y, Fb = T(0.5) * z.x;
         T x = T(0), y = T(0);
         if (l > 0 && a.va) {
-            const T ly = __ldg(P.lamy + l);
+            const T ly = lamy[l];
             if (OPY == 1) {
                 x = Fa * (P.scale / (lxa + ly));
                 if (a.vb) y = Fb * (P.scale / (lxb + ly));
@@ -458,13 +459,69 @@ __device__ __forceinline__ void store_pair(const SolveParams<T>& P, int ph, cons
     }
 }
 
+// Shared-memory layout (bytes): pair buffers | x twiddles | y twiddles | lamy;
+// the tables are staged only when they fit (Tabs::staged).
+struct Tabs {
+    int buf, tx, ty, ly, end;      // offsets and total
+    int nx, ny, nl;                // bytes of each table
+    bool staged;
+};
+__host__ __device__ inline int al16i(int v) { return (v + 15) / 16 * 16; }
+__host__ __device__ inline Tabs tabs_for(int lgx, int lgy, int threads, int esz, int ntx,
+                                         int nty, int my) {
+    Tabs b;
+    const int a1 = buf_cplx(lgx, threads), a2 = buf_cplx(lgy, threads);
+    b.buf = al16i((a1 > a2 ? a1 : a2) * 2 * esz);
+    b.nx = ntx * 2 * esz;
+    b.ny = nty * 2 * esz;
+    b.nl = ((my + 1 + 3) / 4 * 4) * esz;
+    b.tx = b.buf;
+    b.ty = b.tx + al16i(b.nx);
+    b.ly = b.ty + al16i(b.ny);
+    const int total = b.ly + al16i(b.nl);
+    b.staged = total - b.buf <= 48 * 1024;
+    b.end = b.staged ? total : b.buf;
+    return b;
+}
+
 template <typename T, int OPY>
 __global__ void __launch_bounds__(kT, 1)
-solve32_kernel(SolveParams<T> P, int lgx, int lgy) {
+solve32_kernel(SolveParams<T> P, int lgx, int lgy, Tabs tb) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
     CT<T>* bufs = reinterpret_cast<CT<T>*>(smem);
+    const CT<T>* ptx = P.ptx;
+    const CT<T>* pty = P.pty;
+    const T* lamy = P.lamy;
+    const uint32_t bar = smem_u32(&mbar);
+    if (tb.staged) {
+        // the constant tables of both directions, copied once per CTA
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                         "r"(tb.nx + tb.ny + tb.nl) : "memory");
+            if (tb.nx) bulk_copy(smem_u32(smem + tb.tx), P.ptx, tb.nx, bar);
+            if (tb.ny) bulk_copy(smem_u32(smem + tb.ty), P.pty, tb.ny, bar);
+            bulk_copy(smem_u32(smem + tb.ly), P.lamy, tb.nl, bar);
+        }
+        ptx = reinterpret_cast<const CT<T>*>(smem + tb.tx);
+        pty = reinterpret_cast<const CT<T>*>(smem + tb.ty);
+        lamy = reinterpret_cast<const T*>(smem + tb.ly);
+    }
     pdl_wait();
     pdl_trigger();   // the next fine stage may start staging its own inputs
+    if (tb.staged) {
+        const bool ok = mbar_wait(bar, 0, kSpin);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicExch(P.err, 1);
+            (void)mbar_wait(bar, 0, kSpin);     // let copies in flight land
+            return;
+        }
+    }
     const int ph0 = P.split ? P.phase : 0, ph1 = P.split ? P.phase + 1 : 3;
     for (int ph = ph0; ph < ph1; ++ph) {
         if (ph > ph0 && !grid_sync(P.bar, P.bar_extra, kSpin)) {
@@ -472,7 +529,7 @@ solve32_kernel(SolveParams<T> P, int lgx, int lgy) {
             return;
         }
         const Geo32 g = geo32(ph == 1 ? lgy : lgx);
-        const CT<T>* tw = ph == 1 ? P.pty : P.ptx;
+        const CT<T>* tw = ph == 1 ? pty : ptx;
         const int grp = threadIdx.x / g.G, t = threadIdx.x % g.G;
         CT<T>* cb = bufs + grp * g.buf;
         const Sync sy{1 + grp, g.G};
@@ -487,7 +544,7 @@ solve32_kernel(SolveParams<T> P, int lgx, int lgy) {
             const int nfft = ph == 1 ? 2 : 1;
 #pragma unroll 1
             for (int f = 0; f < nfft; ++f) {
-                if (f == 1) mode_solve<T, OPY>(P, a, g, cb, t);
+                if (f == 1) mode_solve<T, OPY>(P, a, g, cb, t, lamy);
                 fft_rt<T>(cb, t, g, tw, sy);
             }
             store_pair<T, OPY>(P, ph, a, g, cb, t);
@@ -517,9 +574,11 @@ int log2i(int v) {
 template <typename T, int OPY>
 cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
     auto k = solve32_kernel<T, OPY>;
-    const size_t sm = solve32_smem_bytes(P.mx, P.my, sizeof(T));
     const int lgx = log2i(2 * P.mx), lgy = log2i(2 * P.my);
     const int threads = cta_threads(lgx, lgy, least_threads());
+    const Tabs tb = tabs_for(lgx, lgy, threads, (int)sizeof(T), (int)pass_table_size(2 * P.mx),
+                             (int)pass_table_size(2 * P.my), P.my);
+    const size_t sm = tb.end;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, per = 0;
@@ -549,12 +608,12 @@ cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
         at[0].val.cooperative = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, k, P, lgx, lgy);
+        return cudaLaunchKernelEx(&cfg, k, P, lgx, lgy, tb);
     }
     SolveParams<T> Q = P;
     for (int ph = 0; ph < 3; ++ph) {
         Q.phase = ph;
-        if ((e = cudaLaunchKernelEx(&cfg, k, Q, lgx, lgy)) != cudaSuccess) return e;
+        if ((e = cudaLaunchKernelEx(&cfg, k, Q, lgx, lgy, tb)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -569,8 +628,8 @@ bool solve32_supports(int mx, int my) {
 
 size_t solve32_smem_bytes(int mx, int my, size_t esz) {
     const int lx = log2i(2 * mx), ly = log2i(2 * my), th = cta_threads(lx, ly, least_threads());
-    const int a = buf_cplx(lx, th), b = buf_cplx(ly, th);
-    return (size_t)(a > b ? a : b) * 2 * esz;
+    return tabs_for(lx, ly, th, (int)esz, (int)pass_table_size(2 * mx),
+                    (int)pass_table_size(2 * my), my).end;
 }
 
 template <typename T>
