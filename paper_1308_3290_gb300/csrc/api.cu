@@ -35,8 +35,8 @@ struct LevelTables {
     void* twy = nullptr;   // e^{i pi t/my}, t < 2 my
     void* lamx = nullptr;  // (2 cos(pi k/mx) - 2)/dxc^2, k = 0..mx
     void* lamy = nullptr;  // (2 cos(pi l/my) - 2)/dyc^2, l = 0..my
-    void* ptx = nullptr;   // radix-32 engine pass twiddles for L = 2 mx (Cx<T>)
-    void* pty = nullptr;   //   and for L = 2 my
+    void* ptx[2] = {nullptr, nullptr};  // warp-group engine pass twiddles for L = 2 mx
+    void* pty[2] = {nullptr, nullptr};  //   and L = 2 my, radix 32 [0] and 16 [1] (Cx<T>)
 };
 
 }  // namespace
@@ -224,16 +224,16 @@ qg_status upload_real(qg_ctx* h, void** out, const std::vector<double>& v) {
 }
 
 // Per-pass twiddles of the radix-32 engine for FFT length L (cached).
-qg_status get_pass_table(qg_ctx* h, int L, void** out) {
-    const int key = -L;   // shares the twiddle cache; negative keys
+qg_status get_pass_table(qg_ctx* h, int L, int rad, void** out) {
+    const int key = -(L * 64 + rad);   // shares the twiddle cache; negative keys
     auto it = h->twcache.find(key);
     if (it != h->twcache.end()) {
         *out = it->second;
         return QG_OK;
     }
-    const size_t n = pass_table_size(L);
+    const size_t n = pass_table_size(L, rad);
     std::vector<double> re(n + 1), im(n + 1), v(2 * (n + 1));
-    pass_table(L, re.data(), im.data());
+    pass_table(L, rad, re.data(), im.data());
     for (size_t k = 0; k <= n; ++k) {
         v[2 * k] = re[k];
         v[2 * k + 1] = im[k];
@@ -264,9 +264,11 @@ qg_status get_level(qg_ctx* h, int lv, const LevelTables** out) {
     t.dyc = h->dy * (double)(1 << lv);
     qg_status s = get_twiddles(h, t.mx, &t.twx);
     if (s == QG_OK) s = get_twiddles(h, t.my, &t.twy);
-    if (s == QG_OK && solve32_supports(t.mx, t.my)) {
-        s = get_pass_table(h, 2 * t.mx, &t.ptx);
-        if (s == QG_OK) s = get_pass_table(h, 2 * t.my, &t.pty);
+    for (int r = 0; r < 2 && s == QG_OK; ++r) {
+        const int rad = r == 0 ? 32 : 16;
+        if (!solve32_supports(t.mx, t.my, rad)) continue;
+        s = get_pass_table(h, 2 * t.mx, rad, &t.ptx[r]);
+        if (s == QG_OK) s = get_pass_table(h, 2 * t.my, rad, &t.pty[r]);
     }
     if (s != QG_OK) return s;
     const double pi = 3.14159265358979323846;
@@ -350,8 +352,9 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
     P.ld_tr = ld_tr;
     P.twx = static_cast<const C*>(t.twx);
     P.twy = static_cast<const C*>(t.twy);
-    P.ptx = static_cast<const C*>(t.ptx);
-    P.pty = static_cast<const C*>(t.pty);
+    const int eng = engine ? engine : engine_for(h, t.mx, t.my);
+    P.ptx = static_cast<const C*>(t.ptx[eng == 33 ? 1 : 0]);
+    P.pty = static_cast<const C*>(t.pty[eng == 33 ? 1 : 0]);
     P.lamx = static_cast<const T*>(t.lamx);
     P.lamy = static_cast<const T*>(t.lamy);
     P.scale = (T)((2.0 / t.mx) * (2.0 / t.my));
@@ -365,21 +368,22 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
     P.err = h->derr;
     P.split = h->split_solve ? 1 : 0;
     KTimer kt(h, s, QG_K_SOLVE);
-    QG_TRY(launch_solve<T>(P, engine ? engine : engine_for(h, t.mx, t.my), s));
+    QG_TRY(launch_solve<T>(P, eng, s));
     return QG_OK;
 }
 
 // ---- solve-engine autotuner ---------------------------------------------
 // The FFT engine of the solve (shared-memory Stockham engine with base
 // radix 4: many threads per sequence pair, or 16: fewer passes and
-// instructions; or the warp-group radix-32 engine of solve32.cu) is chosen
+// instructions; or the warp-group engine of solve32.cu with 32 or 16 values
+// per thread, engines 32 and 33) is chosen
 // per handle when it is created, by timing a few whole steps with each
 // engine that supports the elliptic grid (the solve alone, timed back to
 // back, ranks them differently: in a step the fine sweep has just streamed
 // its fields through L2), and the fastest is kept.  Results are cached per
 // (nx, ny, levels, layers, dtype) for the process and, when the environment
 // variable QG_TUNE_CACHE names a file, in that file (one line
-// "nx ny levels layers esz engine" per entry).  QG_SOLVE_ENGINE=4|16|32
+// "nx ny levels layers esz engine" per entry).  QG_SOLVE_ENGINE=4|16|32|33
 // forces a choice where that engine supports the grid.  Other grids use the
 // size rule.
 
@@ -405,7 +409,7 @@ void tune_file_load() {
     if (!f) return;
     int a, b, c, d, x, e;
     while (std::fscanf(f, "%d %d %d %d %d %d", &a, &b, &c, &d, &x, &e) == 6)
-        if (e == 4 || e == 16 || e == 32) g_tune_cache[TuneKey(a, b, c, d, x)] = e;
+        if (e == 4 || e == 16 || e == 32 || e == 33) g_tune_cache[TuneKey(a, b, c, d, x)] = e;
     std::fclose(f);
 }
 
@@ -430,7 +434,8 @@ template <typename T>
 float time_steps(qg_ctx* h, int engine) {
     const LevelTables* t = nullptr;
     if (get_level(h, h->levels, &t) != QG_OK) return 1e30f;
-    if (!solve_engine_supports(t->mx, t->my, sizeof(T), engine) || (engine == 32 && !t->ptx))
+    if (!solve_engine_supports(t->mx, t->my, sizeof(T), engine) ||
+        (engine >= 32 && !t->ptx[engine == 33 ? 1 : 0]))
         return 1e30f;
     h->solve_engine = engine;
     drop_graph(h);
@@ -461,7 +466,8 @@ qg_status autotune_solve(qg_ctx* h) {
     if (st != QG_OK) return st;
     if (const char* force = std::getenv("QG_SOLVE_ENGINE")) {
         const int e = std::atoi(force);
-        if (solve_engine_supports(t->mx, t->my, sizeof(T), e) && (e != 32 || t->ptx)) {
+        if (solve_engine_supports(t->mx, t->my, sizeof(T), e) &&
+            (e < 32 || t->ptx[e == 33 ? 1 : 0])) {
             h->solve_engine = e;
             return QG_OK;
         }
@@ -478,14 +484,19 @@ qg_status autotune_solve(qg_ctx* h) {
     }
     const float t4 = time_steps<T>(h, 4);
     const float t32 = time_steps<T>(h, 32);
+    const float t33 = time_steps<T>(h, 33);
     const float t16 = time_steps<T>(h, 16);
     // a candidate that cannot run on this grid is a tuning result, not an error
     h->latched = QG_OK;
     (void)cudaGetLastError();
     drop_graph(h);
-    if (t4 >= 1e29f && t16 >= 1e29f && t32 >= 1e29f) return fail(h, QG_ERR_CUDA);
-    h->solve_engine = t16 < t4 ? 16 : 4;
-    if (t32 < (t16 < t4 ? t16 : t4)) h->solve_engine = 32;
+    const float tt[4] = {t4, t16, t32, t33};
+    const int ee[4] = {4, 16, 32, 33};
+    int best = 0;
+    for (int k = 1; k < 4; ++k)
+        if (tt[k] < tt[best]) best = k;
+    if (tt[best] >= 1e29f) return fail(h, QG_ERR_CUDA);
+    h->solve_engine = ee[best];
     // the timing steps ran on the handle's buffers: return them to rest
     cudaStreamSynchronize(h->stream);
     for (void* p : {h->w[0], h->w[1], h->w[2], h->psi}) {

@@ -55,8 +55,8 @@ struct SolveParams {
     T* out[2];
     const typename Cx<T>::type* twx;   // e^{i pi t/mx}, t < 2 mx
     const typename Cx<T>::type* twy;   // e^{i pi t/my}, t < 2 my
-    const typename Cx<T>::type* ptx;   // radix-32 engine: per-pass twiddles, 2 mx
-    const typename Cx<T>::type* pty;   //   (see pass_table_size), and 2 my
+    const typename Cx<T>::type* ptx;   // warp-group engine: per-pass twiddles for
+    const typename Cx<T>::type* pty;   //   2 mx and 2 my (see pass_table_size)
     const T* lamx;                      // (2 cos(pi k/mx) - 2)/dx^2, k = 0..mx
     const T* lamy;                      // (2 cos(pi l/my) - 2)/dy^2, l = 0..my
     T scale, Ro, f1, f2;
@@ -68,21 +68,24 @@ struct SolveParams {
                          // grid barriers; 1: three plain launches, one per pass
     int phase;           // the pass a split launch runs (set by launch_solve)
 };
-// engine: base radix of the FFT passes, 4 or 16 (see dst_engine.cuh), or 32
-// (warp-group engine, solve32.cu; lengths 16 <= mx, my <= 4096)
+// engine: base radix of the FFT passes of the shared-memory engine, 4 or 16
+// (see dst_engine.cuh), or the warp-group engine of solve32.cu with 32
+// (engine 32) or 16 (engine 33) values per thread
 template <typename T>
 cudaError_t launch_solve(const SolveParams<T>& P, int engine, cudaStream_t s);
 size_t solve_smem_bytes(int mx, int my, size_t esz, int engine);
 bool solve_engine_supports(int mx, int my, size_t esz, int engine);
-// The radix-32 engine's twiddle table for an FFT of length L = 2N: for each
-// pass p >= 1 (radix R_p, sub-transform size Ns_p), R_p x Ns_p entries
-// e^{-2 pi i r k / (R_p Ns_p)} at [r Ns_p + k], passes in order.
-size_t pass_table_size(int L);
-void pass_table(int L, double* re, double* im);   // pass_table_size(L) entries
+// The warp-group engine's twiddle table for an FFT of length L = 2N with
+// `rad` values per thread: for each pass p >= 1 (radix R_p, sub-transform
+// size Ns_p), R_p x Ns_p entries e^{-2 pi i r k / (R_p Ns_p)} at
+// [r Ns_p + k], passes in order.
+size_t pass_table_size(int L, int rad);
+void pass_table(int L, int rad, double* re, double* im);   // pass_table_size entries
 template <typename T>
-cudaError_t launch_solve32(const SolveParams<T>& P, cudaStream_t s);
-size_t solve32_smem_bytes(int mx, int my, size_t esz);
-bool solve32_supports(int mx, int my);
+cudaError_t launch_solve32(const SolveParams<T>& P, int rad, cudaStream_t s);
+size_t solve32_smem_bytes(int mx, int my, size_t esz, int rad);
+bool solve32_supports(int mx, int my, int rad);
+inline int warp_engine_radix(int engine) { return engine == 33 ? 16 : 32; }
 
 // Full-weighting restriction applied `levels` times, as one hat-weighted
 // sum (fine -> level `levels`), interior coarse nodes only.

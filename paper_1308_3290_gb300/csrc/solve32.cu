@@ -32,24 +32,26 @@
 
 namespace qg {
 
-size_t pass_table_size(int L) {
-    int lg = 0;
+size_t pass_table_size(int L, int rad) {
+    int lg = 0, lr = 0;
     while ((1 << lg) < L) ++lg;
-    const int np = lg / 5, rem = lg % 5;
+    while ((1 << lr) < rad) ++lr;
+    const int np = lg / lr, rem = lg % lr;
     size_t n = 0;
-    int ns = 32;
-    for (int p = 1; p < np; ++p, ns *= 32) n += (size_t)32 * ns;
+    int ns = rad;
+    for (int p = 1; p < np; ++p, ns *= rad) n += (size_t)rad * ns;
     if (rem > 0 && np >= 1) n += (size_t)(1 << rem) * ns;
     return n;
 }
 
-void pass_table(int L, double* re, double* im) {
-    int lg = 0;
+void pass_table(int L, int rad, double* re, double* im) {
+    int lg = 0, lr = 0;
     while ((1 << lg) < L) ++lg;
-    const int np = lg / 5, rem = lg % 5;
+    while ((1 << lr) < rad) ++lr;
+    const int np = lg / lr, rem = lg % lr;
     const double pi = 3.14159265358979323846;
     size_t o = 0;
-    int ns = 32;
+    int ns = rad;
     auto block = [&](int R, int Ns) {
         for (int r = 0; r < R; ++r)
             for (int k = 0; k < Ns; ++k) {
@@ -59,7 +61,7 @@ void pass_table(int L, double* re, double* im) {
                 ++o;
             }
     };
-    for (int p = 1; p < np; ++p, ns *= 32) block(32, ns);
+    for (int p = 1; p < np; ++p, ns *= rad) block(rad, ns);
     if (rem > 0 && np >= 1) block(1 << rem, ns);
 }
 
@@ -69,33 +71,39 @@ using namespace eng;
 
 constexpr int kT = 256;                 // most threads per CTA
 constexpr int kSpin = 1 << 22;
-constexpr int kMinLog = 5, kMaxLog = 13;   // L = 32 .. 8192
 
 __host__ __device__ constexpr int px(int m) { return m + (m >> 5); }
 
-// Geometry of one FFT length L = 2^lg: N = L/2, G = L/32 threads per pair,
-// np radix-32 passes and a remainder pass of radix 2^rem (rem = 0: none).
+// Geometry of one FFT length L = 2^lg with RAD values per thread (RAD = 32
+// or 16): N = L/2, G = L/RAD threads per pair, np radix-RAD passes and a
+// remainder pass of radix 2^rem (rem = 0: none).
 struct Geo32 {
     int L, N, G, np, rem, buf;
 };
-__host__ __device__ inline Geo32 geo32(int lg) {
+__host__ __device__ inline int log2c(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+__host__ __device__ inline Geo32 geo32(int lg, int rad) {
     Geo32 g;
+    const int lr = log2c(rad);
     g.L = 1 << lg;
     g.N = g.L / 2;
-    g.G = g.L / 32;
-    g.np = lg / 5;
-    g.rem = lg % 5;
+    g.G = g.L / rad;
+    g.np = lg / lr;
+    g.rem = lg % lr;
     g.buf = px(g.L) + 2;    // padded complex per pair
     return g;
 }
 
 // CTA size: at least one pair group of the longer direction.
-__host__ __device__ inline int cta_threads(int lgx, int lgy, int least) {
-    const int g = (1 << (lgx > lgy ? lgx : lgy)) / 32;
+__host__ __device__ inline int cta_threads(int lgx, int lgy, int rad, int least) {
+    const int g = (1 << (lgx > lgy ? lgx : lgy)) / rad;
     return g < least ? least : g;
 }
-__host__ __device__ inline int buf_cplx(int lg, int threads) {
-    const Geo32 g = geo32(lg);
+__host__ __device__ inline int buf_cplx(int lg, int rad, int threads) {
+    const Geo32 g = geo32(lg, rad);
     return (threads / g.G) * g.buf;
 }
 
@@ -193,49 +201,54 @@ __device__ __forceinline__ void dft32(Cplx<T> (&v)[32]) {
     }
 }
 
-// One radix-32 Stockham pass (one 32-point DFT per thread, butterfly j = t):
-// input j + r G, twiddle table entry r NS + k (k = j mod NS), output
-// (j - k) 32 + k + r NS.  The first pass (NS = 1) reads the odd extension of
-// the stored z_0..z_{N-1}: element m = t + r G is z_m (r < 16), 0 (m = N),
+// One radix-RAD Stockham pass (one RAD-point DFT per thread, butterfly
+// j = t): input j + r G, twiddle table entry r NS + k (k = j mod NS), output
+// (j - k) RAD + k + r NS.  The first pass (NS = 1) reads the odd extension of
+// the stored z_0..z_{N-1}: element m = t + r G is z_m (r < RAD/2), 0 (m = N),
 // or -z_{L-m}.
-template <typename T>
-__device__ __forceinline__ void pass32(CT<T>* cb, int t, const Geo32& g, int NS, bool first,
-                                       const CT<T>* __restrict__ tw, const Sync& sy) {
+template <typename T, int RAD>
+__device__ __forceinline__ void passW(CT<T>* cb, int t, const Geo32& g, int NS, bool first,
+                                      const CT<T>* __restrict__ tw, const Sync& sy) {
+    constexpr int H = RAD / 2;
     const int k = t & (NS - 1);
-    Cplx<T> v[32];
+    Cplx<T> v[RAD];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
+    for (int r = 0; r < RAD; ++r) {
         if (!first) {
             v[r] = ldp<T>(cb, t + r * g.G);
-        } else if (r < 16) {
+        } else if (r < H) {
             v[r] = ldp<T>(cb, t + r * g.G);
         } else {
-            const int m = r == 16 ? g.N - t : (32 - r) * g.G - t;
-            const Cplx<T> z = (r == 16 && t == 0) ? Cplx<T>{T(0), T(0)} : ldp<T>(cb, m);
+            const int m = r == H ? g.N - t : (RAD - r) * g.G - t;
+            const Cplx<T> z = (r == H && t == 0) ? Cplx<T>{T(0), T(0)} : ldp<T>(cb, m);
             v[r] = Cplx<T>{-z.x, -z.y};
         }
     }
     if (!first) {
 #pragma unroll
-        for (int r = 1; r < 32; ++r) {
-            const CT<T> w = __ldg(tw + r * NS + k);
+        for (int r = 1; r < RAD; ++r) {
+            const CT<T> w = tw[r * NS + k];
             v[r] = cmul(v[r], w.x, w.y);
         }
     }
-    dft32<T>(v);
+    if constexpr (RAD == 32) dft32<T>(v);
+    else dft<T, RAD>(v);
     sy.sync();
-    const int d = (t - k) * 32 + k;
+    const int d = (t - k) * RAD + k;
 #pragma unroll
-    for (int r = 0; r < 32; ++r) stp<T>(cb, d + r * NS, v[r]);
+    for (int r = 0; r < RAD; ++r) {
+        if constexpr (RAD == 32) stp<T>(cb, d + r * NS, v[r]);
+        else stp<T>(cb, d + r * NS, v[out_slot<RAD>(r)]);
+    }
     sy.sync();
 }
 
-// The remainder pass, radix R < 32: 32/R butterflies j = t + b G per thread.
-// Out of line: inlined next to the radix-32 pass its registers spill.
-template <typename T, int R>
+// The remainder pass, radix R < RAD: RAD/R butterflies j = t + b G per
+// thread.  Out of line: inlined next to the radix-32 pass its registers spill.
+template <typename T, int R, int RAD>
 __device__ __noinline__ void passR(CT<T>* cb, int t, Geo32 g, int NS,
                                    const CT<T>* __restrict__ tw, Sync sy) {
-    constexpr int B = 32 / R;
+    constexpr int B = RAD / R;
     const int stride = g.L / R;
     Cplx<T> v[B][R];
 #pragma unroll
@@ -246,7 +259,7 @@ __device__ __noinline__ void passR(CT<T>* cb, int t, Geo32 g, int NS,
         for (int r = 0; r < R; ++r) v[b][r] = ldp<T>(cb, j + r * stride);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-            const CT<T> w = __ldg(tw + r * NS + k);
+            const CT<T> w = tw[r * NS + k];
             v[b][r] = cmul(v[b][r], w.x, w.y);
         }
         dft<T, R>(v[b]);
@@ -265,20 +278,26 @@ __device__ __noinline__ void passR(CT<T>* cb, int t, Geo32 g, int NS,
 
 // Forward FFT of length L of the odd extension of cb[0..N) in place; the
 // result Z_k is at cb[px(k)], k = 0..L-1.  Starts and ends with a group sync.
-template <typename T>
+template <typename T, int RAD>
 __device__ __forceinline__ void fft_rt(CT<T>* cb, int t, const Geo32& g, const CT<T>* tw,
                                        const Sync& sy) {
     sy.sync();
+    int ns = 1, off = 0;
 #pragma unroll 1
-    for (int p = 0; p < g.np; ++p) pass32<T>(cb, t, g, p == 0 ? 1 : 32, p == 0, tw, sy);
+    for (int p = 0; p < g.np; ++p) {
+        passW<T, RAD>(cb, t, g, ns, p == 0, tw + off, sy);
+        if (p > 0) off += RAD * ns;
+        ns *= RAD;
+    }
     if (g.rem > 0) {
-        const int ns = g.np >= 2 ? 1024 : 32;
-        const CT<T>* tr = tw + (g.np >= 2 ? 1024 : 0);
+        const CT<T>* tr = tw + off;
         switch (g.rem) {
-            case 1: passR<T, 2>(cb, t, g, ns, tr, sy); break;
-            case 2: passR<T, 4>(cb, t, g, ns, tr, sy); break;
-            case 3: passR<T, 8>(cb, t, g, ns, tr, sy); break;
-            default: passR<T, 16>(cb, t, g, ns, tr, sy); break;
+            case 1: passR<T, 2, RAD>(cb, t, g, ns, tr, sy); break;
+            case 2: passR<T, 4, RAD>(cb, t, g, ns, tr, sy); break;
+            case 3: passR<T, 8, RAD>(cb, t, g, ns, tr, sy); break;
+            default:
+                if constexpr (RAD == 32) passR<T, 16, RAD>(cb, t, g, ns, tr, sy);
+                break;
         }
     }
 }
@@ -366,7 +385,7 @@ __device__ __forceinline__ PairAt pair_at(const SolveParams<T>& P, int ph, int p
 //   phase 0: rows of the right-hand side (sum of the partial planes);
 //   phase 1: rows ka, kb of tr (element j at column j - 1);
 //   phase 2: rows of work (element j at column j - 1).
-template <typename T, int OPY>
+template <typename T, int OPY, int RAD>
 __device__ __forceinline__ void load_pair(const SolveParams<T>& P, int ph, const PairAt& a,
                                           const Geo32& g, CT<T>* cb, int t) {
     const T *sa = nullptr, *sb = nullptr;
@@ -379,7 +398,7 @@ __device__ __forceinline__ void load_pair(const SolveParams<T>& P, int ph, const
     }
     const int shift = ph == 0 ? 0 : 1;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < RAD / 8; ++i) {    // N = (RAD/2) G values, 4 per step
         const int c0 = 4 * (t + i * g.G);
         T x[4] = {T(0), T(0), T(0), T(0)}, y[4] = {T(0), T(0), T(0), T(0)};
         if (ph == 0) {
@@ -397,13 +416,13 @@ __device__ __forceinline__ void load_pair(const SolveParams<T>& P, int ph, const
 
 // Between the two y transforms of phase 1: the mode-space solve, Eq. ialpha
 // (OPY 1) or Eqs. isub-1/2 (OPY 2), written back as the next input.
-template <typename T, int OPY>
+template <typename T, int OPY, int RAD>
 __device__ __forceinline__ void mode_solve(const SolveParams<T>& P, const PairAt& a,
                                            const Geo32& g, CT<T>* cb, int t,
                                            const T* __restrict__ lamy) {
     const T lxa = __ldg(P.lamx + a.ra), lxb = __ldg(P.lamx + a.rb);
 #pragma unroll 4
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < RAD / 2; ++i) {
         const int l = t + i * g.G;
         const Cplx<T> z = ldp<T>(cb, l);
         const T Fa = T(-0.5) * z.y, Fb = T(0.5) * z.x;
@@ -429,12 +448,12 @@ __device__ __forceinline__ void mode_solve(const SolveParams<T>& P, const PairAt
 //   phase 0: tr[k][ra - 1], tr[k][rb - 1] (k >= 1);
 //   phase 1: work[j][ka - 1], work[j][kb - 1] (j >= 1);
 //   phase 2: out[ra][k], out[rb][k], k = 0..N-1 (k = 0 is the wall).
-template <typename T, int OPY>
+template <typename T, int OPY, int RAD>
 __device__ __forceinline__ void store_pair(const SolveParams<T>& P, int ph, const PairAt& a,
                                            const Geo32& g, const CT<T>* cb, int t) {
     if (!a.va) return;
 #pragma unroll 4
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < RAD / 2; ++i) {
         const int k = t + i * g.G;
         const CT<T> z = cb[px(k)];
         const T fa = T(-0.5) * z.y, fb = T(0.5) * z.x;
@@ -467,10 +486,10 @@ struct Tabs {
     bool staged;
 };
 __host__ __device__ inline int al16i(int v) { return (v + 15) / 16 * 16; }
-__host__ __device__ inline Tabs tabs_for(int lgx, int lgy, int threads, int esz, int ntx,
-                                         int nty, int my) {
+__host__ __device__ inline Tabs tabs_for(int lgx, int lgy, int rad, int threads, int esz,
+                                         int ntx, int nty, int my) {
     Tabs b;
-    const int a1 = buf_cplx(lgx, threads), a2 = buf_cplx(lgy, threads);
+    const int a1 = buf_cplx(lgx, rad, threads), a2 = buf_cplx(lgy, rad, threads);
     b.buf = al16i((a1 > a2 ? a1 : a2) * 2 * esz);
     b.nx = ntx * 2 * esz;
     b.ny = nty * 2 * esz;
@@ -484,7 +503,7 @@ __host__ __device__ inline Tabs tabs_for(int lgx, int lgy, int threads, int esz,
     return b;
 }
 
-template <typename T, int OPY>
+template <typename T, int OPY, int RAD>
 __global__ void __launch_bounds__(kT, 1)
 solve32_kernel(SolveParams<T> P, int lgx, int lgy, Tabs tb) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -528,7 +547,7 @@ solve32_kernel(SolveParams<T> P, int lgx, int lgy, Tabs tb) {
             if (threadIdx.x == 0) atomicExch(P.err, 1);
             return;
         }
-        const Geo32 g = geo32(ph == 1 ? lgy : lgx);
+        const Geo32 g = geo32(ph == 1 ? lgy : lgx, RAD);
         const CT<T>* tw = ph == 1 ? pty : ptx;
         const int grp = threadIdx.x / g.G, t = threadIdx.x % g.G;
         CT<T>* cb = bufs + grp * g.buf;
@@ -540,14 +559,14 @@ solve32_kernel(SolveParams<T> P, int lgx, int lgy, Tabs tb) {
         const int nslots = (npairs + per - 1) / per;
         for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
             const PairAt a = pair_at<T, OPY>(P, ph, slot * per + grp, npairs);
-            load_pair<T, OPY>(P, ph, a, g, cb, t);
+            load_pair<T, OPY, RAD>(P, ph, a, g, cb, t);
             const int nfft = ph == 1 ? 2 : 1;
 #pragma unroll 1
             for (int f = 0; f < nfft; ++f) {
-                if (f == 1) mode_solve<T, OPY>(P, a, g, cb, t, lamy);
-                fft_rt<T>(cb, t, g, tw, sy);
+                if (f == 1) mode_solve<T, OPY, RAD>(P, a, g, cb, t, lamy);
+                fft_rt<T, RAD>(cb, t, g, tw, sy);
             }
-            store_pair<T, OPY>(P, ph, a, g, cb, t);
+            store_pair<T, OPY, RAD>(P, ph, a, g, cb, t);
             sy.sync();
         }
     }
@@ -571,13 +590,14 @@ int log2i(int v) {
     return r;
 }
 
-template <typename T, int OPY>
+template <typename T, int OPY, int RAD>
 cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
-    auto k = solve32_kernel<T, OPY>;
+    auto k = solve32_kernel<T, OPY, RAD>;
     const int lgx = log2i(2 * P.mx), lgy = log2i(2 * P.my);
-    const int threads = cta_threads(lgx, lgy, least_threads());
-    const Tabs tb = tabs_for(lgx, lgy, threads, (int)sizeof(T), (int)pass_table_size(2 * P.mx),
-                             (int)pass_table_size(2 * P.my), P.my);
+    const int threads = cta_threads(lgx, lgy, RAD, least_threads());
+    const Tabs tb = tabs_for(lgx, lgy, RAD, threads, (int)sizeof(T),
+                             (int)pass_table_size(2 * P.mx, RAD),
+                             (int)pass_table_size(2 * P.my, RAD), P.my);
     const size_t sm = tb.end;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -588,7 +608,7 @@ cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
         return e;
     if (per < 1) return cudaErrorInvalidConfiguration;
     auto slots = [threads](int lg, int npairs) {
-        const int pairs = threads / ((1 << lg) / 32);
+        const int pairs = threads / ((1 << lg) / RAD);
         return (npairs + pairs - 1) / pairs;
     };
     const int rows = (P.my / 2) * P.layers;
@@ -620,25 +640,29 @@ cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
 
 }  // namespace
 
-bool solve32_supports(int mx, int my) {
-    const int lx = log2i(2 * mx), ly = log2i(2 * my);
-    return is_pow2(mx) && is_pow2(my) && lx >= kMinLog && lx <= kMaxLog && ly >= kMinLog &&
-           ly <= kMaxLog;
+// lengths 2N = 2^lg with lg in [log2(RAD), log2(RAD) + 8] (G <= 256 threads)
+bool solve32_supports(int mx, int my, int rad) {
+    const int lx = log2i(2 * mx), ly = log2i(2 * my), lr = log2i(rad);
+    return (rad == 16 || rad == 32) && is_pow2(mx) && is_pow2(my) && lx >= lr && ly >= lr &&
+           lx <= lr + 8 && ly <= lr + 8;
 }
 
-size_t solve32_smem_bytes(int mx, int my, size_t esz) {
-    const int lx = log2i(2 * mx), ly = log2i(2 * my), th = cta_threads(lx, ly, least_threads());
-    return tabs_for(lx, ly, th, (int)esz, (int)pass_table_size(2 * mx),
-                    (int)pass_table_size(2 * my), my).end;
+size_t solve32_smem_bytes(int mx, int my, size_t esz, int rad) {
+    const int lx = log2i(2 * mx), ly = log2i(2 * my);
+    const int th = cta_threads(lx, ly, rad, least_threads());
+    return tabs_for(lx, ly, rad, th, (int)esz, (int)pass_table_size(2 * mx, rad),
+                    (int)pass_table_size(2 * my, rad), my).end;
 }
 
 template <typename T>
-cudaError_t launch_solve32(const SolveParams<T>& P, cudaStream_t s) {
-    if (!solve32_supports(P.mx, P.my) || !P.ptx || !P.pty) return cudaErrorInvalidValue;
-    return P.layers == 2 ? launch32<T, 2>(P, s) : launch32<T, 1>(P, s);
+cudaError_t launch_solve32(const SolveParams<T>& P, int rad, cudaStream_t s) {
+    if (!solve32_supports(P.mx, P.my, rad) || !P.ptx || !P.pty) return cudaErrorInvalidValue;
+    if (rad == 16)
+        return P.layers == 2 ? launch32<T, 2, 16>(P, s) : launch32<T, 1, 16>(P, s);
+    return P.layers == 2 ? launch32<T, 2, 32>(P, s) : launch32<T, 1, 32>(P, s);
 }
 
-template cudaError_t launch_solve32<float>(const SolveParams<float>&, cudaStream_t);
-template cudaError_t launch_solve32<double>(const SolveParams<double>&, cudaStream_t);
+template cudaError_t launch_solve32<float>(const SolveParams<float>&, int, cudaStream_t);
+template cudaError_t launch_solve32<double>(const SolveParams<double>&, int, cudaStream_t);
 
 }  // namespace qg

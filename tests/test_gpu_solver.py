@@ -82,16 +82,16 @@ def test_two_layer_solve_parity():
         b.close()
 
 
-@pytest.mark.parametrize("engine", ["4", "16", "32"])
+@pytest.mark.parametrize("engine", ["4", "16", "32", "33"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_both_fft_engines(engine, dtype, monkeypatch):
-    """The solve has three FFT schedules (shared-memory engine with base
-    radix 4 or 16, warp-group engine with radix 32) chosen by the autotuner;
-    each must meet the same tolerance."""
+    """The solve has four FFT schedules (shared-memory engine with base
+    radix 4 or 16, warp-group engine with 32 or 16 values per thread) chosen
+    by the autotuner; each must meet the same tolerance."""
     require_gpu()
     monkeypatch.setenv("QG_SOLVE_ENGINE", engine)
     shapes = [(64, 128), (512, 1024), (2048, 256)]
-    if engine == "32":
+    if engine in ("32", "33"):
         shapes += [(16, 16), (32, 64), (256, 32), (4096, 64), (1024, 2048)]
     for nx, ny in shapes:
         b = qg.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=0, dt=1e-4, dtype=dtype)
@@ -102,11 +102,12 @@ def test_both_fft_engines(engine, dtype, monkeypatch):
         b.close()
 
 
+@pytest.mark.parametrize("engine", ["32", "33"])
 @pytest.mark.parametrize("levels", [0, 1, 2])
-def test_radix32_engine_in_the_step(levels, monkeypatch):
-    """100 FP64 steps with the warp-group engine forced, one layer and two."""
+def test_warp_engine_in_the_step(levels, engine, monkeypatch):
+    """100 FP64 steps with a warp-group engine forced, one layer and two."""
     require_gpu()
-    monkeypatch.setenv("QG_SOLVE_ENGINE", "32")
+    monkeypatch.setenv("QG_SOLVE_ENGINE", engine)
     nx, ny = 64, 128
     w0 = inputs.perturbation(nx, ny, seed=3) * 50.0
     ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=1e-4)
