@@ -217,6 +217,25 @@ qg_status qg_set_cfl(qg_handle h, double c);
  * Synchronises the handle's stream.                                        */
 qg_status qg_get_time(qg_handle h, double* t, double* dt_last);
 
+/* ---- time-mean statistics (Section 5.1: the time-mean streamfunction) ---
+ * qg_stats_begin -- from now on every step adds psi^n, the streamfunction of
+ * its first stage (CGP steps (ii)-(iv) applied to w^n), to an FP64 sum on
+ * the device: on the elliptic grid for l >= 1 (prolongation is linear, so
+ * the mean of the prolonged fields is the prolonged mean), on the fine grid
+ * for l = 0 and for two layers.  Restarts the sum.  Re-captures the step
+ * graph.  QG_ERR_UNSUPPORTED while an adjoint tape is open.               */
+qg_status qg_stats_begin(qg_handle h);
+
+/* qg_stats_mean_psi -- the mean of psi^n over the steps since
+ * qg_stats_begin, prolonged to the fine grid, into the caller's device
+ * buffer (exchange layout, handle dtype; NULL to read only the count) for
+ * `layer`; *count (may be NULL) = number of steps averaged.
+ * Errors: QG_ERR_ARG when no step has been accumulated.                    */
+qg_status qg_stats_mean_psi(qg_handle h, void* psi_mean, int layer, int64_t* count);
+
+/* qg_stats_end -- stop accumulating (the sum is kept).                     */
+qg_status qg_stats_end(qg_handle h);
+
 /* qg_inject_fault -- failure-detection test switch (the paper has no
  * counterpart).  kind = QG_FAULT_BARRIER_STALL makes every later elliptic
  * solve of the handle wait at its first grid barrier for one arrival more

@@ -40,7 +40,7 @@ __all__ = [
     "forcing_one_layer", "rhs_omega", "cgp_psi", "cgp_rhs", "tvdrk3",
     "cgprk3_step", "run", "rhs_q_form", "cgprk3_step_q_form",
     "kinetic_energy", "enstrophy", "max_velocity", "cfl_dt", "adaptive_dt",
-    "cgprk3_step_adaptive", "run_adaptive",
+    "cgprk3_step_adaptive", "run_adaptive", "mean_psi", "mean_psi_two_layer",
     "two_layer_cgp_psi", "two_layer_rhs", "cgprk3_step_two_layer",
     "interior", "embed",
 ]
@@ -547,3 +547,36 @@ def cgprk3_step_two_layer(Q1: np.ndarray, Q2: np.ndarray, b: TwoLayer):
 def with_levels(b, levels: int):
     """Copy of a basin description with another coarsening level."""
     return replace(b, levels=levels)
+
+
+# ---------------------------------------------------------------------------
+# Time means (Section 5.1: the time-mean streamfunction of the statistically
+# steady flow)
+# ---------------------------------------------------------------------------
+
+def mean_psi(omega0_int: np.ndarray, b: Basin, n0: int, n1: int) -> np.ndarray:
+    """Mean of psi^n = CGP steps (ii)-(iv) applied to w^n over the steps
+    n = n0..n1-1 of the run from w^0 = omega0 (interior array out)."""
+    w = embed(np.asarray(omega0_int, dtype=np.float64))
+    acc = np.zeros_like(w)
+    for n in range(n1):
+        if n >= n0:
+            acc += cgp_psi(w, b)
+        w = cgprk3_step(w, b)
+    return interior(acc) / (n1 - n0)
+
+
+def mean_psi_two_layer(Q1_int: np.ndarray, Q2_int: np.ndarray, b: TwoLayer, n0: int,
+                       n1: int):
+    """Two-layer version of ``mean_psi``: (mean psi_1, mean psi_2)."""
+    a1 = embed(np.asarray(Q1_int, dtype=np.float64))
+    a2 = embed(np.asarray(Q2_int, dtype=np.float64))
+    s1 = np.zeros_like(a1)
+    s2 = np.zeros_like(a2)
+    for n in range(n1):
+        if n >= n0:
+            p1, p2 = two_layer_cgp_psi(a1, a2, b)
+            s1 += p1
+            s2 += p2
+        a1, a2 = cgprk3_step_two_layer(a1, a2, b)
+    return interior(s1) / (n1 - n0), interior(s2) / (n1 - n0)

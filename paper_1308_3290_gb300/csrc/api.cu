@@ -108,6 +108,9 @@ struct qg_ctx {
     Tape* tape = nullptr;          // adjoint tape (qg_tape_begin .. qg_tape_end)
     double cfl = 0.0;              // > 0: adaptive step (Eq. dt) with this CFL number
     double time_host = 0.0;        // model time of two-layer handles (fixed dt)
+    bool stats = false;            // accumulate the first-stage psi of every step
+    double* stat_acc = nullptr;    // its FP64 sum (elliptic grid, or fine for l = 0 / 2 layers)
+    int64_t stat_count = 0;
     double* dclock = nullptr;      // device {umax bits, time, last dt, spare}
 };
 
@@ -558,6 +561,9 @@ qg_status stage(qg_ctx* h, int s_idx, cudaStream_t s) {
     void* wout = h->w[(s_idx + 1) % 3];
     qg_status st = project<T>(h, win, s);
     if (st != QG_OK) return st;
+    if (h->stats && s_idx == 0)
+        QG_TRY(launch_accumulate<T>(h->stat_acc, static_cast<const T*>(h->psi),
+                                    h->plane_f * h->layers, s));
     KTimer kt(h, s, QG_K_FINE);
     if (h->layers == 1) {
         StageParams<T> p;
@@ -626,6 +632,11 @@ qg_status stage_fused(qg_ctx* h, int s_idx, cudaStream_t s) {
                             h->plane_c, s, 4);
     }
     if (st != QG_OK) return st;
+    if (h->stats && s_idx == 0) {
+        const bool fine = h->levels == 0;
+        QG_TRY(launch_accumulate<T>(h->stat_acc, static_cast<const T*>(fine ? h->psi : h->cpsi),
+                                    fine ? h->plane_f : h->plane_c, s));
+    }
     FusedParams<T> p;
     p.nx = h->nx;
     p.ny = h->ny;
@@ -1054,6 +1065,7 @@ qg_status qg_step(qg_handle h, int64_t n) {
     Tape* tp = h->tape;
     if (tp && (tp->reversing || tp->recorded + n > tp->max_steps)) return QG_ERR_ARG;
     if (h->layers == 2) h->time_host += (double)n * h->dt;
+    if (h->stats) h->stat_count += n;
     const size_t bytes = h->plane_f * h->esz;
     for (int64_t k = 0; k < n; ++k) {
         QG_TRY(cudaGraphLaunch(h->gexec, h->stream));
@@ -1103,6 +1115,59 @@ qg_status qg_get_time(qg_handle h, double* t, double* dt_last) {
     }
     if (t) *t = v[1];
     if (dt_last) *dt_last = v[2];
+    return QG_OK;
+}
+
+qg_status qg_stats_begin(qg_handle h) {
+    if (!h) return QG_ERR_ARG;
+    if (h->tape) return QG_ERR_UNSUPPORTED;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    const bool fine = h->levels == 0 || h->layers == 2;
+    const size_t n = fine ? h->plane_f * h->layers : h->plane_c;
+    if (!h->stat_acc) {
+        qg_status s = dev_alloc(h, (void**)&h->stat_acc, n * sizeof(double));
+        if (s != QG_OK) return s;
+    }
+    QG_TRY(cudaMemsetAsync(h->stat_acc, 0, n * sizeof(double), h->stream));
+    h->stat_count = 0;
+    if (!h->stats) {
+        QG_TRY(cudaStreamSynchronize(h->stream));
+        drop_graph(h);
+        h->stats = true;
+    }
+    return QG_OK;
+}
+
+qg_status qg_stats_mean_psi(qg_handle h, void* psi_mean, int layer, int64_t* count) {
+    if (!h || layer < 0 || layer >= h->layers) return QG_ERR_ARG;
+    if (!h->stats || h->stat_count == 0) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    if (count) *count = h->stat_count;
+    if (!psi_mean) return QG_OK;
+    const double sc = 1.0 / (double)h->stat_count;
+    const bool fine = h->levels == 0 || h->layers == 2;
+    const LevelTables* t = nullptr;
+    qg_status st = get_level(h, h->levels, &t);
+    if (st != QG_OK) return st;
+    const double* acc = h->stat_acc + (fine ? (size_t)layer * h->plane_f : 0);
+    const int ld = fine ? h->ldf : t->ldc;
+    const int lv = fine ? 0 : h->levels;
+    if (h->dtype == QG_F64)
+        QG_TRY(launch_mean_out<double>(static_cast<double*>(psi_mean), acc, ld, sc, h->nx, h->ny,
+                                       lv, h->stream));
+    else
+        QG_TRY(launch_mean_out<float>(static_cast<float*>(psi_mean), acc, ld, sc, h->nx, h->ny,
+                                      lv, h->stream));
+    return QG_OK;
+}
+
+qg_status qg_stats_end(qg_handle h) {
+    if (!h) return QG_ERR_ARG;
+    if (h->stats) {
+        QG_TRY(cudaStreamSynchronize(h->stream));
+        drop_graph(h);
+        h->stats = false;
+    }
     return QG_OK;
 }
 
@@ -1349,7 +1414,7 @@ extern "C" {
 
 qg_status qg_tape_begin(qg_handle h, int64_t every, int64_t max_steps) {
     if (!h || every < 1 || max_steps < 1) return QG_ERR_ARG;
-    if (h->layers != 1 || h->cfl > 0.0) return QG_ERR_UNSUPPORTED;
+    if (h->layers != 1 || h->cfl > 0.0 || h->stats) return QG_ERR_UNSUPPORTED;
     if (h->latched != QG_OK) return qg_last_error(h);
     tape_release(h);
     Tape* tp = new (std::nothrow) Tape();
@@ -1585,6 +1650,8 @@ qg_status qg_ensemble_step(qg_ensemble e, int64_t n) {
     }
     qg_status s = ensemble_build(e);
     if (s != QG_OK) return s;
+    for (qg_ctx* h : e->m)
+        if (h->stats) h->stat_count += n;
     for (int64_t k = 0; k < n; ++k)
         if (cudaGraphLaunch(e->gexec, e->stream) != cudaSuccess) {
             (void)cudaGetLastError();

@@ -170,6 +170,14 @@ struct FusedParams {
     int last_stage;
 };
 
+// acc[e] += src[e] for the n elements of a padded plane (FP64 sums).
+template <typename T>
+cudaError_t launch_accumulate(double* acc, const T* src, size_t n, cudaStream_t s);
+// dense[(j-1)(nx-1) + i-1] = scale * (acc prolonged `levels` times)(i, j)
+template <typename T>
+cudaError_t launch_mean_out(T* dense, const double* acc, int ldacc, double scale, int nx,
+                            int ny, int levels, cudaStream_t s);
+
 // u = max over interior fine nodes of |psi_x| and |psi_y| (central
 // differences, Eq. dt) of psi prolonged `levels` times from `psi` (pitch
 // ldp); atomically max-ed into *umax as the bits of a non-negative double.

@@ -236,6 +236,39 @@ cudaError_t launch_cfl_max(const T* psi, int ldp, int nx, int ny, int levels, do
     return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void accumulate_kernel(double* __restrict__ acc, const T* __restrict__ src, size_t n) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * blockDim.x)
+        acc[e] += (double)src[e];
+}
+
+template <typename T>
+__global__ void mean_out_kernel(T* __restrict__ dense, const double* __restrict__ acc, int ldacc,
+                                double scale, int nx, int ny, int levels) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    if (i >= nx || j >= ny) return;
+    dense[(size_t)(j - 1) * (nx - 1) + (i - 1)] = (T)(scale * prolonged_at(acc, ldacc, i, j, levels));
+}
+
+template <typename T>
+cudaError_t launch_accumulate(double* acc, const T* src, size_t n, cudaStream_t s) {
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    accumulate_kernel<T><<<(int)blocks, 256, 0, s>>>(acc, src, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mean_out(T* dense, const double* acc, int ldacc, double scale, int nx,
+                            int ny, int levels, cudaStream_t s) {
+    const dim3 block(32, 8);
+    const dim3 grid((nx - 1 + 31) / 32, (ny - 1 + 7) / 8);
+    mean_out_kernel<T><<<grid, block, 0, s>>>(dense, acc, ldacc, scale, nx, ny, levels);
+    return cudaGetLastError();
+}
+
 cudaError_t copy_in(void* padded, int ld, const void* dense, int nxm1, int nym1,
                     size_t esz, cudaStream_t s) {
     char* dst = static_cast<char*>(padded) + (size_t)(ld + 1) * esz;
@@ -264,7 +297,10 @@ cudaError_t copy_out(void* dense, const void* padded, int ld, int nxm1, int nym1
     template cudaError_t launch_prolong<T>(const T*, int, T*, int, int, int, int,   \
                                            cudaStream_t);                            \
     template cudaError_t launch_cfl_max<T>(const T*, int, int, int, int, double,     \
-                                           double, unsigned long long*, cudaStream_t);
+                                           double, unsigned long long*, cudaStream_t); \
+    template cudaError_t launch_accumulate<T>(double*, const T*, size_t, cudaStream_t); \
+    template cudaError_t launch_mean_out<T>(T*, const double*, int, double, int, int,  \
+                                            int, cudaStream_t);
 QG_INST(float)
 QG_INST(double)
 #undef QG_INST

@@ -40,7 +40,7 @@ EXPORTS = [
     "qg_ensemble_create", "qg_ensemble_member", "qg_ensemble_step",
     "qg_ensemble_kernel_count", "qg_ensemble_synchronize", "qg_ensemble_destroy",
     "qg_tape_begin", "qg_tape_end", "qg_adjoint_step", "qg_energy_gradient",
-    "qg_set_cfl", "qg_get_time",
+    "qg_set_cfl", "qg_get_time", "qg_stats_begin", "qg_stats_mean_psi", "qg_stats_end",
 ]
 
 KERNEL_CLASSES = ["restrict", "solve", "prolong", "fine", "cfl"]
@@ -108,6 +108,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "qg_energy_gradient": [vp, dbl, vp],
         "qg_set_cfl": [vp, dbl],
         "qg_get_time": [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
+        "qg_stats_begin": [vp],
+        "qg_stats_mean_psi": [vp, vp, i32, ctypes.POINTER(i64)],
+        "qg_stats_end": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -253,6 +256,23 @@ def qg_get_time(h: int) -> tuple[float, float]:
     t, dt = ctypes.c_double(), ctypes.c_double()
     _check(load().qg_get_time(h, ctypes.byref(t), ctypes.byref(dt)), "qg_get_time")
     return t.value, dt.value
+
+
+def qg_stats_begin(h: int) -> None:
+    _check(load().qg_stats_begin(h), "qg_stats_begin")
+
+
+def qg_stats_mean_psi(h: int, out=None, layer: int = 0) -> int:
+    """Write the time-mean first-stage psi into `out` (if given); returns the
+    number of steps averaged."""
+    c = ctypes.c_int64()
+    _check(load().qg_stats_mean_psi(h, _ptr(out) if out is not None else None, layer,
+                                    ctypes.byref(c)), "qg_stats_mean_psi")
+    return c.value
+
+
+def qg_stats_end(h: int) -> None:
+    _check(load().qg_stats_end(h), "qg_stats_end")
 
 
 def qg_synchronize(h: int) -> None:

@@ -147,3 +147,49 @@ def test_adaptive_step_matches_oracle(levels, dtype, tol):
     t, dt_last = qg.qg_get_time(b.h)
     assert dt_last == pytest.approx(1e-3, rel=1e-6) and t == pytest.approx(3e-3, rel=1e-6)
     b.close()
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_time_mean_psi_matches_oracle(levels, dtype, tol):
+    """The device-side time mean of the first-stage streamfunction over steps
+    n0..n1-1 (Section 5.1's time-mean field)."""
+    torch = require_gpu()
+    nx, ny, n0, n1 = 64, 128, 5, 25
+    w0 = inputs.perturbation(nx, ny, seed=14) * 50.0
+    ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=1e-4)
+    ref = O.mean_psi(w0, ob, n0, n1)
+    b = qg.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=1e-4, dtype=dtype)
+    b.set_state(w0)
+    b.step(n0)
+    qg.qg_stats_begin(b.h)
+    b.step(n1 - n0)
+    out = torch.empty((ny - 1, nx - 1), dtype=b.tdtype, device="cuda")
+    assert qg.qg_stats_mean_psi(b.h, out) == n1 - n0
+    b.synchronize()
+    assert rel_l2(to_np(out), ref) <= tol
+    qg.qg_stats_end(b.h)
+    b.close()
+
+
+def test_time_mean_psi_two_layers():
+    torch = require_gpu()
+    p = dict(Ro=2.49e-4, Fr=0.087, delta=0.2, sigma=1.43e-3)
+    A = 3.57e-7
+    Q1 = inputs.smooth_field(64, 64, seed=1, amp=0.05, noise=0.01)
+    Q2 = inputs.smooth_field(64, 64, seed=2, amp=0.02, noise=0.01)
+    ob = O.TwoLayer(64, 64, A=A, levels=1, dt=1e-4, **p)
+    r1, r2 = O.mean_psi_two_layer(Q1, Q2, ob, 2, 12)
+    b = qg.Basin(64, 64, Re=p["Ro"] / A, levels=1, dt=1e-4, dtype="f64", layers=2,
+                 y0=-0.5, y1=0.5, **p)
+    b.set_state(Q1, 0)
+    b.set_state(Q2, 1)
+    b.step(2)
+    qg.qg_stats_begin(b.h)
+    b.step(10)
+    for layer, ref in ((0, r1), (1, r2)):
+        out = torch.empty((63, 63), dtype=torch.float64, device="cuda")
+        assert qg.qg_stats_mean_psi(b.h, out, layer) == 10
+        b.synchronize()
+        assert rel_l2(to_np(out), ref) <= 1e-11
+    b.close()

@@ -124,3 +124,24 @@ def test_adaptive_dt_rules():
     w2, dt2 = O.cgprk3_step_adaptive(w, b, 1e9)             # capped
     assert dt2 == b.dt
     assert np.array_equal(w2, O.cgprk3_step(w, b))
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_mean_psi_is_the_projection_of_the_mean_state(levels):
+    """psi^n is linear in w^n (P S R), so the time mean of psi^n equals the
+    projection of the time-mean state, computed here from the states of an
+    independent run."""
+    b = O.Basin(32, 64, levels=levels, dt=1e-4)
+    w0 = inputs.perturbation(32, 64, seed=12) * 50.0
+    got = O.mean_psi(w0, b, 3, 9)
+    w = O.embed(w0)
+    states = []
+    for n in range(9):
+        if n >= 3:
+            states.append(w)
+        w = O.cgprk3_step(w, b)
+    wbar = sum(states) / len(states)
+    mx, my, dxc, dyc = b.coarse()
+    ref = O.interior(O.prolong_levels(O.embed(O.poisson_solve(
+        O.interior(O.restrict_levels(wbar, levels)), mx, my, dxc, dyc)), levels))
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
