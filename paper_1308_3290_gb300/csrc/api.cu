@@ -35,8 +35,8 @@ struct LevelTables {
     void* twy = nullptr;   // e^{i pi t/my}, t < 2 my
     void* lamx = nullptr;  // (2 cos(pi k/mx) - 2)/dxc^2, k = 0..mx
     void* lamy = nullptr;  // (2 cos(pi l/my) - 2)/dyc^2, l = 0..my
-    void* ptx[2] = {nullptr, nullptr};  // warp-group engine pass twiddles for L = 2 mx
-    void* pty[2] = {nullptr, nullptr};  //   and L = 2 my, radix 32 [0] and 16 [1] (Cx<T>)
+    void* ptx[3] = {nullptr, nullptr, nullptr};  // warp-group engine pass twiddles for
+    void* pty[3] = {nullptr, nullptr, nullptr};  //   L = 2 mx and 2 my, engines 32/33/34
 };
 
 }  // namespace
@@ -267,8 +267,8 @@ qg_status get_level(qg_ctx* h, int lv, const LevelTables** out) {
     t.dyc = h->dy * (double)(1 << lv);
     qg_status s = get_twiddles(h, t.mx, &t.twx);
     if (s == QG_OK) s = get_twiddles(h, t.my, &t.twy);
-    for (int r = 0; r < 2 && s == QG_OK; ++r) {
-        const int rad = r == 0 ? 32 : 16;
+    for (int r = 0; r < 3 && s == QG_OK; ++r) {
+        const int rad = warp_engine_radix(32 + r);
         if (!solve32_supports(t.mx, t.my, rad)) continue;
         s = get_pass_table(h, 2 * t.mx, rad, &t.ptx[r]);
         if (s == QG_OK) s = get_pass_table(h, 2 * t.my, rad, &t.pty[r]);
@@ -356,8 +356,8 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
     P.twx = static_cast<const C*>(t.twx);
     P.twy = static_cast<const C*>(t.twy);
     const int eng = engine ? engine : engine_for(h, t.mx, t.my);
-    P.ptx = static_cast<const C*>(t.ptx[eng == 33 ? 1 : 0]);
-    P.pty = static_cast<const C*>(t.pty[eng == 33 ? 1 : 0]);
+    P.ptx = is_warp_engine(eng) ? static_cast<const C*>(t.ptx[eng - 32]) : nullptr;
+    P.pty = is_warp_engine(eng) ? static_cast<const C*>(t.pty[eng - 32]) : nullptr;
     P.lamx = static_cast<const T*>(t.lamx);
     P.lamy = static_cast<const T*>(t.lamy);
     P.scale = (T)((2.0 / t.mx) * (2.0 / t.my));
@@ -378,15 +378,15 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
 // ---- solve-engine autotuner ---------------------------------------------
 // The FFT engine of the solve (shared-memory Stockham engine with base
 // radix 4: many threads per sequence pair, or 16: fewer passes and
-// instructions; or the warp-group engine of solve32.cu with 32 or 16 values
-// per thread, engines 32 and 33) is chosen
+// instructions; or the warp-group engine of solve32.cu with 32, 16 or 8
+// values per thread, engines 32, 33, 34) is chosen
 // per handle when it is created, by timing a few whole steps with each
 // engine that supports the elliptic grid (the solve alone, timed back to
 // back, ranks them differently: in a step the fine sweep has just streamed
 // its fields through L2), and the fastest is kept.  Results are cached per
 // (nx, ny, levels, layers, dtype) for the process and, when the environment
 // variable QG_TUNE_CACHE names a file, in that file (one line
-// "nx ny levels layers esz engine" per entry).  QG_SOLVE_ENGINE=4|16|32|33
+// "nx ny levels layers esz engine" per entry).  QG_SOLVE_ENGINE=4|16|32|33|34
 // forces a choice where that engine supports the grid.  Other grids use the
 // size rule.
 
@@ -412,7 +412,7 @@ void tune_file_load() {
     if (!f) return;
     int a, b, c, d, x, e;
     while (std::fscanf(f, "%d %d %d %d %d %d", &a, &b, &c, &d, &x, &e) == 6)
-        if (e == 4 || e == 16 || e == 32 || e == 33) g_tune_cache[TuneKey(a, b, c, d, x)] = e;
+        if (e == 4 || e == 16 || is_warp_engine(e)) g_tune_cache[TuneKey(a, b, c, d, x)] = e;
     std::fclose(f);
 }
 
@@ -438,7 +438,7 @@ float time_steps(qg_ctx* h, int engine) {
     const LevelTables* t = nullptr;
     if (get_level(h, h->levels, &t) != QG_OK) return 1e30f;
     if (!solve_engine_supports(t->mx, t->my, sizeof(T), engine) ||
-        (engine >= 32 && !t->ptx[engine == 33 ? 1 : 0]))
+        (is_warp_engine(engine) && !t->ptx[engine - 32]))
         return 1e30f;
     h->solve_engine = engine;
     drop_graph(h);
@@ -470,7 +470,7 @@ qg_status autotune_solve(qg_ctx* h) {
     if (const char* force = std::getenv("QG_SOLVE_ENGINE")) {
         const int e = std::atoi(force);
         if (solve_engine_supports(t->mx, t->my, sizeof(T), e) &&
-            (e < 32 || t->ptx[e == 33 ? 1 : 0])) {
+            (!is_warp_engine(e) || t->ptx[e - 32])) {
             h->solve_engine = e;
             return QG_OK;
         }
@@ -488,15 +488,16 @@ qg_status autotune_solve(qg_ctx* h) {
     const float t4 = time_steps<T>(h, 4);
     const float t32 = time_steps<T>(h, 32);
     const float t33 = time_steps<T>(h, 33);
+    const float t34 = time_steps<T>(h, 34);
     const float t16 = time_steps<T>(h, 16);
     // a candidate that cannot run on this grid is a tuning result, not an error
     h->latched = QG_OK;
     (void)cudaGetLastError();
     drop_graph(h);
-    const float tt[4] = {t4, t16, t32, t33};
-    const int ee[4] = {4, 16, 32, 33};
+    const float tt[5] = {t4, t16, t32, t33, t34};
+    const int ee[5] = {4, 16, 32, 33, 34};
     int best = 0;
-    for (int k = 1; k < 4; ++k)
+    for (int k = 1; k < 5; ++k)
         if (tt[k] < tt[best]) best = k;
     if (tt[best] >= 1e29f) return fail(h, QG_ERR_CUDA);
     h->solve_engine = ee[best];

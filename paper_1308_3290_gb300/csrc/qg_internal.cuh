@@ -69,8 +69,8 @@ struct SolveParams {
     int phase;           // the pass a split launch runs (set by launch_solve)
 };
 // engine: base radix of the FFT passes of the shared-memory engine, 4 or 16
-// (see dst_engine.cuh), or the warp-group engine of solve32.cu with 32
-// (engine 32) or 16 (engine 33) values per thread
+// (see dst_engine.cuh), or the warp-group engine of solve32.cu with 32, 16
+// or 8 values per thread (engines 32, 33, 34)
 template <typename T>
 cudaError_t launch_solve(const SolveParams<T>& P, int engine, cudaStream_t s);
 size_t solve_smem_bytes(int mx, int my, size_t esz, int engine);
@@ -85,7 +85,9 @@ template <typename T>
 cudaError_t launch_solve32(const SolveParams<T>& P, int rad, cudaStream_t s);
 size_t solve32_smem_bytes(int mx, int my, size_t esz, int rad);
 bool solve32_supports(int mx, int my, int rad);
-inline int warp_engine_radix(int engine) { return engine == 33 ? 16 : 32; }
+// engines 32, 33, 34: the warp-group engine with 32, 16, 8 values per thread
+inline int warp_engine_radix(int engine) { return engine == 34 ? 8 : (engine == 33 ? 16 : 32); }
+inline bool is_warp_engine(int engine) { return engine >= 32 && engine <= 34; }
 
 // Full-weighting restriction applied `levels` times, as one hat-weighted
 // sum (fine -> level `levels`), interior coarse nodes only.

@@ -354,7 +354,7 @@ size_t solve_smem_bytes(int mx, int my, size_t esz, int engine) {
 }
 
 bool solve_engine_supports(int mx, int my, size_t esz, int engine) {
-    if (engine == 32 || engine == 33) {
+    if (is_warp_engine(engine)) {
         const int rad = warp_engine_radix(engine);
         return solve32_supports(mx, my, rad) && solve32_smem_bytes(mx, my, esz, rad) <= 200 * 1024;
     }
@@ -376,7 +376,7 @@ static cudaError_t launch_engine(const SolveParams<T>& P, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_solve(const SolveParams<T>& P, int engine, cudaStream_t s) {
-    if (engine == 32 || engine == 33) return launch_solve32<T>(P, warp_engine_radix(engine), s);
+    if (is_warp_engine(engine)) return launch_solve32<T>(P, warp_engine_radix(engine), s);
     return engine == 4 ? launch_engine<T, 4>(P, s) : launch_engine<T, 16>(P, s);
 }
 

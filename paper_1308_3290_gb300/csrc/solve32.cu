@@ -294,7 +294,9 @@ __device__ __forceinline__ void fft_rt(CT<T>* cb, int t, const Geo32& g, const C
         switch (g.rem) {
             case 1: passR<T, 2, RAD>(cb, t, g, ns, tr, sy); break;
             case 2: passR<T, 4, RAD>(cb, t, g, ns, tr, sy); break;
-            case 3: passR<T, 8, RAD>(cb, t, g, ns, tr, sy); break;
+            case 3:
+                if constexpr (RAD > 8) passR<T, 8, RAD>(cb, t, g, ns, tr, sy);
+                break;
             default:
                 if constexpr (RAD == 32) passR<T, 16, RAD>(cb, t, g, ns, tr, sy);
                 break;
@@ -504,7 +506,7 @@ __host__ __device__ inline Tabs tabs_for(int lgx, int lgy, int rad, int threads,
 }
 
 template <typename T, int OPY, int RAD>
-__global__ void __launch_bounds__(kT, 1)
+__global__ void __launch_bounds__(kT, (RAD <= 16 && sizeof(T) == 4) ? 2 : 1)
 solve32_kernel(SolveParams<T> P, int lgx, int lgy, Tabs tb) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
@@ -643,8 +645,8 @@ cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
 // lengths 2N = 2^lg with lg in [log2(RAD), log2(RAD) + 8] (G <= 256 threads)
 bool solve32_supports(int mx, int my, int rad) {
     const int lx = log2i(2 * mx), ly = log2i(2 * my), lr = log2i(rad);
-    return (rad == 16 || rad == 32) && is_pow2(mx) && is_pow2(my) && lx >= lr && ly >= lr &&
-           lx <= lr + 8 && ly <= lr + 8;
+    return (rad == 8 || rad == 16 || rad == 32) && is_pow2(mx) && is_pow2(my) && lx >= lr &&
+           ly >= lr && lx <= lr + 8 && ly <= lr + 8;
 }
 
 size_t solve32_smem_bytes(int mx, int my, size_t esz, int rad) {
@@ -657,6 +659,8 @@ size_t solve32_smem_bytes(int mx, int my, size_t esz, int rad) {
 template <typename T>
 cudaError_t launch_solve32(const SolveParams<T>& P, int rad, cudaStream_t s) {
     if (!solve32_supports(P.mx, P.my, rad) || !P.ptx || !P.pty) return cudaErrorInvalidValue;
+    if (rad == 8)
+        return P.layers == 2 ? launch32<T, 2, 8>(P, s) : launch32<T, 1, 8>(P, s);
     if (rad == 16)
         return P.layers == 2 ? launch32<T, 2, 16>(P, s) : launch32<T, 1, 16>(P, s);
     return P.layers == 2 ? launch32<T, 2, 32>(P, s) : launch32<T, 1, 32>(P, s);

@@ -82,7 +82,7 @@ def test_two_layer_solve_parity():
         b.close()
 
 
-@pytest.mark.parametrize("engine", ["4", "16", "32", "33"])
+@pytest.mark.parametrize("engine", ["4", "16", "32", "33", "34"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_both_fft_engines(engine, dtype, monkeypatch):
     """The solve has four FFT schedules (shared-memory engine with base
@@ -91,7 +91,7 @@ def test_both_fft_engines(engine, dtype, monkeypatch):
     require_gpu()
     monkeypatch.setenv("QG_SOLVE_ENGINE", engine)
     shapes = [(64, 128), (512, 1024), (2048, 256)]
-    if engine in ("32", "33"):
+    if engine in ("32", "33", "34"):
         shapes += [(16, 16), (32, 64), (256, 32), (4096, 64), (1024, 2048)]
     for nx, ny in shapes:
         b = qg.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=0, dt=1e-4, dtype=dtype)
@@ -102,7 +102,7 @@ def test_both_fft_engines(engine, dtype, monkeypatch):
         b.close()
 
 
-@pytest.mark.parametrize("engine", ["32", "33"])
+@pytest.mark.parametrize("engine", ["32", "33", "34"])
 @pytest.mark.parametrize("levels", [0, 1, 2])
 def test_warp_engine_in_the_step(levels, engine, monkeypatch):
     """100 FP64 steps with a warp-group engine forced, one layer and two."""
