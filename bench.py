@@ -486,6 +486,17 @@ def ours(args):
                 variants[name]["rooflines"] = {
                     c: kernel_roofline(c, kt, 0, 50) for c in kt if kt[c][1] > 0}
             b.close()
+        # the same workload with the adaptive step of Eq. dt (c = 0.5, capped
+        # by dt) and with the time-mean streamfunction accumulated
+        for name, setup in (("cgp_l2_f32_adaptive_dt", lambda h: qg.qg_set_cfl(h, 0.5)),
+                            ("cgp_l2_f32_time_mean_psi", lambda h: qg.qg_stats_begin(h))):
+            b = make(LEVELS, "f32")
+            setup(b.h)
+            for _ in range(5):
+                qg.qg_step(b.h, 1)
+            ts = time_steps(torch, qg, b.h, stream, 200, flush)
+            variants[name] = {"steps_per_s": 200 / (sum(ts) / 1e3), "ms_per_step": sum(ts) / 200}
+            b.close()
         # two-layer basin of Table 2 Experiment 1 (Section 2.2): square
         # basin, 1024x2048 intervals per layer, l = 1, FP32
         tl = dict(Ro=2.49e-4, Fr=0.087, delta=0.2, sigma=1.43e-3)
