@@ -301,17 +301,20 @@ def time_steps(torch, qg, h, stream, K, flush):
 
 
 def kernel_timing(torch, qg, h, stream, K, flush):
-    qg.qg_set_timing(h, True)
+    """Per kernel class: summed device time and launches over K steps.  One
+    class is bracketed by events at a time (events between kernels take away
+    the next kernel's programmatic early start)."""
     acc = {}
-    for _ in range(K):
-        qg.qg_step(h, 1)
-        t = qg.qg_read_timing(h)
-        for c, (ms, n) in t.items():
-            a = acc.setdefault(c, [0.0, 0])
+    for cls in qg.KERNEL_CLASSES:
+        qg.qg_set_timing_mask(h, [cls])
+        for _ in range(K):
+            qg.qg_step(h, 1)
+            ms, n = qg.qg_read_timing(h)[cls]
+            a = acc.setdefault(cls, [0.0, 0])
             a[0] += ms
             a[1] += n
-        flush.zero_()
-    torch.cuda.synchronize()
+            flush.zero_()
+        torch.cuda.synchronize()
     qg.qg_set_timing(h, False)
     return acc
 
@@ -436,6 +439,8 @@ def ours(args):
 
     def kernel_roofline(c, kt, levels, K):
         ms, n = kt[c]
+        if alg_bytes_per_launch(c, NX, NY, levels, 4) is None:
+            return None
         avg_ms = ms / max(1, n)
         algb = alg_bytes_per_launch(c, NX, NY, levels, 4)
         ach = algb / (avg_ms * 1e-3) / 1e9
@@ -448,6 +453,7 @@ def ours(args):
     dom = max(live, key=lambda c: ktimes[c][0])
     roofline = kernel_roofline(dom, ktimes, LEVELS, Kt)
     rooflines = {c: kernel_roofline(c, ktimes, LEVELS, Kt) for c in live}
+    rooflines = {c: r for c, r in rooflines.items() if r is not None}
 
     # end to end through the C ABI with host buffers
     K_e2e = min(args.steps, 100)

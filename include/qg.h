@@ -173,6 +173,12 @@ typedef enum qg_kernel_class {
  * whole step with timing disabled.  Re-captures the graph.                 */
 qg_status qg_set_timing(qg_handle h, int enable);
 
+/* qg_set_timing_mask -- like qg_set_timing, but only kernels whose class c
+ * has bit (1 << c) set in `mask` are bracketed (0 disables timing).  The
+ * event nodes between kernels change the step's overlap (a bracketed
+ * kernel loses its programmatic early start), so time one class at a time. */
+qg_status qg_set_timing_mask(qg_handle h, uint32_t mask);
+
 /* qg_read_timing -- synchronise and return, per kernel class, the summed
  * device time in milliseconds (ms[QG_K_COUNT]) and the number of launches
  * (launches[QG_K_COUNT]) of the most recent step run with timing enabled.  */

@@ -91,6 +91,7 @@ struct qg_ctx {
     std::vector<void*> allocs;
     // per-kernel timing (bench instrumentation): events recorded in the graph
     bool timing = false;
+    unsigned timing_mask = ~0u;    // kernel classes bracketed by timing events
     int fault = QG_FAULT_NONE;     // failure-detection test switch
     uint64_t graph_gen = 0;        // bumped whenever the captured step is invalidated
     bool split_solve = false;      // solve as three plain launches (ensemble
@@ -297,7 +298,7 @@ struct KTimer {
     KTimer(qg_ctx* h_, cudaStream_t s_, int c) : h(h_), s(s_), cls(c) {
         if (!h->capturing) return;
         h->kernels_per_step += (c == QG_K_SOLVE && h->split_solve) ? 3 : 1;
-        if (!h->timing) return;
+        if (!h->timing || !(h->timing_mask & (1u << c))) return;
         if (h->ev_next + 2 > h->ev_pool.size()) {
             for (int k = 0; k < 2; ++k) {
                 cudaEvent_t e;
@@ -1083,10 +1084,17 @@ qg_status qg_step(qg_handle h, int64_t n) {
 
 qg_status qg_set_timing(qg_handle h, int enable) {
     if (!h) return QG_ERR_ARG;
-    if ((enable != 0) != h->timing) {
+    return qg_set_timing_mask(h, enable ? ~0u : 0u);
+}
+
+qg_status qg_set_timing_mask(qg_handle h, uint32_t mask) {
+    if (!h) return QG_ERR_ARG;
+    const bool on = mask != 0;
+    if (on != h->timing || (on && mask != h->timing_mask)) {
         QG_TRY(cudaStreamSynchronize(h->stream));
         drop_graph(h);
-        h->timing = enable != 0;
+        h->timing = on;
+        h->timing_mask = on ? mask : ~0u;
     }
     return QG_OK;
 }

@@ -41,6 +41,7 @@ EXPORTS = [
     "qg_ensemble_kernel_count", "qg_ensemble_synchronize", "qg_ensemble_destroy",
     "qg_tape_begin", "qg_tape_end", "qg_adjoint_step", "qg_energy_gradient",
     "qg_set_cfl", "qg_get_time", "qg_stats_begin", "qg_stats_mean_psi", "qg_stats_end",
+    "qg_set_timing_mask",
 ]
 
 KERNEL_CLASSES = ["restrict", "solve", "prolong", "fine", "cfl"]
@@ -111,6 +112,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "qg_stats_begin": [vp],
         "qg_stats_mean_psi": [vp, vp, i32, ctypes.POINTER(i64)],
         "qg_stats_end": [vp],
+        "qg_set_timing_mask": [vp, ctypes.c_uint32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -197,6 +199,14 @@ def qg_diagnostics(h: int) -> tuple[float, float, float]:
 
 def qg_set_timing(h: int, enable: bool) -> None:
     _check(load().qg_set_timing(h, 1 if enable else 0), "qg_set_timing")
+
+
+def qg_set_timing_mask(h: int, classes) -> None:
+    """Bracket only the kernels of the named classes (see KERNEL_CLASSES)."""
+    mask = 0
+    for c in classes:
+        mask |= 1 << KERNEL_CLASSES.index(c)
+    _check(load().qg_set_timing_mask(h, mask), "qg_set_timing_mask")
 
 
 def qg_read_timing(h: int) -> dict:
