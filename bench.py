@@ -123,9 +123,16 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+# the source files each kernel class is built from
+KERNEL_SOURCES = {
+    "fine": ["fused.cu", "qg_internal.cuh"],
+    "solve": ["solve32.cu", "solve.cu", "dst_engine.cuh", "qg_internal.cuh"],
+}
+
+
+def kernel_source_hash(cls):
     h = hashlib.sha256()
-    for name in sorted(os.listdir(os.path.join(ROOT, "paper_1308_3290_gb300", "csrc"))):
+    for name in KERNEL_SOURCES.get(cls, []):
         with open(os.path.join(ROOT, "paper_1308_3290_gb300", "csrc", name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -134,16 +141,16 @@ def kernel_source_hash():
 
 def ncu_traffic(cls):
     """DRAM bytes per launch of kernel class `cls` from the committed ncu
-    summary, if it was taken on the current kernel sources."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
+    summary, if it was taken on the current sources of that kernel."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic_2048x4096_l2.txt")
+    if not os.path.exists(p) or cls not in KERNEL_SOURCES:
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("source_hash") != kernel_source_hash():
-        return None
     ent = d.get("kernels", {}).get(cls)
-    return None if ent is None else ent.get("bytes_per_launch_full_size")
+    if ent is None or ent.get("source_hash") != kernel_source_hash(cls):
+        return None
+    return ent.get("bytes_per_launch_full_size")
 
 
 class ClockSampler:

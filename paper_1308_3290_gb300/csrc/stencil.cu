@@ -194,21 +194,77 @@ __device__ __forceinline__ T prolonged_at(const T* __restrict__ c, int ldc, int 
 }
 
 // Eq. dt's denominator: max over interior fine nodes of |psi_x| and |psi_y|
-// (central differences); the block maximum is max-ed into *umax as the bits
-// of a non-negative double (bit order = value order), so the result does not
-// depend on the order of the blocks.
-template <typename T>
-__global__ void cfl_max_kernel(const T* __restrict__ psi, int ldp, int nx, int ny, int levels,
+// (central differences) of psi prolonged `LV` times.  One thread per coarse
+// cell: it interpolates the fine rows y = JF-1 .. JF+F of columns
+// x = IF-1 .. IF+F from the 4 x 4 coarse patch around the cell (zero outside
+// the grid; those values only reach wall nodes, which are skipped), keeps
+// three rows, and takes the differences of the cell's F x F nodes.  The block
+// maximum is max-ed into *umax as the bits of a non-negative double (bit
+// order = value order), so the result does not depend on the block order.
+template <typename T, int LV>
+__global__ void cfl_max_kernel(const T* __restrict__ psi, int ldp, int nx, int ny,
                                double inv2dx, double inv2dy, unsigned long long* umax) {
+    constexpr int F = 1 << LV, W = F + 2;
     __shared__ double red[32];
     double m = 0.0;
-    const long n = (long)(nx - 1) * (ny - 1);
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+    const int mx = nx >> LV, my = ny >> LV;
+    const long ncell = (long)mx * my;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < ncell;
          e += (long)gridDim.x * blockDim.x) {
-        const int i = 1 + (int)(e % (nx - 1)), j = 1 + (int)(e / (nx - 1));
-        const T gx = prolonged_at(psi, ldp, i + 1, j, levels) - prolonged_at(psi, ldp, i - 1, j, levels);
-        const T gy = prolonged_at(psi, ldp, i, j + 1, levels) - prolonged_at(psi, ldp, i, j - 1, levels);
-        m = fmax(m, fmax(fabs((double)gx) * inv2dx, fabs((double)gy) * inv2dy));
+        const int I = (int)(e % mx), J = (int)(e / mx);
+        if constexpr (LV == 0) {   // the fine psi itself: one node per thread
+            if (I < 1 || J < 1) continue;
+            const T* p = psi + (size_t)J * ldp + I;
+            const double gx = fabs((double)(p[1] - p[-1])) * inv2dx;
+            const double gy = fabs((double)(p[ldp] - p[-ldp])) * inv2dy;
+            m = fmax(m, fmax(gx, gy));
+            continue;
+        }
+        T c[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int Jr = J - 1 + r, Iq = I - 1 + q;
+                c[r][q] = (Jr >= 0 && Jr <= my && Iq >= 0 && Iq <= mx)
+                              ? psi[(size_t)Jr * ldp + Iq] : T(0);
+            }
+        T row[3][W];
+#pragma unroll
+        for (int yy = 0; yy < F + 2; ++yy) {
+            const int y = J * F - 1 + yy;
+            // patch row of the lower coarse line and the weight (J F is a
+            // multiple of F, so both depend on yy only)
+            const int jr = 1 + ((yy - 1) >> LV);
+            const T b = T((yy - 1) & (F - 1)) / T(F);
+            T* rv = row[yy % 3];
+#pragma unroll
+            for (int xx = 0; xx < W; ++xx) {
+                const int iq = 1 + ((xx - 1) >> LV);
+                const T a = T((xx - 1) & (F - 1)) / T(F);
+                const T lo = (T(1) - a) * c[jr][iq] + (a > T(0) ? a * c[jr][iq + 1] : T(0));
+                const T hi = (b > T(0)) ? (T(1) - a) * c[jr + 1][iq] +
+                                              (a > T(0) ? a * c[jr + 1][iq + 1] : T(0))
+                                        : T(0);
+                rv[xx] = (T(1) - b) * lo + b * hi;
+            }
+            if (yy >= 2) {
+                const int yc = y - 1;                    // the row whose differences are ready
+                if (yc >= 1 && yc <= ny - 1) {
+                    const T* up = row[yy % 3];
+                    const T* mid = row[(yy + 2) % 3];
+                    const T* dn = row[(yy + 1) % 3];
+#pragma unroll
+                    for (int xx = 1; xx <= F; ++xx) {
+                        const int x = I * F - 1 + xx;
+                        if (x < 1 || x > nx - 1) continue;
+                        const double gx = fabs((double)(mid[xx + 1] - mid[xx - 1])) * inv2dx;
+                        const double gy = fabs((double)(up[xx] - dn[xx])) * inv2dy;
+                        m = fmax(m, fmax(gx, gy));
+                    }
+                }
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -228,11 +284,17 @@ cudaError_t launch_cfl_max(const T* psi, int ldp, int nx, int ny, int levels, do
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long n = (long)(nx - 1) * (ny - 1);
-    long blocks = (n + 255) / 256;
+    const long ncell = (long)(nx >> levels) * (ny >> levels);
+    long blocks = (ncell + 255) / 256;
     if (blocks > 8L * nsm) blocks = 8L * nsm;
-    cfl_max_kernel<T><<<(int)blocks, 256, 0, s>>>(psi, ldp, nx, ny, levels, 0.5 / dx, 0.5 / dy,
-                                                  umax);
+    const double ix = 0.5 / dx, iy = 0.5 / dy;
+    switch (levels) {
+        case 0: cfl_max_kernel<T, 0><<<(int)blocks, 256, 0, s>>>(psi, ldp, nx, ny, ix, iy, umax); break;
+        case 1: cfl_max_kernel<T, 1><<<(int)blocks, 256, 0, s>>>(psi, ldp, nx, ny, ix, iy, umax); break;
+        case 2: cfl_max_kernel<T, 2><<<(int)blocks, 256, 0, s>>>(psi, ldp, nx, ny, ix, iy, umax); break;
+        case 3: cfl_max_kernel<T, 3><<<(int)blocks, 256, 0, s>>>(psi, ldp, nx, ny, ix, iy, umax); break;
+        default: cfl_max_kernel<T, 4><<<(int)blocks, 256, 0, s>>>(psi, ldp, nx, ny, ix, iy, umax); break;
+    }
     return cudaGetLastError();
 }
 
