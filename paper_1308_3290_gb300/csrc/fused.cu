@@ -182,15 +182,19 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
     pdl_wait();
     if (LV == 0 && threadIdx.x == 0) tma_load_2d(smem_u32(sp), &tm_p, x0 - 4, yc - 1, bar);
     // the step size: fixed, or Eq. dt from this step's first streamfunction
-    double dtd = (double)p.dt;
-    if (p.umax) {
-        const double u = __longlong_as_double((long long)*p.umax);
-        dtd = u > 0.0 ? fmin(p.dt_cap, p.cfl_h / u) : p.dt_cap;
-    }
-    const T dt = (T)dtd;
-    if (p.last_stage && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-        p.clock[0] += dtd;
-        p.clock[1] = dtd;
+    // (one FP64 division per CTA, shared through the barrier below)
+    __shared__ T s_dt;
+    if (threadIdx.x == 0) {
+        double dtd = (double)p.dt;
+        if (p.umax) {
+            const double u = __longlong_as_double((long long)*p.umax);
+            dtd = u > 0.0 ? fmin(p.dt_cap, p.cfl_h / u) : p.dt_cap;
+        }
+        s_dt = (T)dtd;
+        if (p.last_stage && blockIdx.x == 0 && blockIdx.y == 0) {
+            p.clock[0] += dtd;
+            p.clock[1] = dtd;
+        }
     }
     const int mx = nx >> LV, my = ny >> LV;
     const int I_lo = (x0 - 1) >> LV;      // may be -1
@@ -210,6 +214,7 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
         (void)mbar_wait(bar, 0, kWaitLimit);     // let copies in flight land
         return;
     }
+    const T dt = s_dt;
 
     // ---- sweep -----------------------------------------------------------
     const int lane = threadIdx.x & 15;

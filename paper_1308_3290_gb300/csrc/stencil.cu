@@ -331,8 +331,56 @@ cudaError_t launch_mean_out(T* dense, const double* acc, int ldacc, double scale
     return cudaGetLastError();
 }
 
+// dense (nym1 rows of nxm1) <-> padded interior, one element per thread and
+// row-contiguous, so both sides are read and written coalesced.
+template <typename W>
+__global__ void repack_kernel(W* __restrict__ dst, const W* __restrict__ src, int nxm1, int nym1,
+                              int ld, int to_padded) {
+    const long n = (long)nxm1 * nym1;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / nxm1), i = (int)(e - (long)j * nxm1);
+        const size_t p = (size_t)(j + 1) * ld + (i + 1);
+        if (to_padded) dst[p] = src[e];
+        else dst[e] = src[p];
+    }
+}
+
+// A pointer the GPU can dereference for `ptr` (device memory, or pinned host
+// memory reached over the C2C link), or null for pageable host memory.
+static const void* device_view(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return ptr;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    return nullptr;
+}
+
+static cudaError_t repack(void* dst, const void* src, int nxm1, int nym1, int ld, size_t esz,
+                          bool to_padded, cudaStream_t s) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long n = (long)nxm1 * nym1;
+    long blocks = (n + 255) / 256;
+    if (blocks > 16L * nsm) blocks = 16L * nsm;
+    if (esz == 8)
+        repack_kernel<double><<<(int)blocks, 256, 0, s>>>(static_cast<double*>(dst),
+                                                          static_cast<const double*>(src), nxm1,
+                                                          nym1, ld, to_padded ? 1 : 0);
+    else
+        repack_kernel<float><<<(int)blocks, 256, 0, s>>>(static_cast<float*>(dst),
+                                                         static_cast<const float*>(src), nxm1,
+                                                         nym1, ld, to_padded ? 1 : 0);
+    return cudaGetLastError();
+}
+
 cudaError_t copy_in(void* padded, int ld, const void* dense, int nxm1, int nym1,
                     size_t esz, cudaStream_t s) {
+    if (const void* v = device_view(dense)) return repack(padded, v, nxm1, nym1, ld, esz, true, s);
     char* dst = static_cast<char*>(padded) + (size_t)(ld + 1) * esz;
     return cudaMemcpy2DAsync(dst, (size_t)ld * esz, dense, (size_t)nxm1 * esz,
                              (size_t)nxm1 * esz, nym1, cudaMemcpyDefault, s);
@@ -340,6 +388,8 @@ cudaError_t copy_in(void* padded, int ld, const void* dense, int nxm1, int nym1,
 
 cudaError_t copy_out(void* dense, const void* padded, int ld, int nxm1, int nym1,
                      size_t esz, cudaStream_t s) {
+    if (const void* v = device_view(dense))
+        return repack(const_cast<void*>(v), padded, nxm1, nym1, ld, esz, false, s);
     const char* src = static_cast<const char*>(padded) + (size_t)(ld + 1) * esz;
     return cudaMemcpy2DAsync(dense, (size_t)nxm1 * esz, src, (size_t)ld * esz,
                              (size_t)nxm1 * esz, nym1, cudaMemcpyDefault, s);
