@@ -296,12 +296,21 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
 #pragma unroll
     for (int m = 0; m < NM; ++m) accA[m] = accB[m] = accE[m] = T(0);
     if (active) {
-        T W[3][6], P[3][6];
+        // rows of w^(s) and psi, and the horizontal psi differences of each
+        // row, H(y)_q = psi(x_q + 1, y) - psi(x_q - 1, y), in rotating slots;
+        // T(y) = H(y) + H(y - 1) carried from row to row
+        T W[3][6], P[3][6], H[3][4], Tb[4];
         row_halo(sw, ys - 1, W[0]);
         load_psi(0, ys - 1, P[0]);
         row_halo(sw, ys, W[1]);
         load_psi(1, ys, P[1]);
-
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            H[0][q] = P[0][q + 2] - P[0][q];
+            H[1][q] = P[1][q + 2] - P[1][q];
+            Tb[q] = H[1][q] + H[0][q];
+        }
+        const T c_lap0 = T(-2) * (p.c_lapx + p.c_lapy);
 
     #pragma unroll
         for (int o = 0; o < RY; ++o) {
@@ -321,16 +330,18 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
     #pragma unroll
                 for (int q = 0; q < 4; ++q) fv[q] = fr;
             }
-            // differences shared by the four nodes: vertical psi differences per
-            // column, horizontal psi differences per row
-            T V[6], Hb[4], Hc[4], Ha[4];
+            // differences shared by the four nodes: vertical psi differences
+            // V_c per column and their neighbour sums S_c = V_c + V_{c+1}; the
+            // new row's horizontal differences and Ta = H(y+1) + H(y)
+            T V[6], S[5], Ta[4];
     #pragma unroll
             for (int c = 0; c < 6; ++c) V[c] = P[sa][c] - P[sb][c];
     #pragma unroll
+            for (int c = 0; c < 5; ++c) S[c] = V[c] + V[c + 1];
+    #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                Hb[q] = P[sb][q + 2] - P[sb][q];
-                Hc[q] = P[sc][q + 2] - P[sc][q];
-                Ha[q] = P[sa][q + 2] - P[sa][q];
+                H[sa][q] = P[sa][q + 2] - P[sa][q];
+                Ta[q] = H[sa][q] + H[sc][q];
             }
             T out[4];
     #pragma unroll
@@ -340,27 +351,31 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                 const T q00 = W[sc][i];
                 const T qm0 = W[sc][i - 1], q10 = W[sc][i + 1], q0m = W[sb][i], q01 = W[sa][i];
                 const T qmm = W[sb][i - 1], q1m = W[sb][i + 1], qm1 = W[sa][i - 1], q11 = W[sa][i + 1];
-                // Arakawa J1 + J2 + J3 (Eqs. j1-j3) with
-                //   J1 = -(q10 - qm0) V_i + (q01 - q0m) Hc_i
-                //   J2 = -q10 V_{i+1} + qm0 V_{i-1} + q01 Ha_i - q0m Hb_i
-                //   J3 = -q11 (p01 - p10) + qmm (pm0 - p0m) + qm1 (p01 - pm0) - q1m (p10 - p0m)
-                T jac = -(q10 - qm0) * V[i];
-                jac = fma(q01 - q0m, Hc[q], jac);
-                jac = fma(-q10, V[i + 1], jac);
-                jac = fma(qm0, V[i - 1], jac);
-                jac = fma(q01, Ha[q], jac);
-                jac = fma(-q0m, Hb[q], jac);
+                // Arakawa J1 + J2 + J3 (Eqs. j1-j3) gathered by neighbour of q:
+                //   edge neighbours (J1 + J2): -q10 (V_i + V_{i+1}) + qm0 (V_{i-1} + V_i)
+                //                              + q01 (Hc + Ha) - q0m (Hc + Hb)
+                //   corners (J3): -q11 (p01 - p10) + qmm (pm0 - p0m)
+                //                 + qm1 (p01 - pm0) - q1m (p10 - p0m)
+                T jac = -q10 * S[i];
+                jac = fma(qm0, S[i - 1], jac);
+                jac = fma(q01, Ta[q], jac);
+                jac = fma(-q0m, Tb[q], jac);
                 jac = fma(-q11, p01 - p10, jac);
                 jac = fma(qmm, pm0 - p0m, jac);
                 jac = fma(qm1, p01 - pm0, jac);
                 jac = fma(-q1m, p10 - p0m, jac);
                 // (1/Ro) J(psi, y) in Arakawa's form: (4 c_j + c_{j+1} + c_{j-1})/(6 Ro)
-                const T beta = fma(T(4), Hc[q], Ha[q] + Hb[q]);
-                const T lap = (q10 + qm0 - T(2) * q00) * p.c_lapx + (q01 + q0m - T(2) * q00) * p.c_lapy;
-                T Gv = fma(-p.c_jac, jac, fv[q] + lap);
-                Gv = fma(-p.c_beta, beta, Gv);
+                const T beta = fma(T(4), H[sc][q], H[sa][q] + H[sb][q]);
+                // G = F + (1/Re) lap w - J(psi, w)/(12 dx dy) - beta/(12 Ro dx)
+                T Gv = fma(-p.c_beta, beta, fv[q]);
+                Gv = fma(-p.c_jac, jac, Gv);
+                Gv = fma(c_lap0, q00, Gv);
+                Gv = fma(p.c_lapy, q01 + q0m, Gv);
+                Gv = fma(p.c_lapx, q10 + qm0, Gv);
                 out[q] = fma(p.a, wn[q], p.b * fma(dt, Gv, q00));
             }
+    #pragma unroll
+            for (int q = 0; q < 4; ++q) Tb[q] = Ta[q];
             const bool quad_ok = row_ok && xq >= 1 && xq + 3 <= nx - 1;
             if (quad_ok) {
                 stg4(p.wout + ro + xq, out);

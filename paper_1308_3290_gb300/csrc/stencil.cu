@@ -206,7 +206,10 @@ __global__ void cfl_max_kernel(const T* __restrict__ psi, int ldp, int nx, int n
                                double inv2dx, double inv2dy, unsigned long long* umax) {
     constexpr int F = 1 << LV, W = F + 2;
     __shared__ double red[32];
-    double m = 0.0;
+    // maxima of |psi(x+1) - psi(x-1)| and |psi(y+1) - psi(y-1)| in the
+    // working precision (FP64 arithmetic per node is slow on this GPU); the
+    // scaling by 1/(2 dx), 1/(2 dy) is monotone, so it is applied once
+    T ax = T(0), ay = T(0);
     const int mx = nx >> LV, my = ny >> LV;
     const long ncell = (long)mx * my;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < ncell;
@@ -215,9 +218,8 @@ __global__ void cfl_max_kernel(const T* __restrict__ psi, int ldp, int nx, int n
         if constexpr (LV == 0) {   // the fine psi itself: one node per thread
             if (I < 1 || J < 1) continue;
             const T* p = psi + (size_t)J * ldp + I;
-            const double gx = fabs((double)(p[1] - p[-1])) * inv2dx;
-            const double gy = fabs((double)(p[ldp] - p[-ldp])) * inv2dy;
-            m = fmax(m, fmax(gx, gy));
+            ax = fmax(ax, fabs(p[1] - p[-1]));
+            ay = fmax(ay, fabs(p[ldp] - p[-ldp]));
             continue;
         }
         T c[4][4];
@@ -258,14 +260,14 @@ __global__ void cfl_max_kernel(const T* __restrict__ psi, int ldp, int nx, int n
                     for (int xx = 1; xx <= F; ++xx) {
                         const int x = I * F - 1 + xx;
                         if (x < 1 || x > nx - 1) continue;
-                        const double gx = fabs((double)(mid[xx + 1] - mid[xx - 1])) * inv2dx;
-                        const double gy = fabs((double)(up[xx] - dn[xx])) * inv2dy;
-                        m = fmax(m, fmax(gx, gy));
+                        ax = fmax(ax, fabs(mid[xx + 1] - mid[xx - 1]));
+                        ay = fmax(ay, fabs(up[xx] - dn[xx]));
                     }
                 }
             }
         }
     }
+    double m = fmax((double)ax * inv2dx, (double)ay * inv2dy);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
