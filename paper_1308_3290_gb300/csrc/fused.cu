@@ -132,7 +132,7 @@ struct Plan {
 };
 
 template <typename T, int LV>
-__global__ void __launch_bounds__(Plan<T, LV>::THREADS, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(Plan<T, LV>::THREADS, 2)
 fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                   const __grid_constant__ CUtensorMap tm_wn,
                   const __grid_constant__ CUtensorMap tm_p,
