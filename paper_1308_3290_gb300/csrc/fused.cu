@@ -49,7 +49,7 @@ constexpr int SWX = TX + 8; // halo tile row: fine x in [x0 - 4, x0 + 68)
 template <int LV> struct Sweep { static constexpr int RY = (1 << LV) > 8 ? (1 << LV) : 8; };
 
 // fine rows per CTA
-template <typename T> struct Rows { static constexpr int value = 128; };
+template <typename T> struct Rows { static constexpr int value = 96; };
 template <> struct Rows<double> { static constexpr int value = 64; };
 
 template <typename T>
@@ -132,7 +132,7 @@ struct Plan {
 };
 
 template <typename T, int LV>
-__global__ void __launch_bounds__(Plan<T, LV>::THREADS, 2)
+__global__ void __launch_bounds__(Plan<T, LV>::THREADS, sizeof(T) == 4 ? 3 : 2)
 fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                   const __grid_constant__ CUtensorMap tm_wn,
                   const __grid_constant__ CUtensorMap tm_p,
