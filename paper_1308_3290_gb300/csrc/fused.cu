@@ -49,7 +49,7 @@ constexpr int SWX = TX + 8; // halo tile row: fine x in [x0 - 4, x0 + 68)
 template <int LV> struct Sweep { static constexpr int RY = (1 << LV) > 8 ? (1 << LV) : 8; };
 
 // fine rows per CTA
-template <typename T> struct Rows { static constexpr int value = 96; };
+template <typename T> struct Rows { static constexpr int value = 128; };
 template <> struct Rows<double> { static constexpr int value = 64; };
 
 template <typename T>
@@ -296,20 +296,12 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
 #pragma unroll
     for (int m = 0; m < NM; ++m) accA[m] = accB[m] = accE[m] = T(0);
     if (active) {
-        // rows of w^(s) and psi, and the horizontal psi differences of each
-        // row, H(y)_q = psi(x_q + 1, y) - psi(x_q - 1, y), in rotating slots;
-        // T(y) = H(y) + H(y - 1) carried from row to row
-        T W[3][6], P[3][6], H[3][4], Tb[4];
+        // rows y-1, y, y+1 of w^(s) and psi in rotating slots
+        T W[3][6], P[3][6];
         row_halo(sw, ys - 1, W[0]);
         load_psi(0, ys - 1, P[0]);
         row_halo(sw, ys, W[1]);
         load_psi(1, ys, P[1]);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            H[0][q] = P[0][q + 2] - P[0][q];
-            H[1][q] = P[1][q + 2] - P[1][q];
-            Tb[q] = H[1][q] + H[0][q];
-        }
         const T c_lap0 = T(-2) * (p.c_lapx + p.c_lapy);
 
     #pragma unroll
@@ -331,17 +323,21 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                 for (int q = 0; q < 4; ++q) fv[q] = fr;
             }
             // differences shared by the four nodes: vertical psi differences
-            // V_c per column and their neighbour sums S_c = V_c + V_{c+1}; the
-            // new row's horizontal differences and Ta = H(y+1) + H(y)
-            T V[6], S[5], Ta[4];
+            // V_c per column and their neighbour sums S_c = V_c + V_{c+1};
+            // horizontal differences H of rows y-1, y, y+1 and the sums
+            // Ta = H(y+1) + H(y), Tb = H(y) + H(y-1)
+            T V[6], S[5], Ha[4], Hb[4], Hc[4], Ta[4], Tb[4];
     #pragma unroll
             for (int c = 0; c < 6; ++c) V[c] = P[sa][c] - P[sb][c];
     #pragma unroll
             for (int c = 0; c < 5; ++c) S[c] = V[c] + V[c + 1];
     #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                H[sa][q] = P[sa][q + 2] - P[sa][q];
-                Ta[q] = H[sa][q] + H[sc][q];
+                Ha[q] = P[sa][q + 2] - P[sa][q];
+                Hb[q] = P[sb][q + 2] - P[sb][q];
+                Hc[q] = P[sc][q + 2] - P[sc][q];
+                Ta[q] = Ha[q] + Hc[q];
+                Tb[q] = Hc[q] + Hb[q];
             }
             T out[4];
     #pragma unroll
@@ -365,7 +361,7 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                 jac = fma(qm1, p01 - pm0, jac);
                 jac = fma(-q1m, p10 - p0m, jac);
                 // (1/Ro) J(psi, y) in Arakawa's form: (4 c_j + c_{j+1} + c_{j-1})/(6 Ro)
-                const T beta = fma(T(4), H[sc][q], H[sa][q] + H[sb][q]);
+                const T beta = fma(T(4), Hc[q], Ha[q] + Hb[q]);
                 // G = F + (1/Re) lap w - J(psi, w)/(12 dx dy) - beta/(12 Ro dx)
                 T Gv = fma(-p.c_beta, beta, fv[q]);
                 Gv = fma(-p.c_jac, jac, Gv);
@@ -374,8 +370,7 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                 Gv = fma(p.c_lapx, q10 + qm0, Gv);
                 out[q] = fma(p.a, wn[q], p.b * fma(dt, Gv, q00));
             }
-    #pragma unroll
-            for (int q = 0; q < 4; ++q) Tb[q] = Ta[q];
+
             const bool quad_ok = row_ok && xq >= 1 && xq + 3 <= nx - 1;
             if (quad_ok) {
                 stg4(p.wout + ro + xq, out);
