@@ -102,7 +102,8 @@ struct qg_ctx {
     int64_t kernels_per_step = 0;
     bool capturing = false;
     // TMA tensor maps of the fine buffers (halo and interior boxes)
-    CUtensorMap tm_halo[3], tm_int[3], tm_psi, tm_f;
+    // (per layer: [k][layer]; the second layer's maps exist for two layers)
+    CUtensorMap tm_halo[3][2], tm_int[3][2], tm_psi, tm_f;
     int solve_engine = 4;          // FFT base radix of the step's solve (autotuned)
     int* derr = nullptr;           // device error flag of bounded waits
     unsigned* dbar = nullptr;      // grid-barrier counters of the solve kernel
@@ -511,7 +512,8 @@ qg_status autotune_solve(qg_ctx* h) {
         if (p) QG_TRY(cudaMemsetAsync(p, 0, h->plane_c * h->layers * h->esz, h->stream));
     }
     if (h->ct) QG_TRY(cudaMemsetAsync(h->ct, 0, h->plane_t * h->layers * h->esz, h->stream));
-    if (h->part) QG_TRY(cudaMemsetAsync(h->part, 0, 4 * h->plane_c * h->esz, h->stream));
+    if (h->part)
+        QG_TRY(cudaMemsetAsync(h->part, 0, 4 * (size_t)h->layers * h->plane_c * h->esz, h->stream));
     QG_TRY(cudaMemsetAsync(h->dclock, 0, sizeof(double) * 4, h->stream));
     h->part_valid = false;
     QG_TRY(cudaStreamSynchronize(h->stream));
@@ -612,6 +614,60 @@ qg_status stage(qg_ctx* h, int s_idx, cudaStream_t s) {
     return QG_OK;
 }
 
+// Two-layer stage with the fused fine kernel (l >= 1): the coupled solve of
+// both layers from their partial planes has run; one fused launch per layer
+// prolongs both psi (its own for the Jacobian and the beta term, both for
+// the relative vorticity of the dissipation, Eq. pv-non), updates Q_i and
+// leaves R^l Q_i^(s+1) in that layer's partial planes.
+template <typename T>
+qg_status stage_fused2(qg_ctx* h, int s_idx, const LevelTables& t, cudaStream_t s) {
+    static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double B[3] = {1.0, 0.25, 2.0 / 3.0};
+    void* win = h->w[s_idx];
+    void* wout = h->w[(s_idx + 1) % 3];
+    const double Av = h->Ro / h->Re;    // lateral eddy viscosity A (Re = Ro/A)
+    for (int L = 0; L < 2; ++L) {
+        FusedParams<T> p;
+        p.nx = h->nx;
+        p.ny = h->ny;
+        p.ld = h->ldf;
+        p.psi = plane<T>(h->cpsi, h->plane_c, L);
+        p.psi_o = plane<T>(h->cpsi, h->plane_c, 1 - L);
+        p.ldp = t.ldc;
+        p.w = plane<T>(win, h->plane_f, L);
+        p.wn = plane<T>(h->w[0], h->plane_f, L);
+        p.wout = plane<T>(wout, h->plane_f, L);
+        p.frow = L == 0 ? static_cast<const T*>(h->frow) : nullptr;
+        p.f2d = nullptr;
+        for (int q = 0; q < 4; ++q) p.part[q] = plane<T>(h->part, h->plane_c, 4 * L + q);
+        p.ldc = t.ldc;
+        p.err = h->derr;
+        p.c_jac = (T)(1.0 / (12.0 * h->dx * h->dy));
+        p.c_beta = (T)(1.0 / (12.0 * h->dx));
+        p.c_lapx = (T)(Av / (h->dx * h->dx));
+        p.c_lapy = (T)(Av / (h->dy * h->dy));
+        p.dt = (T)h->dt;
+        p.a = (T)A[s_idx];
+        p.b = (T)B[s_idx];
+        p.inv_Ro = (T)(1.0 / h->Ro);
+        p.k_p = (T)((L == 0 ? h->Fr / h->delta : h->Fr / (1.0 - h->delta)) / h->Ro);
+        p.drag = L == 1 ? (T)h->sigma : T(0);
+        p.umax = nullptr;
+        p.cfl_h = 0.0;
+        p.dt_cap = h->dt;
+        p.clock = h->dclock + 1;
+        p.last_stage = s_idx == 2 && L == 1;
+        FineMaps m;
+        m.w = h->tm_halo[s_idx][L];
+        m.wn = h->tm_int[0][L];
+        m.psi = h->tm_psi;
+        m.f = h->tm_f;
+        KTimer kt(h, s, QG_K_FINE);
+        QG_TRY(launch_fine_fused<T>(p, m, h->levels, s, true));
+    }
+    return QG_OK;
+}
+
 // One-layer stage with the fused fine kernel.  On entry the restriction of
 // w^(s) is in the partial planes (l >= 1) or w^(s) itself is the elliptic
 // right-hand side (l = 0); the stage solves for psibar^(s), then the fused
@@ -637,8 +693,9 @@ qg_status stage_fused(qg_ctx* h, int s_idx, cudaStream_t s) {
     if (h->stats && s_idx == 0) {
         const bool fine = h->levels == 0;
         QG_TRY(launch_accumulate<T>(h->stat_acc, static_cast<const T*>(fine ? h->psi : h->cpsi),
-                                    fine ? h->plane_f : h->plane_c, s));
+                                    (fine ? h->plane_f : h->plane_c) * h->layers, s));
     }
+    if (h->layers == 2) return stage_fused2<T>(h, s_idx, *t, s);
     FusedParams<T> p;
     p.nx = h->nx;
     p.ny = h->ny;
@@ -661,6 +718,8 @@ qg_status stage_fused(qg_ctx* h, int s_idx, cudaStream_t s) {
     p.dt = (T)h->dt;
     p.a = (T)A[s_idx];
     p.b = (T)B[s_idx];
+    p.psi_o = nullptr;
+    p.inv_Ro = p.k_p = p.drag = T(0);
     p.umax = nullptr;
     p.cfl_h = h->cfl * std::fmin(h->dx, h->dy);
     p.dt_cap = h->dt;
@@ -678,8 +737,8 @@ qg_status stage_fused(qg_ctx* h, int s_idx, cudaStream_t s) {
         }
     }
     FineMaps m;
-    m.w = h->tm_halo[s_idx];
-    m.wn = h->tm_int[0];
+    m.w = h->tm_halo[s_idx][0];
+    m.wn = h->tm_int[0][0];
     m.psi = h->tm_psi;
     m.f = h->tm_f;
     KTimer kt(h, s, QG_K_FINE);
@@ -694,17 +753,20 @@ qg_status init_partials(qg_ctx* h, cudaStream_t s) {
     const LevelTables* t = nullptr;
     qg_status st = get_level(h, h->levels, &t);
     if (st != QG_OK) return fail(h, st);
-    QG_TRY(cudaMemsetAsync(h->part, 0, 4 * h->plane_c * sizeof(T), s));
-    QG_TRY(launch_restrict<T>(static_cast<const T*>(h->w[0]), h->ldf,
-                              static_cast<T*>(h->part), t->ldc, t->mx, t->my,
-                              h->levels, s));
+    QG_TRY(cudaMemsetAsync(h->part, 0, 4 * (size_t)h->layers * h->plane_c * sizeof(T), s));
+    for (int L = 0; L < h->layers; ++L)
+        QG_TRY(launch_restrict<T>(plane<T>(h->w[0], h->plane_f, L), h->ldf,
+                                  plane<T>(h->part, h->plane_c, 4 * L), t->ldc, t->mx, t->my,
+                                  h->levels, s));
     return QG_OK;
 }
 
 template <typename T>
 qg_status enqueue_step(qg_ctx* h, cudaStream_t s) {
     for (int k = 0; k < 3; ++k) {
-        qg_status st = (h->layers == 1) ? stage_fused<T>(h, k, s) : stage<T>(h, k, s);
+        // the fused path: one layer at any level, two layers when coarsened
+        qg_status st = (h->layers == 1 || h->levels >= 1) ? stage_fused<T>(h, k, s)
+                                                          : stage<T>(h, k, s);
         if (st != QG_OK) return st;
     }
     return QG_OK;
@@ -833,23 +895,27 @@ static qg_status create_ctx(const qg_basin* b, int layers, double Re, double Ro,
     h->ld_t = padded_ld(my);
     h->plane_t = (size_t)(mx + 1) * h->ld_t;
     if (s == QG_OK) guard(dev_alloc(h, &h->ct, h->plane_t * layers * h->esz));
-    if (s == QG_OK && layers == 1 && levels >= 1) guard(dev_alloc(h, &h->part, 4 * h->plane_c * h->esz));
+    if (s == QG_OK && levels >= 1)
+        guard(dev_alloc(h, &h->part, 4 * (size_t)layers * h->plane_c * h->esz));
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->derr, sizeof(int) * 4));
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dbar, sizeof(unsigned) * 4));
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dclock, sizeof(double) * 4));
-    if (s == QG_OK && layers == 1) {
+    if (s == QG_OK) {
         const int rows = (int)fine_tile_rows(h->esz);
         for (int k = 0; k < 3 && s == QG_OK; ++k) {
-            if (make_tensor_map(&h->tm_halo[k], h->w[k], h->nx, h->ny, h->ldf, h->esz,
-                                fine_halo_cols(), rows + 2) != cudaSuccess ||
-                make_tensor_map(&h->tm_int[k], h->w[k], h->nx, h->ny, h->ldf, h->esz,
-                                fine_block_cols(), rows) != cudaSuccess)
-                guard(QG_ERR_CUDA);
+            for (int L = 0; L < layers && s == QG_OK; ++L) {
+                const void* base = static_cast<const char*>(h->w[k]) + L * h->plane_f * h->esz;
+                if (make_tensor_map(&h->tm_halo[k][L], base, h->nx, h->ny, h->ldf, h->esz,
+                                    fine_halo_cols(), rows + 2) != cudaSuccess ||
+                    make_tensor_map(&h->tm_int[k][L], base, h->nx, h->ny, h->ldf, h->esz,
+                                    fine_block_cols(), rows) != cudaSuccess)
+                    guard(QG_ERR_CUDA);
+            }
         }
         if (s == QG_OK && make_tensor_map(&h->tm_psi, h->psi, h->nx, h->ny, h->ldf, h->esz,
                                           fine_halo_cols(), rows + 2) != cudaSuccess)
             guard(QG_ERR_CUDA);
-        h->tm_f = h->tm_int[0];
+        h->tm_f = h->tm_int[0][0];
     }
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dpart, sizeof(double) * 5 * diag_blocks()));
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dout, sizeof(double) * 8));
@@ -1131,8 +1197,8 @@ qg_status qg_stats_begin(qg_handle h) {
     if (!h) return QG_ERR_ARG;
     if (h->tape) return QG_ERR_UNSUPPORTED;
     if (h->latched != QG_OK) return qg_last_error(h);
-    const bool fine = h->levels == 0 || h->layers == 2;
-    const size_t n = fine ? h->plane_f * h->layers : h->plane_c;
+    const bool fine = h->levels == 0;
+    const size_t n = (fine ? h->plane_f : h->plane_c) * h->layers;
     if (!h->stat_acc) {
         qg_status s = dev_alloc(h, (void**)&h->stat_acc, n * sizeof(double));
         if (s != QG_OK) return s;
@@ -1154,11 +1220,11 @@ qg_status qg_stats_mean_psi(qg_handle h, void* psi_mean, int layer, int64_t* cou
     if (count) *count = h->stat_count;
     if (!psi_mean) return QG_OK;
     const double sc = 1.0 / (double)h->stat_count;
-    const bool fine = h->levels == 0 || h->layers == 2;
+    const bool fine = h->levels == 0;
     const LevelTables* t = nullptr;
     qg_status st = get_level(h, h->levels, &t);
     if (st != QG_OK) return st;
-    const double* acc = h->stat_acc + (fine ? (size_t)layer * h->plane_f : 0);
+    const double* acc = h->stat_acc + (size_t)layer * (fine ? h->plane_f : h->plane_c);
     const int ld = fine ? h->ldf : t->ldc;
     const int lv = fine ? 0 : h->levels;
     if (h->dtype == QG_F64)

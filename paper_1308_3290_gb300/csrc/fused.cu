@@ -112,7 +112,7 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Shared-memory plan of one CTA (byte offsets, 128-byte aligned).
-template <typename T, int LV>
+template <typename T, int LV, bool TL = false>
 struct Plan {
     static constexpr int RC = Rows<T>::value;
     static constexpr int RY = Sweep<LV>::RY;
@@ -126,18 +126,19 @@ struct Plan {
     static constexpr size_t WN = al(W + sizeof(T) * (RC + 2) * SWX);          // RC x TX
     static constexpr size_t P = al(WN + sizeof(T) * RC * TX);                 // (RC+2) x SWX (l = 0)
     static constexpr size_t CP = al(P + (LV == 0 ? sizeof(T) * (RC + 2) * SWX : 0));  // l >= 1
-    static constexpr size_t FF = al(CP + (LV > 0 ? sizeof(T) * CPY * CPX : 0));       // RC x TX
+    static constexpr size_t CP2 = al(CP + (LV > 0 ? sizeof(T) * CPY * CPX : 0));      // two layers
+    static constexpr size_t FF = al(CP2 + (TL ? sizeof(T) * CPY * CPX : 0));          // RC x TX
     static constexpr size_t END_NOF = FF;                 // without a forcing field
     static constexpr size_t END = al(FF + sizeof(T) * RC * TX);
 };
 
-template <typename T, int LV>
-__global__ void __launch_bounds__(Plan<T, LV>::THREADS, sizeof(T) == 4 ? 3 : 2)
+template <typename T, int LV, bool TL>
+__global__ void __launch_bounds__(Plan<T, LV, TL>::THREADS, (sizeof(T) == 4 && !TL) ? 3 : 2)
 fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                   const __grid_constant__ CUtensorMap tm_wn,
                   const __grid_constant__ CUtensorMap tm_p,
                   const __grid_constant__ CUtensorMap tm_f, FusedParams<T> p) {
-    using PL = Plan<T, LV>;
+    using PL = Plan<T, LV, TL>;
     constexpr int F = 1 << LV;
     constexpr int RC = PL::RC;
     constexpr int RY = PL::RY;
@@ -152,6 +153,7 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
     T* sp = reinterpret_cast<T*>(smem + PL::P);
     T* sf = reinterpret_cast<T*>(smem + PL::FF);
     T* cp = reinterpret_cast<T*>(smem + PL::CP);
+    T* cp2 = reinterpret_cast<T*>(smem + PL::CP2);   // the other layer's psi (two layers)
 
     const int nx = p.nx, ny = p.ny, ld = p.ld;
     const int x0 = blockIdx.x * TX;
@@ -203,8 +205,9 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
         for (int e = threadIdx.x; e < PL::CPX * PL::CPY; e += blockDim.x) {
             const int ii = e % PL::CPX, jj = e / PL::CPX;
             const int I = I_lo + ii, J = J_lo + jj;
-            cp[e] = (I >= 0 && I <= mx && J >= 0 && J <= my)
-                        ? __ldg(p.psi + (size_t)J * p.ldp + I) : T(0);
+            const bool in = I >= 0 && I <= mx && J >= 0 && J <= my;
+            cp[e] = in ? __ldg(p.psi + (size_t)J * p.ldp + I) : T(0);
+            if constexpr (TL) cp2[e] = in ? __ldg(p.psi_o + (size_t)J * p.ldp + I) : T(0);
         }
     }
     const bool arrived = mbar_wait(bar, 0, kWaitLimit);
@@ -236,13 +239,13 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
         v[0] = left; v[1] = c[0]; v[2] = c[1]; v[3] = c[2]; v[4] = c[3]; v[5] = right;
     };
     const int Ib = (xq - 1) >> LV;
-    T c0[4], c1[4];
-    auto coarse_row = [&](int J, T c[4]) {
-        const T* r = cp + (J - J_lo) * PL::CPX + (Ib - I_lo);
+    T c0[4], c1[4], d0[4], d1[4];    // coarse rows around y of psi (and of the other layer)
+    auto coarse_row = [&](const T* patch, int J, T (&c)[4]) {
+        const T* r = patch + (J - J_lo) * PL::CPX + (Ib - I_lo);
 #pragma unroll
         for (int k = 0; k < 4; ++k) c[k] = r[k];
     };
-    auto psi_row = [&](int y, T v[6]) {
+    auto psi_row = [&](int y, const T (&c0)[4], const T (&c1)[4], T v[6]) {
         if (y < 0 || y >= ny) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) v[k] = T(0);
@@ -275,33 +278,52 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
         // columns at or beyond a wall interpolate between the zero wall
         // values and the zero fill of the patch, so they come out zero
     };
-    // psi of sweep row rr (fine row y = ys - 1 + rr)
-    auto load_psi = [&](int rr, int y, T v[6]) {
+    // psi of sweep row rr (fine row y = ys - 1 + rr), and for two layers
+    // the other layer's psi of that row
+    auto load_psi = [&](int rr, int y, T v[6], T* vo) {
         if (LV == 0) {
             row_halo(sp, y, v);
         } else {
             if (rr <= 1) {
-                coarse_row(y >> LV, c0);
-                coarse_row((y >> LV) + 1, c1);
+                coarse_row(cp, y >> LV, c0);
+                coarse_row(cp, (y >> LV) + 1, c1);
+                if constexpr (TL) {
+                    coarse_row(cp2, y >> LV, d0);
+                    coarse_row(cp2, (y >> LV) + 1, d1);
+                }
             } else if (((rr - 1) & (F - 1)) == 0) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) c0[k] = c1[k];
-                coarse_row((y >> LV) + 1, c1);
+                coarse_row(cp, (y >> LV) + 1, c1);
+                if constexpr (TL) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) d0[k] = d1[k];
+                    coarse_row(cp2, (y >> LV) + 1, d1);
+                }
             }
-            psi_row(y, v);
+            psi_row(y, c0, c1, v);
+            if constexpr (TL) psi_row(y, d0, d1, vo);
         }
+    };
+    // two layers: w_i = Q_i/Ro + k_p (psi_i - psi_j) on a row (Eq. pv-non)
+    auto w_row = [&](const T q[6], const T ps[6], const T po[6], T v[6]) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = fma(p.k_p, ps[k] - po[k], p.inv_Ro * q[k]);
     };
 
     T accA[NM], accB[NM], accE[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) accA[m] = accB[m] = accE[m] = T(0);
     if (active) {
-        // rows y-1, y, y+1 of w^(s) and psi in rotating slots
-        T W[3][6], P[3][6];
+        // rows y-1, y, y+1 of w^(s) and psi in rotating slots (two layers:
+        // also the relative vorticity WV of the dissipation)
+        T W[3][6], P[3][6], WV[TL ? 3 : 1][6], PO[TL ? 6 : 1];
         row_halo(sw, ys - 1, W[0]);
-        load_psi(0, ys - 1, P[0]);
+        load_psi(0, ys - 1, P[0], PO);
+        if constexpr (TL) w_row(W[0], P[0], PO, WV[0]);
         row_halo(sw, ys, W[1]);
-        load_psi(1, ys, P[1]);
+        load_psi(1, ys, P[1], PO);
+        if constexpr (TL) w_row(W[1], P[1], PO, WV[1]);
         const T c_lap0 = T(-2) * (p.c_lapx + p.c_lapy);
 
     #pragma unroll
@@ -309,7 +331,8 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
             const int y = ys + o;
             const int sb = o % 3, sc = (o + 1) % 3, sa = (o + 2) % 3;
             row_halo(sw, y + 1, W[sa]);
-            load_psi(o + 2, y + 1, P[sa]);
+            load_psi(o + 2, y + 1, P[sa], PO);
+            if constexpr (TL) w_row(W[sa], P[sa], PO, WV[sa]);
             const bool row_ok = y >= 1 && y <= ny - 1;
             const size_t ro = (size_t)y * ld;
             T wn[4] = {T(0), T(0), T(0), T(0)};
@@ -318,7 +341,8 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
             if (use_f) {
                 lds4(sf + (y - yc) * TX + 4 * lane, fv);
             } else {
-                const T fr = __ldg(p.frow + (y <= ny ? y : ny));
+                // (the bottom layer of two has no wind: frow is null there)
+                const T fr = (!TL || p.frow) ? __ldg(p.frow + (y <= ny ? y : ny)) : T(0);
     #pragma unroll
                 for (int q = 0; q < 4; ++q) fv[q] = fr;
             }
@@ -365,9 +389,17 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                 // G = F + (1/Re) lap w - J(psi, w)/(12 dx dy) - beta/(12 Ro dx)
                 T Gv = fma(-p.c_beta, beta, fv[q]);
                 Gv = fma(-p.c_jac, jac, Gv);
-                Gv = fma(c_lap0, q00, Gv);
-                Gv = fma(p.c_lapy, q01 + q0m, Gv);
-                Gv = fma(p.c_lapx, q10 + qm0, Gv);
+                if constexpr (TL) {
+                    // A lap w_i - drag w_i (Eq. ge-non)
+                    const T v00 = WV[sc][i];
+                    Gv = fma(c_lap0 - p.drag, v00, Gv);
+                    Gv = fma(p.c_lapy, WV[sa][i] + WV[sb][i], Gv);
+                    Gv = fma(p.c_lapx, WV[sc][i + 1] + WV[sc][i - 1], Gv);
+                } else {
+                    Gv = fma(c_lap0, q00, Gv);
+                    Gv = fma(p.c_lapy, q01 + q0m, Gv);
+                    Gv = fma(p.c_lapx, q10 + qm0, Gv);
+                }
                 out[q] = fma(p.a, wn[q], p.b * fma(dt, Gv, q00));
             }
 
@@ -477,12 +509,12 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
     }
 }
 
-template <typename T, int LV>
+template <typename T, int LV, bool TL>
 cudaError_t launch_sweep(const FusedParams<T>& p, const FineMaps& m, cudaStream_t s) {
-    using PL = Plan<T, LV>;
+    using PL = Plan<T, LV, TL>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(fine_sweep_kernel<T, LV>,
+        cudaError_t e = cudaFuncSetAttribute(fine_sweep_kernel<T, LV, TL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)PL::END);
         if (e != cudaSuccess) return e;
@@ -500,20 +532,29 @@ cudaError_t launch_sweep(const FusedParams<T>& p, const FineMaps& m, cudaStream_
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, fine_sweep_kernel<T, LV>, m.w, m.wn, m.psi, m.f, p);
+    return cudaLaunchKernelEx(&cfg, fine_sweep_kernel<T, LV, TL>, m.w, m.wn, m.psi, m.f, p);
 }
 
 }  // namespace
 
 template <typename T>
 cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int levels,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool two_layer) {
+    if (two_layer) {   // l >= 1 only: the other layer's psi comes from the elliptic grid
+        switch (levels) {
+            case 1: return launch_sweep<T, 1, true>(p, m, s);
+            case 2: return launch_sweep<T, 2, true>(p, m, s);
+            case 3: return launch_sweep<T, 3, true>(p, m, s);
+            case 4: return launch_sweep<T, 4, true>(p, m, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (levels) {
-        case 0: return launch_sweep<T, 0>(p, m, s);
-        case 1: return launch_sweep<T, 1>(p, m, s);
-        case 2: return launch_sweep<T, 2>(p, m, s);
-        case 3: return launch_sweep<T, 3>(p, m, s);
-        case 4: return launch_sweep<T, 4>(p, m, s);
+        case 0: return launch_sweep<T, 0, false>(p, m, s);
+        case 1: return launch_sweep<T, 1, false>(p, m, s);
+        case 2: return launch_sweep<T, 2, false>(p, m, s);
+        case 3: return launch_sweep<T, 3, false>(p, m, s);
+        case 4: return launch_sweep<T, 4, false>(p, m, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -525,8 +566,8 @@ int fine_halo_cols() { return SWX; }
 int fine_block_cols() { return TX; }
 
 template cudaError_t launch_fine_fused<float>(const FusedParams<float>&, const FineMaps&, int,
-                                              cudaStream_t);
+                                              cudaStream_t, bool);
 template cudaError_t launch_fine_fused<double>(const FusedParams<double>&, const FineMaps&, int,
-                                               cudaStream_t);
+                                               cudaStream_t, bool);
 
 }  // namespace qg

@@ -170,6 +170,12 @@ struct FusedParams {
     double cfl_h, dt_cap;
     double* clock;         // {time, last dt}: the last stage adds its dt
     int last_stage;
+    // Two-layer stage (Section 2.2, Eq. ge-non; layer i, other layer j): the
+    // state is Q_i, the dissipation acts on w_i = Q_i/Ro + k_p (psi_i - psi_j)
+    // (Eq. pv-non, k_p = Fr/(delta_i Ro)), c_beta = 1/(12 dx), c_lap = A/dx^2,
+    // A/dy^2, drag = sigma for the bottom layer; frow may be null (no wind).
+    const T* psi_o;        // the other layer's elliptic-grid psi (two layers)
+    T inv_Ro, k_p, drag;
 };
 
 // acc[e] += src[e] for the n elements of a padded plane (FP64 sums).
@@ -195,7 +201,7 @@ struct FineMaps {
 };
 template <typename T>
 cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int levels,
-                              cudaStream_t s);
+                              cudaStream_t s, bool two_layer = false);
 size_t fine_tile_rows(size_t esz);   // fine rows per CTA
 int fine_part_period_x(int levels);  // coarse columns between tile edges
 int fine_part_period_y(int levels, size_t esz);  // coarse rows between CTA edges
