@@ -35,3 +35,27 @@ def test_two_layer_steps(dtype, tol, levels, nx, ny):
     assert rel_l2(g1, O.interior(a1)) <= tol
     assert rel_l2(g2, O.interior(a2)) <= tol
     b.close()
+
+
+def test_two_layer_full_size_one_step():
+    """One step of the two-layer 1024 x 2048, l = 1, FP32 workload the
+    benchmark times (Table 2 Experiment 1), against one FP64 oracle step."""
+    require_gpu()
+    nx, ny = 1024, 2048
+    p = dict(Ro=2.49e-4, Fr=0.087, delta=0.2, sigma=1.43e-3)
+    A = 3.57e-7
+    Q1 = inputs.smooth_field(nx, ny, seed=3, amp=0.05, noise=0.01)
+    Q2 = inputs.smooth_field(nx, ny, seed=4, amp=0.02, noise=0.01)
+    ob = O.TwoLayer(nx, ny, A=A, levels=1, dt=1e-5, **p)
+    a1, a2 = O.cgprk3_step_two_layer(O.embed(Q1), O.embed(Q2), ob)
+    b = qg.Basin(nx, ny, Re=p["Ro"] / A, levels=1, dt=1e-5, dtype="f32", layers=2,
+                 y0=-0.5, y1=0.5, **p)
+    b.set_state(Q1, 0)
+    b.synchronize()
+    b.set_state(Q2, 1)
+    b.step(1)
+    for layer, q0, ref in ((0, Q1, O.interior(a1)), (1, Q2, O.interior(a2))):
+        got = to_np(b.state(layer))
+        assert rel_l2(got, ref) <= 1e-6
+        assert rel_l2(got - q0, ref - q0) <= 1e-3
+    b.close()
