@@ -333,18 +333,41 @@ cudaError_t launch_mean_out(T* dense, const double* acc, int ldacc, double scale
     return cudaGetLastError();
 }
 
-// dense (nym1 rows of nxm1) <-> padded interior, one element per thread and
-// row-contiguous, so both sides are read and written coalesced.
+// dense (nym1 rows of nxm1) <-> padded interior.  The dense side (often
+// pinned host memory reached over the C2C link) moves in 16-byte vectors
+// of the flat array when it is 16-byte aligned, the padded side element by
+// element; both are row-contiguous, so both sides coalesce.
 template <typename W>
 __global__ void repack_kernel(W* __restrict__ dst, const W* __restrict__ src, int nxm1, int nym1,
                               int ld, int to_padded) {
+    constexpr int V = 16 / sizeof(W);
     const long n = (long)nxm1 * nym1;
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+    const W* dense_r = to_padded ? src : nullptr;
+    W* dense_w = to_padded ? nullptr : dst;
+    const bool vec = ((reinterpret_cast<uintptr_t>(to_padded ? (const void*)src : (const void*)dst)
+                       & 15) == 0);
+    const long nv = vec ? n / V : 0;
+    auto pad = [&](long e) { const int j = (int)(e / nxm1); return (size_t)(j + 1) * ld + (e - (long)j * nxm1) + 1; };
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < nv;
+         g += (long)gridDim.x * blockDim.x) {
+        W v[V];
+        if (to_padded) {
+            const uint4 u = reinterpret_cast<const uint4*>(dense_r)[g];
+            memcpy(v, &u, 16);
+#pragma unroll
+            for (int k = 0; k < V; ++k) dst[pad(g * V + k)] = v[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; ++k) v[k] = src[pad(g * V + k)];
+            uint4 u;
+            memcpy(&u, v, 16);
+            reinterpret_cast<uint4*>(dense_w)[g] = u;
+        }
+    }
+    for (long e = nv * V + (long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (long)gridDim.x * blockDim.x) {
-        const int j = (int)(e / nxm1), i = (int)(e - (long)j * nxm1);
-        const size_t p = (size_t)(j + 1) * ld + (i + 1);
-        if (to_padded) dst[p] = src[e];
-        else dst[e] = src[p];
+        if (to_padded) dst[pad(e)] = src[e];
+        else dst[e] = src[pad(e)];
     }
 }
 
