@@ -56,7 +56,9 @@ typedef enum qg_dtype {
 } qg_dtype;
 
 /* Basin geometry and run constants.
- * nx, ny      fine-grid intervals; powers of two, 8 <= nx, ny <= 8192.
+ * nx, ny      fine-grid intervals; powers of two, 8 <= nx, ny <= 8192
+ *             (FP64: <= 4096 where the grid is solved; larger FP64 elliptic
+ *             grids are rejected with QG_ERR_SHAPE).
  * x0..y1      basin extent.  The one-layer experiments of Section 5.1 use
  *             [0,1] x [-1,1]; the two-layer ones of Section 5.2 a square.
  * forcing_amp amplitude a of the double-gyre wind forcing: a sin(pi y)/Ro in
