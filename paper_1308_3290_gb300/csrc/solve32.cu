@@ -624,12 +624,17 @@ cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
     cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     if (!P.split) {
+        // cooperative (grid barriers), and allowed to start while the fine
+        // stage before it finishes: the table copies precede the kernel's
+        // programmatic wait, every read of the stage's output follows it
         at[0].id = cudaLaunchAttributeCooperative;
         at[0].val.cooperative = 1;
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[1].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = 2;
         return cudaLaunchKernelEx(&cfg, k, P, lgx, lgy, tb);
     }
     SolveParams<T> Q = P;
