@@ -114,7 +114,6 @@ struct qg_ctx {
     double* stat_acc = nullptr;    // its FP64 sum (elliptic grid, or fine for l = 0 / 2 layers)
     int64_t stat_count = 0;
     double* dclock = nullptr;      // device {umax bits, time, last dt, spare}
-    void* stage = nullptr;         // staging buffer of one dense field (host exchange)
 };
 
 namespace qg {
@@ -992,19 +991,11 @@ qg_status qg_synchronize(qg_handle h) {
     return qg_last_error(h);
 }
 
-// The staging buffer of host exchanges, allocated on first use.
-static qg_status ensure_stage(qg_ctx* h) {
-    if (h->stage) return QG_OK;
-    return dev_alloc(h, &h->stage, (size_t)(h->nx - 1) * (h->ny - 1) * h->esz);
-}
-
 qg_status qg_set_state(qg_handle h, const void* field, int layer) {
     if (!h || !field || layer < 0 || layer >= h->layers) return QG_ERR_ARG;
     if (h->latched != QG_OK) return qg_last_error(h);
     char* dst = static_cast<char*>(h->w[0]) + (size_t)layer * h->plane_f * h->esz;
-    qg_status st = ensure_stage(h);
-    if (st != QG_OK) return st;
-    QG_TRY(copy_in(dst, h->ldf, field, h->nx - 1, h->ny - 1, h->esz, h->stream, h->stage));
+    QG_TRY(copy_in(dst, h->ldf, field, h->nx - 1, h->ny - 1, h->esz, h->stream));
     h->part_valid = false;
     h->time_host = 0.0;
     QG_TRY(cudaMemsetAsync(h->dclock, 0, sizeof(double) * 4, h->stream));
@@ -1015,9 +1006,7 @@ qg_status qg_get_state(qg_handle h, void* field, int layer) {
     if (!h || !field || layer < 0 || layer >= h->layers) return QG_ERR_ARG;
     if (h->latched != QG_OK) return qg_last_error(h);
     const char* src = static_cast<const char*>(h->w[0]) + (size_t)layer * h->plane_f * h->esz;
-    qg_status st = ensure_stage(h);
-    if (st != QG_OK) return st;
-    QG_TRY(copy_out(field, src, h->ldf, h->nx - 1, h->ny - 1, h->esz, h->stream, h->stage));
+    QG_TRY(copy_out(field, src, h->ldf, h->nx - 1, h->ny - 1, h->esz, h->stream));
     return QG_OK;
 }
 

@@ -240,11 +240,9 @@ cudaError_t launch_diagnostics(const T* psi, const T* w, int nx, int ny, int ld,
 int diag_blocks();
 
 // Copies between the dense exchange layout and the padded node layout.
-// `stage`: optional device buffer of nxm1 * nym1 elements for pinned host
-// buffers (one contiguous DMA copy, then a device repack).
 cudaError_t copy_in(void* padded, int ld, const void* dense, int nxm1,
-                    int nym1, size_t esz, cudaStream_t s, void* stage = nullptr);
+                    int nym1, size_t esz, cudaStream_t s);
 cudaError_t copy_out(void* dense, const void* padded, int ld, int nxm1,
-                     int nym1, size_t esz, cudaStream_t s, void* stage = nullptr);
+                     int nym1, size_t esz, cudaStream_t s);
 
 }  // namespace qg

@@ -371,17 +371,17 @@ __global__ void repack_kernel(W* __restrict__ dst, const W* __restrict__ src, in
     }
 }
 
-// Kind of a caller buffer: 1 device (or managed) memory, 2 pinned host
-// memory, 0 pageable host memory.
-static int buffer_kind(const void* ptr) {
+// A pointer the GPU can dereference for `ptr` (device memory, or pinned host
+// memory reached over the C2C link), or null for pageable host memory.
+static const void* device_view(const void* ptr) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
         (void)cudaGetLastError();
-        return 0;
+        return nullptr;
     }
-    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 1;
-    if (a.type == cudaMemoryTypeHost) return 2;
-    return 0;
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return ptr;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    return nullptr;
 }
 
 static cudaError_t repack(void* dst, const void* src, int nxm1, int nym1, int ld, size_t esz,
@@ -403,32 +403,21 @@ static cudaError_t repack(void* dst, const void* src, int nxm1, int nym1, int ld
     return cudaGetLastError();
 }
 
-// Device buffers are repacked by a kernel; pinned host buffers go through
-// one contiguous DMA copy into the device staging buffer `stage` (when
-// given) and a device repack; pageable host buffers through 2-D copies.
+// Device buffers and pinned host buffers (read or written in place over the
+// C2C link, which beats a DMA copy plus a device repack) are repacked by a
+// kernel; pageable host buffers go through 2-D copies.
 cudaError_t copy_in(void* padded, int ld, const void* dense, int nxm1, int nym1,
-                    size_t esz, cudaStream_t s, void* stage) {
-    const int kind = buffer_kind(dense);
-    if (kind == 1) return repack(padded, dense, nxm1, nym1, ld, esz, true, s);
-    if (kind == 2 && stage) {
-        cudaError_t e = cudaMemcpyAsync(stage, dense, (size_t)nxm1 * nym1 * esz,
-                                        cudaMemcpyHostToDevice, s);
-        return e != cudaSuccess ? e : repack(padded, stage, nxm1, nym1, ld, esz, true, s);
-    }
+                    size_t esz, cudaStream_t s) {
+    if (const void* v = device_view(dense)) return repack(padded, v, nxm1, nym1, ld, esz, true, s);
     char* dst = static_cast<char*>(padded) + (size_t)(ld + 1) * esz;
     return cudaMemcpy2DAsync(dst, (size_t)ld * esz, dense, (size_t)nxm1 * esz,
                              (size_t)nxm1 * esz, nym1, cudaMemcpyDefault, s);
 }
 
 cudaError_t copy_out(void* dense, const void* padded, int ld, int nxm1, int nym1,
-                     size_t esz, cudaStream_t s, void* stage) {
-    const int kind = buffer_kind(dense);
-    if (kind == 1) return repack(dense, padded, nxm1, nym1, ld, esz, false, s);
-    if (kind == 2 && stage) {
-        cudaError_t e = repack(stage, padded, nxm1, nym1, ld, esz, false, s);
-        return e != cudaSuccess ? e : cudaMemcpyAsync(dense, stage, (size_t)nxm1 * nym1 * esz,
-                                                      cudaMemcpyDeviceToHost, s);
-    }
+                     size_t esz, cudaStream_t s) {
+    if (const void* v = device_view(dense))
+        return repack(const_cast<void*>(v), padded, nxm1, nym1, ld, esz, false, s);
     const char* src = static_cast<const char*>(padded) + (size_t)(ld + 1) * esz;
     return cudaMemcpy2DAsync(dense, (size_t)nxm1 * esz, src, (size_t)ld * esz,
                              (size_t)nxm1 * esz, nym1, cudaMemcpyDefault, s);
