@@ -263,31 +263,45 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int lim
     return false;
 }
 
+// Generation of the grid barrier `bar` (thread 0; 0 elsewhere).  Read in
+// the phase before the barrier, off its critical path: the generation
+// cannot advance before this CTA arrives.
+__device__ __forceinline__ unsigned grid_gen(const unsigned* bar) {
+    unsigned g = 0;
+    if (threadIdx.x == 0)
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+    return g;
+}
+
 // Grid-wide barrier with a bounded wait.  bar[0] counts arrivals, bar[1] is
-// the generation; the last of gridDim.x + extra arrivals releases it.
+// the generation, g0 its value from grid_gen in this phase.  The arrival is
+// an acq_rel atomic, so the CTA's writes of the phase (ordered before thread
+// 0 by the CTA barrier) are visible to whoever acquires after it; the last of
+// gridDim.x + extra arrivals resets the count and advances the generation
+// with a release, and the others poll the generation with acquire loads.
 // Returns false (on every thread) when the wait ran out.
-__device__ inline bool grid_sync(unsigned* bar, unsigned extra, int limit) {
+__device__ inline bool grid_sync(unsigned* bar, unsigned extra, int limit, unsigned g0) {
     __syncthreads();
     int ok = 1;
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = bar + 1;
-        const unsigned g0 = *gen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1 + extra) {
-            bar[0] = 0;
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        unsigned old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                     : "=r"(old) : "l"(bar) : "memory");
+        if (old == gridDim.x - 1 + extra) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
         } else {
-            int i = 0;
-            while (*gen == g0) {
-                if (++i > limit) {
+            for (int i = 0;; ++i) {
+                unsigned g;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];"
+                             : "=r"(g) : "l"(bar + 1) : "memory");
+                if (g != g0) break;
+                if (i >= limit) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
         }
-        __threadfence();
     }
     return __syncthreads_and(ok) != 0;
 }

@@ -241,6 +241,7 @@ solve_kernel(SolveParams<T> P) {
     const C* twx = Lo.twx_smem ? stwx : P.twx;
     const C* twy = Lo.twy_smem ? stwy : P.twy;
     const bool all = P.split == 0;
+    unsigned g0 = grid_gen(P.bar);
 
     // 1. x pass of the right-hand side, transposed into tr
     if (all || P.phase == 0) {
@@ -259,10 +260,11 @@ solve_kernel(SolveParams<T> P) {
         io.transpose = true;
         run_phase<T, NBM, E>(io, 0, bufs, twx, P.lamx, slamy, P.scale, P.Ro, P.f1, P.f2);
     }
-    if (all && !grid_sync(P.bar, P.bar_extra, kSpinLimit)) {
+    if (all && !grid_sync(P.bar, P.bar_extra, kSpinLimit, g0)) {
         if (threadIdx.x == 0) atomicExch(P.err, 1);
         return;
     }
+    g0 = grid_gen(P.bar);
     // 2. y pass with the mode-space solve, transposed back into work
     if (all || P.phase == 1) {
         const T* trin[8] = {P.tr[0], nullptr, nullptr, nullptr, P.tr[1], nullptr, nullptr, nullptr};
@@ -280,7 +282,7 @@ solve_kernel(SolveParams<T> P) {
         io.transpose = true;
         run_phase<T, NBM, E>(io, OPY, bufs, twy, P.lamx, slamy, P.scale, P.Ro, P.f1, P.f2);
     }
-    if (all && !grid_sync(P.bar, P.bar_extra, kSpinLimit)) {
+    if (all && !grid_sync(P.bar, P.bar_extra, kSpinLimit, g0)) {
         if (threadIdx.x == 0) atomicExch(P.err, 1);
         return;
     }

@@ -102,9 +102,10 @@ __host__ __device__ inline int cta_threads(int lgx, int lgy, int rad, int least)
     const int g = (1 << (lgx > lgy ? lgx : lgy)) / rad;
     return g < least ? least : g;
 }
+// two buffers per pair (the passes alternate between them)
 __host__ __device__ inline int buf_cplx(int lg, int rad, int threads) {
     const Geo32 g = geo32(lg, rad);
-    return (threads / g.G) * g.buf;
+    return (threads / g.G) * 2 * g.buf;
 }
 
 // Group barrier: the G threads of one pair.
@@ -201,26 +202,28 @@ __device__ __forceinline__ void dft32(Cplx<T> (&v)[32]) {
     }
 }
 
-// One radix-RAD Stockham pass (one RAD-point DFT per thread, butterfly
-// j = t): input j + r G, twiddle table entry r NS + k (k = j mod NS), output
-// (j - k) RAD + k + r NS.  The first pass (NS = 1) reads the odd extension of
-// the stored z_0..z_{N-1}: element m = t + r G is z_m (r < RAD/2), 0 (m = N),
-// or -z_{L-m}.
+// One radix-RAD Stockham pass from buffer `in` to buffer `out` (one
+// RAD-point DFT per thread, butterfly j = t): input j + r G, twiddle table
+// entry r NS + k (k = j mod NS), output (j - k) RAD + k + r NS.  The first
+// pass (NS = 1) reads the odd extension of the stored z_0..z_{N-1}: element
+// m = t + r G is z_m (r < RAD/2), 0 (m = N), or -z_{L-m}.  The two buffers
+// alternate, so one group sync after the stores orders both this pass's
+// reads before the next pass's writes and its writes before the next reads.
 template <typename T, int RAD>
-__device__ __forceinline__ void passW(CT<T>* cb, int t, const Geo32& g, int NS, bool first,
-                                      const CT<T>* __restrict__ tw, const Sync& sy) {
+__device__ __forceinline__ void passW(const CT<T>* in, CT<T>* out, int t, const Geo32& g, int NS,
+                                      bool first, const CT<T>* __restrict__ tw, const Sync& sy) {
     constexpr int H = RAD / 2;
     const int k = t & (NS - 1);
     Cplx<T> v[RAD];
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
         if (!first) {
-            v[r] = ldp<T>(cb, t + r * g.G);
+            v[r] = ldp<T>(in, t + r * g.G);
         } else if (r < H) {
-            v[r] = ldp<T>(cb, t + r * g.G);
+            v[r] = ldp<T>(in, t + r * g.G);
         } else {
             const int m = r == H ? g.N - t : (RAD - r) * g.G - t;
-            const Cplx<T> z = (r == H && t == 0) ? Cplx<T>{T(0), T(0)} : ldp<T>(cb, m);
+            const Cplx<T> z = (r == H && t == 0) ? Cplx<T>{T(0), T(0)} : ldp<T>(in, m);
             v[r] = Cplx<T>{-z.x, -z.y};
         }
     }
@@ -233,12 +236,11 @@ __device__ __forceinline__ void passW(CT<T>* cb, int t, const Geo32& g, int NS, 
     }
     if constexpr (RAD == 32) dft32<T>(v);
     else dft<T, RAD>(v);
-    sy.sync();
     const int d = (t - k) * RAD + k;
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
-        if constexpr (RAD == 32) stp<T>(cb, d + r * NS, v[r]);
-        else stp<T>(cb, d + r * NS, v[out_slot<RAD>(r)]);
+        if constexpr (RAD == 32) stp<T>(out, d + r * NS, v[r]);
+        else stp<T>(out, d + r * NS, v[out_slot<RAD>(r)]);
     }
     sy.sync();
 }
@@ -246,7 +248,7 @@ __device__ __forceinline__ void passW(CT<T>* cb, int t, const Geo32& g, int NS, 
 // The remainder pass, radix R < RAD: RAD/R butterflies j = t + b G per
 // thread.  Out of line: inlined next to the radix-32 pass its registers spill.
 template <typename T, int R, int RAD>
-__device__ __noinline__ void passR(CT<T>* cb, int t, Geo32 g, int NS,
+__device__ __noinline__ void passR(const CT<T>* in, CT<T>* out, int t, Geo32 g, int NS,
                                    const CT<T>* __restrict__ tw, Sync sy) {
     constexpr int B = RAD / R;
     const int stride = g.L / R;
@@ -256,7 +258,7 @@ __device__ __noinline__ void passR(CT<T>* cb, int t, Geo32 g, int NS,
         const int j = t + b * g.G;
         const int k = j & (NS - 1);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[b][r] = ldp<T>(cb, j + r * stride);
+        for (int r = 0; r < R; ++r) v[b][r] = ldp<T>(in, j + r * stride);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
             const CT<T> w = tw[r * NS + k];
@@ -264,44 +266,49 @@ __device__ __noinline__ void passR(CT<T>* cb, int t, Geo32 g, int NS,
         }
         dft<T, R>(v[b]);
     }
-    sy.sync();
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         const int j = t + b * g.G;
         const int k = j & (NS - 1);
         const int d = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) stp<T>(cb, d + r * NS, v[b][out_slot<R>(r)]);
+        for (int r = 0; r < R; ++r) stp<T>(out, d + r * NS, v[b][out_slot<R>(r)]);
     }
     sy.sync();
 }
 
-// Forward FFT of length L of the odd extension of cb[0..N) in place; the
-// result Z_k is at cb[px(k)], k = 0..L-1.  Starts and ends with a group sync.
+// Forward FFT of length L of the odd extension of a[0..N); the passes
+// alternate between a and b, and the result Z_k, k = 0..L-1, is at
+// [px(k)] of the buffer returned.  Starts and ends with a group sync.
 template <typename T, int RAD>
-__device__ __forceinline__ void fft_rt(CT<T>* cb, int t, const Geo32& g, const CT<T>* tw,
-                                       const Sync& sy) {
+__device__ __forceinline__ CT<T>* fft_rt(CT<T>* a, CT<T>* b, int t, const Geo32& g,
+                                         const CT<T>* tw, const Sync& sy) {
     sy.sync();
     int ns = 1, off = 0;
 #pragma unroll 1
     for (int p = 0; p < g.np; ++p) {
-        passW<T, RAD>(cb, t, g, ns, p == 0, tw + off, sy);
+        passW<T, RAD>(a, b, t, g, ns, p == 0, tw + off, sy);
+        CT<T>* c = a;
+        a = b;
+        b = c;
         if (p > 0) off += RAD * ns;
         ns *= RAD;
     }
     if (g.rem > 0) {
         const CT<T>* tr = tw + off;
         switch (g.rem) {
-            case 1: passR<T, 2, RAD>(cb, t, g, ns, tr, sy); break;
-            case 2: passR<T, 4, RAD>(cb, t, g, ns, tr, sy); break;
+            case 1: passR<T, 2, RAD>(a, b, t, g, ns, tr, sy); break;
+            case 2: passR<T, 4, RAD>(a, b, t, g, ns, tr, sy); break;
             case 3:
-                if constexpr (RAD > 8) passR<T, 8, RAD>(cb, t, g, ns, tr, sy);
+                if constexpr (RAD > 8) passR<T, 8, RAD>(a, b, t, g, ns, tr, sy);
                 break;
             default:
-                if constexpr (RAD == 32) passR<T, 16, RAD>(cb, t, g, ns, tr, sy);
+                if constexpr (RAD == 32) passR<T, 16, RAD>(a, b, t, g, ns, tr, sy);
                 break;
         }
+        return b;
     }
+    return a;
 }
 
 template <typename T>
@@ -544,15 +551,18 @@ solve32_kernel(SolveParams<T> P, int lgx, int lgy, Tabs tb) {
         }
     }
     const int ph0 = P.split ? P.phase : 0, ph1 = P.split ? P.phase + 1 : 3;
+    unsigned g0 = 0;
     for (int ph = ph0; ph < ph1; ++ph) {
-        if (ph > ph0 && !grid_sync(P.bar, P.bar_extra, kSpin)) {
+        if (ph > ph0 && !grid_sync(P.bar, P.bar_extra, kSpin, g0)) {
             if (threadIdx.x == 0) atomicExch(P.err, 1);
             return;
         }
+        if (ph + 1 < ph1) g0 = grid_gen(P.bar);
         const Geo32 g = geo32(ph == 1 ? lgy : lgx, RAD);
         const CT<T>* tw = ph == 1 ? pty : ptx;
         const int grp = threadIdx.x / g.G, t = threadIdx.x % g.G;
-        CT<T>* cb = bufs + grp * g.buf;
+        CT<T>* cb = bufs + 2 * grp * g.buf;
+        CT<T>* cb2 = cb + g.buf;
         const Sync sy{1 + grp, g.G};
         int npairs;
         if (ph == 1) npairs = OPY == 2 ? P.mx - 1 : P.mx / 2;
@@ -563,12 +573,13 @@ solve32_kernel(SolveParams<T> P, int lgx, int lgy, Tabs tb) {
             const PairAt a = pair_at<T, OPY>(P, ph, slot * per + grp, npairs);
             load_pair<T, OPY, RAD>(P, ph, a, g, cb, t);
             const int nfft = ph == 1 ? 2 : 1;
+            CT<T>* res = cb;
 #pragma unroll 1
             for (int f = 0; f < nfft; ++f) {
-                if (f == 1) mode_solve<T, OPY, RAD>(P, a, g, cb, t, lamy);
-                fft_rt<T, RAD>(cb, t, g, tw, sy);
+                if (f == 1) mode_solve<T, OPY, RAD>(P, a, g, res, t, lamy);
+                res = fft_rt<T, RAD>(res, res == cb ? cb2 : cb, t, g, tw, sy);
             }
-            store_pair<T, OPY, RAD>(P, ph, a, g, cb, t);
+            store_pair<T, OPY, RAD>(P, ph, a, g, res, t);
             sy.sync();
         }
     }
