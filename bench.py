@@ -62,6 +62,13 @@ def parse():
     ap.add_argument("--ny", type=int, default=NY)
     ap.add_argument("--levels", type=int, default=LEVELS)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--study", choices=["mean-fields"],
+                    help="long-run time-mean study of Section 5.1 instead of the benchmark")
+    ap.add_argument("--experiments", default="I,II")
+    ap.add_argument("--t0", type=float, default=10.0)
+    ap.add_argument("--t1", type=float, default=50.0)
+    ap.add_argument("--study-dt", type=float, default=1e-5)
+    ap.add_argument("--study-out", default="")
     return ap.parse_args()
 
 
@@ -559,9 +566,102 @@ def ours(args):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# long-run statistics (Section 5.1)
+# ---------------------------------------------------------------------------
+
+# (label, nx, ny, levels): the 256 x 512 DNS, CGP of it at l = 1, 2, 3, and
+# the three runs whose elliptic grid is 16 x 32 (Figs. of the 16 x 32 set)
+STUDY_RUNS = [
+    ("DNS 256x512:256x512", 256, 512, 0),
+    ("CGP 256x512:128x256", 256, 512, 1),
+    ("CGP 256x512:64x128", 256, 512, 2),
+    ("CGP 256x512:32x64", 256, 512, 3),
+    ("coarse 16x32:16x32", 16, 32, 0),
+    ("CGP 32x64:16x32", 32, 64, 1),
+    ("CGP 64x128:16x32", 64, 128, 2),
+]
+STUDY_EXPERIMENTS = {"I": (200.0, 0.0016), "II": (312.5, 0.0025)}
+
+
+def study_mean_fields(args):
+    """Time-mean streamfunction of each run in STUDY_RUNS over t in [t0, t1]
+    from rest (Section 5.1: t in [10, 50], Exp I and II), every run of an
+    experiment one member of an ensemble stepped together at a fixed dt; the
+    error of each mean field against the DNS mean at the run's own nodes."""
+    import numpy as np
+    import torch
+    from paper_1308_3290_gb300 import build, qg
+    build.build()
+    qg.load()
+    n0 = int(round(args.t0 / args.study_dt))
+    n1 = int(round(args.t1 / args.study_dt))
+    chunk = 20000
+    report = {"study": "time-mean psi, Section 5.1", "t0": args.t0, "t1": args.t1,
+              "dt": args.study_dt, "steps": n1, "mean_over_steps": n1 - n0, "dtype": "f32",
+              "experiments": {}}
+    names = args.experiments.split(",")
+    members, owner = [], []
+    for name in names:
+        Re, Ro = STUDY_EXPERIMENTS[name]
+        for run in STUDY_RUNS:
+            members.append(dict(nx=run[1], ny=run[2], Re=Re, Ro=Ro, levels=run[3],
+                                dt=args.study_dt))
+            owner.append((name, run))
+    ens = qg.Ensemble(members, dtype="f32")
+    for i, m in enumerate(members):
+        ens.member(i).set_state(np.zeros((m["ny"] - 1, m["nx"] - 1)))
+    t_start = time.perf_counter()
+    done = 0
+    while done < n0:
+        k = min(chunk, n0 - done)
+        ens.step(k)
+        done += k
+    ens.synchronize()
+    for i in range(len(members)):
+        qg.qg_stats_begin(ens.member(i).h)
+    while done < n1:
+        k = min(chunk, n1 - done)
+        ens.step(k)
+        done += k
+    ens.synchronize()
+    wall = time.perf_counter() - t_start
+    report["wall_s"] = wall
+    report["ensemble_members"] = len(members)
+    report["ensemble_steps_per_s"] = n1 / wall
+    for name in names:
+        Re, Ro = STUDY_EXPERIMENTS[name]
+        idx = [i for i, (nm, _) in enumerate(owner) if nm == name]
+        means = []
+        for i in idx:
+            v = ens.member(i)
+            out = torch.empty((v.ny - 1, v.nx - 1), dtype=torch.float32, device="cuda")
+            cnt = qg.qg_stats_mean_psi(v.h, out)
+            ens.synchronize()
+            means.append((out.double().cpu().numpy(), cnt, qg.qg_diagnostics(v.h)[0]))
+        dns = means[0][0]
+        runs = []
+        for (label, nx, ny, lv), (m, cnt, ke) in zip(STUDY_RUNS, means):
+            s = 256 // nx
+            ref = dns[s - 1::s, s - 1::s]
+            runs.append({"run": label, "levels": lv, "samples": cnt,
+                         "psi_min": float(m.min()), "psi_max": float(m.max()),
+                         "rel_l2_vs_dns": float(np.linalg.norm(m - ref) / np.linalg.norm(ref)),
+                         "final_ke": ke})
+        report["experiments"][name] = {"Re": Re, "Ro": Ro, "runs": runs}
+        print(json.dumps({"experiment": name, **report["experiments"][name]}), flush=True)
+    print(json.dumps({"wall_s": wall, "ensemble_steps_per_s": n1 / wall}), flush=True)
+    ens.close()
+    if args.study_out:
+        with open(args.study_out, "w") as f:
+            json.dump(report, f, indent=1)
+
+
 def main():
     args = parse()
-    if args.profile_only:
+    if args.study:
+        study_mean_fields(args)
+    elif args.profile_only:
         profile_only(args)
     elif args.impl == "reference":
         reference_arm(args)

@@ -95,3 +95,34 @@ def test_ensemble_of_96_basins_steps():
         ke, z, u = ens.member(i).diagnostics()
         assert np.isfinite(ke) and ke > 0 and np.isfinite(z)
     ens.close()
+
+
+def test_ensemble_member_time_mean_matches_oracle():
+    """Time-mean psi (Section 5.1's statistic) accumulated on ensemble
+    members, as the long-run study of the 16 x 32 elliptic set does: members
+    with l = 0, 1, 2 started from rest, the mean over steps n0..n1-1 against
+    the oracle's."""
+    torch = require_gpu()
+    runs = [(16, 32, 0), (32, 64, 1), (64, 128, 2)]
+    members = [dict(nx=nx, ny=ny, Re=200.0, Ro=0.0016, levels=lv, dt=1e-4)
+               for nx, ny, lv in runs]
+    n0, n1 = 10, 40
+    ens = qg.Ensemble(members, dtype="f64")
+    for i, m in enumerate(members):
+        ens.member(i).set_state(np.zeros((m["ny"] - 1, m["nx"] - 1)))
+    ens.step(n0)
+    ens.synchronize()
+    for i in range(len(members)):
+        qg.qg_stats_begin(ens.member(i).h)
+    ens.step(n1 - n0)
+    ens.synchronize()
+    for i, m in enumerate(members):
+        v = ens.member(i)
+        out = torch.empty((m["ny"] - 1, m["nx"] - 1), dtype=torch.float64, device="cuda")
+        assert qg.qg_stats_mean_psi(v.h, out) == n1 - n0
+        ens.synchronize()
+        w0 = np.zeros((m["ny"] - 1, m["nx"] - 1))
+        ob = O.Basin(m["nx"], m["ny"], Re=200.0, Ro=0.0016, levels=m["levels"], dt=1e-4)
+        ref = O.mean_psi(w0, ob, n0, n1)
+        assert rel_l2(to_np(out), ref) <= 1e-12, (i, rel_l2(to_np(out), ref))
+    ens.close()
