@@ -220,6 +220,31 @@ qg_status qg_poisson_solve_noalloc(int32_t nx, int32_t ny, double dx, double dy,
  * open).  Re-captures the step graph.  Errors: QG_ERR_ARG for c < 0.     */
 qg_status qg_set_cfl(qg_handle h, double c);
 
+/* ---- the elliptic solver of the CGP step (Section 3) -------------------
+ * CGP does not depend on the Poisson solver used on the coarse grid; the
+ * paper names the V-cycle multigrid as the choice where sine transforms do
+ * not apply.                                                               */
+typedef enum qg_solver {
+    QG_SOLVER_FFT = 0,        /* sine transforms (Section 4.3), the default  */
+    QG_SOLVER_MULTIGRID = 1   /* geometric V(2,2) cycles                      */
+} qg_solver;
+
+/* qg_set_solver -- the solver of h's steps and of qg_poisson_solve.
+ * QG_SOLVER_MULTIGRID: `cycles` (1..64) V(2,2) cycles per solve of
+ * lap_h psi = f (red-black Gauss-Seidel smoothing; full weighting, Eq. res,
+ * of the residual; bilinear prolongation, Eq. pro, of the correction;
+ * grids halved until the shorter side has 2 intervals).  In the step each
+ * solve starts from the streamfunction of the previous solve (zero after
+ * qg_set_state); qg_poisson_solve starts from zero.  The result is the
+ * discrete solution to within the cycles' convergence (about a factor 10
+ * per cycle), not to rounding.  One-layer handles whose elliptic grid has
+ * sides within a factor 4 of each other and spacings within a factor 2
+ * (point smoothing with full coarsening; QG_ERR_UNSUPPORTED otherwise, or
+ * while an adjoint tape is open; qg_poisson_solve at a level whose grid
+ * does not qualify returns QG_ERR_UNSUPPORTED).  `cycles` is ignored for
+ * QG_SOLVER_FFT.  Re-captures the step graph.  Errors: QG_ERR_ARG.        */
+qg_status qg_set_solver(qg_handle h, qg_solver kind, int32_t cycles);
+
 /* qg_get_time -- model time since creation or the last qg_set_state, and
  * the size of the last step (host pointers; either may be NULL).
  * Synchronises the handle's stream.                                        */

@@ -39,6 +39,15 @@ struct LevelTables {
     void* pty[3] = {nullptr, nullptr, nullptr};  //   L = 2 mx and 2 my, engines 32/33/34
 };
 
+// Multigrid hierarchy below one elliptic grid (multigrid.cu): grids 1..nl-1
+// (grid 0 is the caller's psi; rhs[0] holds its summed right-hand side),
+// each psi and rhs with (my + 1) rows of pitch ld and zero walls.
+struct MGPlan {
+    int nl = 0, tail = 0;
+    std::vector<int> mx, my, ld;
+    std::vector<void*> psi, rhs;
+};
+
 }  // namespace
 
 // Forward states kept for the adjoint (one layer): the state at every
@@ -114,6 +123,9 @@ struct qg_ctx {
     double* stat_acc = nullptr;    // its FP64 sum (elliptic grid, or fine for l = 0 / 2 layers)
     int64_t stat_count = 0;
     double* dclock = nullptr;      // device {umax bits, time, last dt, spare}
+    int solver = QG_SOLVER_FFT;    // elliptic solver of the step and qg_poisson_solve
+    int mg_cycles = 4;             // V-cycles per multigrid solve
+    std::map<long, MGPlan> mg;     // multigrid hierarchies by (mx, my)
 };
 
 namespace qg {
@@ -331,11 +343,100 @@ T* plane(void* base, size_t plane_elems, int layer) {
 int engine_rule(int mx, int my);
 int engine_for(qg_ctx* h, int mx, int my);
 
+// ---- multigrid (qg_set_solver) -------------------------------------------
+// Grids whose sides are within a factor 4 of each other (halving down to a
+// shorter side of 2 intervals leaves a line of at most 7 unknowns) and
+// whose spacings are within a factor 2 (point Gauss-Seidel with full
+// coarsening smooths poorly on strongly anisotropic grids).
+bool mg_supports(int mx, int my, double dx, double dy) {
+    const int lo = mx < my ? mx : my, hi = mx < my ? my : mx;
+    const double r = dx > dy ? dx / dy : dy / dx;
+    return lo >= 2 && hi <= 4 * lo && r <= 2.0 + 1e-12;
+}
+
+qg_status get_mg(qg_ctx* h, int mx, int my, const MGPlan** out) {
+    const long key = (long)mx * 65536 + my;
+    auto it = h->mg.find(key);
+    if (it != h->mg.end()) {
+        *out = &it->second;
+        return QG_OK;
+    }
+    MGPlan p;
+    for (int x = mx, y = my;; x /= 2, y /= 2) {
+        p.mx.push_back(x);
+        p.my.push_back(y);
+        p.ld.push_back(padded_ld(x));
+        if ((x < y ? x : y) <= 2) break;
+    }
+    p.nl = (int)p.mx.size();
+    // the tail: the longest run of coarsest grids that fits one CTA's shared
+    // memory (at least the coarsest grid itself)
+    p.tail = p.nl - 1;
+    while (p.tail > 0 && p.nl - p.tail < kMaxTail &&
+           mg_tail_smem(&p.mx[p.tail - 1], &p.my[p.tail - 1], p.nl - p.tail + 1, h->esz) <=
+               160 * 1024)
+        --p.tail;
+    if (mg_reserve_tail_smem(mg_tail_smem(&p.mx[p.tail], &p.my[p.tail], p.nl - p.tail, h->esz),
+                             h->esz) != cudaSuccess)
+        return QG_ERR_CUDA;
+    p.psi.assign(p.nl, nullptr);
+    p.rhs.assign(p.nl, nullptr);
+    for (int k = 0; k < p.nl; ++k) {
+        const size_t bytes = (size_t)(p.my[k] + 1) * p.ld[k] * h->esz;
+        qg_status s = dev_alloc(h, &p.rhs[k], bytes);
+        if (s == QG_OK && k > 0) s = dev_alloc(h, &p.psi[k], bytes);
+        if (s != QG_OK) return s;
+    }
+    auto r = h->mg.emplace(key, std::move(p));
+    *out = &r.first->second;
+    return QG_OK;
+}
+
+// lap_h psi = (sum of the nparts planes of `in`) on the grid of t, in place
+// in `out` (the guess: out's contents, or zero), with h->mg_cycles V-cycles.
+template <typename T>
+qg_status mg_solve_level(qg_ctx* h, const LevelTables& t, const void* in, int nparts, void* out,
+                         size_t pl, cudaStream_t s, bool zero) {
+    const MGPlan* mp = nullptr;
+    qg_status st = get_mg(h, t.mx, t.my, &mp);
+    if (st != QG_OK) return fail(h, st);
+    if (mp->ld[0] != t.ldc) return fail(h, QG_ERR_CUDA);
+    MGSumParams<T> q = {};
+    for (int k = 0; k < nparts; ++k) q.in[k] = plane<T>(const_cast<void*>(in), pl, k);
+    q.nin = nparts;
+    q.ld_in = t.ldc;
+    q.rhs = static_cast<T*>(mp->rhs[0]);
+    q.psi = static_cast<T*>(out);
+    q.mx = t.mx;
+    q.my = t.my;
+    q.ld = t.ldc;
+    q.zero = zero ? 1 : 0;
+    std::vector<MGLevelDesc<T>> lv(mp->nl);
+    double dx = t.dxc, dy = t.dyc;
+    for (int k = 0; k < mp->nl; ++k, dx *= 2, dy *= 2) {
+        lv[k].psi = k == 0 ? static_cast<T*>(out) : static_cast<T*>(mp->psi[k]);
+        lv[k].rhs_w = static_cast<T*>(mp->rhs[k]);
+        lv[k].rhs = lv[k].rhs_w;
+        lv[k].mx = mp->mx[k];
+        lv[k].my = mp->my[k];
+        lv[k].ld = lv[k].ldr = mp->ld[k];
+        lv[k].cx = (T)(1.0 / (dx * dx));
+        lv[k].cy = (T)(1.0 / (dy * dy));
+    }
+    KTimer kt(h, s, QG_K_SOLVE);
+    if (h->capturing) h->kernels_per_step += h->mg_cycles * mg_cycle_launches(mp->tail);
+    QG_TRY(launch_mg_sum<T>(q, s));
+    for (int c = 0; c < h->mg_cycles; ++c) QG_TRY(launch_mg_cycle<T>(lv.data(), mp->nl, mp->tail, s));
+    return QG_OK;
+}
+
 template <typename T>
 qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr, int ld_tr,
                       size_t pl_tr, void* work, void* out, size_t pl, cudaStream_t s,
                       int nparts = 1, int engine = 0) {
     using C = typename Cx<T>::type;
+    if (h->solver == QG_SOLVER_MULTIGRID && h->layers == 1)
+        return mg_solve_level<T>(h, t, in, nparts, out, pl, s, false);
     SolveParams<T> P = {};
     P.mx = t.mx;
     P.my = t.my;
@@ -998,6 +1099,9 @@ qg_status qg_set_state(qg_handle h, const void* field, int layer) {
     QG_TRY(copy_in(dst, h->ldf, field, h->nx - 1, h->ny - 1, h->esz, h->stream));
     h->part_valid = false;
     h->time_host = 0.0;
+    if (h->solver == QG_SOLVER_MULTIGRID)   // the first solve's guess: zero
+        QG_TRY(cudaMemsetAsync(h->levels ? h->cpsi : h->psi, 0,
+                               (h->levels ? h->plane_c : h->plane_f) * h->esz, h->stream));
     QG_TRY(cudaMemsetAsync(h->dclock, 0, sizeof(double) * 4, h->stream));
     return QG_OK;
 }
@@ -1047,30 +1151,42 @@ qg_status qg_set_forcing(qg_handle h, const void* forcing) {
 qg_status qg_poisson_solve(qg_handle h, const void* rhs, void* psi, int level) {
     if (!h || !rhs || !psi || level < 0 || level > h->levels) return QG_ERR_ARG;
     if (h->latched != QG_OK) return qg_last_error(h);
+    if (h->solver == QG_SOLVER_MULTIGRID &&
+        !mg_supports(h->nx >> level, h->ny >> level, h->dx, h->dy))
+        return QG_ERR_UNSUPPORTED;
     const LevelTables* t = nullptr;
     qg_status s = get_level(h, level, &t);
     if (s != QG_OK) return fail(h, s);
     const size_t pl = (size_t)(t->my + 1) * t->ldc;
     const int ld_tr = padded_ld(t->my);
     const size_t pl_tr = (size_t)(t->mx + 1) * ld_tr;
-    const size_t bytes = (pl + pl_tr) * h->layers * h->esz;
+    // (the multigrid path keeps its result in the second part)
+    const size_t bytes = (pl + (pl_tr > pl ? pl_tr : pl)) * h->layers * h->esz;
     void* buf = nullptr;
     QG_TRY(cudaMallocAsync(&buf, bytes, h->stream));
     void* tbuf = static_cast<char*>(buf) + pl * h->layers * h->esz;
     cudaError_t e = cudaMemsetAsync(buf, 0, bytes, h->stream);
     const size_t dense = (size_t)(t->mx - 1) * (t->my - 1) * h->esz;
+    void* buf_out = buf;
     for (int L = 0; L < h->layers && e == cudaSuccess; ++L)
         e = copy_in(static_cast<char*>(buf) + L * pl * h->esz, t->ldc,
                     static_cast<const char*>(rhs) + L * dense, t->mx - 1, t->my - 1,
                     h->esz, h->stream);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && h->solver == QG_SOLVER_MULTIGRID) {
+        s = h->dtype == QG_F64
+                ? mg_solve_level<double>(h, *t, buf, 1, tbuf, pl, h->stream, true)
+                : mg_solve_level<float>(h, *t, buf, 1, tbuf, pl, h->stream, true);
+        if (s != QG_OK) e = cudaErrorUnknown;
+        buf_out = tbuf;
+    } else if (e == cudaSuccess) {
         s = h->dtype == QG_F64
                 ? solve_level<double>(h, *t, buf, tbuf, ld_tr, pl_tr, buf, buf, pl, h->stream)
                 : solve_level<float>(h, *t, buf, tbuf, ld_tr, pl_tr, buf, buf, pl, h->stream);
         if (s != QG_OK) e = cudaErrorUnknown;
     }
     for (int L = 0; L < h->layers && e == cudaSuccess; ++L)
-        e = copy_out(static_cast<char*>(psi) + L * dense, static_cast<char*>(buf) + L * pl * h->esz,
+        e = copy_out(static_cast<char*>(psi) + L * dense,
+                     static_cast<char*>(buf_out) + L * pl * h->esz,
                      t->ldc, t->mx - 1, t->my - 1, h->esz, h->stream);
     cudaFreeAsync(buf, h->stream);
     if (s != QG_OK) return s;
@@ -1172,6 +1288,32 @@ qg_status qg_set_cfl(qg_handle h, double c) {
         QG_TRY(cudaStreamSynchronize(h->stream));
         drop_graph(h);
         h->cfl = c;
+    }
+    return QG_OK;
+}
+
+qg_status qg_set_solver(qg_handle h, qg_solver kind, int32_t cycles) {
+    if (!h || (kind != QG_SOLVER_FFT && kind != QG_SOLVER_MULTIGRID)) return QG_ERR_ARG;
+    if (kind == QG_SOLVER_MULTIGRID) {
+        if (cycles < 1 || cycles > 64) return QG_ERR_ARG;
+        if (h->layers != 1 || h->tape ||
+            !mg_supports(h->nx >> h->levels, h->ny >> h->levels, h->dx, h->dy))
+            return QG_ERR_UNSUPPORTED;
+    }
+    if (h->latched != QG_OK) return qg_last_error(h);
+    QG_TRY(cudaStreamSynchronize(h->stream));
+    if (kind == QG_SOLVER_MULTIGRID) {
+        // the hierarchy of the step's grid now: no allocation during capture
+        const MGPlan* mp = nullptr;
+        qg_status s = get_mg(h, h->nx >> h->levels, h->ny >> h->levels, &mp);
+        if (s != QG_OK) return s;
+    }
+    drop_graph(h);
+    h->solver = kind;
+    if (kind == QG_SOLVER_MULTIGRID) {
+        h->mg_cycles = cycles;
+        QG_TRY(cudaMemsetAsync(h->levels ? h->cpsi : h->psi, 0,
+                               (h->levels ? h->plane_c : h->plane_f) * h->esz, h->stream));
     }
     return QG_OK;
 }
@@ -1489,7 +1631,8 @@ extern "C" {
 
 qg_status qg_tape_begin(qg_handle h, int64_t every, int64_t max_steps) {
     if (!h || every < 1 || max_steps < 1) return QG_ERR_ARG;
-    if (h->layers != 1 || h->cfl > 0.0 || h->stats) return QG_ERR_UNSUPPORTED;
+    if (h->layers != 1 || h->cfl > 0.0 || h->stats || h->solver != QG_SOLVER_FFT)
+        return QG_ERR_UNSUPPORTED;
     if (h->latched != QG_OK) return qg_last_error(h);
     tape_release(h);
     Tape* tp = new (std::nothrow) Tape();

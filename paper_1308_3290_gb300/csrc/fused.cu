@@ -245,16 +245,18 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
 #pragma unroll
         for (int k = 0; k < 4; ++k) c[k] = r[k];
     };
-    auto psi_row = [&](int y, const T (&c0)[4], const T (&c1)[4], T v[6]) {
+    // ph = y mod 2^l, known at compile time in the unrolled sweep (ys is a
+    // multiple of RY, itself a multiple of 2^l)
+    auto psi_row = [&](int y, int ph, const T (&c0)[4], const T (&c1)[4], T v[6]) {
         if (y < 0 || y >= ny) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) v[k] = T(0);
             return;
         }
-        const T b = T(y & (F - 1)) * (T(1) / T(F));
+        const T b = T(ph) * (T(1) / T(F));
         T cv[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) cv[k] = (T(1) - b) * c0[k] + b * c1[k];
+        for (int k = 0; k < 4; ++k) cv[k] = ph == 0 ? c0[k] : (T(1) - b) * c0[k] + b * c1[k];
         if (LV == 1) {
             v[0] = T(0.5) * (cv[0] + cv[1]); v[1] = cv[1];
             v[2] = T(0.5) * (cv[1] + cv[2]); v[3] = cv[2];
@@ -301,8 +303,9 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                     coarse_row(cp2, (y >> LV) + 1, d1);
                 }
             }
-            psi_row(y, c0, c1, v);
-            if constexpr (TL) psi_row(y, d0, d1, vo);
+            const int ph = (rr - 1) & (F - 1);
+            psi_row(y, ph, c0, c1, v);
+            if constexpr (TL) psi_row(y, ph, d0, d1, vo);
         }
     };
     // two layers: w_i = Q_i/Ro + k_p (psi_i - psi_j) on a row (Eq. pv-non)

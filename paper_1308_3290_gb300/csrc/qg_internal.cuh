@@ -239,6 +239,41 @@ cudaError_t launch_diagnostics(const T* psi, const T* w, int nx, int ny, int ld,
                                int nblocks, double* out, cudaStream_t s);
 int diag_blocks();
 
+// ---- geometric multigrid (multigrid.cu) ----------------------------------
+constexpr int kMaxTail = 14;          // levels the one-CTA tail can hold
+template <typename T>
+struct MGLevelDesc {                  // one grid of the hierarchy
+    T* psi;                           // (my+1) rows of pitch ld, zero walls
+    const T* rhs;                     // right-hand side, pitch ldr
+    T* rhs_w;                         // the same, writable (levels >= 1)
+    int mx, my, ld, ldr;
+    T cx, cy;                         // 1/dx^2, 1/dy^2 of this grid
+};
+template <typename T>
+struct MGTail {                       // levels handled by one CTA in shared memory
+    int n;
+    int mx[kMaxTail], my[kMaxTail];
+    T cx[kMaxTail], cy[kMaxTail];
+    T* psi;                           // first tail level (global): guess in, result out
+    const T* rhs;
+    int ld, ldr;
+};
+template <typename T>
+struct MGSumParams {                  // rhs = in[0] + in[1] + ..., psi = 0 if zero
+    const T* in[4];
+    int nin, ld_in;
+    T* rhs;
+    T* psi;
+    int mx, my, ld, zero;
+};
+size_t mg_tail_smem(const int* mx, const int* my, int n, size_t esz);
+int mg_cycle_launches(int tail);      // kernels of one V-cycle
+cudaError_t mg_reserve_tail_smem(size_t bytes, size_t esz);
+template <typename T>
+cudaError_t launch_mg_sum(const MGSumParams<T>& q, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mg_cycle(const MGLevelDesc<T>* lv, int nl, int tail, cudaStream_t s);
+
 // Copies between the dense exchange layout and the padded node layout.
 cudaError_t copy_in(void* padded, int ld, const void* dense, int nxm1,
                     int nym1, size_t esz, cudaStream_t s);

@@ -22,7 +22,9 @@ LIB_PATH = os.path.join(_HERE, "libqgcgp.so")
 
 QG_F32, QG_F64 = 0, 1
 QG_FAULT_NONE, QG_FAULT_BARRIER_STALL = 0, 1
-QG_ERR_TIMEOUT = 7
+QG_SOLVER_FFT, QG_SOLVER_MULTIGRID = 0, 1
+QG_OK, QG_ERR_ARG, QG_ERR_SHAPE, QG_ERR_CUDA, QG_ERR_OOM = 0, 1, 2, 3, 4
+QG_ERR_TIMEOUT, QG_ERR_UNSUPPORTED = 7, 8
 
 STATUS = {
     0: "QG_OK", 1: "QG_ERR_ARG", 2: "QG_ERR_SHAPE", 3: "QG_ERR_CUDA",
@@ -40,7 +42,7 @@ EXPORTS = [
     "qg_ensemble_create", "qg_ensemble_member", "qg_ensemble_step",
     "qg_ensemble_kernel_count", "qg_ensemble_synchronize", "qg_ensemble_destroy",
     "qg_tape_begin", "qg_tape_end", "qg_adjoint_step", "qg_energy_gradient",
-    "qg_set_cfl", "qg_get_time", "qg_stats_begin", "qg_stats_mean_psi", "qg_stats_end",
+    "qg_set_cfl", "qg_set_solver", "qg_get_time", "qg_stats_begin", "qg_stats_mean_psi", "qg_stats_end",
     "qg_set_timing_mask",
 ]
 
@@ -108,6 +110,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "qg_adjoint_step": [vp, i64, vp, vp],
         "qg_energy_gradient": [vp, dbl, vp],
         "qg_set_cfl": [vp, dbl],
+        "qg_set_solver": [vp, i32, i32],
         "qg_get_time": [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
         "qg_stats_begin": [vp],
         "qg_stats_mean_psi": [vp, vp, i32, ctypes.POINTER(i64)],
@@ -259,6 +262,10 @@ def qg_energy_gradient(h: int, scale: float, g) -> None:
 
 def qg_set_cfl(h: int, c: float) -> None:
     _check(load().qg_set_cfl(h, c), "qg_set_cfl")
+
+
+def qg_set_solver(h: int, kind: int, cycles: int = 4) -> None:
+    _check(load().qg_set_solver(h, kind, cycles), "qg_set_solver")
 
 
 def qg_get_time(h: int) -> tuple[float, float]:
