@@ -1002,7 +1002,7 @@ static qg_status create_ctx(const qg_basin* b, int layers, double Re, double Ro,
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dbar, sizeof(unsigned) * 4));
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dclock, sizeof(double) * 4));
     if (s == QG_OK) {
-        const int rows = fine_box_rows(h->esz);
+        const int rows = (int)fine_tile_rows(h->esz);
         for (int k = 0; k < 3 && s == QG_OK; ++k) {
             for (int L = 0; L < layers && s == QG_OK; ++L) {
                 const void* base = static_cast<const char*>(h->w[k]) + L * h->plane_f * h->esz;
@@ -1142,7 +1142,7 @@ qg_status qg_set_forcing(qg_handle h, const void* forcing) {
     }
     h->f2d = h->f2d_buf;
     if (make_tensor_map(&h->tm_f, h->f2d, h->nx, h->ny, h->ldf, h->esz, fine_block_cols(),
-                        fine_box_rows(h->esz)) != cudaSuccess)
+                        (int)fine_tile_rows(h->esz)) != cudaSuccess)
         return fail(h, QG_ERR_CUDA);
     QG_TRY(copy_in(h->f2d, h->ldf, forcing, h->nx - 1, h->ny - 1, h->esz, h->stream));
     return QG_OK;

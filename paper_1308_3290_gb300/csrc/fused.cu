@@ -118,20 +118,14 @@ struct Plan {
     static constexpr int RY = Sweep<LV>::RY;
     static constexpr int G = RC / RY;               // groups per CTA
     static constexpr int THREADS = 16 * G;
-    // the tile arrives in NH row chunks, each on its own mbarrier, so the
-    // groups of the first chunk start while the second is in flight
-    static constexpr int NH = 2;
-    static constexpr int RB = RC / NH;              // rows of a chunk
-    static constexpr size_t al(size_t v) { return (v + 127) / 128 * 128; }
-    // elements between the halo chunks (each chunk starts 128-byte aligned)
-    static constexpr int HS = (int)(al(sizeof(T) * (RB + 2) * SWX) / sizeof(T));
     static constexpr int F = 1 << LV;
     static constexpr int CPX = TX / F + 4;
     static constexpr int CPY = RC / F + 3;
-    static constexpr size_t W = 0;                                             // NH chunks of HS
-    static constexpr size_t WN = al(W + sizeof(T) * NH * HS);                 // RC x TX
-    static constexpr size_t P = al(WN + sizeof(T) * RC * TX);                 // NH chunks (l = 0)
-    static constexpr size_t CP = al(P + (LV == 0 ? sizeof(T) * NH * HS : 0));         // l >= 1
+    static constexpr size_t al(size_t v) { return (v + 127) / 128 * 128; }
+    static constexpr size_t W = 0;                                             // (RC+2) x SWX
+    static constexpr size_t WN = al(W + sizeof(T) * (RC + 2) * SWX);          // RC x TX
+    static constexpr size_t P = al(WN + sizeof(T) * RC * TX);                 // (RC+2) x SWX (l = 0)
+    static constexpr size_t CP = al(P + (LV == 0 ? sizeof(T) * (RC + 2) * SWX : 0));  // l >= 1
     static constexpr size_t CP2 = al(CP + (LV > 0 ? sizeof(T) * CPY * CPX : 0));      // two layers
     static constexpr size_t FF = al(CP2 + (TL ? sizeof(T) * CPY * CPX : 0));          // RC x TX
     static constexpr size_t END_NOF = FF;                 // without a forcing field
@@ -151,8 +145,7 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
     constexpr int NM = RY / F + 1;                  // node rows a group touches
     constexpr int G = (F >= 4) ? F / 4 : 1;          // threads per coarse cell
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int NH = PL::NH, RB = PL::RB;
-    __shared__ __align__(8) uint64_t mbar[NH];
+    __shared__ __align__(8) uint64_t mbar;
     // restriction partial sums of node rows on the seam between two groups
     __shared__ T seam[(LV > 0) ? PL::G : 1][(LV > 0) ? TX / (1 << LV) + 1 : 1];
     T* sw = reinterpret_cast<T*>(smem + PL::W);
@@ -167,38 +160,29 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
     const int yc = blockIdx.y * RC;
     const bool use_wn = p.a != T(0);
     const bool use_f = p.f2d != nullptr;
-    const uint32_t bar0 = smem_u32(&mbar[0]);
-    constexpr uint32_t kBarStride = sizeof(uint64_t);
+    const uint32_t bar = smem_u32(&mbar);
 
     // ---- stage the inputs ------------------------------------------------
     if (threadIdx.x == 0) {
-        for (int h = 0; h < NH; ++h) mbar_init(bar0 + h * kBarStride, 1);
+        mbar_init(bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
     // w^(s), w^n and the forcing were written before the solve this kernel
     // follows began (the solve is launched in stream order), so their copies
     // start before the programmatic wait; psi comes from the solve itself.
-    // Chunk h: halo rows yc - 1 + h RB .. yc + (h + 1) RB at element h HS of
-    // the halo tiles, interior rows yc + h RB .. at row h RB.
     if (threadIdx.x == 0) {
-        uint32_t bytes = sizeof(T) * (RB + 2) * SWX;
-        if (use_wn) bytes += sizeof(T) * RB * TX;
-        if (LV == 0) bytes += sizeof(T) * (RB + 2) * SWX;
-        if (use_f) bytes += sizeof(T) * RB * TX;
-        for (int h = 0; h < NH; ++h) {
-            const uint32_t b = bar0 + h * kBarStride;
-            mbar_expect_tx(b, bytes);
-            tma_load_2d(smem_u32(sw + h * PL::HS), &tm_w, x0 - 4, yc - 1 + h * RB, b);
-            if (use_wn) tma_load_2d(smem_u32(swn + h * RB * TX), &tm_wn, x0, yc + h * RB, b);
-            if (use_f) tma_load_2d(smem_u32(sf + h * RB * TX), &tm_f, x0, yc + h * RB, b);
-        }
+        uint32_t bytes = sizeof(T) * (RC + 2) * SWX;
+        if (use_wn) bytes += sizeof(T) * RC * TX;
+        if (LV == 0) bytes += sizeof(T) * (RC + 2) * SWX;
+        if (use_f) bytes += sizeof(T) * RC * TX;
+        mbar_expect_tx(bar, bytes);
+        tma_load_2d(smem_u32(sw), &tm_w, x0 - 4, yc - 1, bar);
+        if (use_wn) tma_load_2d(smem_u32(swn), &tm_wn, x0, yc, bar);
+        if (use_f) tma_load_2d(smem_u32(sf), &tm_f, x0, yc, bar);
     }
     pdl_wait();
-    if (LV == 0 && threadIdx.x == 0)
-        for (int h = 0; h < NH; ++h)
-            tma_load_2d(smem_u32(sp + h * PL::HS), &tm_p, x0 - 4, yc - 1 + h * RB,
-                        bar0 + h * kBarStride);
+    if (LV == 0 && threadIdx.x == 0) tma_load_2d(smem_u32(sp), &tm_p, x0 - 4, yc - 1, bar);
     // the step size: fixed, or Eq. dt from this step's first streamfunction
     // (one FP64 division per CTA, shared through the barrier below)
     __shared__ T s_dt;
@@ -226,30 +210,26 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
             if constexpr (TL) cp2[e] = in ? __ldg(p.psi_o + (size_t)J * p.ldp + I) : T(0);
         }
     }
-    __syncthreads();                     // the patch and s_dt
-    const T dt = s_dt;
-    const int lane = threadIdx.x & 15;
-    const int grp = threadIdx.x >> 4;
-    // each group waits for its own chunk only; a wait that runs out sets the
-    // error flag and the group skips its rows (the CTA still reaches the
-    // barrier of the epilogue), after letting the copies in flight land
-    const int hh = grp / (PL::G / NH);
-    const bool arrived = mbar_wait(bar0 + hh * kBarStride, 0, kWaitLimit);
+    const bool arrived = mbar_wait(bar, 0, kWaitLimit);
+    __syncthreads();
     if (!arrived) {
-        atomicExch(p.err, 1);
-        for (int h = 0; h < NH; ++h) (void)mbar_wait(bar0 + h * kBarStride, 0, kWaitLimit);
+        if (threadIdx.x == 0) atomicExch(p.err, 1);
+        (void)mbar_wait(bar, 0, kWaitLimit);     // let copies in flight land
+        return;
     }
+    const T dt = s_dt;
 
     // ---- sweep -----------------------------------------------------------
+    const int lane = threadIdx.x & 15;
+    const int grp = threadIdx.x >> 4;
     const unsigned gm = 0xFFFFu << (16 * (grp & 1));
     const int ys = yc + grp * RY;
-    const bool active = ys < ny && arrived;          // uniform in the group
+    const bool active = ys < ny;                     // uniform in the group
     const int xq = x0 + 4 * lane;
 
-    // row y of a halo tile (w^(s) or the fine psi) in this group's chunk:
-    // own quad + shuffled halos
+    // row y of a halo tile (w^(s) or the fine psi): own quad + shuffled halos
     auto row_halo = [&](const T* tile, int y, T v[6]) {
-        const T* r = tile + hh * PL::HS + (y - yc + 1 - hh * RB) * SWX;
+        const T* r = tile + (y - yc + 1) * SWX;
         T c[4];
         lds4(r + 4 * lane + 4, c);
         T left = __shfl_up_sync(gm, c[3], 1, 16);
@@ -583,7 +563,6 @@ cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int le
 }
 
 size_t fine_tile_rows(size_t esz) { return esz == 8 ? Rows<double>::value : Rows<float>::value; }
-int fine_box_rows(size_t esz) { return (int)fine_tile_rows(esz) / Plan<float, 0>::NH; }
 int fine_part_period_x(int levels) { return TX >> levels; }
 int fine_part_period_y(int levels, size_t esz) { return (int)fine_tile_rows(esz) >> levels; }
 int fine_halo_cols() { return SWX; }

@@ -203,7 +203,6 @@ template <typename T>
 cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int levels,
                               cudaStream_t s, bool two_layer = false);
 size_t fine_tile_rows(size_t esz);   // fine rows per CTA
-int fine_box_rows(size_t esz);       // rows of one TMA box (a chunk of a tile)
 int fine_part_period_x(int levels);  // coarse columns between tile edges
 int fine_part_period_y(int levels, size_t esz);  // coarse rows between CTA edges
 int fine_halo_cols();                // columns of a halo box
