@@ -111,3 +111,38 @@ def test_multigrid_unsupported_cases():
         qg.qg_tape_begin(b.h, 1, 10)
     assert e.value.status == qg.QG_ERR_UNSUPPORTED
     b.close()
+
+
+def test_multigrid_with_adaptive_step_and_time_mean():
+    """The solver switch composes with the adaptive step (Eq. dt) and the
+    time-mean statistics: 12 warm-started cycles per solve follow the
+    oracle's exact-solve trajectory, step sizes and mean psi."""
+    torch = require_gpu()
+    nx, ny, n, c = 64, 128, 30, 0.3
+    w0 = inputs.perturbation(nx, ny, seed=3) * 50.0
+    ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=1, dt=1e-3)
+    ref, dts = O.run_adaptive(w0, ob, n, c)
+    b = qg.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=1, dt=1e-3, dtype="f64")
+    qg.qg_set_solver(b.h, qg.QG_SOLVER_MULTIGRID, 12)
+    qg.qg_set_cfl(b.h, c)
+    b.set_state(w0)
+    b.step(n)
+    assert rel_l2(to_np(b.state()), ref) <= 1e-9
+    t, dt_last = qg.qg_get_time(b.h)
+    assert t == pytest.approx(sum(dts), rel=1e-9)
+    assert dt_last == pytest.approx(dts[-1], rel=1e-9)
+    b.close()
+
+    ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=2, dt=1e-4)
+    ref = O.mean_psi(w0, ob, 5, 25)
+    b = qg.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=2, dt=1e-4, dtype="f64")
+    qg.qg_set_solver(b.h, qg.QG_SOLVER_MULTIGRID, 12)
+    b.set_state(w0)
+    b.step(5)
+    qg.qg_stats_begin(b.h)
+    b.step(20)
+    out = torch.empty((ny - 1, nx - 1), dtype=torch.float64, device="cuda")
+    assert qg.qg_stats_mean_psi(b.h, out) == 20
+    b.synchronize()
+    assert rel_l2(to_np(out), ref) <= 1e-9
+    b.close()
