@@ -274,6 +274,12 @@ cudaError_t launch_mg_sum(const MGSumParams<T>& q, cudaStream_t s);
 template <typename T>
 cudaError_t launch_mg_cycle(const MGLevelDesc<T>* lv, int nl, int tail, cudaStream_t s);
 
+// Resident CTAs per SM and SM count for `kernel` at (threads, smem) on the
+// current device, its dynamic shared-memory limit raised to smem; looked up
+// once per (kernel, threads, smem, device) and cached (the eager launch
+// paths -- adjoint sweeps, stand-alone solves -- launch thousands of times).
+cudaError_t launch_shape(const void* kernel, int threads, size_t smem, int* per_sm, int* nsm);
+
 // Copies between the dense exchange layout and the padded node layout.
 cudaError_t copy_in(void* padded, int ld, const void* dense, int nxm1,
                     int nym1, size_t esz, cudaStream_t s);

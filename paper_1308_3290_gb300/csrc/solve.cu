@@ -19,10 +19,63 @@
 // directions and the y eigenvalues are bulk-copied into shared memory once.
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "dst_engine.cuh"
 #include "qg_internal.cuh"
 
 namespace qg {
+
+cudaError_t launch_shape(const void* kernel, int threads, size_t smem, int* per_sm, int* nsm) {
+    struct Key {
+        const void* k;
+        int threads;
+        size_t smem;
+        int dev;
+        bool operator<(const Key& o) const {
+            return std::tie(k, threads, smem, dev) < std::tie(o.k, o.threads, o.smem, o.dev);
+        }
+    };
+    static std::mutex mu;
+    static std::map<Key, std::pair<int, int>> cache;
+    static std::map<std::pair<const void*, int>, size_t> limit;   // smem limit set per kernel
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const Key key{kernel, threads, smem, dev};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *per_sm = it->second.first;
+            *nsm = it->second.second;
+            return cudaSuccess;
+        }
+    }
+    {
+        // the limit only ever rises: a launch of a cached shape must still fit
+        std::lock_guard<std::mutex> lock(mu);
+        size_t& cur = limit[{kernel, dev}];
+        if (smem > cur) {
+            if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem)) != cudaSuccess)
+                return e;
+            cur = smem;
+        }
+    }
+    int n = 0, per = 0;
+    if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem)) != cudaSuccess)
+        return e;
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = {per, n};
+    *per_sm = per;
+    *nsm = n;
+    return cudaSuccess;
+}
+
 namespace {
 
 using namespace eng;
@@ -308,13 +361,10 @@ solve_kernel(SolveParams<T> P) {
 template <typename T, int NBM, int OPY, int E>
 cudaError_t launch_one(const SolveParams<T>& P, size_t sm, cudaStream_t s) {
     auto k = solve_kernel<T, NBM, OPY, E>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    int dev = 0, nsm = 0, per = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int threads = solve_threads(P.mx, P.my, E);
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, sm)) != cudaSuccess) return e;
+    int nsm = 0, per = 0;
+    cudaError_t e = launch_shape(reinterpret_cast<const void*>(k), threads, sm, &per, &nsm);
+    if (e != cudaSuccess) return e;
     if (per < 1) return cudaErrorInvalidConfiguration;
     // no more CTAs than the largest phase has slots
     auto slots = [threads](int N, int pairs) {

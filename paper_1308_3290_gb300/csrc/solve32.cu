@@ -612,13 +612,9 @@ cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
                              (int)pass_table_size(2 * P.mx, RAD),
                              (int)pass_table_size(2 * P.my, RAD), P.my);
     const size_t sm = tb.end;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int nsm = 0, per = 0;
+    cudaError_t e = launch_shape(reinterpret_cast<const void*>(k), threads, sm, &per, &nsm);
     if (e != cudaSuccess) return e;
-    int dev = 0, nsm = 0, per = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, sm)) != cudaSuccess)
-        return e;
     if (per < 1) return cudaErrorInvalidConfiguration;
     auto slots = [threads](int lg, int npairs) {
         const int pairs = threads / ((1 << lg) / RAD);
