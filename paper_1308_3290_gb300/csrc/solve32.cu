@@ -540,6 +540,21 @@ solve32_kernel(SolveParams<T> P, int lgx, int lgy, Tabs tb) {
         pty = reinterpret_cast<const CT<T>*>(smem + tb.ty);
         lamy = reinterpret_cast<const T*>(smem + tb.ly);
     }
+    // While the stage before is still writing them, touch (L2 prefetch) the
+    // rows of the right-hand side this thread reads first, so that their
+    // address translations are in place when the data is ready.
+    if (!P.split || P.phase == 0) {
+        const Geo32 g = geo32(lgx, RAD);
+        const int npairs = (P.my / 2) * P.layers;
+        const int per = blockDim.x / g.G;
+        const PairAt a = pair_at<T, OPY>(P, 0, blockIdx.x * per + threadIdx.x / g.G, npairs);
+        const int c0 = 4 * (threadIdx.x % g.G);
+        if (a.va) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(P.in[a.layer][0] + (size_t)a.ra * P.ld + c0));
+            if (a.vb)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(P.in[a.layer][0] + (size_t)a.rb * P.ld + c0));
+        }
+    }
     pdl_wait();
     pdl_trigger();   // the next fine stage may start staging its own inputs
     if (tb.staged) {
