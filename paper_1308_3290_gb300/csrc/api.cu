@@ -1718,7 +1718,7 @@ struct qg_ensemble_s {
 
 namespace {
 
-constexpr int kEnsembleLanes = 8;
+constexpr int kEnsembleLanes = 16;
 
 void ensemble_free(qg_ensemble e) {
     if (!e) return;
