@@ -76,6 +76,8 @@ struct qg_ctx {
     size_t plane_f = 0;            // elements of one fine plane
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;    // private stream used for graph capture
+    cudaStream_t side = nullptr;   // two layers: the second layer's fine stage branch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void* w[3] = {nullptr, nullptr, nullptr};  // w^n, w^(1), w^(2) (layers planes each)
     void* psi = nullptr;           // fine psi (layers planes)
     void* cw = nullptr;            // elliptic-grid work (layers planes)
@@ -727,7 +729,16 @@ qg_status stage_fused2(qg_ctx* h, int s_idx, const LevelTables& t, cudaStream_t 
     void* win = h->w[s_idx];
     void* wout = h->w[(s_idx + 1) % 3];
     const double Av = h->Ro / h->Re;    // lateral eddy viscosity A (Re = Ro/A)
+    // The layers' fine stages are independent (each reads both layers' psi
+    // and writes only its own fields and partial planes): the second runs on
+    // a branch beside the first, so that the two half-GPU grids fill it.
+    cudaStream_t s1 = h->side ? h->side : s;
+    if (s1 != s) {
+        QG_TRY(cudaEventRecord(h->ev_fork, s));
+        QG_TRY(cudaStreamWaitEvent(s1, h->ev_fork, 0));
+    }
     for (int L = 0; L < 2; ++L) {
+        const cudaStream_t sl = L == 1 ? s1 : s;
         FusedParams<T> p;
         p.nx = h->nx;
         p.ny = h->ny;
@@ -763,8 +774,12 @@ qg_status stage_fused2(qg_ctx* h, int s_idx, const LevelTables& t, cudaStream_t 
         m.wn = h->tm_int[0][L];
         m.psi = h->tm_psi;
         m.f = h->tm_f;
-        KTimer kt(h, s, QG_K_FINE);
-        QG_TRY(launch_fine_fused<T>(p, m, h->levels, s, true));
+        KTimer kt(h, sl, QG_K_FINE);
+        QG_TRY(launch_fine_fused<T>(p, m, h->levels, sl, true));
+    }
+    if (s1 != s) {
+        QG_TRY(cudaEventRecord(h->ev_join, s1));
+        QG_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
     }
     return QG_OK;
 }
@@ -986,6 +1001,11 @@ static qg_status create_ctx(const qg_basin* b, int layers, double Re, double Ro,
         if (st != QG_OK && s == QG_OK) s = st;
     };
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) guard(QG_ERR_CUDA);
+    if (s == QG_OK && layers == 2 &&
+        (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess))
+        guard(QG_ERR_CUDA);
 
     const size_t fb = h->plane_f * layers * h->esz;
     const size_t cb = h->plane_c * layers * h->esz;
@@ -1057,6 +1077,9 @@ qg_status qg_destroy(qg_handle h) {
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->hout) cudaFreeHost(h->hout);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
     return QG_OK;
 }
