@@ -228,10 +228,29 @@ __device__ __forceinline__ void passW(const CT<T>* in, CT<T>* out, int t, const 
         }
     }
     if (!first) {
+        if constexpr (RAD == 8) {
+            // w^1 and w^4 from the table, the other powers as products (at
+            // most two roundings deep): 2 shared-memory loads instead of 7
+            const CT<T> a = tw[NS + k], b = tw[4 * NS + k];
+            const Cplx<T> w1{a.x, a.y}, w4{b.x, b.y};
+            const Cplx<T> w2 = cmul(w1, w1.x, w1.y);
+            const Cplx<T> w3 = cmul(w2, w1.x, w1.y);
+            const Cplx<T> w5 = cmul(w4, w1.x, w1.y);
+            const Cplx<T> w6 = cmul(w4, w2.x, w2.y);
+            const Cplx<T> w7 = cmul(w4, w3.x, w3.y);
+            v[1] = cmul(v[1], w1.x, w1.y);
+            v[2] = cmul(v[2], w2.x, w2.y);
+            v[3] = cmul(v[3], w3.x, w3.y);
+            v[4] = cmul(v[4], w4.x, w4.y);
+            v[5] = cmul(v[5], w5.x, w5.y);
+            v[6] = cmul(v[6], w6.x, w6.y);
+            v[7] = cmul(v[7], w7.x, w7.y);
+        } else {
 #pragma unroll
-        for (int r = 1; r < RAD; ++r) {
-            const CT<T> w = tw[r * NS + k];
-            v[r] = cmul(v[r], w.x, w.y);
+            for (int r = 1; r < RAD; ++r) {
+                const CT<T> w = tw[r * NS + k];
+                v[r] = cmul(v[r], w.x, w.y);
+            }
         }
     }
     if constexpr (RAD == 32) dft32<T>(v);
