@@ -72,7 +72,7 @@ using namespace eng;
 constexpr int kT = 256;                 // most threads per CTA
 constexpr int kSpin = 1 << 22;
 
-__host__ __device__ constexpr int px(int m) { return m + (m >> 5); }
+__host__ __device__ constexpr int px(int m) { return m + (m >> 4); }
 
 // Geometry of one FFT length L = 2^lg with RAD values per thread (RAD = 32
 // or 16): N = L/2, G = L/RAD threads per pair, np radix-RAD passes and a
