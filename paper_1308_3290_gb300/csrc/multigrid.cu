@@ -4,7 +4,8 @@
 // do not apply).
 //
 // lap_h psi = f on an mx x my grid of intervals with psi = 0 on the walls
-// (the 5-point operator of Eq. 5 with the grid's own spacings).  One V(2,2)
+// (the 5-point operator whose eigenvalues Eq. ialpha gives, Section 4.3,
+// with the grid's own spacings).  One V(2,2)
 // cycle:
 //   - two red-black Gauss-Seidel sweeps (each point solves its own 5-point
 //     equation for the current neighbours);

@@ -25,7 +25,7 @@ def eigenvalue(nx, ny, dx, dy, k, l):
 
 
 def lap_h(psi, dx, dy):
-    """The 5-point Laplacian (Eq. 5's discrete operator) with psi = 0 on the
+    """The 5-point Laplacian (the operator whose eigenvalues Eq. ialpha gives) with psi = 0 on the
     boundary, in FP64."""
     p = np.pad(psi.astype(np.float64), 1)
     return ((p[1:-1, 2:] - 2 * p[1:-1, 1:-1] + p[1:-1, :-2]) / dx ** 2
