@@ -10,6 +10,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -23,6 +24,17 @@
 #include <vector>
 
 #include "qg_internal.cuh"
+
+namespace {
+// NVTX range around a public call (shown by Nsight Systems and by
+// ncu --nvtx); the header-only NVTX 3 API costs nothing without a tool.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 using namespace qg;
 
@@ -1116,6 +1128,7 @@ qg_status qg_synchronize(qg_handle h) {
 }
 
 qg_status qg_set_state(qg_handle h, const void* field, int layer) {
+    NvtxRange nvtx_range("qg_set_state");
     if (!h || !field || layer < 0 || layer >= h->layers) return QG_ERR_ARG;
     if (h->latched != QG_OK) return qg_last_error(h);
     char* dst = static_cast<char*>(h->w[0]) + (size_t)layer * h->plane_f * h->esz;
@@ -1130,6 +1143,7 @@ qg_status qg_set_state(qg_handle h, const void* field, int layer) {
 }
 
 qg_status qg_get_state(qg_handle h, void* field, int layer) {
+    NvtxRange nvtx_range("qg_get_state");
     if (!h || !field || layer < 0 || layer >= h->layers) return QG_ERR_ARG;
     if (h->latched != QG_OK) return qg_last_error(h);
     const char* src = static_cast<const char*>(h->w[0]) + (size_t)layer * h->plane_f * h->esz;
@@ -1172,6 +1186,7 @@ qg_status qg_set_forcing(qg_handle h, const void* forcing) {
 }
 
 qg_status qg_poisson_solve(qg_handle h, const void* rhs, void* psi, int level) {
+    NvtxRange nvtx_range("qg_poisson_solve");
     if (!h || !rhs || !psi || level < 0 || level > h->levels) return QG_ERR_ARG;
     if (h->latched != QG_OK) return qg_last_error(h);
     if (h->solver == QG_SOLVER_MULTIGRID &&
@@ -1251,14 +1266,17 @@ static qg_status transfer(qg_handle h, const void* src, void* dst, int levels, b
 }
 
 qg_status qg_restrict(qg_handle h, const void* fine, void* coarse, int levels) {
+    NvtxRange nvtx_range("qg_restrict");
     return transfer(h, fine, coarse, levels, true);
 }
 
 qg_status qg_prolong(qg_handle h, const void* coarse, void* fine, int levels) {
+    NvtxRange nvtx_range("qg_prolong");
     return transfer(h, coarse, fine, levels, false);
 }
 
 qg_status qg_step(qg_handle h, int64_t n) {
+    NvtxRange nvtx_range("qg_step");
     if (!h || n < 0) return QG_ERR_ARG;
     if (h->latched != QG_OK) return qg_last_error(h);
     if (n == 0) return QG_OK;
@@ -1379,6 +1397,7 @@ qg_status qg_stats_begin(qg_handle h) {
 }
 
 qg_status qg_stats_mean_psi(qg_handle h, void* psi_mean, int layer, int64_t* count) {
+    NvtxRange nvtx_range("qg_stats_mean_psi");
     if (!h || layer < 0 || layer >= h->layers) return QG_ERR_ARG;
     if (!h->stats || h->stat_count == 0) return QG_ERR_ARG;
     if (h->latched != QG_OK) return qg_last_error(h);
@@ -1447,6 +1466,7 @@ qg_status qg_step_kernel_count(qg_handle h, int64_t* count) {
 }
 
 qg_status qg_diagnostics(qg_handle h, double* ke, double* enstrophy, double* max_vel) {
+    NvtxRange nvtx_range("qg_diagnostics");
     if (!h) return QG_ERR_ARG;
     if (h->latched != QG_OK) return qg_last_error(h);
     qg_status s = project_any(h, h->w[0], h->stream);
@@ -1709,6 +1729,7 @@ qg_status qg_tape_end(qg_handle h) {
 }
 
 qg_status qg_adjoint_step(qg_handle h, int64_t n, void* lambda, void* dJdF) {
+    NvtxRange nvtx_range("qg_adjoint_step");
     if (!h || !lambda || !dJdF || !h->tape || n < 0 || n > h->tape->cursor) return QG_ERR_ARG;
     if (h->latched != QG_OK) return qg_last_error(h);
     if (n == 0) return QG_OK;
@@ -1876,6 +1897,7 @@ qg_status qg_ensemble_member(qg_ensemble e, int index, qg_handle* out) {
 }
 
 qg_status qg_ensemble_step(qg_ensemble e, int64_t n) {
+    NvtxRange nvtx_range("qg_ensemble_step");
     if (!e || n < 0) return QG_ERR_ARG;
     for (qg_ctx* h : e->m)
         if (h->latched != QG_OK) return qg_last_error(h);

@@ -24,7 +24,7 @@ QG_F32, QG_F64 = 0, 1
 QG_FAULT_NONE, QG_FAULT_BARRIER_STALL = 0, 1
 QG_SOLVER_FFT, QG_SOLVER_MULTIGRID = 0, 1
 QG_OK, QG_ERR_ARG, QG_ERR_SHAPE, QG_ERR_CUDA, QG_ERR_OOM = 0, 1, 2, 3, 4
-QG_ERR_TIMEOUT, QG_ERR_UNSUPPORTED = 7, 8
+QG_ERR_NONFINITE, QG_ERR_CFL, QG_ERR_TIMEOUT, QG_ERR_UNSUPPORTED = 5, 6, 7, 8
 
 STATUS = {
     0: "QG_OK", 1: "QG_ERR_ARG", 2: "QG_ERR_SHAPE", 3: "QG_ERR_CUDA",
