@@ -145,3 +145,45 @@ def test_mean_psi_is_the_projection_of_the_mean_state(levels):
     ref = O.interior(O.prolong_levels(O.embed(O.poisson_solve(
         O.interior(O.restrict_levels(wbar, levels)), mx, my, dxc, dyc)), levels))
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_run_adaptive_threads_states_and_steps():
+    """run_adaptive is the loop of Eq. dt steps: capped (c huge) it is the
+    fixed-step run exactly; below the cap each step's dt is Eq. dt of that
+    step's own first streamfunction and the states follow TVDRK3 with it."""
+    b = O.Basin(32, 64, levels=1, dt=1e-3)
+    w0 = inputs.perturbation(32, 64, seed=31) * 50.0
+    w, dts = O.run_adaptive(w0, b, 4, 1e9)
+    assert dts == [b.dt] * 4
+    assert np.array_equal(w, O.run(w0, b, 4))
+    u0 = O.max_velocity(O.cgp_psi(O.embed(w0), b), b.dx, b.dy)
+    c = 0.3 * b.dt * u0 / min(b.dx, b.dy)          # Eq. dt below the cap
+    w, dts = O.run_adaptive(w0, b, 4, c)
+    s = O.embed(w0)
+    for k in range(4):
+        psi = O.cgp_psi(s, b)
+        dt = min(b.dt, c * min(b.dx, b.dy) / O.max_velocity(psi, b.dx, b.dy))
+        assert dts[k] == pytest.approx(dt, rel=1e-15)
+        s = O.tvdrk3(s, lambda x: O.cgp_rhs(x, b), dts[k])
+    assert np.array_equal(w, O.interior(s))
+    assert max(dts) < b.dt
+
+
+def test_two_layer_mean_psi_is_the_projection_of_the_mean_states():
+    """Both layers' psi are linear in (Q1, Q2) (restriction, the coupled solve
+    of Eqs. isub-1/2, prolongation), so their time means over steps n0..n1-1
+    equal the projection of the mean states of an independent run."""
+    b = O.TwoLayer(32, 32, levels=1, dt=1e-4)
+    Q1 = inputs.smooth_field(32, 32, seed=1, amp=0.05, noise=0.01)
+    Q2 = inputs.smooth_field(32, 32, seed=2, amp=0.02, noise=0.01)
+    m1, m2 = O.mean_psi_two_layer(Q1, Q2, b, 2, 7)
+    a1, a2 = O.embed(Q1), O.embed(Q2)
+    s1, s2 = [], []
+    for n in range(7):
+        if n >= 2:
+            s1.append(a1)
+            s2.append(a2)
+        a1, a2 = O.cgprk3_step_two_layer(a1, a2, b)
+    p1, p2 = O.two_layer_cgp_psi(sum(s1) / 5, sum(s2) / 5, b)
+    for got, ref in ((m1, O.interior(p1)), (m2, O.interior(p2))):
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
