@@ -146,3 +146,32 @@ def test_multigrid_with_adaptive_step_and_time_mean():
     b.synchronize()
     assert rel_l2(to_np(out), ref) <= 1e-9
     b.close()
+
+
+def test_multigrid_on_an_ensemble_member_equals_a_standalone_handle():
+    """The solver switch on one member of an ensemble: its steps are bitwise
+    those of a stand-alone handle with the same switch (the V-cycles do not
+    depend on how the member's graph is launched); the other members keep
+    the sine transforms and follow the oracle."""
+    require_gpu()
+    members = [dict(nx=64, ny=128, Re=200.0, Ro=0.0016, levels=1, dt=1e-4),
+               dict(nx=128, ny=256, Re=200.0, Ro=0.0016, levels=2, dt=5e-5)]
+    w = [inputs.perturbation(m["nx"], m["ny"], seed=60 + i) * 40.0 for i, m in enumerate(members)]
+    ens = qg.Ensemble(members, dtype="f32")
+    qg.qg_set_solver(ens.member(1).h, qg.QG_SOLVER_MULTIGRID, 3)
+    for i in range(2):
+        ens.member(i).set_state(w[i])
+    ens.step(15)
+    ens.synchronize()
+    m = members[1]
+    solo = qg.Basin(m["nx"], m["ny"], Re=m["Re"], Ro=m["Ro"], levels=m["levels"], dt=m["dt"],
+                    dtype="f32")
+    qg.qg_set_solver(solo.h, qg.QG_SOLVER_MULTIGRID, 3)
+    solo.set_state(w[1])
+    solo.step(15)
+    assert np.array_equal(to_np(ens.member(1).state()), to_np(solo.state()))
+    m0 = members[0]
+    ref = O.run(w[0], O.Basin(m0["nx"], m0["ny"], Re=200.0, Ro=0.0016, levels=1, dt=1e-4), 15)
+    assert rel_l2(to_np(ens.member(0).state()), ref) <= 1e-5
+    solo.close()
+    ens.close()
