@@ -297,7 +297,7 @@ qg_status get_level(qg_ctx* h, int lv, const LevelTables** out) {
     if (s == QG_OK) s = get_twiddles(h, t.my, &t.twy);
     for (int r = 0; r < 3 && s == QG_OK; ++r) {
         const int rad = warp_engine_radix(32 + r);
-        if (!solve32_supports(t.mx, t.my, rad)) continue;
+        if (!solve32_supports(t.mx, t.my, rad, h->esz)) continue;
         s = get_pass_table(h, 2 * t.mx, rad, &t.ptx[r]);
         if (s == QG_OK) s = get_pass_table(h, 2 * t.my, rad, &t.pty[r]);
     }

@@ -84,7 +84,7 @@ void pass_table(int L, int rad, double* re, double* im);   // pass_table_size en
 template <typename T>
 cudaError_t launch_solve32(const SolveParams<T>& P, int rad, cudaStream_t s);
 size_t solve32_smem_bytes(int mx, int my, size_t esz, int rad);
-bool solve32_supports(int mx, int my, int rad);
+bool solve32_supports(int mx, int my, int rad, size_t esz);
 // engines 32, 33, 34: the warp-group engine with 32, 16, 8 values per thread
 inline int warp_engine_radix(int engine) { return engine == 34 ? 8 : (engine == 33 ? 16 : 32); }
 inline bool is_warp_engine(int engine) { return engine >= 32 && engine <= 34; }

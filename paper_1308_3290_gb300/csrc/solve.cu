@@ -408,7 +408,8 @@ size_t solve_smem_bytes(int mx, int my, size_t esz, int engine) {
 bool solve_engine_supports(int mx, int my, size_t esz, int engine) {
     if (is_warp_engine(engine)) {
         const int rad = warp_engine_radix(engine);
-        return solve32_supports(mx, my, rad) && solve32_smem_bytes(mx, my, esz, rad) <= 200 * 1024;
+        return solve32_supports(mx, my, rad, esz) &&
+               solve32_smem_bytes(mx, my, esz, rad) <= 200 * 1024;
     }
     if (engine != 4 && engine != 16) return false;
     const int nbm = nb_for(mx, engine) > nb_for(my, engine) ? nb_for(mx, engine) : nb_for(my, engine);

@@ -69,7 +69,12 @@ namespace {
 
 using namespace eng;
 
-constexpr int kT = 256;                 // most threads per CTA
+// most threads per CTA: 512 for FP32 with 16 values per thread (a pair of
+// length-8192 sequences in one group: 2 N = 8192 for the full 2048 x 4096
+// grid), else 256
+__host__ __device__ constexpr int max_cta(int rad, int esz) {
+    return (rad == 16 && esz == 4) ? 512 : 256;
+}
 constexpr int kSpin = 1 << 22;
 
 __host__ __device__ constexpr int px(int m) { return m + (m >> 4); }
@@ -532,7 +537,8 @@ __host__ __device__ inline Tabs tabs_for(int lgx, int lgy, int rad, int threads,
 }
 
 template <typename T, int OPY, int RAD>
-__global__ void __launch_bounds__(kT, (RAD <= 16 && sizeof(T) == 4) ? 2 : 1)
+__global__ void __launch_bounds__(max_cta(RAD, (int)sizeof(T)),
+                                  (RAD == 8 && sizeof(T) == 4) ? 2 : 1)
 solve32_kernel(SolveParams<T> P, int lgx, int lgy, Tabs tb) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
@@ -688,11 +694,13 @@ cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
 
 }  // namespace
 
-// lengths 2N = 2^lg with lg in [log2(RAD), log2(RAD) + 8] (G <= 256 threads)
-bool solve32_supports(int mx, int my, int rad) {
+// lengths 2N = 2^lg with G = 2^lg / RAD threads per pair within one CTA
+// (G <= max_cta(RAD, esz))
+bool solve32_supports(int mx, int my, int rad, size_t esz) {
     const int lx = log2i(2 * mx), ly = log2i(2 * my), lr = log2i(rad);
+    const int lt = log2i(max_cta(rad, (int)esz));
     return (rad == 8 || rad == 16 || rad == 32) && is_pow2(mx) && is_pow2(my) && lx >= lr &&
-           ly >= lr && lx <= lr + 8 && ly <= lr + 8;
+           ly >= lr && lx <= lr + lt && ly <= lr + lt;
 }
 
 size_t solve32_smem_bytes(int mx, int my, size_t esz, int rad) {
@@ -704,7 +712,8 @@ size_t solve32_smem_bytes(int mx, int my, size_t esz, int rad) {
 
 template <typename T>
 cudaError_t launch_solve32(const SolveParams<T>& P, int rad, cudaStream_t s) {
-    if (!solve32_supports(P.mx, P.my, rad) || !P.ptx || !P.pty) return cudaErrorInvalidValue;
+    if (!solve32_supports(P.mx, P.my, rad, sizeof(T)) || !P.ptx || !P.pty)
+        return cudaErrorInvalidValue;
     if (rad == 8)
         return P.layers == 2 ? launch32<T, 2, 8>(P, s) : launch32<T, 1, 8>(P, s);
     if (rad == 16)
