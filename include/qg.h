@@ -21,7 +21,7 @@
  * values, x fastest, in the handle's dtype (float for QG_F32, double for
  * QG_F64).  Pointers may be device pointers or host pointers (pageable host
  * memory makes the copy synchronous; pinned host memory keeps it
- * asynchronous).  The caller owns every pointer it passes; the handle owns
+ * asynchronous: a kernel reads or writes it in place).  The caller owns every pointer it passes; the handle owns
  * its internal state and workspace (device memory allocated in qg_create).
  *
  * Threading.  One handle is used by one host thread at a time; calls on
@@ -43,7 +43,8 @@ typedef enum qg_status {
     QG_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed  */
     QG_ERR_OOM = 4,          /* device allocation failed                     */
     QG_ERR_NONFINITE = 5,    /* the state holds NaN or Inf                   */
-    QG_ERR_CFL = 6,          /* CFL number above the handle's limit          */
+    QG_ERR_CFL = 6,          /* reserved (no call checks a CFL limit; see
+                                qg_set_cfl for the adaptive step)           */
     QG_ERR_TIMEOUT = 7,      /* a bounded device-side wait ran out           */
     QG_ERR_UNSUPPORTED = 8,  /* valid request this build does not provide    */
     QG_ERR_NO_DEVICE = 9     /* no usable CUDA device                        */
