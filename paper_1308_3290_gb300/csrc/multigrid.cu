@@ -22,6 +22,8 @@
 // shared memory.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "qg_internal.cuh"
 
 namespace qg {
@@ -241,7 +243,9 @@ int blocks_for(long n) {
 // most any hierarchy uses (called when a hierarchy is built, outside any
 // stream capture).
 cudaError_t mg_reserve_tail_smem(size_t bytes, size_t esz) {
+    static std::mutex mu;             // handles on other host threads share it
     static size_t have[2] = {0, 0};
+    std::lock_guard<std::mutex> lock(mu);
     const int k = esz == 8 ? 1 : 0;
     if (bytes <= have[k]) return cudaSuccess;
     const cudaError_t e =
