@@ -112,6 +112,7 @@ struct qg_ctx {
     cudaGraphExec_t gexec = nullptr;
     qg_status latched = QG_OK;
     std::vector<void*> allocs;
+    size_t alloc_bytes = 0;        // device bytes held through dev_alloc
     // per-kernel timing (bench instrumentation): events recorded in the graph
     bool timing = false;
     unsigned timing_mask = ~0u;    // kernel classes bracketed by timing events
@@ -193,7 +194,17 @@ qg_status cuda_status(qg_ctx* h, cudaError_t e) {
         if (e_ != cudaSuccess) return cuda_status(h, e_); \
     } while (0)
 
+// QG_ALLOC_LIMIT_BYTES (a test hook for the out-of-memory path): the device
+// bytes one handle may hold; an allocation past it fails as a failed
+// cudaMalloc does, with QG_ERR_OOM.
 qg_status dev_alloc(qg_ctx* h, void** p, size_t bytes) {
+    if (const char* lim = std::getenv("QG_ALLOC_LIMIT_BYTES")) {
+        const unsigned long long cap = std::strtoull(lim, nullptr, 10);
+        if (cap > 0 && h->alloc_bytes + bytes > cap) {
+            *p = nullptr;
+            return QG_ERR_OOM;
+        }
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -201,6 +212,7 @@ qg_status dev_alloc(qg_ctx* h, void** p, size_t bytes) {
         return e == cudaErrorMemoryAllocation ? QG_ERR_OOM : QG_ERR_CUDA;
     }
     h->allocs.push_back(*p);
+    h->alloc_bytes += bytes;
     e = cudaMemset(*p, 0, bytes);
     return e == cudaSuccess ? QG_OK : QG_ERR_CUDA;
 }

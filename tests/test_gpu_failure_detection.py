@@ -53,3 +53,24 @@ def test_stalled_barrier_is_reported_and_recovered():
     assert rel_l2(to_np(psi), O.poisson_solve(rhs, nx, ny, 1.0 / nx, 2.0 / ny)) <= 1e-12
     b.close()
     assert np.isfinite(torch.ones(4, device="cuda").sum().item())
+
+
+def test_allocation_failure_is_reported_and_released(monkeypatch):
+    """An allocation past the injected limit fails like a failed cudaMalloc:
+    qg_create returns QG_ERR_OOM, frees what it had allocated, and a handle
+    can be created once the limit is lifted."""
+    torch = require_gpu()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    monkeypatch.setenv("QG_ALLOC_LIMIT_BYTES", str(16 << 20))   # the basin needs ~50 MB
+    for _ in range(3):
+        with pytest.raises(qg.QGError) as e:
+            qg.Basin(1024, 2048, Re=200.0, Ro=0.0016, levels=1, dt=1e-5, dtype="f32")
+        assert e.value.status == qg.QG_ERR_OOM
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (32 << 20)   # nothing held back
+    monkeypatch.delenv("QG_ALLOC_LIMIT_BYTES")
+    b = qg.Basin(1024, 2048, Re=200.0, Ro=0.0016, levels=1, dt=1e-5, dtype="f32")
+    b.step(1)
+    b.synchronize()
+    b.close()
