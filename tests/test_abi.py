@@ -71,6 +71,18 @@ def test_calls_on_null_handle(lib):
     assert lib.qg_set_state(None, None, 0) == 1
     assert lib.qg_synchronize(None) == 1
     assert lib.qg_inject_fault(None, 1) == 1
+    assert lib.qg_set_solver(None, 1, 4) == 1
+    assert lib.qg_set_cfl(None, 0.5) == 1
+    assert lib.qg_stats_begin(None) == 1
+    assert lib.qg_stats_end(None) == 1
+    assert lib.qg_tape_begin(None, 1, 10) == 1
+    assert lib.qg_adjoint_step(None, 1, None, None) == 1
+    assert lib.qg_get_time(None, None, None) == 1
+    assert lib.qg_set_timing_mask(None, 1) == 1
+    assert lib.qg_ensemble_step(None, 1) == 1
+    assert lib.qg_ensemble_destroy(None) == 0
+    e = ctypes.c_void_p()
+    assert lib.qg_ensemble_create(None, None, None, None, 0, 0, None, ctypes.byref(e)) == 1
 
 
 def test_no_device_is_reported():
