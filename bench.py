@@ -335,6 +335,39 @@ def kernel_timing(torch, qg, h, stream, K, flush):
     return acc
 
 
+def small_basin_variant(torch, qg, inputs, stream, flush):
+    """The 64x128, l = 1 basin (elliptic grid 32x64) in FP32 with the
+    autotuned solve and with each kind of solve kernel forced: shared-memory
+    FFT (4), warp-group FFT (34) and the matrix form on the tensor cores
+    (40).  Steps/s of the whole step and the mean solve launch."""
+    out = {}
+    prev = os.environ.get("QG_SOLVE_ENGINE")
+    w = inputs.gyre_state(64, 128, seed=SEED)
+    try:
+        for eng in ("auto", "4", "34", "40"):
+            if eng == "auto":
+                os.environ.pop("QG_SOLVE_ENGINE", None)
+            else:
+                os.environ["QG_SOLVE_ENGINE"] = eng
+            b = qg.Basin(64, 128, Re=RE, Ro=RO, levels=1, dt=2e-5, dtype="f32", stream=stream)
+            b.set_state(w)
+            for _ in range(20):
+                qg.qg_step(b.h, 1)
+            K = 1000
+            ts = time_steps(torch, qg, b.h, stream, K, flush)
+            kt = kernel_timing(torch, qg, b.h, stream, 50, flush)
+            ms, n = kt["solve"]
+            out[eng] = {"engine": qg.qg_solve_engine(b.h), "steps_per_s": K / (sum(ts) / 1e3),
+                        "ms_per_step": sum(ts) / K, "solve_us": 1e3 * ms / max(1, n)}
+            b.close()
+    finally:
+        if prev is None:
+            os.environ.pop("QG_SOLVE_ENGINE", None)
+        else:
+            os.environ["QG_SOLVE_ENGINE"] = prev
+    return out
+
+
 def ensemble_members(count=96, seed=4):
     """Independent one-layer basins of four sizes, Re ~ U[200, 1000], forcing
     amplitude ~ U[0.5, 1.5], Ro = 0.0016, CGP level 1 or 2, seeded."""
@@ -550,6 +583,7 @@ def ours(args):
         variants["two_layer_1024x2048_l1_f32"] = {"steps_per_s": 100 / (sum(ts) / 1e3),
                                                   "ms_per_step": sum(ts) / 100}
         b.close()
+        variants["small_64x128_l1_f32"] = small_basin_variant(torch, qg, inputs, stream, flush)
         variants["ensemble_96_f32"] = ensemble_variant(torch, qg, inputs, stream, flush)
         variants["adjoint_256x512_l1_f32"] = adjoint_variant(torch, qg, inputs, stream)
 

@@ -246,6 +246,18 @@ typedef enum qg_solver {
  * QG_SOLVER_FFT.  Re-captures the step graph.  Errors: QG_ERR_ARG.        */
 qg_status qg_set_solver(qg_handle h, qg_solver kind, int32_t cycles);
 
+/* qg_solve_engine -- which kernel the step's elliptic solves run on (host
+ * pointer): chosen when the handle is created by timing whole steps with
+ * every candidate that supports the elliptic grid (the QG_SOLVE_ENGINE
+ * environment variable forces a supported one).  4 or 16: shared-memory
+ * Stockham FFT with base radix 4 or 16; 32, 33, 34: warp-group FFT with 32,
+ * 16 or 8 values per thread; 40: the sine sums as dense matrix products on
+ * the tensor cores, 3xTF32 (one-layer FP32 grids of at most 64 x 128 or
+ * 128 x 64 intervals); 0: the multigrid solver (qg_set_solver).  These are
+ * implementations of the same sine-transform solve of Section 4.3, equal to
+ * rounding.  No device work.  Errors: QG_ERR_ARG.                          */
+qg_status qg_solve_engine(qg_handle h, int32_t* engine);
+
 /* qg_get_time -- model time since creation or the last qg_set_state, and
  * the size of the last step (host pointers; either may be NULL).
  * Synchronises the handle's stream.                                        */

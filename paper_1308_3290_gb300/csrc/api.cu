@@ -21,9 +21,11 @@
 #include <mutex>
 #include <new>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "qg_internal.cuh"
+#include "solve_mtx.h"
 
 namespace {
 // NVTX range around a public call (shown by Nsight Systems and by
@@ -49,6 +51,7 @@ struct LevelTables {
     void* lamy = nullptr;  // (2 cos(pi l/my) - 2)/dyc^2, l = 0..my
     void* ptx[3] = {nullptr, nullptr, nullptr};  // warp-group engine pass twiddles for
     void* pty[3] = {nullptr, nullptr, nullptr};  //   L = 2 mx and 2 my, engines 32/33/34
+    void* mtab = nullptr;  // matrix engine (FP32, one layer): sine matrices and 1/lambda
 };
 
 // Multigrid hierarchy below one elliptic grid (multigrid.cu): grids 1..nl-1
@@ -313,6 +316,14 @@ qg_status get_level(qg_ctx* h, int lv, const LevelTables** out) {
         s = get_pass_table(h, 2 * t.mx, rad, &t.ptx[r]);
         if (s == QG_OK) s = get_pass_table(h, 2 * t.my, rad, &t.pty[r]);
     }
+    if (s == QG_OK && h->esz == 4 && mtx_supports(t.mx, t.my, 4, h->layers)) {
+        std::vector<float> m(mtx_table_floats(t.mx, t.my));
+        mtx_table(t.mx, t.my, t.dxc, t.dyc, m.data());
+        s = dev_alloc(h, &t.mtab, m.size() * sizeof(float));
+        if (s == QG_OK &&
+            cudaMemcpy(t.mtab, m.data(), m.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            s = QG_ERR_CUDA;
+    }
     if (s != QG_OK) return s;
     const double pi = 3.14159265358979323846;
     // padded to a multiple of 4 entries: the solve copies them in 16-byte units
@@ -500,6 +511,15 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
     P.err = h->derr;
     P.split = h->split_solve ? 1 : 0;
     KTimer kt(h, s, QG_K_SOLVE);
+    if (eng == kMatrixEngine) {
+        // one launch whether or not the FFT solves are split
+        if (h->capturing && h->split_solve) h->kernels_per_step -= 2;
+        if constexpr (std::is_same<T, float>::value)
+            QG_TRY(launch_solve_mtx(P, static_cast<const float*>(t.mtab), s));
+        else
+            QG_TRY(cudaErrorInvalidValue);
+        return QG_OK;
+    }
     QG_TRY(launch_solve<T>(P, eng, s));
     return QG_OK;
 }
@@ -508,14 +528,15 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
 // The FFT engine of the solve (shared-memory Stockham engine with base
 // radix 4: many threads per sequence pair, or 16: fewer passes and
 // instructions; or the warp-group engine of solve32.cu with 32, 16 or 8
-// values per thread, engines 32, 33, 34) is chosen
-// per handle when it is created, by timing a few whole steps with each
+// values per thread, engines 32, 33, 34; or, on small one-layer FP32 grids,
+// the matrix-form solve on the tensor cores of solve_mtx.cu, engine 40) is
+// chosen per handle when it is created, by timing a few whole steps with each
 // engine that supports the elliptic grid (the solve alone, timed back to
 // back, ranks them differently: in a step the fine sweep has just streamed
 // its fields through L2), and the fastest is kept.  Results are cached per
 // (nx, ny, levels, layers, dtype) for the process and, when the environment
 // variable QG_TUNE_CACHE names a file, in that file (one line
-// "nx ny levels layers esz engine" per entry).  QG_SOLVE_ENGINE=4|16|32|33|34
+// "nx ny levels layers esz engine" per entry).  QG_SOLVE_ENGINE=4|16|32|33|34|40
 // forces a choice where that engine supports the grid.  Other grids use the
 // size rule.
 
@@ -525,6 +546,12 @@ int engine_for(qg_ctx* h, int mx, int my) {
     const LevelTables* t = nullptr;
     if (get_level(h, h->levels, &t) == QG_OK && t->mx == mx && t->my == my) return h->solve_engine;
     return engine_rule(mx, my);
+}
+
+// Whether engine e can solve the level with tables t on handle h.
+bool engine_ok(const qg_ctx* h, const LevelTables* t, size_t esz, int e) {
+    if (e == kMatrixEngine) return t->mtab && mtx_supports(t->mx, t->my, esz, h->layers);
+    return solve_engine_supports(t->mx, t->my, esz, e) && (!is_warp_engine(e) || t->ptx[e - 32]);
 }
 
 using TuneKey = std::tuple<int, int, int, int, int>;
@@ -541,7 +568,8 @@ void tune_file_load() {
     if (!f) return;
     int a, b, c, d, x, e;
     while (std::fscanf(f, "%d %d %d %d %d %d", &a, &b, &c, &d, &x, &e) == 6)
-        if (e == 4 || e == 16 || is_warp_engine(e)) g_tune_cache[TuneKey(a, b, c, d, x)] = e;
+        if (e == 4 || e == 16 || is_warp_engine(e) || e == kMatrixEngine)
+            g_tune_cache[TuneKey(a, b, c, d, x)] = e;
     std::fclose(f);
 }
 
@@ -566,9 +594,7 @@ template <typename T>
 float time_steps(qg_ctx* h, int engine) {
     const LevelTables* t = nullptr;
     if (get_level(h, h->levels, &t) != QG_OK) return 1e30f;
-    if (!solve_engine_supports(t->mx, t->my, sizeof(T), engine) ||
-        (is_warp_engine(engine) && !t->ptx[engine - 32]))
-        return 1e30f;
+    if (!engine_ok(h, t, sizeof(T), engine)) return 1e30f;
     h->solve_engine = engine;
     drop_graph(h);
     if (build_graph(h) != QG_OK) return 1e30f;
@@ -598,8 +624,7 @@ qg_status autotune_solve(qg_ctx* h) {
     if (st != QG_OK) return st;
     if (const char* force = std::getenv("QG_SOLVE_ENGINE")) {
         const int e = std::atoi(force);
-        if (solve_engine_supports(t->mx, t->my, sizeof(T), e) &&
-            (!is_warp_engine(e) || t->ptx[e - 32])) {
+        if (engine_ok(h, t, sizeof(T), e)) {
             h->solve_engine = e;
             return QG_OK;
         }
@@ -619,14 +644,15 @@ qg_status autotune_solve(qg_ctx* h) {
     const float t33 = time_steps<T>(h, 33);
     const float t34 = time_steps<T>(h, 34);
     const float t16 = time_steps<T>(h, 16);
+    const float t40 = time_steps<T>(h, kMatrixEngine);
     // a candidate that cannot run on this grid is a tuning result, not an error
     h->latched = QG_OK;
     (void)cudaGetLastError();
     drop_graph(h);
-    const float tt[5] = {t4, t16, t32, t33, t34};
-    const int ee[5] = {4, 16, 32, 33, 34};
+    const float tt[6] = {t4, t16, t32, t33, t34, t40};
+    const int ee[6] = {4, 16, 32, 33, 34, kMatrixEngine};
     int best = 0;
-    for (int k = 1; k < 5; ++k)
+    for (int k = 1; k < 6; ++k)
         if (tt[k] < tt[best]) best = k;
     if (tt[best] >= 1e29f) return fail(h, QG_ERR_CUDA);
     h->solve_engine = ee[best];
@@ -1466,6 +1492,12 @@ qg_status qg_read_timing(qg_handle h, double* ms, int32_t* launches) {
         ms[u.first] += t;
         launches[u.first] += 1;
     }
+    return QG_OK;
+}
+
+qg_status qg_solve_engine(qg_handle h, int32_t* engine) {
+    if (!h || !engine) return QG_ERR_ARG;
+    *engine = h->solver == QG_SOLVER_MULTIGRID ? 0 : h->solve_engine;
     return QG_OK;
 }
 

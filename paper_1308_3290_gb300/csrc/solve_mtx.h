@@ -1,0 +1,34 @@
+// The matrix-form elliptic solve (solve_mtx.cu): declarations for the host
+// code that builds its tables and picks it as a solve engine.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "qg_internal.cuh"
+
+namespace qg {
+
+// Engine number of the matrix-form solve among the autotuner's candidates
+// (the FFT engines are 4, 16 and 32-34).
+constexpr int kMatrixEngine = 40;
+
+// One-layer FP32 elliptic grids whose sine matrices and work arrays fit in
+// one CTA's shared memory (Mx, My powers of two >= 2, at most 128 x 128
+// interior nodes in practice: 64 x 128 and 128 x 64 fit, 128 x 128 does not).
+bool mtx_supports(int mx, int my, size_t esz, int layers);
+size_t mtx_smem_bytes(int mx, int my);
+
+// The constant table of one elliptic grid: S_x (padded), S_y (padded) and
+// the scaled inverse eigenvalues (2/Mx)(2/My)/lambda_kl of Eq. ialpha, in
+// the layout the kernel copies into shared memory; FP64-evaluated, stored
+// FP32.  mtx_table_floats(mx, my) entries.
+size_t mtx_table_floats(int mx, int my);
+void mtx_table(int mx, int my, double dx, double dy, float* out);
+
+// The solve of one level: P as for launch_solve (one layer, FP32; P.split
+// is ignored: one single-CTA launch either way), tab the device copy of
+// mtx_table.
+cudaError_t launch_solve_mtx(const SolveParams<float>& P, const float* tab, cudaStream_t s);
+
+}  // namespace qg

@@ -43,7 +43,7 @@ EXPORTS = [
     "qg_ensemble_kernel_count", "qg_ensemble_synchronize", "qg_ensemble_destroy",
     "qg_tape_begin", "qg_tape_end", "qg_adjoint_step", "qg_energy_gradient",
     "qg_set_cfl", "qg_set_solver", "qg_get_time", "qg_stats_begin", "qg_stats_mean_psi", "qg_stats_end",
-    "qg_set_timing_mask",
+    "qg_set_timing_mask", "qg_solve_engine",
 ]
 
 KERNEL_CLASSES = ["restrict", "solve", "prolong", "fine", "cfl"]
@@ -111,6 +111,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "qg_energy_gradient": [vp, dbl, vp],
         "qg_set_cfl": [vp, dbl],
         "qg_set_solver": [vp, i32, i32],
+        "qg_solve_engine": [vp, ctypes.POINTER(i32)],
         "qg_get_time": [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
         "qg_stats_begin": [vp],
         "qg_stats_mean_psi": [vp, vp, i32, ctypes.POINTER(i64)],
@@ -266,6 +267,15 @@ def qg_set_cfl(h: int, c: float) -> None:
 
 def qg_set_solver(h: int, kind: int, cycles: int = 4) -> None:
     _check(load().qg_set_solver(h, kind, cycles), "qg_set_solver")
+
+
+def qg_solve_engine(h: int) -> int:
+    """The elliptic-solve kernel of the handle's step: 4, 16 (shared-memory
+    FFT), 32, 33, 34 (warp-group FFT), 40 (matrix form on the tensor cores),
+    0 (multigrid)."""
+    e = ctypes.c_int32()
+    _check(load().qg_solve_engine(h, ctypes.byref(e)), "qg_solve_engine")
+    return e.value
 
 
 def qg_get_time(h: int) -> tuple[float, float]:

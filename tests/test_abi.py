@@ -79,6 +79,7 @@ def test_calls_on_null_handle(lib):
     assert lib.qg_adjoint_step(None, 1, None, None) == 1
     assert lib.qg_get_time(None, None, None) == 1
     assert lib.qg_set_timing_mask(None, 1) == 1
+    assert lib.qg_solve_engine(None, None) == 1
     assert lib.qg_ensemble_step(None, 1) == 1
     assert lib.qg_ensemble_destroy(None) == 0
     e = ctypes.c_void_p()
