@@ -14,8 +14,8 @@ namespace qg {
 constexpr int kMatrixEngine = 40;
 
 // One-layer FP32 elliptic grids whose sine matrices and work arrays fit in
-// one CTA's shared memory (Mx, My powers of two >= 2, at most 128 x 128
-// interior nodes in practice: 64 x 128 and 128 x 64 fit, 128 x 128 does not).
+// 200 KB of one CTA's shared memory (Mx, My powers of two): up to 64 x 128
+// or 128 x 64 intervals (156 KB); 128 x 128 would need 270 KB.
 bool mtx_supports(int mx, int my, size_t esz, int layers);
 size_t mtx_smem_bytes(int mx, int my);
 
