@@ -85,9 +85,10 @@ def test_two_layer_solve_parity():
 @pytest.mark.parametrize("engine", ["4", "16", "32", "33", "34"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_both_fft_engines(engine, dtype, monkeypatch):
-    """The solve has four FFT schedules (shared-memory engine with base
-    radix 4 or 16, warp-group engine with 32 or 16 values per thread) chosen
-    by the autotuner; each must meet the same tolerance."""
+    """The solve has five FFT schedules (shared-memory engine with base
+    radix 4 or 16, warp-group engine with 32, 16 or 8 values per thread)
+    chosen by the autotuner; each must meet the same tolerance (the matrix
+    form of small grids has its own tests)."""
     require_gpu()
     monkeypatch.setenv("QG_SOLVE_ENGINE", engine)
     shapes = [(64, 128), (512, 1024), (2048, 256)]
