@@ -163,3 +163,94 @@ def test_adjoint_pins_reject_mistakes():
     assert not ok(flipped_beta)
     assert not ok(no_projection)
     assert not ok(transposed_operands)
+
+
+def test_two_layer_solve_pins_reject_mistakes():
+    """The dense block solve of Eq. sub-pr rejects swapped layer-thickness
+    factors and a flipped coupling sign in Eqs. isub-1/2."""
+    nx, ny = 8, 16
+    dx, dy = 1.0 / nx, 2.0 / ny
+    Ro, Fr, d = 2.49e-4, 0.087, 0.2
+    rng = np.random.default_rng(23)
+    Q1 = rng.normal(size=(ny - 1, nx - 1))
+    Q2 = rng.normal(size=(ny - 1, nx - 1))
+    Lm = Ro * dense_laplacian(nx, ny, dx, dy)
+    I = np.eye(Lm.shape[0])
+    f1, f2 = Fr / d, Fr / (1 - d)
+    M = np.block([[Lm - f1 * I, f1 * I], [f2 * I, Lm - f2 * I]])
+    sol = np.linalg.solve(M, np.concatenate([Q1.ravel(), Q2.ravel()]))
+
+    def ok(solve):
+        p1, p2 = solve(Q1, Q2)
+        got = np.concatenate([p1.ravel(), p2.ravel()])
+        return np.linalg.norm(got - sol) <= 1e-12 * np.linalg.norm(sol)
+
+    def spectral(c1, c2, sign):
+        def solve(A, B):
+            Ah, Bh = O.sine_analysis(A, nx, ny), O.sine_analysis(B, nx, ny)
+            a = O.alpha(nx, ny, dx, dy, Ro)
+            den = a * (a - c1 - c2)
+            P1 = (a * Ah - c2 * Ah + sign * c1 * Bh) / den
+            P2 = (a * Bh - c2 * Ah + sign * c1 * Bh) / den
+            return O.sine_synthesis(P1, nx, ny), O.sine_synthesis(P2, nx, ny)
+        return solve
+
+    assert ok(lambda A, B: O.elliptic_two_layer(A, B, nx, ny, dx, dy, Ro, Fr, d))
+    assert ok(spectral(f1, f2, -1.0))          # the same algebra, restated
+    assert not ok(spectral(f2, f1, -1.0))      # thickness factors swapped
+    assert not ok(spectral(f1, f2, +1.0))      # coupling sign flipped
+
+
+def test_energy_pins_reject_mistakes():
+    """The summation-by-parts identity of the kinetic energy rejects central
+    differences and a dropped y-edge sum."""
+    b = O.Basin(32, 64, levels=0)
+    w = O.embed(np.random.default_rng(24).normal(size=(63, 31)))
+    psi = O.cgp_psi(w, b)
+    target = -0.5 * b.dx * b.dy * np.sum(O.interior(psi) * O.laplacian5(psi, b.dx, b.dy))
+
+    def ok(E):
+        return abs(E(psi, b.dx, b.dy) - target) <= 1e-12 * abs(target)
+
+    def central(p, dx, dy):
+        ex = (p[1:-1, 2:] - p[1:-1, :-2]) / (2 * dx)
+        ey = (p[2:, 1:-1] - p[:-2, 1:-1]) / (2 * dy)
+        return 0.5 * dx * dy * float(np.sum(ex * ex) + np.sum(ey * ey))
+
+    def x_edges_only(p, dx, dy):
+        ex = (p[:, 1:] - p[:, :-1]) / dx
+        return 0.5 * dx * dy * float(np.sum(ex * ex))
+
+    assert ok(O.kinetic_energy)
+    assert not ok(central)
+    assert not ok(x_edges_only)
+
+
+def test_cfl_pins_reject_mistakes():
+    """The closed form of max |grad psi| on a sine mode rejects one-sided
+    differences and a dropped factor 2 in the central difference."""
+    nx, ny = 32, 64
+    dx, dy = 1.0 / nx, 2.0 / ny
+    i = np.arange(nx + 1)[None, :]
+    j = np.arange(ny + 1)[:, None]
+    psi = 1.5 * np.sin(np.pi * i / nx) * np.sin(np.pi * j / ny)
+    ux = 1.5 * np.cos(np.pi / nx) * np.sin(np.pi / nx) / dx
+    uy = 1.5 * np.cos(np.pi / ny) * np.sin(np.pi / ny) / dy
+    u = max(ux, uy)
+
+    def ok(mv):
+        return abs(mv(psi, dx, dy) - u) <= 1e-13 * u
+
+    def one_sided(p, dx, dy):
+        px = (p[1:-1, 2:] - p[1:-1, 1:-1]) / dx
+        py = (p[2:, 1:-1] - p[1:-1, 1:-1]) / dy
+        return float(max(np.abs(px).max(), np.abs(py).max()))
+
+    def no_half(p, dx, dy):
+        px = (p[1:-1, 2:] - p[1:-1, :-2]) / dx
+        py = (p[2:, 1:-1] - p[:-2, 1:-1]) / dy
+        return float(max(np.abs(px).max(), np.abs(py).max()))
+
+    assert ok(O.max_velocity)
+    assert not ok(one_sided)
+    assert not ok(no_half)

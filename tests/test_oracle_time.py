@@ -103,6 +103,31 @@ def test_cfl_dt_formula():
     assert O.cfl_dt(psi, b.dx, b.dy, 0.5) == pytest.approx(0.5 * b.dx / u)
 
 
+def max_velocity_of_sine_mode(nx, ny, dx, dy, a):
+    """Closed form of max |psi_x|, |psi_y| (central differences over the
+    interior nodes) for psi = a sin(pi i/nx) sin(pi j/ny): the x difference
+    is a cos(pi i/nx) sin(pi/nx)/dx sin(pi j/ny), largest at i = 1,
+    j = ny/2; the y difference likewise at i = nx/2, j = 1."""
+    ux = a * np.cos(np.pi / nx) * np.sin(np.pi / nx) / dx
+    uy = a * np.cos(np.pi / ny) * np.sin(np.pi / ny) / dy
+    return max(ux, uy)
+
+
+@pytest.mark.parametrize("nx,ny,y0,y1", [(16, 32, -1.0, 1.0), (32, 16, -1.0, 1.0),
+                                         (64, 64, -0.5, 0.5)])
+def test_max_velocity_and_cfl_dt_closed_form(nx, ny, y0, y1):
+    """Eq. dt's denominator and step on a sine mode whose central
+    differences have a closed form."""
+    b = O.Basin(nx, ny, levels=0, y0=y0, y1=y1)
+    i = np.arange(nx + 1)[None, :]
+    j = np.arange(ny + 1)[:, None]
+    a = 2.5
+    psi = a * np.sin(np.pi * i / nx) * np.sin(np.pi * j / ny)
+    u = max_velocity_of_sine_mode(nx, ny, b.dx, b.dy, a)
+    assert O.max_velocity(psi, b.dx, b.dy) == pytest.approx(u, rel=1e-13)
+    assert O.cfl_dt(psi, b.dx, b.dy, 0.7) == pytest.approx(0.7 * min(b.dx, b.dy) / u, rel=1e-13)
+
+
 def test_adaptive_dt_rules():
     """Eq. dt with the cap: from rest the basin's dt; a capped step is the
     fixed step; otherwise c min(dx, dy) / max|grad psi| and the step is
