@@ -254,3 +254,32 @@ def test_cfl_pins_reject_mistakes():
     assert ok(O.max_velocity)
     assert not ok(one_sided)
     assert not ok(no_half)
+
+
+def test_projection_order_pin_rejects_piecewise_constant_prolongation():
+    """Prolonging psi by copying each coarse value to its fine cell (instead
+    of Eq. pro's bilinear averages) drops the CGP projection to first order,
+    which the order pin rejects."""
+    from tests.test_oracle_transfer import cgp_error_ratios
+
+    def copy_prolong(c):
+        f = np.zeros((2 * c.shape[0] - 1, 2 * c.shape[1] - 1))
+        f[::2, ::2] = c
+        f[1::2, ::2] = c[:-1, :]
+        f[::2, 1::2] = c[:, :-1]
+        f[1::2, 1::2] = c[:-1, :-1]
+        f[0, :] = f[-1, :] = 0.0
+        f[:, 0] = f[:, -1] = 0.0
+        return f
+
+    def psi_copy(w, b):
+        mx, my = b.nx >> b.levels, b.ny >> b.levels
+        s = float(1 << b.levels)
+        wb = O.restrict_levels(w, b.levels)
+        p = O.embed(O.poisson_solve(O.interior(wb), mx, my, b.dx * s, b.dy * s))
+        for _ in range(b.levels):
+            p = copy_prolong(p)
+        return p
+
+    _, r = cgp_error_ratios(psi_copy)
+    assert not all(3.5 < q < 5.0 for q in r), r

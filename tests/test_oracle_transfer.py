@@ -92,3 +92,35 @@ def test_restriction_of_interior_never_reads_walls():
     f[0, :] = f[-1, :] = f[:, 0] = f[:, -1] = 123.0
     c = O.restrict_levels(f, 2)
     assert np.all(c[1:-1, 1:-1] == 0.0)
+
+
+def smooth_vorticity(b):
+    """Two low modes of the basin, zero on the walls."""
+    X, Y = np.meshgrid(O.grid_x(b), O.grid_y(b))
+    s = (Y - b.y0) / (b.y1 - b.y0)
+    w = np.sin(np.pi * X) * np.sin(np.pi * s) + 0.5 * np.sin(2 * np.pi * X) * np.sin(3 * np.pi * s)
+    w[0, :] = w[-1, :] = 0.0
+    w[:, 0] = w[:, -1] = 0.0
+    return w
+
+
+def cgp_error_ratios(psi_fn, nx=128, ny=256, levels=(1, 2, 3)):
+    """Relative distance of the projected psi (restrict, solve on the
+    elliptic grid, prolong: Section 3) from the full-grid psi, per level,
+    and the ratios between successive levels."""
+    b0 = O.Basin(nx, ny, levels=0)
+    w = smooth_vorticity(b0)
+    p0 = O.cgp_psi(w, b0)
+    e = [np.linalg.norm(psi_fn(w, O.with_levels(b0, l)) - p0) / np.linalg.norm(p0)
+         for l in levels]
+    return e, [e[k + 1] / e[k] for k in range(len(e) - 1)]
+
+
+def test_cgp_projection_is_second_order_in_the_elliptic_spacing():
+    """Full weighting, the 5-point solve and bilinear prolongation are each
+    second order, so for a smooth field the CGP streamfunction approaches
+    the full-grid one by a factor 4 per halving of the elliptic spacing."""
+    e, r = cgp_error_ratios(O.cgp_psi)
+    assert e[0] < 1e-3
+    for q in r:
+        assert 3.5 < q < 5.0, r
