@@ -470,6 +470,7 @@ def ours(args):
         flush.zero_()
     torch.cuda.synchronize()
     per_step_kernels = qg.qg_step_kernel_count(h)
+    solve_engine = qg.qg_solve_engine(h)
 
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
@@ -611,6 +612,7 @@ def ours(args):
                        "parallelism": f"{world} independent replica(s)"},
             "roofline": roofline, "rooflines": rooflines, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": per_step_kernels * args.steps,
+            "solve_engine": solve_engine,
             "clocks": clocks, "variants": variants,
         }
         print(json.dumps(line), flush=True)
