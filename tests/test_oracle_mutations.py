@@ -283,3 +283,97 @@ def test_projection_order_pin_rejects_piecewise_constant_prolongation():
 
     _, r = cgp_error_ratios(psi_copy)
     assert not all(3.5 < q < 5.0 for q in r), r
+
+
+def _two_layer_rhs_variant(drag=-1.0, drag_layer=2, visc=1.0, k_forcing=2.0, swap_fr=False):
+    """The right-hand side of Eq. ge-non restated with switches for planted
+    mistakes; with the defaults it is the oracle's algebra."""
+    def rhs(Q1, Q2, b):
+        psi1, psi2 = O.two_layer_cgp_psi(Q1, Q2, b)
+        Y = np.repeat(O.grid_y(b)[:, None], b.nx + 1, axis=1)
+        f1, f2 = b.Fr / b.delta, b.Fr / (1.0 - b.delta)
+        if swap_fr:
+            f1, f2 = f2, f1
+        w1 = O.embed((O.interior(Q1) - f1 * O.interior(psi2 - psi1)) / b.Ro)
+        w2 = O.embed((O.interior(Q2) - f2 * O.interior(psi1 - psi2)) / b.Ro)
+        y = O.grid_y(b)[1:-1]
+        F1 = np.repeat((b.amp * np.sin(k_forcing * np.pi * y))[:, None], b.nx - 1, axis=1)
+        A = visc * b.A
+        G1 = (-O.arakawa(psi1, Q1, b.dx, b.dy) - O.arakawa(psi1, Y, b.dx, b.dy)
+              + A * O.laplacian5(w1, b.dx, b.dy) + F1)
+        G2 = (-O.arakawa(psi2, Q2, b.dx, b.dy) - O.arakawa(psi2, Y, b.dx, b.dy)
+              + A * O.laplacian5(w2, b.dx, b.dy))
+        if drag_layer == 2:
+            G2 = G2 + drag * b.sigma * O.interior(w2)
+        else:
+            G1 = G1 + drag * b.sigma * O.interior(w1)
+        return G1, G2
+    return rhs
+
+
+def _two_layer_step_variant(rhs, weights=((0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0))):
+    """TVDRK3 (Eq. TVDRK) over both layers with a pluggable right-hand side
+    and stage weights."""
+    def step(Q1, Q2, b):
+        def upd(a1, a2, c1, c2, s):
+            G1, G2 = rhs(c1, c2, b)
+            n1 = O.embed(s[0] * O.interior(a1) + s[1] * (O.interior(c1) + b.dt * G1))
+            n2 = O.embed(s[0] * O.interior(a2) + s[1] * (O.interior(c2) + b.dt * G2))
+            return n1, n2
+        a1, a2 = upd(Q1, Q2, Q1, Q2, weights[0])
+        b1, b2 = upd(Q1, Q2, a1, a2, weights[1])
+        return upd(Q1, Q2, b1, b2, weights[2])
+    return step
+
+
+def test_two_layer_model_pins_reject_mistakes():
+    """The decoupled limit, the drag energy-decay rate and the term-by-term
+    pins of the two-layer model reject a flipped or misplaced drag, a wrong
+    viscosity factor, the one-layer forcing wavenumber, swapped thickness
+    factors in the recovered vorticity and a wrong TVDRK3 stage weight."""
+    from tests.test_oracle_two_layer import decoupled_limit_error, drag_rates, term_errors
+
+    def pins(rhs, weights=None):
+        step = (_two_layer_step_variant(rhs) if weights is None
+                else _two_layer_step_variant(rhs, weights))
+        r1, r2, want = drag_rates(step)
+        return {
+            "decoupled": decoupled_limit_error(step, 1) <= 1e-11,
+            "drag": abs(r2 - want) <= 1e-6 * abs(want) and abs(r1) <= 1e-6 * abs(want),
+            "terms": term_errors(rhs) <= 1e-9,
+        }
+
+    assert all(pins(_two_layer_rhs_variant()).values())          # the same algebra, restated
+    assert not pins(_two_layer_rhs_variant(drag=+1.0))["drag"]
+    assert not pins(_two_layer_rhs_variant(drag_layer=1))["drag"]
+    assert not pins(_two_layer_rhs_variant(drag=+1.0))["terms"]
+    bad_visc = pins(_two_layer_rhs_variant(visc=2.0))
+    assert not bad_visc["decoupled"] and not bad_visc["terms"]
+    bad_forcing = pins(_two_layer_rhs_variant(k_forcing=1.0))
+    assert not bad_forcing["decoupled"] and not bad_forcing["terms"]
+    assert not pins(_two_layer_rhs_variant(swap_fr=True))["terms"]
+    wrong_stage = ((0.0, 1.0), (0.5, 0.5), (1.0 / 3.0, 2.0 / 3.0))
+    assert not pins(_two_layer_rhs_variant(), wrong_stage)["decoupled"]
+
+
+def test_forcing_pin_rejects_mistakes():
+    """The closed-form values of sin(pi y) reject a cosine profile, the
+    two-layer wavenumber, a forcing multiplied instead of divided by Ro and
+    a dropped amplitude."""
+    from tests.test_oracle_two_layer import forcing_error
+
+    def variant(fn=np.sin, k=1.0, by_ro=True, use_amp=True):
+        def forcing(b):
+            if b.forcing is not None:
+                return np.asarray(b.forcing, dtype=np.float64)
+            y = O.grid_y(b)[1:-1]
+            a = b.amp if use_amp else 1.0
+            row = a * fn(k * np.pi * y) * (1.0 / b.Ro if by_ro else b.Ro)
+            return np.repeat(row[:, None], b.nx - 1, axis=1)
+        return forcing
+
+    assert forcing_error(variant()) <= 1e-14
+    assert forcing_error(variant(fn=np.cos)) > 1e-3
+    assert forcing_error(variant(k=2.0)) > 1e-3
+    assert forcing_error(variant(by_ro=False)) > 1e-3
+    assert forcing_error(variant(use_amp=False)) > 1e-3
