@@ -43,8 +43,8 @@ typedef enum qg_status {
     QG_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed  */
     QG_ERR_OOM = 4,          /* device allocation failed                     */
     QG_ERR_NONFINITE = 5,    /* the state holds NaN or Inf                   */
-    QG_ERR_CFL = 6,          /* reserved (no call checks a CFL limit; see
-                                qg_set_cfl for the adaptive step)           */
+    QG_ERR_CFL = 6,          /* qg_set_cfl asked for a Courant number above
+                                1, beyond what Eq. dt allows                */
     QG_ERR_TIMEOUT = 7,      /* a bounded device-side wait ran out           */
     QG_ERR_UNSUPPORTED = 8,  /* valid request this build does not provide    */
     QG_ERR_NO_DEVICE = 9     /* no usable CUDA device                        */
@@ -201,9 +201,13 @@ qg_status qg_step_kernel_count(qg_handle h, int64_t* count);
  * library-owned 32 MiB device array that every GPU loading the library keeps
  * until exit.  The padded grid, its transposed spectrum and the tables must
  * fit in it (for example up to 1024 x 2048 intervals in FP32 or 1024 x 1024
- * in FP64); larger requests return QG_ERR_SHAPE.  rhs and psi are DEVICE pointers in the level-0
- * exchange layout of that grid; work is enqueued on cuda_stream on the
- * current device.  The first call on a device looks up the array's device
+ * in FP64), and one of the shared-memory FFT engines (base radix 4 or 16)
+ * must take the grid; other requests return QG_ERR_SHAPE.  rhs and psi are
+ * DEVICE pointers in the level-0 exchange layout of that grid; work is
+ * enqueued on cuda_stream on the current device, and the call waits for that
+ * stream before it returns, so that it can read the solve's error word:
+ * a bounded grid-barrier wait that ran out returns QG_ERR_TIMEOUT and leaves
+ * psi unwritten.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress): make it before any stream capture starts.
  * All calls share the array: each clears what must start at zero, and calls
  * whose GPU work overlaps (unordered streams) race and give wrong results.  */
@@ -218,7 +222,8 @@ qg_status qg_poisson_solve_noalloc(int32_t nx, int32_t ny, double dx, double dy,
  * device; the paper states c <= 1); basin.dt caps the step (a flow at rest
  * has no Eq. dt bound).  c = 0: the fixed basin.dt again.  One-layer
  * handles only (QG_ERR_UNSUPPORTED otherwise, or while an adjoint tape is
- * open).  Re-captures the step graph.  Errors: QG_ERR_ARG for c < 0.     */
+ * open).  Re-captures the step graph.  Errors: QG_ERR_ARG for c < 0,
+ * QG_ERR_CFL for c > 1 (the paper states Eq. dt for c <= 1).              */
 qg_status qg_set_cfl(qg_handle h, double c);
 
 /* ---- the elliptic solver of the CGP step (Section 3) -------------------

@@ -989,7 +989,7 @@ const char* qg_status_string(qg_status s) {
         case QG_ERR_CUDA: return "CUDA error";
         case QG_ERR_OOM: return "device out of memory";
         case QG_ERR_NONFINITE: return "state is not finite";
-        case QG_ERR_CFL: return "CFL limit exceeded";
+        case QG_ERR_CFL: return "Courant number above 1 (Eq. dt)";
         case QG_ERR_TIMEOUT: return "device wait timed out";
         case QG_ERR_UNSUPPORTED: return "unsupported request";
         case QG_ERR_NO_DEVICE: return "no CUDA device";
@@ -1362,6 +1362,8 @@ qg_status qg_set_timing_mask(qg_handle h, uint32_t mask) {
 
 qg_status qg_set_cfl(qg_handle h, double c) {
     if (!h || !(c >= 0.0) || !std::isfinite(c)) return QG_ERR_ARG;
+    // Eq. dt is stated for Courant numbers c <= 1 (Section 4.2)
+    if (c > 1.0) return QG_ERR_CFL;
     if (c > 0.0 && (h->layers != 1 || h->tape)) return QG_ERR_UNSUPPORTED;
     if (c != h->cfl) {
         QG_TRY(cudaStreamSynchronize(h->stream));

@@ -17,9 +17,14 @@
 // All calls share the one array and it keeps the contents of the last call:
 // each call clears the part that must start at zero, and two calls whose work
 // overlaps on the GPU (different streams, no ordering between them) race on
-// it.  The paper has no counterpart to this entry point.
+// it.  Each call waits for its stream at the end and reads the solve's error
+// word back (into a stack variable: no pinned buffer is allocated), so that a
+// grid-barrier wait that ran out of its bound is reported as QG_ERR_TIMEOUT
+// rather than as success.  The paper has no counterpart to this entry point.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 #include "qg_internal.cuh"
@@ -83,7 +88,8 @@ Layout layout(int nx, int ny, size_t esz) {
 
 template <typename T>
 qg_status solve(unsigned char* base, const Layout& Lo, int nx, int ny, double dx,
-                double dy, const void* rhs, void* psi, cudaStream_t s) {
+                double dy, const void* rhs, void* psi, int engine, bool stall,
+                cudaStream_t s) {
     using C = typename Cx<T>::type;
     const int ld = round_up(nx + 1, 32);
     T* grid = reinterpret_cast<T*>(base + Lo.grid);
@@ -119,10 +125,28 @@ qg_status solve(unsigned char* base, const Layout& Lo, int nx, int ny, double dx
     P.scale = (T)((2.0 / nx) * (2.0 / ny));
     P.bar = bar;
     P.err = reinterpret_cast<int*>(bar + 2);
-    const int engine = (long)nx * ny >= (1L << 21) ? 16 : 4;
+    P.bar_extra = stall ? 1u : 0u;
     if (launch_solve<T>(P, engine, s) != cudaSuccess) return QG_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpyAsync(&err, P.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return QG_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return QG_ERR_CUDA;
+    if (err) return QG_ERR_TIMEOUT;
+    // psi is written only when the solve completed
     if (copy_out(psi, grid, ld, nx - 1, ny - 1, esz, s) != cudaSuccess) return QG_ERR_CUDA;
     return QG_OK;
+}
+
+// The shared-memory FFT engine for an nx x ny request: base radix 16 for
+// grids of 2^21 nodes or more, radix 4 below (the faster of the two there),
+// falling back to the other radix when the first cannot take the grid's
+// longer side or shared memory; 0 when neither can.
+int pick_engine(int nx, int ny, size_t esz) {
+    const int first = (long)nx * ny >= (1L << 21) ? 16 : 4;
+    const int second = first == 16 ? 4 : 16;
+    if (solve_engine_supports(nx, ny, esz, first)) return first;
+    if (solve_engine_supports(nx, ny, esz, second)) return second;
+    return 0;
 }
 
 }  // namespace
@@ -141,8 +165,13 @@ extern "C" qg_status qg_poisson_solve_noalloc(int32_t nx, int32_t ny, double dx,
         return QG_ERR_SHAPE;
     const size_t esz = dtype == QG_F64 ? 8 : 4;
     if (layout(nx, ny, esz).total > kNoAllocBytes) return QG_ERR_SHAPE;
-    if (solve_smem_bytes(nx, ny, esz, (long)nx * ny >= (1L << 21) ? 16 : 4) > 200 * 1024)
-        return QG_ERR_SHAPE;
+    const int engine = pick_engine(nx, ny, esz);
+    if (!engine) return QG_ERR_SHAPE;
+    // QG_NOALLOC_STALL=1 (a test hook for the timeout path): the solve's first
+    // grid barrier waits for one arrival more than the grid has, so its
+    // bounded wait runs out and the call returns QG_ERR_TIMEOUT.
+    const char* st = std::getenv("QG_NOALLOC_STALL");
+    const bool stall = st && std::strcmp(st, "1") == 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -164,6 +193,6 @@ extern "C" qg_status qg_poisson_solve_noalloc(int32_t nx, int32_t ny, double dx,
     }
     const Layout Lo = layout(nx, ny, esz);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    return dtype == QG_F64 ? solve<double>(base, Lo, nx, ny, dx, dy, rhs, psi, s)
-                           : solve<float>(base, Lo, nx, ny, dx, dy, rhs, psi, s);
+    return dtype == QG_F64 ? solve<double>(base, Lo, nx, ny, dx, dy, rhs, psi, engine, stall, s)
+                           : solve<float>(base, Lo, nx, ny, dx, dy, rhs, psi, engine, stall, s);
 }

@@ -5,7 +5,7 @@ import pytest
 
 from oracle import qg_oracle as O
 from paper_1308_3290_gb300 import inputs, qg
-from tests.gpu_util import rel_l2, require_gpu, to_np
+from tests.gpu_util import assert_fields_close, rel_l2, require_gpu, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -32,8 +32,8 @@ def test_two_layer_steps(dtype, tol, levels, nx, ny):
     b.set_state(Q2, 1)
     b.step(50)
     g1, g2 = to_np(b.state(0)), to_np(b.state(1))
-    assert rel_l2(g1, O.interior(a1)) <= tol
-    assert rel_l2(g2, O.interior(a2)) <= tol
+    assert_fields_close(g1, O.interior(a1), tol)
+    assert_fields_close(g2, O.interior(a2), tol)
     b.close()
 
 
@@ -56,6 +56,7 @@ def test_two_layer_full_size_one_step():
     b.step(1)
     for layer, q0, ref in ((0, Q1, O.interior(a1)), (1, Q2, O.interior(a2))):
         got = to_np(b.state(layer))
-        assert rel_l2(got, ref) <= 1e-6
-        assert rel_l2(got - q0, ref - q0) <= 1e-3
+        assert_fields_close(got, ref, 1e-6, max_tol=64 * 2.0 ** -24)
+        assert_fields_close(got - q0, ref - q0, 1e-3, max_tol=1.0)
+        assert np.abs((got - q0) - (ref - q0)).max() <= 64 * 2.0 ** -24 * np.abs(q0).max()
     b.close()
