@@ -132,6 +132,7 @@ struct qg_ctx {
     // (per layer: [k][layer]; the second layer's maps exist for two layers)
     CUtensorMap tm_halo[3][2], tm_int[3][2], tm_psi, tm_f;
     int solve_engine = 4;          // FFT base radix of the step's solve (autotuned)
+    bool engine_forced = false;    // solve_engine was forced by QG_SOLVE_ENGINE
     int* derr = nullptr;           // device error flag of bounded waits
     unsigned* dbar = nullptr;      // grid-barrier counters of the solve kernel
     Tape* tape = nullptr;          // adjoint tape (qg_tape_begin .. qg_tape_end)
@@ -626,6 +627,7 @@ qg_status autotune_solve(qg_ctx* h) {
         const int e = std::atoi(force);
         if (engine_ok(h, t, sizeof(T), e)) {
             h->solve_engine = e;
+            h->engine_forced = true;
             return QG_OK;
         }
     }
@@ -1793,28 +1795,82 @@ qg_status qg_energy_gradient(qg_handle h, double scale, void* g) {
 }  // extern "C"
 
 // ---- ensembles -------------------------------------------------------------
+// One ensemble step is one CUDA graph.  Members whose elliptic grids have the
+// same shape and spacings (so the same solver tables) form a group; members
+// of different groups never interact, so each group's three TVDRK3 stages
+// run as one chain on a branch of its own, beside the other groups:
+//   * one solve launch per stage for the whole group: the warp-group FFT
+//     engine as a work queue over the slots of all members (no grid
+//     barriers, so groups can share the GPU), or the matrix form with one
+//     CTA per member; each member's right-hand side, arrays and error flag
+//     come from a device table.  A group that cannot batch (multigrid, or a
+//     non-batching engine forced through QG_SOLVE_ENGINE) solves member by
+//     member with the handles' own launches;
+//   * the per-member extras of the first stage (time-mean accumulation, the
+//     maximum velocity of Eq. dt);
+//   * one fused fine-stage launch per CGP level among the group's members,
+//     over all their tiles, each CTA reading its member's tensor maps and
+//     parameters from a device table.
+// Within a branch the launches follow each other with programmatic
+// dependent launch, as in a single basin's step.
+
+#define QG_TRY_E(expr)                        \
+    do {                                      \
+        const qg_status qg_s_ = (expr);       \
+        if (qg_s_ != QG_OK) return qg_s_;     \
+    } while (0)
+
+// Programmatic dependent launch inside a group's branch: off, because a
+// dependent kernel that starts early holds SM resources idle in its wait
+// while the other branches have work for them.
+constexpr bool kEnsemblePdl = false;
+
+struct EnsFineGroup {
+    int lv = 0;
+    bool f2d = false;                 // some member uses a forcing field
+    std::vector<int> members;
+    void* dmem = nullptr;             // FineMember<T>[3 stages][members]
+    int4* dtiles = nullptr;
+    int ntiles = 0;
+};
+
+struct EnsSolveGroup {
+    int mx = 0, my = 0, engine = 0;   // engine 0: the members solve on their own
+    double dxc = 0, dyc = 0;
+    std::vector<int> members;
+    void* dmem = nullptr;             // SolveMember<T>[3 stages][members]
+    unsigned* dq = nullptr;           // work-queue counters of the batched solve
+    std::vector<EnsFineGroup> fine;   // the members by CGP level
+};
 
 struct qg_ensemble_s {
     std::vector<qg_ctx*> m;
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;             // capture origin
-    std::vector<cudaStream_t> lanes;        // concurrent branches of the step graph
+    std::vector<cudaStream_t> lanes;        // one branch per group
     std::vector<cudaEvent_t> ev;            // fork event, then one join event per lane
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::vector<uint64_t> gen;              // members' graph_gen when it was captured
+    std::vector<EnsSolveGroup> sg;
+    std::vector<void*> dallocs;             // device tables of the batched launches
     int64_t kernels = 0;
 };
 
 namespace {
 
-constexpr int kEnsembleLanes = 16;
+void ensemble_tables_free(qg_ensemble e) {
+    for (void* p : e->dallocs) cudaFree(p);
+    e->dallocs.clear();
+    e->sg.clear();
+}
 
 void ensemble_free(qg_ensemble e) {
     if (!e) return;
     if (e->stream) cudaStreamSynchronize(e->stream);
     if (e->gexec) cudaGraphExecDestroy(e->gexec);
     if (e->graph) cudaGraphDestroy(e->graph);
+    ensemble_tables_free(e);
     for (qg_ctx* h : e->m) qg_destroy(h);
     for (cudaEvent_t v : e->ev) cudaEventDestroy(v);
     for (cudaStream_t s : e->lanes) cudaStreamDestroy(s);
@@ -1822,33 +1878,389 @@ void ensemble_free(qg_ensemble e) {
     delete e;
 }
 
-// Members sorted by fine nodes, largest first, each on the lane with the
-// least work so far: the branches of the graph end at about the same time.
-std::vector<int> ensemble_placement(const qg_ensemble e) {
-    const int n = (int)e->m.size(), L = (int)e->lanes.size();
-    std::vector<int> order(n), lane(n, 0);
-    for (int i = 0; i < n; ++i) order[i] = i;
-    auto work = [&](int i) { return (double)e->m[i]->nx * e->m[i]->ny; };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
-    std::vector<double> load(L, 0.0);
-    for (int i : order) {
-        int best = 0;
-        for (int k = 1; k < L; ++k)
-            if (load[k] < load[best]) best = k;
-        lane[i] = best;
-        load[best] += work(i);
+// At least n branch streams and n + 1 events.
+qg_status ensemble_lanes(qg_ensemble e, size_t n) {
+    while (e->lanes.size() < n) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return QG_ERR_CUDA;
+        e->lanes.push_back(s);
     }
-    return lane;
+    while (e->ev.size() < n + 1) {
+        cudaEvent_t v = nullptr;
+        if (cudaEventCreateWithFlags(&v, cudaEventDisableTiming) != cudaSuccess) return QG_ERR_CUDA;
+        e->ev.push_back(v);
+    }
+    return QG_OK;
+}
+
+qg_status ens_alloc(qg_ensemble e, void** p, size_t bytes) {
+    *p = nullptr;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return QG_ERR_OOM;
+    }
+    e->dallocs.push_back(*p);
+    return QG_OK;
+}
+
+// The engines a group of members can solve with in one launch: the
+// warp-group FFT engines and the matrix form that take the group's grid;
+// none when a member uses the multigrid solver.  An engine forced through
+// QG_SOLVE_ENGINE is the only candidate, and none when it does not batch
+// (then every member solves as a handle of its own would).
+std::vector<int> batch_engines(qg_ensemble e, const EnsSolveGroup& g) {
+    std::vector<int> out;
+    for (int i : g.members)
+        if (e->m[i]->solver != QG_SOLVER_FFT) return out;
+    qg_ctx* h0 = e->m[g.members[0]];
+    const LevelTables* t = nullptr;
+    if (get_level(h0, h0->levels, &t) != QG_OK) return out;
+    const int own = h0->solve_engine;
+    if (h0->engine_forced) {
+        if ((is_warp_engine(own) || own == kMatrixEngine) && engine_ok(h0, t, h0->esz, own))
+            out.push_back(own);
+        return out;
+    }
+    for (int cand : {34, 33, 32, (int)kMatrixEngine})
+        if (engine_ok(h0, t, h0->esz, cand)) out.push_back(cand);
+    return out;
+}
+
+template <typename T>
+FusedParams<T> fused_params(qg_ctx* h, int s_idx, const LevelTables& t) {
+    static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double B[3] = {1.0, 0.25, 2.0 / 3.0};
+    FusedParams<T> p = {};
+    p.nx = h->nx;
+    p.ny = h->ny;
+    p.ld = h->ldf;
+    p.psi = static_cast<const T*>(h->levels == 0 ? h->psi : h->cpsi);
+    p.ldp = h->levels == 0 ? h->ldf : t.ldc;
+    p.w = static_cast<const T*>(h->w[s_idx]);
+    p.wn = static_cast<const T*>(h->w[0]);
+    p.wout = static_cast<T*>(h->w[(s_idx + 1) % 3]);
+    p.frow = static_cast<const T*>(h->frow);
+    p.f2d = static_cast<const T*>(h->f2d);
+    for (int q = 0; q < 4; ++q) p.part[q] = h->part ? plane<T>(h->part, h->plane_c, q) : nullptr;
+    p.ldc = t.ldc;
+    p.err = h->derr;
+    p.c_jac = (T)(1.0 / (12.0 * h->dx * h->dy));
+    p.c_beta = (T)(1.0 / (12.0 * h->Ro * h->dx));
+    p.c_lapx = (T)(1.0 / (h->Re * h->dx * h->dx));
+    p.c_lapy = (T)(1.0 / (h->Re * h->dy * h->dy));
+    p.dt = (T)h->dt;
+    p.a = (T)A[s_idx];
+    p.b = (T)B[s_idx];
+    p.psi_o = nullptr;
+    p.inv_Ro = p.k_p = p.drag = T(0);
+    p.umax = h->cfl > 0.0 ? reinterpret_cast<const unsigned long long*>(h->dclock) : nullptr;
+    p.cfl_h = h->cfl * std::fmin(h->dx, h->dy);
+    p.dt_cap = h->dt;
+    p.clock = h->dclock + 1;
+    p.last_stage = s_idx == 2;
+    return p;
+}
+
+template <typename T>
+qg_status tune_group(qg_ensemble e, EnsSolveGroup& g, const std::vector<int>& cands);
+
+// Group the members and upload the tables of the batched launches.
+template <typename T>
+qg_status ensemble_tables(qg_ensemble e) {
+    ensemble_tables_free(e);
+    const int n = (int)e->m.size();
+    // members, largest first: big tiles start first, small ones fill the tail
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (double)e->m[a]->nx * e->m[a]->ny > (double)e->m[b]->nx * e->m[b]->ny;
+    });
+    for (int i : order) {
+        qg_ctx* h = e->m[i];
+        const LevelTables* t = nullptr;
+        qg_status st = get_level(h, h->levels, &t);
+        if (st != QG_OK) return st;
+        EnsSolveGroup* g = nullptr;
+        for (auto& c : e->sg)
+            if (c.mx == t->mx && c.my == t->my && c.dxc == t->dxc && c.dyc == t->dyc) g = &c;
+        if (!g) {
+            e->sg.emplace_back();
+            g = &e->sg.back();
+            g->mx = t->mx;
+            g->my = t->my;
+            g->dxc = t->dxc;
+            g->dyc = t->dyc;
+        }
+        g->members.push_back(i);
+        EnsFineGroup* f = nullptr;
+        for (auto& c : g->fine)
+            if (c.lv == h->levels) f = &c;
+        if (!f) {
+            g->fine.emplace_back();
+            f = &g->fine.back();
+            f->lv = h->levels;
+        }
+        f->members.push_back(i);
+        if (h->f2d) f->f2d = true;
+    }
+    // the groups with the most fine points first (their branches start first)
+    auto points = [&](const EnsSolveGroup& g) {
+        double p = 0;
+        for (int i : g.members) p += (double)e->m[i]->nx * e->m[i]->ny;
+        return p;
+    };
+    std::stable_sort(e->sg.begin(), e->sg.end(),
+                     [&](const EnsSolveGroup& a, const EnsSolveGroup& b) { return points(a) > points(b); });
+    for (auto& g : e->sg) {
+        const std::vector<int> cands = batch_engines(e, g);
+        g.engine = 0;
+        if (cands.empty()) continue;
+        const int nm = (int)g.members.size();
+        std::vector<SolveMember<T>> tab(3 * (size_t)nm);
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < nm; ++j) {
+                qg_ctx* h = e->m[g.members[j]];
+                SolveMember<T>& M = tab[(size_t)k * nm + j];
+                M = {};
+                if (h->levels == 0) {
+                    M.in[0] = static_cast<const T*>(h->w[k]);
+                    M.nin = 1;
+                    M.part_px = M.part_py = 1;
+                    M.out = static_cast<T*>(h->psi);
+                } else {
+                    for (int q = 0; q < 4; ++q) M.in[q] = plane<T>(h->part, h->plane_c, q);
+                    M.nin = 4;
+                    M.part_px = fine_part_period_x(h->levels);
+                    M.part_py = fine_part_period_y(h->levels, sizeof(T));
+                    M.out = static_cast<T*>(h->cpsi);
+                }
+                M.tr = static_cast<T*>(h->ct);
+                M.work = static_cast<T*>(h->cw);
+                M.err = h->derr;
+            }
+        const size_t nq = 2 + 3 * (size_t)nm;
+        QG_TRY_E(ens_alloc(e, &g.dmem, tab.size() * sizeof(SolveMember<T>)));
+        QG_TRY_E(ens_alloc(e, reinterpret_cast<void**>(&g.dq), nq * sizeof(unsigned)));
+        if (cudaMemcpy(g.dmem, tab.data(), tab.size() * sizeof(SolveMember<T>),
+                       cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemset(g.dq, 0, nq * sizeof(unsigned)) != cudaSuccess)
+            return QG_ERR_CUDA;
+        QG_TRY_E(tune_group<T>(e, g, cands));
+    }
+    const int TX = fine_block_cols();
+    const int RC = (int)fine_tile_rows(sizeof(T));
+    for (auto& g : e->sg) {
+        for (auto& f : g.fine) {
+            const int nm = (int)f.members.size();
+            std::vector<FineMember<T>> tab(3 * (size_t)nm);
+            std::vector<int4> tiles;
+            for (int j = 0; j < nm; ++j) {
+                qg_ctx* h = e->m[f.members[j]];
+                const LevelTables* t = nullptr;
+                qg_status st = get_level(h, h->levels, &t);
+                if (st != QG_OK) return st;
+                for (int k = 0; k < 3; ++k) {
+                    FineMember<T>& M = tab[(size_t)k * nm + j];
+                    M.w = h->tm_halo[k][0];
+                    M.wn = h->tm_int[0][0];
+                    M.psi = h->tm_psi;
+                    M.f = h->tm_f;
+                    M.p = fused_params<T>(h, k, *t);
+                }
+                const int gx = (h->nx + TX - 1) / TX, gy = (h->ny + RC - 1) / RC;
+                for (int by = 0; by < gy; ++by)
+                    for (int bx = 0; bx < gx; ++bx) tiles.push_back(make_int4(j, bx, by, 0));
+            }
+            f.ntiles = (int)tiles.size();
+            QG_TRY_E(ens_alloc(e, &f.dmem, tab.size() * sizeof(FineMember<T>)));
+            QG_TRY_E(ens_alloc(e, reinterpret_cast<void**>(&f.dtiles), tiles.size() * sizeof(int4)));
+            if (cudaMemcpy(f.dmem, tab.data(), tab.size() * sizeof(FineMember<T>),
+                           cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(f.dtiles, tiles.data(), tiles.size() * sizeof(int4),
+                           cudaMemcpyHostToDevice) != cudaSuccess)
+                return QG_ERR_CUDA;
+        }
+    }
+    return QG_OK;
+}
+
+// The batched solve of stage k of group g with engine `engine`.
+template <typename T>
+qg_status group_solve(qg_ensemble e, const EnsSolveGroup& g, int engine, int k, cudaStream_t s) {
+    using C = typename Cx<T>::type;
+    qg_ctx* h0 = e->m[g.members[0]];
+    const LevelTables* t = nullptr;
+    qg_status st = get_level(h0, h0->levels, &t);
+    if (st != QG_OK) return st;
+    SolveParams<T> P = {};
+    P.mx = t->mx;
+    P.my = t->my;
+    P.layers = 1;
+    P.ld = t->ldc;
+    P.ld_tr = h0->ld_t;
+    P.twx = static_cast<const C*>(t->twx);
+    P.twy = static_cast<const C*>(t->twy);
+    if (is_warp_engine(engine)) {
+        P.ptx = static_cast<const C*>(t->ptx[engine - 32]);
+        P.pty = static_cast<const C*>(t->pty[engine - 32]);
+    }
+    P.lamx = static_cast<const T*>(t->lamx);
+    P.lamy = static_cast<const T*>(t->lamy);
+    P.scale = (T)((2.0 / t->mx) * (2.0 / t->my));
+    P.bar = g.dq;
+    P.err = h0->derr;
+    P.batch = static_cast<const SolveMember<T>*>(g.dmem) + (size_t)k * g.members.size();
+    P.nbatch = (int)g.members.size();
+    P.no_pdl = kEnsemblePdl ? 0 : 1;
+    if (engine == kMatrixEngine) {
+        if constexpr (std::is_same<T, float>::value)
+            return cuda_status(h0, launch_solve_mtx(P, static_cast<const float*>(t->mtab), s));
+        else
+            return QG_ERR_CUDA;
+    }
+    return cuda_status(h0, launch_solve<T>(P, engine, s));
+}
+
+// The batched solve's engine for a group: each candidate timed on the
+// group's own arrays (a few launches; the solves overwrite only work arrays
+// and streamfunctions that every stage recomputes), the fastest kept.
+// Results are cached per (grid, spacings, members, dtype) for the process.
+std::mutex g_batch_tune_mutex;
+std::map<std::tuple<int, int, double, double, int, int>, int> g_batch_tune;
+
+template <typename T>
+qg_status tune_group(qg_ensemble e, EnsSolveGroup& g, const std::vector<int>& cands) {
+    if (cands.size() == 1) {
+        g.engine = cands[0];
+        return QG_OK;
+    }
+    const auto key = std::make_tuple(g.mx, g.my, g.dxc, g.dyc, (int)g.members.size(), (int)sizeof(T));
+    {
+        std::lock_guard<std::mutex> lock(g_batch_tune_mutex);
+        auto it = g_batch_tune.find(key);
+        if (it != g_batch_tune.end()) {
+            g.engine = it->second;
+            return QG_OK;
+        }
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return QG_ERR_CUDA;
+    float best = 1e30f;
+    int pick = cands[0];
+    for (int cand : cands) {
+        bool ok = true;
+        for (int r = 0; r < 2 && ok; ++r) ok = group_solve<T>(e, g, cand, 0, e->stream) == QG_OK;
+        ok = ok && cudaEventRecord(a, e->stream) == cudaSuccess;
+        for (int r = 0; r < 5 && ok; ++r) ok = group_solve<T>(e, g, cand, 0, e->stream) == QG_OK;
+        ok = ok && cudaEventRecord(b, e->stream) == cudaSuccess &&
+             cudaEventSynchronize(b) == cudaSuccess;
+        float ms = 1e30f;
+        if (ok && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best) {
+            best = ms;
+            pick = cand;
+        }
+        (void)cudaGetLastError();
+        for (int i : g.members) e->m[i]->latched = QG_OK;   // a candidate failing is a result
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    g.engine = pick;
+    std::lock_guard<std::mutex> lock(g_batch_tune_mutex);
+    g_batch_tune[key] = pick;
+    return QG_OK;
+}
+
+// Enqueue the three stages of one group's step on s (captured).
+template <typename T>
+qg_status group_enqueue(qg_ensemble e, const EnsSolveGroup& g, cudaStream_t s) {
+    for (int k = 0; k < 3; ++k) {
+        qg_ctx* h0 = e->m[g.members[0]];
+        const LevelTables* t = nullptr;
+        qg_status st = get_level(h0, h0->levels, &t);
+        if (st != QG_OK) return st;
+        if (!g.engine) {
+            // the members' own solves
+            for (int i : g.members) {
+                qg_ctx* h = e->m[i];
+                const LevelTables* ti = nullptr;
+                st = get_level(h, h->levels, &ti);
+                if (st != QG_OK) return st;
+                h->kernels_per_step = 0;
+                h->capturing = true;
+                if (h->levels == 0)
+                    st = solve_level<T>(h, *ti, h->w[k], h->ct, h->ld_t, h->plane_t, h->cw,
+                                        h->psi, h->plane_f, s, 1);
+                else
+                    st = solve_level<T>(h, *ti, h->part, h->ct, h->ld_t, h->plane_t, h->cw,
+                                        h->cpsi, h->plane_c, s, 4);
+                h->capturing = false;
+                e->kernels += h->kernels_per_step;
+                if (st != QG_OK) return st;
+            }
+        } else {
+            QG_TRY_E(group_solve<T>(e, g, g.engine, k, s));
+            ++e->kernels;
+        }
+        if (k == 0) {
+            for (int i : g.members) {
+                qg_ctx* h = e->m[i];
+                const bool fine = h->levels == 0;
+                if (h->stats) {
+                    QG_TRY_E(cuda_status(h, launch_accumulate<T>(
+                        h->stat_acc, static_cast<const T*>(fine ? h->psi : h->cpsi),
+                        (fine ? h->plane_f : h->plane_c) * h->layers, s)));
+                    ++e->kernels;
+                }
+                if (h->cfl > 0.0) {
+                    const LevelTables* ti = nullptr;
+                    st = get_level(h, h->levels, &ti);
+                    if (st != QG_OK) return st;
+                    QG_TRY_E(cuda_status(h, cudaMemsetAsync(h->dclock, 0, sizeof(double), s)));
+                    QG_TRY_E(cuda_status(h, launch_cfl_max<T>(
+                        static_cast<const T*>(fine ? h->psi : h->cpsi), fine ? h->ldf : ti->ldc,
+                        h->nx, h->ny, h->levels, h->dx, h->dy,
+                        reinterpret_cast<unsigned long long*>(h->dclock), s)));
+                    ++e->kernels;
+                }
+            }
+        }
+        for (const auto& f : g.fine) {
+            const FineMember<T>* fm =
+                static_cast<const FineMember<T>*>(f.dmem) + (size_t)k * f.members.size();
+            QG_TRY_E(cuda_status(e->m[f.members[0]],
+                                 launch_fine_batch<T>(fm, f.dtiles, f.ntiles, f.lv, f.f2d,
+                                                      kEnsemblePdl, s)));
+            ++e->kernels;
+        }
+    }
+    return QG_OK;
+}
+
+// Enqueue one ensemble step on s (captured into the graph): the groups'
+// chains on branches forked from and joined back into s.
+template <typename T>
+qg_status ensemble_enqueue(qg_ensemble e, cudaStream_t s) {
+    e->kernels = 0;
+    QG_TRY_E(ensemble_lanes(e, e->sg.size()));
+    if (cudaEventRecord(e->ev[0], s) != cudaSuccess) return QG_ERR_CUDA;
+    for (size_t k = 0; k < e->sg.size(); ++k) {
+        if (cudaStreamWaitEvent(e->lanes[k], e->ev[0], 0) != cudaSuccess) return QG_ERR_CUDA;
+        QG_TRY_E(group_enqueue<T>(e, e->sg[k], e->lanes[k]));
+        if (cudaEventRecord(e->ev[1 + k], e->lanes[k]) != cudaSuccess ||
+            cudaStreamWaitEvent(s, e->ev[1 + k], 0) != cudaSuccess)
+            return QG_ERR_CUDA;
+    }
+    return QG_OK;
 }
 
 qg_status ensemble_build(qg_ensemble e) {
-    // a member whose own step graph was invalidated (new forcing field,
-    // timing, fault switch) invalidates the ensemble's too
+    // a member whose own step changed (new forcing field, adaptive step,
+    // statistics, solver, fault switch) invalidates the ensemble's graph
     bool stale = e->gen.size() != e->m.size();
     for (size_t i = 0; i < e->m.size() && !stale; ++i) stale = e->gen[i] != e->m[i]->graph_gen;
     if (e->gexec && !stale) return QG_OK;
+    cudaStreamSynchronize(e->stream);
     if (e->gexec) {
-        cudaStreamSynchronize(e->stream);
         cudaGraphExecDestroy(e->gexec);
         e->gexec = nullptr;
     }
@@ -1856,29 +2268,15 @@ qg_status ensemble_build(qg_ensemble e) {
         cudaGraphDestroy(e->graph);
         e->graph = nullptr;
     }
-    const std::vector<int> lane = ensemble_placement(e);
+    const bool f64 = e->m[0]->dtype == QG_F64;
+    qg_status st = f64 ? ensemble_tables<double>(e) : ensemble_tables<float>(e);
+    if (st != QG_OK) return st;
     if (cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return QG_ERR_CUDA;
-    qg_status st = QG_OK;
-    bool ok = cudaEventRecord(e->ev[0], e->cap) == cudaSuccess;
-    for (size_t k = 0; k < e->lanes.size() && ok; ++k)
-        ok = cudaStreamWaitEvent(e->lanes[k], e->ev[0], 0) == cudaSuccess;
-    e->kernels = 0;
-    for (size_t i = 0; i < e->m.size() && ok && st == QG_OK; ++i) {
-        qg_ctx* h = e->m[i];
-        h->kernels_per_step = 0;
-        h->capturing = true;
-        st = enqueue_step_any(h, e->lanes[lane[i]]);
-        h->capturing = false;
-        e->kernels += h->kernels_per_step;
-    }
-    for (size_t k = 0; k < e->lanes.size() && ok; ++k) {
-        ok = cudaEventRecord(e->ev[1 + k], e->lanes[k]) == cudaSuccess &&
-             cudaStreamWaitEvent(e->cap, e->ev[1 + k], 0) == cudaSuccess;
-    }
+    st = f64 ? ensemble_enqueue<double>(e, e->cap) : ensemble_enqueue<float>(e, e->cap);
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(e->cap, &g);
-    if (st != QG_OK || !ok || ce != cudaSuccess) {
+    if (st != QG_OK || ce != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         (void)cudaGetLastError();
         return st != QG_OK ? st : QG_ERR_CUDA;
@@ -1915,18 +2313,7 @@ qg_status qg_ensemble_create(const qg_basin* basins, const double* Re, const dou
         }
         e->m.push_back(h);
     }
-    const int L = count < kEnsembleLanes ? count : kEnsembleLanes;
-    bool ok = cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) == cudaSuccess;
-    for (int k = 0; k < L && ok; ++k) {
-        cudaStream_t s = nullptr;
-        ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
-        if (ok) e->lanes.push_back(s);
-    }
-    for (int k = 0; k <= L && ok; ++k) {
-        cudaEvent_t v = nullptr;
-        ok = cudaEventCreateWithFlags(&v, cudaEventDisableTiming) == cudaSuccess;
-        if (ok) e->ev.push_back(v);
-    }
+    const bool ok = cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
         ensemble_free(e);
         (void)cudaGetLastError();

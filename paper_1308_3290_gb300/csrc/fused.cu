@@ -132,12 +132,13 @@ struct Plan {
     static constexpr size_t END = al(FF + sizeof(T) * RC * TX);
 };
 
+// The work of one CTA: the tile (bx, by) of one basin, whose tensor maps and
+// parameters the two kernels below take from the launch (one basin) or from
+// a table in device memory (a batch of ensemble members).
 template <typename T, int LV, bool TL>
-__global__ void __launch_bounds__(Plan<T, LV, TL>::THREADS, (sizeof(T) == 4 && !TL) ? 3 : 2)
-fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
-                  const __grid_constant__ CUtensorMap tm_wn,
-                  const __grid_constant__ CUtensorMap tm_p,
-                  const __grid_constant__ CUtensorMap tm_f, FusedParams<T> p) {
+__device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtensorMap* tm_wn,
+                                           const CUtensorMap* tm_p, const CUtensorMap* tm_f,
+                                           const FusedParams<T>& p, int bx, int by) {
     using PL = Plan<T, LV, TL>;
     constexpr int F = 1 << LV;
     constexpr int RC = PL::RC;
@@ -156,8 +157,8 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
     T* cp2 = reinterpret_cast<T*>(smem + PL::CP2);   // the other layer's psi (two layers)
 
     const int nx = p.nx, ny = p.ny, ld = p.ld;
-    const int x0 = blockIdx.x * TX;
-    const int yc = blockIdx.y * RC;
+    const int x0 = bx * TX;
+    const int yc = by * RC;
     const bool use_wn = p.a != T(0);
     const bool use_f = p.f2d != nullptr;
     const uint32_t bar = smem_u32(&mbar);
@@ -177,12 +178,12 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
         if (LV == 0) bytes += sizeof(T) * (RC + 2) * SWX;
         if (use_f) bytes += sizeof(T) * RC * TX;
         mbar_expect_tx(bar, bytes);
-        tma_load_2d(smem_u32(sw), &tm_w, x0 - 4, yc - 1, bar);
-        if (use_wn) tma_load_2d(smem_u32(swn), &tm_wn, x0, yc, bar);
-        if (use_f) tma_load_2d(smem_u32(sf), &tm_f, x0, yc, bar);
+        tma_load_2d(smem_u32(sw), tm_w, x0 - 4, yc - 1, bar);
+        if (use_wn) tma_load_2d(smem_u32(swn), tm_wn, x0, yc, bar);
+        if (use_f) tma_load_2d(smem_u32(sf), tm_f, x0, yc, bar);
     }
     pdl_wait();
-    if (LV == 0 && threadIdx.x == 0) tma_load_2d(smem_u32(sp), &tm_p, x0 - 4, yc - 1, bar);
+    if (LV == 0 && threadIdx.x == 0) tma_load_2d(smem_u32(sp), tm_p, x0 - 4, yc - 1, bar);
     // the step size: fixed, or Eq. dt from this step's first streamfunction
     // (one FP64 division per CTA, shared through the barrier below)
     __shared__ T s_dt;
@@ -193,7 +194,7 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
             dtd = u > 0.0 ? fmin(p.dt_cap, p.cfl_h / u) : p.dt_cap;
         }
         s_dt = (T)dtd;
-        if (p.last_stage && blockIdx.x == 0 && blockIdx.y == 0) {
+        if (p.last_stage && bx == 0 && by == 0) {
             p.clock[0] += dtd;
             p.clock[1] = dtd;
         }
@@ -246,7 +247,9 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
         for (int k = 0; k < 4; ++k) c[k] = r[k];
     };
     // ph = y mod 2^l, known at compile time in the unrolled sweep (ys is a
-    // multiple of RY, itself a multiple of 2^l)
+    // multiple of RY, itself a multiple of 2^l).  Sums of products are
+    // written as explicit fma: left to the compiler, the two instantiations
+    // of this body (one basin, batch) could contract them differently.
     auto psi_row = [&](int y, int ph, const T (&c0)[4], const T (&c1)[4], T v[6]) {
         if (y < 0 || y >= ny) {
 #pragma unroll
@@ -256,16 +259,16 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
         const T b = T(ph) * (T(1) / T(F));
         T cv[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) cv[k] = ph == 0 ? c0[k] : (T(1) - b) * c0[k] + b * c1[k];
+        for (int k = 0; k < 4; ++k) cv[k] = ph == 0 ? c0[k] : fma(b, c1[k], (T(1) - b) * c0[k]);
         if (LV == 1) {
             v[0] = T(0.5) * (cv[0] + cv[1]); v[1] = cv[1];
             v[2] = T(0.5) * (cv[1] + cv[2]); v[3] = cv[2];
             v[4] = T(0.5) * (cv[2] + cv[3]); v[5] = cv[3];
         } else if (LV == 2) {
-            v[0] = T(0.25) * cv[0] + T(0.75) * cv[1]; v[1] = cv[1];
-            v[2] = T(0.75) * cv[1] + T(0.25) * cv[2];
+            v[0] = fma(T(0.75), cv[1], T(0.25) * cv[0]); v[1] = cv[1];
+            v[2] = fma(T(0.25), cv[2], T(0.75) * cv[1]);
             v[3] = T(0.5) * (cv[1] + cv[2]);
-            v[4] = T(0.25) * cv[1] + T(0.75) * cv[2]; v[5] = cv[2];
+            v[4] = fma(T(0.75), cv[2], T(0.25) * cv[1]); v[5] = cv[2];
         } else {
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
@@ -274,7 +277,7 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                 const T a = T(x & (F - 1)) * (T(1) / T(F));
                 const T lo = cell == 0 ? cv[0] : (cell == 1 ? cv[1] : cv[2]);
                 const T hi = cell == 0 ? cv[1] : (cell == 1 ? cv[2] : cv[3]);
-                v[k] = (T(1) - a) * lo + a * hi;
+                v[k] = fma(a, hi, (T(1) - a) * lo);
             }
         }
         // columns at or beyond a wall interpolate between the zero wall
@@ -421,9 +424,9 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                 // x shares of this row
                 T xa, xb = T(0), xe;
                 if (LV == 1) {
-                    const T A = T(0.5) * out[0] + T(0.25) * out[1];
+                    const T A = fma(T(0.25), out[1], T(0.5) * out[0]);
                     const T C = T(0.25) * out[3];
-                    xb = T(0.25) * out[1] + T(0.5) * out[2] + T(0.25) * out[3];
+                    xb = fma(T(0.25), out[3], fma(T(0.5), out[2], T(0.25) * out[1]));
                     const T Cp = __shfl_up_sync(gm, C, 1, 16);
                     xa = A + (lane > 0 ? Cp : T(0));
                     xe = C;
@@ -513,6 +516,60 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
 }
 
 template <typename T, int LV, bool TL>
+__global__ void __launch_bounds__(Plan<T, LV, TL>::THREADS, (sizeof(T) == 4 && !TL) ? 3 : 2)
+fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
+                  const __grid_constant__ CUtensorMap tm_wn,
+                  const __grid_constant__ CUtensorMap tm_p,
+                  const __grid_constant__ CUtensorMap tm_f, FusedParams<T> p) {
+    sweep_tile<T, LV, TL>(&tm_w, &tm_wn, &tm_p, &tm_f, p, blockIdx.x, blockIdx.y);
+}
+
+// Batched fine stage of an ensemble: CTA c sweeps tile (tiles[c].y,
+// tiles[c].z) of member tiles[c].x; the member's tensor maps and parameters
+// are read from `fm` in device memory (written by the host before the
+// launch).  One layer only.
+template <typename T, int LV>
+__global__ void __launch_bounds__(Plan<T, LV, false>::THREADS, sizeof(T) == 4 ? 3 : 2)
+fine_batch_kernel(const FineMember<T>* __restrict__ fm, const int4* __restrict__ tiles) {
+    const int4 t = tiles[blockIdx.x];
+    const FineMember<T>* E = fm + t.x;
+    if (threadIdx.x == 0) {
+        // the tensor maps live in global memory: order the copy proxy's reads
+        // of them after the host's writes
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&E->w) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&E->wn) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&E->psi) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&E->f) : "memory");
+    }
+    sweep_tile<T, LV, false>(&E->w, &E->wn, &E->psi, &E->f, E->p, t.y, t.z);
+}
+
+template <typename T, int LV>
+cudaError_t launch_batch(const FineMember<T>* fm, const int4* tiles, int ntiles, bool forcing_field,
+                         bool pdl, cudaStream_t s) {
+    using PL = Plan<T, LV, false>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(fine_batch_kernel<T, LV>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)PL::END);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ntiles);
+    cfg.blockDim = dim3(PL::THREADS);
+    cfg.dynamicSmemBytes = forcing_field ? PL::END : PL::END_NOF;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, fine_batch_kernel<T, LV>, fm, tiles);
+}
+
+template <typename T, int LV, bool TL>
 cudaError_t launch_sweep(const FusedParams<T>& p, const FineMaps& m, cudaStream_t s) {
     using PL = Plan<T, LV, TL>;
     static bool attr_set = false;
@@ -561,6 +618,25 @@ cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int le
         default: return cudaErrorInvalidValue;
     }
 }
+
+template <typename T>
+cudaError_t launch_fine_batch(const FineMember<T>* fm, const int4* tiles, int ntiles, int levels,
+                              bool forcing_field, bool pdl, cudaStream_t s) {
+    if (ntiles < 1) return cudaSuccess;
+    switch (levels) {
+        case 0: return launch_batch<T, 0>(fm, tiles, ntiles, forcing_field, pdl, s);
+        case 1: return launch_batch<T, 1>(fm, tiles, ntiles, forcing_field, pdl, s);
+        case 2: return launch_batch<T, 2>(fm, tiles, ntiles, forcing_field, pdl, s);
+        case 3: return launch_batch<T, 3>(fm, tiles, ntiles, forcing_field, pdl, s);
+        case 4: return launch_batch<T, 4>(fm, tiles, ntiles, forcing_field, pdl, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_fine_batch<float>(const FineMember<float>*, const int4*, int, int, bool,
+                                              bool, cudaStream_t);
+template cudaError_t launch_fine_batch<double>(const FineMember<double>*, const int4*, int, int,
+                                               bool, bool, cudaStream_t);
 
 size_t fine_tile_rows(size_t esz) { return esz == 8 ? Rows<double>::value : Rows<float>::value; }
 int fine_part_period_x(int levels) { return TX >> levels; }

@@ -43,6 +43,20 @@ struct DstLaunch {
 // transposed layout (mx + 1 rows of pitch ld_tr).  bar: two zero-initialised
 // counters of the grid barrier.  One cooperative launch, or (split) one
 // plain launch per pass.
+// Per-member fields of a batched solve launch (ensembles): the members of a
+// batch share the elliptic grid and its tables (mx, my, ld, ld_tr, twiddle
+// and eigenvalue tables, scale); each has its own right-hand side planes,
+// transposed spectrum, work and output arrays and error flag.  One layer.
+template <typename T>
+struct SolveMember {
+    const T* in[4];
+    int nin, part_px, part_py;
+    T* tr;
+    T* work;
+    T* out;
+    int* err;
+};
+
 template <typename T>
 struct SolveParams {
     int mx, my, layers;
@@ -67,6 +81,17 @@ struct SolveParams {
     int split;           // 0: the three passes in one cooperative launch with
                          // grid barriers; 1: three plain launches, one per pass
     int phase;           // the pass a split launch runs (set by launch_solve)
+    // Batch (ensembles): when non-null, one launch solves the nbatch
+    // members' systems; their fields replace in/nin/part_*/tr/work/out/err
+    // of this struct (split must be 0).  Warp-group engines: a work queue
+    // whose counters are bar[0 .. 2 + 3 nbatch), zero before the first
+    // launch and left zero by every launch; the matrix form: one CTA per
+    // member.
+    const SolveMember<T>* batch;
+    int nbatch;
+    int no_pdl;          // 1: launch without programmatic dependent launch
+                         // (kernels on concurrent branches: a dependent that
+                         // started early would hold SM resources idle)
 };
 // engine: base radix of the FFT passes of the shared-memory engine, 4 or 16
 // (see dst_engine.cuh), or the warp-group engine of solve32.cu with 32, 16
@@ -202,6 +227,20 @@ struct FineMaps {
 template <typename T>
 cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int levels,
                               cudaStream_t s, bool two_layer = false);
+// One member of a batched fine-stage launch (ensembles): the tensor maps of
+// its stage and its parameters, in device memory (the TMA unit reads the
+// maps from there; 64-byte aligned).
+template <typename T>
+struct alignas(64) FineMember {
+    CUtensorMap w, wn, psi, f;
+    FusedParams<T> p;
+};
+// One layer: CTA c sweeps the tile (tiles[c].y, tiles[c].z) of member
+// tiles[c].x; `levels` is every member's CGP level; forcing_field when any
+// member uses a forcing field.
+template <typename T>
+cudaError_t launch_fine_batch(const FineMember<T>* fm, const int4* tiles, int ntiles, int levels,
+                              bool forcing_field, bool pdl, cudaStream_t s);
 size_t fine_tile_rows(size_t esz);   // fine rows per CTA
 int fine_part_period_x(int levels);  // coarse columns between tile edges
 int fine_part_period_y(int levels, size_t esz);  // coarse rows between CTA edges

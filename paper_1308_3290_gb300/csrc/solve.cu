@@ -430,6 +430,7 @@ static cudaError_t launch_engine(const SolveParams<T>& P, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_solve(const SolveParams<T>& P, int engine, cudaStream_t s) {
     if (is_warp_engine(engine)) return launch_solve32<T>(P, warp_engine_radix(engine), s);
+    if (P.batch) return cudaErrorInvalidValue;   // batches: warp-group engines only
     return engine == 4 ? launch_engine<T, 4>(P, s) : launch_engine<T, 16>(P, s);
 }
 

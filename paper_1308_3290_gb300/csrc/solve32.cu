@@ -536,6 +536,36 @@ __host__ __device__ inline Tabs tabs_for(int lgx, int lgy, int rad, int threads,
     return b;
 }
 
+// Set the error flag of the solve, or of every member of a batch.
+template <typename T, bool BATCH>
+__device__ __forceinline__ void raise_err(const SolveParams<T>& P) {
+    if constexpr (BATCH) {
+        for (int i = 0; i < P.nbatch; ++i) atomicExch(P.batch[i].err, 1);
+    } else {
+        atomicExch(P.err, 1);
+    }
+}
+
+// One slot of phase ph: the pair of this thread's group, loaded, transformed
+// (phase 1: forward, mode solve, inverse) and stored.
+template <typename T, int OPY, int RAD>
+__device__ __forceinline__ void solve_slot(const SolveParams<T>& P, int ph, int slot, int npairs,
+                                           int per, int grp, int t, const Geo32& g, CT<T>* cb,
+                                           CT<T>* cb2, const CT<T>* tw, const T* lamy,
+                                           const Sync& sy) {
+    const PairAt a = pair_at<T, OPY>(P, ph, slot * per + grp, npairs);
+    load_pair<T, OPY, RAD>(P, ph, a, g, cb, t);
+    const int nfft = ph == 1 ? 2 : 1;
+    CT<T>* res = cb;
+#pragma unroll 1
+    for (int f = 0; f < nfft; ++f) {
+        if (f == 1) mode_solve<T, OPY, RAD>(P, a, g, res, t, lamy);
+        res = fft_rt<T, RAD>(res, res == cb ? cb2 : cb, t, g, tw, sy);
+    }
+    store_pair<T, OPY, RAD>(P, ph, a, g, res, t);
+    sy.sync();
+}
+
 template <typename T, int OPY, int RAD>
 __global__ void __launch_bounds__(max_cta(RAD, (int)sizeof(T)),
                                   (RAD == 8 && sizeof(T) == 4) ? 2 : 1)
@@ -585,7 +615,7 @@ solve32_kernel(SolveParams<T> P, int lgx, int lgy, Tabs tb) {
     if (tb.staged) {
         const bool ok = mbar_wait(bar, 0, kSpin);
         if (!__syncthreads_and(ok)) {
-            if (threadIdx.x == 0) atomicExch(P.err, 1);
+            if (threadIdx.x == 0) raise_err<T, false>(P);
             (void)mbar_wait(bar, 0, kSpin);     // let copies in flight land
             return;
         }
@@ -594,7 +624,7 @@ solve32_kernel(SolveParams<T> P, int lgx, int lgy, Tabs tb) {
     unsigned g0 = 0;
     for (int ph = ph0; ph < ph1; ++ph) {
         if (ph > ph0 && !grid_sync(P.bar, P.bar_extra, kSpin, g0)) {
-            if (threadIdx.x == 0) atomicExch(P.err, 1);
+            if (threadIdx.x == 0) raise_err<T, false>(P);
             return;
         }
         if (ph + 1 < ph1) g0 = grid_gen(P.bar);
@@ -609,20 +639,140 @@ solve32_kernel(SolveParams<T> P, int lgx, int lgy, Tabs tb) {
         else npairs = (P.my / 2) * P.layers;
         const int per = blockDim.x / g.G;
         const int nslots = (npairs + per - 1) / per;
-        for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
-            const PairAt a = pair_at<T, OPY>(P, ph, slot * per + grp, npairs);
-            load_pair<T, OPY, RAD>(P, ph, a, g, cb, t);
-            const int nfft = ph == 1 ? 2 : 1;
-            CT<T>* res = cb;
-#pragma unroll 1
-            for (int f = 0; f < nfft; ++f) {
-                if (f == 1) mode_solve<T, OPY, RAD>(P, a, g, res, t, lamy);
-                res = fft_rt<T, RAD>(res, res == cb ? cb2 : cb, t, g, tw, sy);
-            }
-            store_pair<T, OPY, RAD>(P, ph, a, g, res, t);
-            sy.sync();
+        for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x)
+            solve_slot<T, OPY, RAD>(P, ph, slot, npairs, per, grp, t, g, cb, cb2, tw, lamy, sy);
+    }
+}
+
+// Batched solve of an ensemble group as a work queue, without grid barriers
+// (so that groups can run side by side on concurrent graph branches: a
+// cooperative grid is not guaranteed to be co-resident with other work).
+// The work items are the slots of the three phases of every member, phase
+// by phase and member by member; CTAs claim them in that order from the
+// counter q[0].  An item of phase ph >= 1 of member m first waits (bounded)
+// until the q[2 + 3 m + ph - 1] items of phase ph - 1 of member m are done;
+// those were claimed before it by CTAs that are running, and depend on no
+// later item, so the wait ends without any co-residency.  A wait that runs
+// out sets the member's error flag and the item is counted done unprocessed
+// (its results are garbage, as the flag says).  The last CTA to leave resets
+// the counters for the next launch.
+__device__ __forceinline__ bool wait_count(const unsigned* c, unsigned want, int limit) {
+    for (int i = 0; i < limit; ++i) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+        if (v >= want) return true;
+    }
+    return false;
+}
+
+template <typename T, int OPY, int RAD>
+__device__ __forceinline__ void solve_queue(const SolveParams<T>& P, int lgx, int lgy,
+                                            CT<T>* bufs, const CT<T>* ptx, const CT<T>* pty,
+                                            const T* lamy, bool broken) {
+    __shared__ int s_item;
+    unsigned* q = P.bar;
+    const int nb = P.nbatch;
+    const Geo32 gx = geo32(lgx, RAD), gy = geo32(lgy, RAD);
+    const int perx = blockDim.x / gx.G, pery = blockDim.x / gy.G;
+    const int npx = P.my / 2, npy = P.mx / 2;            // one layer
+    const int ns0 = (npx + perx - 1) / perx, ns1 = (npy + pery - 1) / pery;
+    const int n0 = nb * ns0, n1 = n0 + nb * ns1, total = n1 + nb * ns0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(q, 1u);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= total) break;
+        int ph, m, slot;
+        if (item < n0) {
+            ph = 0; m = item / ns0; slot = item - m * ns0;
+        } else if (item < n1) {
+            ph = 1; m = (item - n0) / ns1; slot = item - n0 - m * ns1;
+        } else {
+            ph = 2; m = (item - n1) / ns0; slot = item - n1 - m * ns0;
+        }
+        const SolveMember<T>& M = P.batch[m];
+        int ok = broken ? 0 : 1;
+        if (ok && ph > 0 && threadIdx.x == 0)
+            ok = wait_count(q + 2 + 3 * m + ph - 1, (unsigned)(ph == 1 ? ns0 : ns1), kSpin);
+        if (__syncthreads_and(ok)) {
+            const Geo32& g = ph == 1 ? gy : gx;
+            const int grp = threadIdx.x / g.G, t = threadIdx.x % g.G;
+            CT<T>* cb = bufs + 2 * grp * g.buf;
+            CT<T>* cb2 = cb + g.buf;
+            const Sync sy{1 + grp, g.G};
+            SolveParams<T> Q = P;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Q.in[0][k] = M.in[k];
+            Q.nin = M.nin;
+            Q.part_px = M.part_px;
+            Q.part_py = M.part_py;
+            Q.tr[0] = M.tr;
+            Q.work[0] = M.work;
+            Q.out[0] = M.out;
+            solve_slot<T, OPY, RAD>(Q, ph, slot, ph == 1 ? npy : npx, ph == 1 ? pery : perx, grp,
+                                    t, g, cb, cb2, ph == 1 ? pty : ptx, lamy, sy);
+            __syncthreads();
+        } else if (threadIdx.x == 0) {
+            atomicExch(M.err, 1);
+        }
+        if (threadIdx.x == 0) {
+            // this CTA's stores of the item are ordered before the count by
+            // the CTA barrier above and the release
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(q + 2 + 3 * m + ph)
+                         : "memory");
         }
     }
+    if (threadIdx.x == 0) {
+        unsigned old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(q + 1)
+                     : "memory");
+        if (old == gridDim.x - 1) {
+            for (int i = 0; i < 2 + 3 * nb; ++i) q[i] = 0u;
+        }
+    }
+}
+
+template <typename T, int OPY, int RAD>
+__global__ void __launch_bounds__(max_cta(RAD, (int)sizeof(T)),
+                                  (RAD == 8 && sizeof(T) == 4) ? 2 : 1)
+solve32_batch_kernel(SolveParams<T> P, int lgx, int lgy, Tabs tb) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    CT<T>* bufs = reinterpret_cast<CT<T>*>(smem);
+    const CT<T>* ptx = P.ptx;
+    const CT<T>* pty = P.pty;
+    const T* lamy = P.lamy;
+    const uint32_t bar = smem_u32(&mbar);
+    if (tb.staged) {
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                         "r"(tb.nx + tb.ny + tb.nl) : "memory");
+            if (tb.nx) bulk_copy(smem_u32(smem + tb.tx), P.ptx, tb.nx, bar);
+            if (tb.ny) bulk_copy(smem_u32(smem + tb.ty), P.pty, tb.ny, bar);
+            bulk_copy(smem_u32(smem + tb.ly), P.lamy, tb.nl, bar);
+        }
+        ptx = reinterpret_cast<const CT<T>*>(smem + tb.tx);
+        pty = reinterpret_cast<const CT<T>*>(smem + tb.ty);
+        lamy = reinterpret_cast<const T*>(smem + tb.ly);
+    }
+    pdl_wait();
+    pdl_trigger();
+    bool broken = false;
+    if (tb.staged) {
+        const bool ok = mbar_wait(bar, 0, kSpin);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) raise_err<T, true>(P);
+            (void)mbar_wait(bar, 0, kSpin);     // let copies in flight land
+            broken = true;   // claim items and count them done unprocessed
+        }
+    }
+    solve_queue<T, OPY, RAD>(P, lgx, lgy, bufs, ptx, pty, lamy, broken);
 }
 
 int least_threads() {
@@ -643,9 +793,11 @@ int log2i(int v) {
     return r;
 }
 
-template <typename T, int OPY, int RAD>
+template <typename T, int OPY, int RAD, bool BATCH = false>
 cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
-    auto k = solve32_kernel<T, OPY, RAD>;
+    void (*k)(SolveParams<T>, int, int, Tabs);
+    if constexpr (BATCH) k = solve32_batch_kernel<T, OPY, RAD>;
+    else k = solve32_kernel<T, OPY, RAD>;
     const int lgx = log2i(2 * P.mx), lgy = log2i(2 * P.my);
     const int threads = cta_threads(lgx, lgy, RAD, least_threads());
     const Tabs tb = tabs_for(lgx, lgy, RAD, threads, (int)sizeof(T),
@@ -664,6 +816,7 @@ cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
     const int cols = OPY == 2 ? P.mx - 1 : P.mx / 2;
     int want = slots(lgx, rows);
     if (slots(lgy, cols) > want) want = slots(lgy, cols);
+    if (BATCH) want = P.nbatch * (2 * slots(lgx, rows) + slots(lgy, cols));   // queue items
     int grid = per * nsm;
     if (want < grid) grid = want;
     cudaLaunchConfig_t cfg = {};
@@ -672,6 +825,16 @@ cudaError_t launch32(const SolveParams<T>& P, cudaStream_t s) {
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;
     cudaLaunchAttribute at[2];
+    if (BATCH) {
+        // the work queue needs no co-residency: a plain launch, allowed to
+        // start while the kernel before it finishes (the table copies
+        // precede the programmatic wait) unless no_pdl
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = P.no_pdl ? nullptr : at;
+        cfg.numAttrs = P.no_pdl ? 0 : 1;
+        return cudaLaunchKernelEx(&cfg, k, P, lgx, lgy, tb);
+    }
     if (!P.split) {
         // cooperative (grid barriers), and allowed to start while the fine
         // stage before it finishes: the table copies precede the kernel's
@@ -714,6 +877,12 @@ template <typename T>
 cudaError_t launch_solve32(const SolveParams<T>& P, int rad, cudaStream_t s) {
     if (!solve32_supports(P.mx, P.my, rad, sizeof(T)) || !P.ptx || !P.pty)
         return cudaErrorInvalidValue;
+    if (P.batch) {
+        if (P.layers != 1 || P.split || P.nbatch < 1) return cudaErrorInvalidValue;
+        if (rad == 8) return launch32<T, 1, 8, true>(P, s);
+        if (rad == 16) return launch32<T, 1, 16, true>(P, s);
+        return launch32<T, 1, 32, true>(P, s);
+    }
     if (rad == 8)
         return P.layers == 2 ? launch32<T, 2, 8>(P, s) : launch32<T, 1, 8>(P, s);
     if (rad == 16)

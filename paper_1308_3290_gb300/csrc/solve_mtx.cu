@@ -158,8 +158,22 @@ __device__ __forceinline__ void mm3(const float* A, int lda, const float* B, int
     }
 }
 
+// One solve per CTA: the handle's (BATCH false, one CTA) or member
+// blockIdx.x of a batch, whose fields replace the per-member ones of P.
+template <bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1)
-solve_mtx_kernel(SolveParams<float> P, const float* __restrict__ tab, MtxGeo g) {
+solve_mtx_kernel(SolveParams<float> Pk, const float* __restrict__ tab, MtxGeo g) {
+    SolveParams<float> P = Pk;
+    if constexpr (BATCH) {
+        const SolveMember<float>& M = Pk.batch[blockIdx.x];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) P.in[0][q] = M.in[q];
+        P.nin = M.nin;
+        P.part_px = M.part_px;
+        P.part_py = M.part_py;
+        P.out[0] = M.out;
+        P.err = M.err;
+    }
     extern __shared__ __align__(16) float sm[];
     __shared__ __align__(8) uint64_t mbar;
     const uint32_t bar = smem_u32(&mbar);
@@ -275,18 +289,21 @@ void mtx_table(int mx, int my, double dx, double dy, float* out) {
 }
 
 cudaError_t launch_solve_mtx(const SolveParams<float>& P, const float* tab, cudaStream_t s) {
-    if (!mtx_supports(P.mx, P.my, sizeof(float), P.layers) || !tab || P.nin < 1 ||
-        (P.nin > 1 && (P.part_px < 1 || P.part_py < 1)))
+    // (a batch's members carry their own right-hand side planes)
+    if (!mtx_supports(P.mx, P.my, sizeof(float), P.layers) || !tab ||
+        (!P.batch && (P.nin < 1 || (P.nin > 1 && (P.part_px < 1 || P.part_py < 1)))))
         return cudaErrorInvalidValue;
     const MtxGeo g = mtx_geo(P.mx, P.my);
     const size_t sm = (size_t)g.end * sizeof(float);
     int per = 0, nsm = 0;
-    cudaError_t e = launch_shape(reinterpret_cast<const void*>(solve_mtx_kernel), kThreads, sm,
-                                 &per, &nsm);
+    const bool batch = P.batch != nullptr;
+    if (batch && P.nbatch < 1) return cudaErrorInvalidValue;
+    auto k = batch ? solve_mtx_kernel<true> : solve_mtx_kernel<false>;
+    cudaError_t e = launch_shape(reinterpret_cast<const void*>(k), kThreads, sm, &per, &nsm);
     if (e != cudaSuccess) return e;
     if (per < 1) return cudaErrorInvalidConfiguration;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(1);
+    cfg.gridDim = dim3(batch ? P.nbatch : 1);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;
@@ -296,9 +313,9 @@ cudaError_t launch_solve_mtx(const SolveParams<float>& P, const float* tab, cuda
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, solve_mtx_kernel, P, tab, g);
+    cfg.attrs = P.no_pdl ? nullptr : at;
+    cfg.numAttrs = P.no_pdl ? 0 : 1;
+    return cudaLaunchKernelEx(&cfg, k, P, tab, g);
 }
 
 }  // namespace qg

@@ -46,14 +46,34 @@ def test_ensemble_matches_oracle(dtype, tol):
     ens.close()
 
 
-def test_ensemble_equals_standalone_handles(monkeypatch):
-    """With the same FFT schedule the ensemble's results are bitwise those
-    of stand-alone handles (the split solve does the same arithmetic)."""
+def _groups(members):
+    """Launches per TVDRK3 stage of a batched ensemble step: the members
+    whose elliptic grids share shape and spacings form a group with one
+    solve launch, and one fine-stage launch per CGP level among its
+    members.  Returns (solve launches, fine launches)."""
+    groups = {}
+    for m in members:
+        key = (m["nx"] >> m["levels"], m["ny"] >> m["levels"],
+               (1.0 / m["nx"]) * 2 ** m["levels"], (2.0 / m["ny"]) * 2 ** m["levels"])
+        groups.setdefault(key, set()).add(m["levels"])
+    return len(groups), sum(len(v) for v in groups.values())
+
+
+@pytest.mark.parametrize("engine", [34, 40, 4])
+def test_ensemble_equals_standalone_handles(engine, monkeypatch):
+    """The batched step (one solve launch per group of equal elliptic grids,
+    one fine-stage launch per level) does the same arithmetic as stand-alone
+    handles: with the same solve engine the states are bitwise equal.  With
+    the warp-group engine (34) and the matrix form (40) the solves are
+    batched; the shared-memory engine (4) does not batch, so each member
+    solves with its own three launches."""
     require_gpu()
-    monkeypatch.setenv("QG_SOLVE_ENGINE", "4")
+    monkeypatch.setenv("QG_SOLVE_ENGINE", str(engine))
     ens = qg.Ensemble(MEMBERS, dtype="f32")
     solo = [qg.Basin(m["nx"], m["ny"], Re=m["Re"], Ro=m["Ro"], levels=m["levels"], dt=m["dt"],
                      amp=m["amp"], dtype="f32") for m in MEMBERS]
+    for b in solo:
+        assert qg.qg_solve_engine(b.h) == engine
     for i, m in enumerate(MEMBERS):
         w = inputs.perturbation(m["nx"], m["ny"], seed=40 + i) * 50.0
         ens.member(i).set_state(w)
@@ -65,12 +85,11 @@ def test_ensemble_equals_standalone_handles(monkeypatch):
     for i, b in enumerate(solo):
         b.synchronize()
         assert np.array_equal(to_np(ens.member(i).state()), to_np(b.state())), i
-    counts = sum(qg.qg_step_kernel_count(b.h) for b in solo)
     for b in solo:
         b.close()
-    # each member's solve is three launches instead of one
-    n_solves = 3 * len(MEMBERS)      # one per TVDRK3 stage
-    assert ens.kernel_count() == counts + 2 * n_solves
+    n_solve, n_fine = _groups(MEMBERS)
+    per_stage = n_solve + n_fine if engine != 4 else 3 * len(MEMBERS) + n_fine
+    assert ens.kernel_count() == 3 * per_stage
     ens.close()
 
 
@@ -89,6 +108,10 @@ def test_ensemble_of_96_basins_steps():
     ens = qg.Ensemble(members, dtype="f32")
     for i, m in enumerate(members):
         ens.member(i).set_state(inputs.perturbation(m["nx"], m["ny"], seed=1000 + i))
+    # batched: one solve launch per elliptic-grid group, one fine launch per
+    # level, per stage
+    n_solve, n_fine = _groups(members)
+    assert ens.kernel_count() <= 3 * (n_solve + n_fine) <= 40
     ens.step(5)
     ens.synchronize()
     for i in (0, 17, 95):

@@ -109,8 +109,10 @@ def test_matrix_engine_unsupported_grids_fall_back(monkeypatch):
 
 def test_matrix_engine_in_an_ensemble_equals_standalone_handles(monkeypatch):
     """Ensemble members on the matrix engine: bitwise the stand-alone
-    handles' steps, and one launch per solve in both (the FFT engines split
-    an ensemble member's solve into three)."""
+    handles' steps; the ensemble solves each group of equal elliptic grids
+    (here 32 x 64 for three members at levels 0, 1, 2, and 32 x 16 for one)
+    in one launch with one CTA per member, and sweeps each level's members
+    of a group in one launch."""
     require_gpu()
     monkeypatch.setenv("QG_SOLVE_ENGINE", str(MATRIX))
     members = [
@@ -135,7 +137,8 @@ def test_matrix_engine_in_an_ensemble_equals_standalone_handles(monkeypatch):
     for i, b in enumerate(solo):
         b.synchronize()
         assert np.array_equal(to_np(ens.member(i).state()), to_np(b.state())), i
-    assert ens.kernel_count() == sum(qg.qg_step_kernel_count(b.h) for b in solo)
+    assert sum(qg.qg_step_kernel_count(b.h) for b in solo) == 3 * 2 * len(members)
+    assert ens.kernel_count() == 3 * (2 + 4)
     m = members[1]
     ref = O.run(w[1], O.Basin(m["nx"], m["ny"], Re=m["Re"], Ro=m["Ro"], levels=m["levels"],
                               dt=m["dt"], amp=m["amp"]), 10)
