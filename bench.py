@@ -471,6 +471,7 @@ def ours(args):
     torch.cuda.synchronize()
     per_step_kernels = qg.qg_step_kernel_count(h)
     solve_engine = qg.qg_solve_engine(h)
+    stencil_tile = qg.qg_stencil_tile(h)
 
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
@@ -613,6 +614,7 @@ def ours(args):
             "roofline": roofline, "rooflines": rooflines, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": per_step_kernels * args.steps,
             "solve_engine": solve_engine,
+            "stencil_tile_rows": stencil_tile,
             "clocks": clocks, "variants": variants,
         }
         print(json.dumps(line), flush=True)

@@ -160,6 +160,15 @@ qg_status qg_step(qg_handle h, int64_t n);
 qg_status qg_diagnostics(qg_handle h, double* ke, double* enstrophy,
                          double* max_vel);
 
+/* qg_energy_accumulate -- *acc += scale * E, E the basin-integrated kinetic
+ * energy of the current state as qg_diagnostics reports it (Section 5.2;
+ * psi from the CGP projection, steps (ii)-(iv) of Section 3), added in FP64
+ * on the device.  acc: a caller DEVICE pointer to one double.  Asynchronous
+ * on the handle's stream (no synchronisation): for sums of the energy over
+ * many steps, such as the time-mean energy of an adjoint objective.
+ * Errors: QG_ERR_ARG.                                                      */
+qg_status qg_energy_accumulate(qg_handle h, double scale, double* acc);
+
 /* Kernel classes of the step, for qg_read_timing.                          */
 typedef enum qg_kernel_class {
     QG_K_RESTRICT = 0,   /* restriction (Eq. res), when not fused            */
@@ -262,6 +271,16 @@ qg_status qg_set_solver(qg_handle h, qg_solver kind, int32_t cycles);
  * implementations of the same sine-transform solve of Section 4.3, equal to
  * rounding.  No device work.  Errors: QG_ERR_ARG.                          */
 qg_status qg_solve_engine(qg_handle h, int32_t* engine);
+
+/* qg_stencil_tile -- the fine rows per CTA of the step's fused fine-grid
+ * kernel (host pointer; the tile is 64 fine columns wide): chosen when the
+ * handle is created by timing whole steps with each height the build
+ * offers for the handle (128, 64 or 32 for one-layer FP32 handles; 64 for
+ * FP64 and 128 for two layers, fixed), after the solve engine
+ * (qg_solve_engine); QG_FINE_ROWS forces an offered height.  Ensemble
+ * members keep the default.  The heights give the same results to
+ * rounding.  No device work.  Errors: QG_ERR_ARG.                         */
+qg_status qg_stencil_tile(qg_handle h, int32_t* rows);
 
 /* qg_get_time -- model time since creation or the last qg_set_state, and
  * the size of the last step (host pointers; either may be NULL).

@@ -1,14 +1,15 @@
 """Gradient of a time-mean kinetic energy with respect to the wind-forcing
 field, as a ``torch.autograd.Function`` over the library's tape and adjoint
-calls (qg_tape_begin, qg_step, qg_diagnostics, qg_energy_gradient,
+calls (qg_tape_begin, qg_step, qg_energy_accumulate, qg_energy_gradient,
 qg_adjoint_step).  The paper has no adjoint; the objective is the basin
 kinetic energy of Section 5.2 averaged over a window of steps.
 
     J(F) = 1/(N - n0 + 1) * sum_{n = n0..N} E(psi^n),   psi^n = P^l S R^l w^n
 
 All arithmetic runs in the library's kernels; this module only orders the
-calls: a forward sweep that records the states and sums E, and a reverse
-sweep that adds dE/dw at each time of the window and steps the adjoint back.
+calls: a forward sweep that records the states and sums E on the device
+(qg_energy_accumulate: no synchronisation per step), and a reverse sweep
+that adds dE/dw at each time of the window and steps the adjoint back.
 """
 from __future__ import annotations
 
@@ -23,7 +24,8 @@ class MeanKineticEnergy(torch.autograd.Function):
     F: forcing field (ny-1, nx-1) on the basin's device and dtype (the
     gradient is taken with respect to it); basin: a one-layer ``qg.Basin``;
     w0: the initial state; nsteps: N; first: n0; every: checkpoint interval
-    of the tape (1 keeps every state).  Returns a 0-d float64 tensor."""
+    of the tape (1 keeps every state).  Returns a 0-d float64 tensor on F's
+    device."""
 
     @staticmethod
     def forward(ctx, F, basin, w0, nsteps: int, first: int, every: int = 1):
@@ -31,16 +33,18 @@ class MeanKineticEnergy(torch.autograd.Function):
         basin.set_forcing(F)
         basin.set_state(w0)
         qg.qg_tape_begin(h, every, nsteps)
-        acc = 0.0
+        K = nsteps - first + 1
+        J = torch.zeros((), dtype=torch.float64, device=F.device)
         if first == 0:
-            acc += basin.diagnostics()[0]
+            qg.qg_energy_accumulate(h, 1.0 / K, J)
         for n in range(1, nsteps + 1):
             basin.step(1)
             if n >= first:
-                acc += basin.diagnostics()[0]
+                qg.qg_energy_accumulate(h, 1.0 / K, J)
+        qg.qg_synchronize(h)
         ctx.basin, ctx.nsteps, ctx.first = basin, nsteps, first
         ctx.shape, ctx.dtype, ctx.device = F.shape, F.dtype, F.device
-        return torch.tensor(acc / (nsteps - first + 1), dtype=torch.float64)
+        return J
 
     @staticmethod
     def backward(ctx, grad_J):

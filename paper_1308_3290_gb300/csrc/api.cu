@@ -133,6 +133,8 @@ struct qg_ctx {
     CUtensorMap tm_halo[3][2], tm_int[3][2], tm_psi, tm_f;
     int solve_engine = 4;          // FFT base radix of the step's solve (autotuned)
     bool engine_forced = false;    // solve_engine was forced by QG_SOLVE_ENGINE
+    int fine_rows = 0;             // fine rows per CTA of the fused stage (autotuned)
+    bool member = false;           // an ensemble member (keeps the default tile)
     int* derr = nullptr;           // device error flag of bounded waits
     unsigned* dbar = nullptr;      // grid-barrier counters of the solve kernel
     Tape* tape = nullptr;          // adjoint tape (qg_tape_begin .. qg_tape_end)
@@ -196,6 +198,13 @@ qg_status cuda_status(qg_ctx* h, cudaError_t e) {
     do {                                            \
         cudaError_t e_ = (expr);                    \
         if (e_ != cudaSuccess) return cuda_status(h, e_); \
+    } while (0)
+
+// A call returning qg_status: latch and return its error.
+#define QG_TRY_S(expr)                              \
+    do {                                            \
+        const qg_status st_ = (expr);               \
+        if (st_ != QG_OK) return fail(h, st_);      \
     } while (0)
 
 // QG_ALLOC_LIMIT_BYTES (a test hook for the out-of-memory path): the device
@@ -490,7 +499,7 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
     P.part_px = P.part_py = 1;
     if (nparts > 1) {
         P.part_px = fine_part_period_x(h->levels);
-        P.part_py = fine_part_period_y(h->levels, sizeof(T));
+        P.part_py = fine_part_period_y(h->levels, h->fine_rows);
     }
     P.ld = t.ldc;
     P.ld_tr = ld_tr;
@@ -555,9 +564,36 @@ bool engine_ok(const qg_ctx* h, const LevelTables* t, size_t esz, int e) {
     return solve_engine_supports(t->mx, t->my, esz, e) && (!is_warp_engine(e) || t->ptx[e - 32]);
 }
 
+// TMA tensor maps of the fine buffers for the handle's tile height: halo
+// boxes of w^(s) and the fine psi, interior boxes of w^n and the forcing.
+qg_status fine_maps(qg_ctx* h) {
+    const int rows = h->fine_rows;
+    for (int k = 0; k < 3; ++k) {
+        for (int L = 0; L < h->layers; ++L) {
+            const void* base = static_cast<const char*>(h->w[k]) + L * h->plane_f * h->esz;
+            if (make_tensor_map(&h->tm_halo[k][L], base, h->nx, h->ny, h->ldf, h->esz,
+                                fine_halo_cols(), rows + 2) != cudaSuccess ||
+                make_tensor_map(&h->tm_int[k][L], base, h->nx, h->ny, h->ldf, h->esz,
+                                fine_block_cols(), rows) != cudaSuccess)
+                return QG_ERR_CUDA;
+        }
+    }
+    if (make_tensor_map(&h->tm_psi, h->psi, h->nx, h->ny, h->ldf, h->esz, fine_halo_cols(),
+                        rows + 2) != cudaSuccess)
+        return QG_ERR_CUDA;
+    if (h->f2d) {
+        if (make_tensor_map(&h->tm_f, h->f2d, h->nx, h->ny, h->ldf, h->esz, fine_block_cols(),
+                            rows) != cudaSuccess)
+            return QG_ERR_CUDA;
+    } else {
+        h->tm_f = h->tm_int[0][0];
+    }
+    return QG_OK;
+}
+
 using TuneKey = std::tuple<int, int, int, int, int>;
 std::mutex g_tune_mutex;
-std::map<TuneKey, int> g_tune_cache;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;   // (engine, fine rows)
 bool g_tune_file_read = false;
 
 void tune_file_load() {
@@ -567,20 +603,21 @@ void tune_file_load() {
     if (!path) return;
     FILE* f = std::fopen(path, "r");
     if (!f) return;
-    int a, b, c, d, x, e;
-    while (std::fscanf(f, "%d %d %d %d %d %d", &a, &b, &c, &d, &x, &e) == 6)
-        if (e == 4 || e == 16 || is_warp_engine(e) || e == kMatrixEngine)
-            g_tune_cache[TuneKey(a, b, c, d, x)] = e;
+    int a, b, c, d, x, e, r;
+    while (std::fscanf(f, "%d %d %d %d %d %d %d", &a, &b, &c, &d, &x, &e, &r) == 7)
+        if ((e == 4 || e == 16 || is_warp_engine(e) || e == kMatrixEngine) &&
+            fine_rows_supported((size_t)x, d, r))
+            g_tune_cache[TuneKey(a, b, c, d, x)] = {e, r};
     std::fclose(f);
 }
 
-void tune_file_store(const TuneKey& k, int e) {
+void tune_file_store(const TuneKey& k, int e, int rows) {
     const char* path = std::getenv("QG_TUNE_CACHE");
     if (!path) return;
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
-                 std::get<3>(k), std::get<4>(k), e);
+    std::fprintf(f, "%d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+                 std::get<3>(k), std::get<4>(k), e, rows);
     std::fclose(f);
 }
 
@@ -623,6 +660,24 @@ qg_status autotune_solve(qg_ctx* h) {
     const LevelTables* t = nullptr;
     qg_status st = get_level(h, h->levels, &t);
     if (st != QG_OK) return st;
+    // the tile heights the fused fine stage may take on this handle
+    // (ensemble members keep the default: their batched sweep uses it)
+    std::vector<int> rows_cand{h->fine_rows};
+    if (!h->member)
+        for (int r : {64, 32})
+            if (fine_rows_supported(h->esz, h->layers, r)) rows_cand.push_back(r);
+    int forced_rows = 0;
+    if (const char* fr = std::getenv("QG_FINE_ROWS")) {
+        const int r = std::atoi(fr);
+        if (std::find(rows_cand.begin(), rows_cand.end(), r) != rows_cand.end()) forced_rows = r;
+    }
+    auto set_rows = [&](int r) -> qg_status {
+        if (r == h->fine_rows) return QG_OK;
+        h->fine_rows = r;
+        drop_graph(h);
+        return fine_maps(h);
+    };
+    if (forced_rows) QG_TRY_S(set_rows(forced_rows));
     if (const char* force = std::getenv("QG_SOLVE_ENGINE")) {
         const int e = std::atoi(force);
         if (engine_ok(h, t, sizeof(T), e)) {
@@ -636,8 +691,10 @@ qg_status autotune_solve(qg_ctx* h) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         tune_file_load();
         auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) {
-            h->solve_engine = it->second;
+        if (it != g_tune_cache.end() &&
+            std::find(rows_cand.begin(), rows_cand.end(), it->second.second) != rows_cand.end()) {
+            h->solve_engine = it->second.first;
+            if (!forced_rows) QG_TRY_S(set_rows(it->second.second));
             return QG_OK;
         }
     }
@@ -658,6 +715,24 @@ qg_status autotune_solve(qg_ctx* h) {
         if (tt[k] < tt[best]) best = k;
     if (tt[best] >= 1e29f) return fail(h, QG_ERR_CUDA);
     h->solve_engine = ee[best];
+    // then the fine stage's tile height, with that engine
+    if (!forced_rows && rows_cand.size() > 1) {
+        const int r0 = h->fine_rows;
+        float tbest = tt[best];
+        int rbest = r0;
+        for (size_t k = 1; k < rows_cand.size(); ++k) {
+            if (set_rows(rows_cand[k]) != QG_OK) break;
+            const float tr = time_steps<T>(h, h->solve_engine);
+            if (tr < tbest) {
+                tbest = tr;
+                rbest = rows_cand[k];
+            }
+        }
+        h->latched = QG_OK;
+        (void)cudaGetLastError();
+        QG_TRY_S(set_rows(rbest));
+        drop_graph(h);
+    }
     // the timing steps ran on the handle's buffers: return them to rest
     cudaStreamSynchronize(h->stream);
     for (void* p : {h->w[0], h->w[1], h->w[2], h->psi}) {
@@ -673,8 +748,8 @@ qg_status autotune_solve(qg_ctx* h) {
     h->part_valid = false;
     QG_TRY(cudaStreamSynchronize(h->stream));
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = h->solve_engine;
-    tune_file_store(key, h->solve_engine);
+    g_tune_cache[key] = {h->solve_engine, h->fine_rows};
+    tune_file_store(key, h->solve_engine, h->fine_rows);
     return QG_OK;
 }
 
@@ -827,7 +902,7 @@ qg_status stage_fused2(qg_ctx* h, int s_idx, const LevelTables& t, cudaStream_t 
         m.psi = h->tm_psi;
         m.f = h->tm_f;
         KTimer kt(h, sl, QG_K_FINE);
-        QG_TRY(launch_fine_fused<T>(p, m, h->levels, sl, true));
+        QG_TRY(launch_fine_fused<T>(p, m, h->levels, sl, true, h->fine_rows));
     }
     if (s1 != s) {
         QG_TRY(cudaEventRecord(h->ev_join, s1));
@@ -910,7 +985,7 @@ qg_status stage_fused(qg_ctx* h, int s_idx, cudaStream_t s) {
     m.psi = h->tm_psi;
     m.f = h->tm_f;
     KTimer kt(h, s, QG_K_FINE);
-    QG_TRY(launch_fine_fused<T>(p, m, h->levels, s));
+    QG_TRY(launch_fine_fused<T>(p, m, h->levels, s, false, h->fine_rows));
     return QG_OK;
 }
 
@@ -1044,6 +1119,7 @@ static qg_status create_ctx(const qg_basin* b, int layers, double Re, double Ro,
     h->delta = b->delta; h->sigma = b->sigma; h->dt = b->dt; h->amp = b->forcing_amp;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     h->split_solve = split;
+    h->member = split;   // ensemble members are the handles created with split solves
     h->ldf = padded_ld(h->nx);
     h->plane_f = (size_t)(h->ny + 1) * h->ldf;
     const int mx = h->nx >> levels, my = h->ny >> levels;
@@ -1074,21 +1150,8 @@ static qg_status create_ctx(const qg_basin* b, int layers, double Re, double Ro,
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dbar, sizeof(unsigned) * 4));
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dclock, sizeof(double) * 4));
     if (s == QG_OK) {
-        const int rows = (int)fine_tile_rows(h->esz);
-        for (int k = 0; k < 3 && s == QG_OK; ++k) {
-            for (int L = 0; L < layers && s == QG_OK; ++L) {
-                const void* base = static_cast<const char*>(h->w[k]) + L * h->plane_f * h->esz;
-                if (make_tensor_map(&h->tm_halo[k][L], base, h->nx, h->ny, h->ldf, h->esz,
-                                    fine_halo_cols(), rows + 2) != cudaSuccess ||
-                    make_tensor_map(&h->tm_int[k][L], base, h->nx, h->ny, h->ldf, h->esz,
-                                    fine_block_cols(), rows) != cudaSuccess)
-                    guard(QG_ERR_CUDA);
-            }
-        }
-        if (s == QG_OK && make_tensor_map(&h->tm_psi, h->psi, h->nx, h->ny, h->ldf, h->esz,
-                                          fine_halo_cols(), rows + 2) != cudaSuccess)
-            guard(QG_ERR_CUDA);
-        h->tm_f = h->tm_int[0][0];
+        h->fine_rows = (int)fine_tile_rows(h->esz);
+        guard(fine_maps(h));
     }
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dpart, sizeof(double) * 5 * diag_blocks()));
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dout, sizeof(double) * 8));
@@ -1219,7 +1282,7 @@ qg_status qg_set_forcing(qg_handle h, const void* forcing) {
     }
     h->f2d = h->f2d_buf;
     if (make_tensor_map(&h->tm_f, h->f2d, h->nx, h->ny, h->ldf, h->esz, fine_block_cols(),
-                        (int)fine_tile_rows(h->esz)) != cudaSuccess)
+                        h->fine_rows) != cudaSuccess)
         return fail(h, QG_ERR_CUDA);
     QG_TRY(copy_in(h->f2d, h->ldf, forcing, h->nx - 1, h->ny - 1, h->esz, h->stream));
     return QG_OK;
@@ -1505,6 +1568,12 @@ qg_status qg_solve_engine(qg_handle h, int32_t* engine) {
     return QG_OK;
 }
 
+qg_status qg_stencil_tile(qg_handle h, int32_t* rows) {
+    if (!h || !rows) return QG_ERR_ARG;
+    *rows = h->fine_rows;
+    return QG_OK;
+}
+
 qg_status qg_step_kernel_count(qg_handle h, int64_t* count) {
     if (!h || !count) return QG_ERR_ARG;
     qg_status s = build_graph(h);
@@ -1542,6 +1611,26 @@ qg_status qg_diagnostics(qg_handle h, double* ke, double* enstrophy, double* max
     if (ke) *ke = E;
     if (enstrophy) *enstrophy = Z;
     if (max_vel) *max_vel = U;
+    return QG_OK;
+}
+
+qg_status qg_energy_accumulate(qg_handle h, double scale, double* acc) {
+    NvtxRange nvtx_range("qg_energy_accumulate");
+    if (!h || !acc || !std::isfinite(scale)) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    qg_status s = project_any(h, h->w[0], h->stream);
+    if (s != QG_OK) return s;
+    if (h->dtype == QG_F64)
+        QG_TRY(launch_diagnostics<double>((const double*)h->psi, (const double*)h->w[0], h->nx,
+                                          h->ny, h->ldf, h->dx, h->dy, h->dpart, diag_blocks(),
+                                          h->dout, h->stream));
+    else
+        QG_TRY(launch_diagnostics<float>((const float*)h->psi, (const float*)h->w[0], h->nx,
+                                         h->ny, h->ldf, h->dx, h->dy, h->dpart, diag_blocks(),
+                                         h->dout, h->stream));
+    // E = 1/2 dx dy (sx/dx^2 + sy/dy^2), as qg_diagnostics forms it
+    const double c0 = scale * 0.5 * h->dy / h->dx, c1 = scale * 0.5 * h->dx / h->dy;
+    QG_TRY(launch_energy_add(h->dout, c0, c1, acc, h->stream));
     return QG_OK;
 }
 
@@ -2031,7 +2120,7 @@ qg_status ensemble_tables(qg_ensemble e) {
                     for (int q = 0; q < 4; ++q) M.in[q] = plane<T>(h->part, h->plane_c, q);
                     M.nin = 4;
                     M.part_px = fine_part_period_x(h->levels);
-                    M.part_py = fine_part_period_y(h->levels, sizeof(T));
+                    M.part_py = fine_part_period_y(h->levels, h->fine_rows);
                     M.out = static_cast<T*>(h->cpsi);
                 }
                 M.tr = static_cast<T*>(h->ct);

@@ -89,9 +89,22 @@ diag_final_kernel(const double* __restrict__ partial, int nblocks,
     if (threadIdx.x < 5) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// acc += c0 out[0] + c1 out[1]: the kinetic energy of Section 5.2 from the
+// two edge sums of diag_final_kernel, scaled, added in FP64 by one thread.
+__global__ void energy_add_kernel(const double* __restrict__ out, double c0, double c1,
+                                  double* __restrict__ acc) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) acc[0] += c0 * out[0] + c1 * out[1];
+}
+
 }  // namespace
 
 int diag_blocks() { return kDiagBlocks; }
+
+cudaError_t launch_energy_add(const double* out, double c0, double c1, double* acc,
+                              cudaStream_t s) {
+    energy_add_kernel<<<1, 32, 0, s>>>(out, c0, c1, acc);
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_diagnostics(const T* psi, const T* w, int nx, int ny, int ld,

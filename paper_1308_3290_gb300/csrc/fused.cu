@@ -48,7 +48,9 @@ constexpr int SWX = TX + 8; // halo tile row: fine x in [x0 - 4, x0 + 68)
 // cover whole coarse cells for the partial-sum planes)
 template <int LV> struct Sweep { static constexpr int RY = (1 << LV) > 8 ? (1 << LV) : 8; };
 
-// fine rows per CTA
+// fine rows per CTA: FP32 one-layer sweeps are built for 128, 64 and 32
+// (the autotuner picks one per handle); FP64 and two-layer sweeps use 64
+// and 128 rows
 template <typename T> struct Rows { static constexpr int value = 128; };
 template <> struct Rows<double> { static constexpr int value = 64; };
 
@@ -112,12 +114,16 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Shared-memory plan of one CTA (byte offsets, 128-byte aligned).
-template <typename T, int LV, bool TL = false>
+template <typename T, int LV, bool TL = false, int RC_ = Rows<T>::value>
 struct Plan {
-    static constexpr int RC = Rows<T>::value;
+    static constexpr int RC = RC_;
     static constexpr int RY = Sweep<LV>::RY;
     static constexpr int G = RC / RY;               // groups per CTA
     static constexpr int THREADS = 16 * G;
+    // CTAs per SM the registers are budgeted for: FP32 one-layer sweeps as
+    // many as make 768 threads, FP64 and two-layer ones 512 or 256 threads
+    static constexpr int MINB_RAW = ((sizeof(T) == 4 && !TL) ? 768 : 512) / THREADS;
+    static constexpr int MINB = MINB_RAW < 1 ? 1 : (MINB_RAW > 16 ? 16 : MINB_RAW);
     static constexpr int F = 1 << LV;
     static constexpr int CPX = TX / F + 4;
     static constexpr int CPY = RC / F + 3;
@@ -135,11 +141,11 @@ struct Plan {
 // The work of one CTA: the tile (bx, by) of one basin, whose tensor maps and
 // parameters the two kernels below take from the launch (one basin) or from
 // a table in device memory (a batch of ensemble members).
-template <typename T, int LV, bool TL>
+template <typename T, int LV, bool TL, int RCT>
 __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtensorMap* tm_wn,
                                            const CUtensorMap* tm_p, const CUtensorMap* tm_f,
                                            const FusedParams<T>& p, int bx, int by) {
-    using PL = Plan<T, LV, TL>;
+    using PL = Plan<T, LV, TL, RCT>;
     constexpr int F = 1 << LV;
     constexpr int RC = PL::RC;
     constexpr int RY = PL::RY;
@@ -515,13 +521,13 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
     }
 }
 
-template <typename T, int LV, bool TL>
-__global__ void __launch_bounds__(Plan<T, LV, TL>::THREADS, (sizeof(T) == 4 && !TL) ? 3 : 2)
+template <typename T, int LV, bool TL, int RCT>
+__global__ void __launch_bounds__(Plan<T, LV, TL, RCT>::THREADS, Plan<T, LV, TL, RCT>::MINB)
 fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                   const __grid_constant__ CUtensorMap tm_wn,
                   const __grid_constant__ CUtensorMap tm_p,
                   const __grid_constant__ CUtensorMap tm_f, FusedParams<T> p) {
-    sweep_tile<T, LV, TL>(&tm_w, &tm_wn, &tm_p, &tm_f, p, blockIdx.x, blockIdx.y);
+    sweep_tile<T, LV, TL, RCT>(&tm_w, &tm_wn, &tm_p, &tm_f, p, blockIdx.x, blockIdx.y);
 }
 
 // Batched fine stage of an ensemble: CTA c sweeps tile (tiles[c].y,
@@ -541,7 +547,7 @@ fine_batch_kernel(const FineMember<T>* __restrict__ fm, const int4* __restrict__
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&E->psi) : "memory");
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&E->f) : "memory");
     }
-    sweep_tile<T, LV, false>(&E->w, &E->wn, &E->psi, &E->f, E->p, t.y, t.z);
+    sweep_tile<T, LV, false, Rows<T>::value>(&E->w, &E->wn, &E->psi, &E->f, E->p, t.y, t.z);
 }
 
 template <typename T, int LV>
@@ -569,12 +575,12 @@ cudaError_t launch_batch(const FineMember<T>* fm, const int4* tiles, int ntiles,
     return cudaLaunchKernelEx(&cfg, fine_batch_kernel<T, LV>, fm, tiles);
 }
 
-template <typename T, int LV, bool TL>
+template <typename T, int LV, bool TL, int RCT>
 cudaError_t launch_sweep(const FusedParams<T>& p, const FineMaps& m, cudaStream_t s) {
-    using PL = Plan<T, LV, TL>;
+    using PL = Plan<T, LV, TL, RCT>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(fine_sweep_kernel<T, LV, TL>,
+        cudaError_t e = cudaFuncSetAttribute(fine_sweep_kernel<T, LV, TL, RCT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)PL::END);
         if (e != cudaSuccess) return e;
@@ -592,32 +598,49 @@ cudaError_t launch_sweep(const FusedParams<T>& p, const FineMaps& m, cudaStream_
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, fine_sweep_kernel<T, LV, TL>, m.w, m.wn, m.psi, m.f, p);
+    return cudaLaunchKernelEx(&cfg, fine_sweep_kernel<T, LV, TL, RCT>, m.w, m.wn, m.psi, m.f, p);
 }
 
 }  // namespace
 
-template <typename T>
-cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int levels,
-                              cudaStream_t s, bool two_layer) {
-    if (two_layer) {   // l >= 1 only: the other layer's psi comes from the elliptic grid
-        switch (levels) {
-            case 1: return launch_sweep<T, 1, true>(p, m, s);
-            case 2: return launch_sweep<T, 2, true>(p, m, s);
-            case 3: return launch_sweep<T, 3, true>(p, m, s);
-            case 4: return launch_sweep<T, 4, true>(p, m, s);
-            default: return cudaErrorInvalidValue;
-        }
-    }
+template <typename T, int RCT>
+cudaError_t launch_rows(const FusedParams<T>& p, const FineMaps& m, int levels, cudaStream_t s) {
     switch (levels) {
-        case 0: return launch_sweep<T, 0, false>(p, m, s);
-        case 1: return launch_sweep<T, 1, false>(p, m, s);
-        case 2: return launch_sweep<T, 2, false>(p, m, s);
-        case 3: return launch_sweep<T, 3, false>(p, m, s);
-        case 4: return launch_sweep<T, 4, false>(p, m, s);
+        case 0: return launch_sweep<T, 0, false, RCT>(p, m, s);
+        case 1: return launch_sweep<T, 1, false, RCT>(p, m, s);
+        case 2: return launch_sweep<T, 2, false, RCT>(p, m, s);
+        case 3: return launch_sweep<T, 3, false, RCT>(p, m, s);
+        case 4: return launch_sweep<T, 4, false, RCT>(p, m, s);
         default: return cudaErrorInvalidValue;
     }
 }
+
+template <typename T>
+cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int levels,
+                              cudaStream_t s, bool two_layer, int rows) {
+    constexpr int R0 = Rows<T>::value;
+    if (two_layer) {   // l >= 1 only: the other layer's psi comes from the elliptic grid
+        if (rows != R0) return cudaErrorInvalidValue;
+        switch (levels) {
+            case 1: return launch_sweep<T, 1, true, R0>(p, m, s);
+            case 2: return launch_sweep<T, 2, true, R0>(p, m, s);
+            case 3: return launch_sweep<T, 3, true, R0>(p, m, s);
+            case 4: return launch_sweep<T, 4, true, R0>(p, m, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (rows == R0) return launch_rows<T, R0>(p, m, levels, s);
+    if constexpr (sizeof(T) == 4) {
+        if (rows == 64) return launch_rows<T, 64>(p, m, levels, s);
+        if (rows == 32) return launch_rows<T, 32>(p, m, levels, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_fine_fused<float>(const FusedParams<float>&, const FineMaps&, int,
+                                              cudaStream_t, bool, int);
+template cudaError_t launch_fine_fused<double>(const FusedParams<double>&, const FineMaps&, int,
+                                               cudaStream_t, bool, int);
 
 template <typename T>
 cudaError_t launch_fine_batch(const FineMember<T>* fm, const int4* tiles, int ntiles, int levels,
@@ -639,14 +662,13 @@ template cudaError_t launch_fine_batch<double>(const FineMember<double>*, const 
                                                bool, bool, cudaStream_t);
 
 size_t fine_tile_rows(size_t esz) { return esz == 8 ? Rows<double>::value : Rows<float>::value; }
+bool fine_rows_supported(size_t esz, int layers, int rows) {
+    if (rows == (int)fine_tile_rows(esz)) return true;
+    return esz == 4 && layers == 1 && (rows == 64 || rows == 32);
+}
 int fine_part_period_x(int levels) { return TX >> levels; }
-int fine_part_period_y(int levels, size_t esz) { return (int)fine_tile_rows(esz) >> levels; }
+int fine_part_period_y(int levels, int rows) { return rows >> levels; }
 int fine_halo_cols() { return SWX; }
 int fine_block_cols() { return TX; }
-
-template cudaError_t launch_fine_fused<float>(const FusedParams<float>&, const FineMaps&, int,
-                                              cudaStream_t, bool);
-template cudaError_t launch_fine_fused<double>(const FusedParams<double>&, const FineMaps&, int,
-                                               cudaStream_t, bool);
 
 }  // namespace qg

@@ -224,9 +224,11 @@ cudaError_t launch_cfl_max(const T* psi, int ldp, int nx, int ny, int levels, do
 struct FineMaps {
     CUtensorMap w, wn, psi, f;
 };
+// rows: the fine rows per CTA (fine_tile_rows, or a tuned height that
+// fine_rows_supported accepts; the tensor maps' boxes must match it)
 template <typename T>
 cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int levels,
-                              cudaStream_t s, bool two_layer = false);
+                              cudaStream_t s, bool two_layer, int rows);
 // One member of a batched fine-stage launch (ensembles): the tensor maps of
 // its stage and its parameters, in device memory (the TMA unit reads the
 // maps from there; 64-byte aligned).
@@ -241,9 +243,10 @@ struct alignas(64) FineMember {
 template <typename T>
 cudaError_t launch_fine_batch(const FineMember<T>* fm, const int4* tiles, int ntiles, int levels,
                               bool forcing_field, bool pdl, cudaStream_t s);
-size_t fine_tile_rows(size_t esz);   // fine rows per CTA
+size_t fine_tile_rows(size_t esz);   // default fine rows per CTA (batched sweeps too)
+bool fine_rows_supported(size_t esz, int layers, int rows);   // other tuned heights
 int fine_part_period_x(int levels);  // coarse columns between tile edges
-int fine_part_period_y(int levels, size_t esz);  // coarse rows between CTA edges
+int fine_part_period_y(int levels, int rows);  // coarse rows between CTA edges
 int fine_halo_cols();                // columns of a halo box
 int fine_block_cols();               // columns of an interior box
 
@@ -277,6 +280,9 @@ cudaError_t launch_diagnostics(const T* psi, const T* w, int nx, int ny, int ld,
                                double dx, double dy, double* partial,
                                int nblocks, double* out, cudaStream_t s);
 int diag_blocks();
+// acc[0] += c0 out[0] + c1 out[1] (out: the FP64 results of launch_diagnostics)
+cudaError_t launch_energy_add(const double* out, double c0, double c1, double* acc,
+                              cudaStream_t s);
 
 // ---- geometric multigrid (multigrid.cu) ----------------------------------
 constexpr int kMaxTail = 14;          // levels the one-CTA tail can hold

@@ -77,3 +77,13 @@ def perturbed_forcing_field(nx: int, ny: int, seed: int, Ro: float,
         k, l = rng.integers(1, 5, size=2)
         pert += rng.normal(0.0, amp) * np.sin(np.pi * k * xs)[None, :] * np.sin(np.pi * l * ys)[:, None]
     return base + pert / Ro
+
+
+def unit_directions(nx: int, ny: int, count: int, seed: int) -> np.ndarray:
+    """`count` seeded random fields of unit root-mean-square value, each an
+    interior array (ny - 1, nx - 1): directions for directional derivatives
+    with respect to a field."""
+    rng = np.random.default_rng(seed)
+    out = rng.normal(size=(count, ny - 1, nx - 1))
+    rms = np.sqrt(np.mean(out * out, axis=(1, 2)))
+    return out / rms[:, None, None]

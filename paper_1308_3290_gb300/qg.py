@@ -43,7 +43,7 @@ EXPORTS = [
     "qg_ensemble_kernel_count", "qg_ensemble_synchronize", "qg_ensemble_destroy",
     "qg_tape_begin", "qg_tape_end", "qg_adjoint_step", "qg_energy_gradient",
     "qg_set_cfl", "qg_set_solver", "qg_get_time", "qg_stats_begin", "qg_stats_mean_psi", "qg_stats_end",
-    "qg_set_timing_mask", "qg_solve_engine",
+    "qg_set_timing_mask", "qg_solve_engine", "qg_energy_accumulate", "qg_stencil_tile",
 ]
 
 KERNEL_CLASSES = ["restrict", "solve", "prolong", "fine", "cfl"]
@@ -117,6 +117,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "qg_stats_mean_psi": [vp, vp, i32, ctypes.POINTER(i64)],
         "qg_stats_end": [vp],
         "qg_set_timing_mask": [vp, ctypes.c_uint32],
+        "qg_energy_accumulate": [vp, dbl, vp],
+        "qg_stencil_tile": [vp, ctypes.POINTER(i32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -201,6 +203,12 @@ def qg_diagnostics(h: int) -> tuple[float, float, float]:
     return ke.value, z.value, u.value
 
 
+def qg_energy_accumulate(h: int, scale: float, acc) -> None:
+    """acc (a device float64 tensor of one element) += scale * kinetic
+    energy of the current state; asynchronous on the handle's stream."""
+    _check(load().qg_energy_accumulate(h, scale, _ptr(acc)), "qg_energy_accumulate")
+
+
 def qg_set_timing(h: int, enable: bool) -> None:
     _check(load().qg_set_timing(h, 1 if enable else 0), "qg_set_timing")
 
@@ -276,6 +284,13 @@ def qg_solve_engine(h: int) -> int:
     e = ctypes.c_int32()
     _check(load().qg_solve_engine(h, ctypes.byref(e)), "qg_solve_engine")
     return e.value
+
+
+def qg_stencil_tile(h: int) -> int:
+    """Fine rows per CTA of the fused fine-grid kernel (autotuned)."""
+    r = ctypes.c_int32()
+    _check(load().qg_stencil_tile(h, ctypes.byref(r)), "qg_stencil_tile")
+    return r.value
 
 
 def qg_get_time(h: int) -> tuple[float, float]:

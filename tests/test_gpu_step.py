@@ -60,6 +60,27 @@ def test_fp32_100_steps(levels):
     assert_fields_close(got, ref, 1e-4)
 
 
+@pytest.mark.parametrize("rows", [128, 64, 32])
+@pytest.mark.parametrize("levels", [0, 1, 2, 3])
+def test_each_stencil_tile_matches_oracle(rows, levels, monkeypatch):
+    """Every fine-stage tile height the autotuner may pick (forced through
+    QG_FINE_ROWS) follows the oracle: FP32, 100 steps, within 1e-4 element
+    by element, with the tile seams of that height checked on their own."""
+    require_gpu()
+    nx, ny = 128, 256
+    monkeypatch.setenv("QG_FINE_ROWS", str(rows))
+    w0 = inputs.perturbation(nx, ny, seed=16) * 50.0
+    ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=5e-5)
+    ref = O.run(w0, ob, 100)
+    b = qg.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=5e-5, dtype="f32")
+    assert qg.qg_stencil_tile(b.h) == rows
+    b.set_state(w0)
+    b.step(100)
+    got = to_np(b.state())
+    b.close()
+    assert_fields_close(got, ref, 1e-4, yper=rows)
+
+
 @pytest.fixture(scope="module")
 def oracle_512x1024_l0():
     """100 FP64 oracle steps of a 512 x 1024 basin at l = 0: its elliptic grid
