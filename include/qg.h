@@ -282,6 +282,16 @@ qg_status qg_solve_engine(qg_handle h, int32_t* engine);
  * rounding.  No device work.  Errors: QG_ERR_ARG.                         */
 qg_status qg_stencil_tile(qg_handle h, int32_t* rows);
 
+/* qg_bounds_check_result -- in a library built with QG_BOUNDS_CHECK (the
+ * checked build: every kernel index of the fine stage, the FFT and matrix
+ * solves and the transfers is compared with its buffer's extent before the
+ * access, and a failed check skips the access instead of trapping):
+ * synchronises the device and returns in *site the number of the first
+ * check that failed since the last call (0 if none), then clears it.  The
+ * paper has no counterpart; this stands in for a memory checker.  Normal
+ * builds return QG_ERR_UNSUPPORTED with *site = 0.  Errors: QG_ERR_ARG.   */
+qg_status qg_bounds_check_result(int32_t* site);
+
 /* qg_get_time -- model time since creation or the last qg_set_state, and
  * the size of the last step (host pointers; either may be NULL).
  * Synchronises the handle's stream.                                        */

@@ -18,6 +18,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqgcgp.so")
+# the bounds-checked variant (-DQG_BOUNDS_CHECK): every kernel index is
+# compared with its buffer's extent; used by the checked-build tests only
+LIB_BOUNDS = os.path.join(HERE, "libqgcgp_bounds.so")
+VARIANTS = {"": (LIB, BUILD_DIR, []),
+            "bounds": (LIB_BOUNDS, os.path.join(BUILD_DIR, "bounds"), ["-DQG_BOUNDS_CHECK"])}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
          "-Xptxas", "-warn-spills", "-I", os.path.join(ROOT, "include")]
@@ -39,23 +44,26 @@ def _deps() -> list[str]:
             + [os.path.join(ROOT, "include", "qg.h"), os.path.abspath(__file__)])
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile and link the library; return its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          variant: str = "") -> str:
+    """Compile and link the library (variant "bounds": the bounds-checked
+    one); return its path."""
+    lib, build_dir, vflags = VARIANTS[variant]
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
-    flags = FLAGS + list(extra_flags or [])
+    flags = FLAGS + vflags + list(extra_flags or [])
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *ARCH, *flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -66,13 +74,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(sources())) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [cc, *ARCH, "-shared", "--cudart=static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

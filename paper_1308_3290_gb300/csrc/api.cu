@@ -1568,6 +1568,27 @@ qg_status qg_solve_engine(qg_handle h, int32_t* engine) {
     return QG_OK;
 }
 
+qg_status qg_bounds_check_result(int32_t* site) {
+    if (!site) return QG_ERR_ARG;
+#ifdef QG_BOUNDS_CHECK
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        (void)cudaGetLastError();
+        return QG_ERR_CUDA;
+    }
+    int first = 0;
+    for (int v : {bounds_site_fused(), bounds_site_solve32(), bounds_site_stencil(),
+                  bounds_site_mtx()}) {
+        if (v < 0) return QG_ERR_CUDA;
+        if (!first) first = v;
+    }
+    *site = first;
+    return QG_OK;
+#else
+    *site = 0;
+    return QG_ERR_UNSUPPORTED;
+#endif
+}
+
 qg_status qg_stencil_tile(qg_handle h, int32_t* rows) {
     if (!h || !rows) return QG_ERR_ARG;
     *rows = h->fine_rows;

@@ -37,6 +37,7 @@
 // and the row sine transform adds P0 + P1 + P2 + P3 in that order.
 #include <cuda_runtime.h>
 
+#include "bounds.cuh"
 #include "qg_internal.cuh"
 
 namespace qg {
@@ -184,9 +185,14 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
         if (LV == 0) bytes += sizeof(T) * (RC + 2) * SWX;
         if (use_f) bytes += sizeof(T) * RC * TX;
         mbar_expect_tx(bar, bytes);
-        tma_load_2d(smem_u32(sw), tm_w, x0 - 4, yc - 1, bar);
-        if (use_wn) tma_load_2d(smem_u32(swn), tm_wn, x0, yc, bar);
-        if (use_f) tma_load_2d(smem_u32(sf), tm_f, x0, yc, bar);
+        // box x coordinates are multiples of 16 bytes (x0 is a multiple of
+        // 64 nodes, the halo box starts 4 nodes left of it)
+        if (QG_IN(((x0 - 4) * (int)sizeof(T)) & 15, 1, 1))
+            tma_load_2d(smem_u32(sw), tm_w, x0 - 4, yc - 1, bar);
+        if (use_wn && QG_IN((x0 * (int)sizeof(T)) & 15, 1, 2))
+            tma_load_2d(smem_u32(swn), tm_wn, x0, yc, bar);
+        if (use_f && QG_IN((x0 * (int)sizeof(T)) & 15, 1, 3))
+            tma_load_2d(smem_u32(sf), tm_f, x0, yc, bar);
     }
     pdl_wait();
     if (LV == 0 && threadIdx.x == 0) tma_load_2d(smem_u32(sp), tm_p, x0 - 4, yc - 1, bar);
@@ -212,7 +218,8 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
         for (int e = threadIdx.x; e < PL::CPX * PL::CPY; e += blockDim.x) {
             const int ii = e % PL::CPX, jj = e / PL::CPX;
             const int I = I_lo + ii, J = J_lo + jj;
-            const bool in = I >= 0 && I <= mx && J >= 0 && J <= my;
+            const bool in = I >= 0 && I <= mx && J >= 0 && J <= my &&
+                            QG_IN((long long)J * p.ldp + I, (long long)(my + 1) * p.ldp, 4);
             cp[e] = in ? __ldg(p.psi + (size_t)J * p.ldp + I) : T(0);
             if constexpr (TL) cp2[e] = in ? __ldg(p.psi_o + (size_t)J * p.ldp + I) : T(0);
         }
@@ -237,8 +244,10 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
     // row y of a halo tile (w^(s) or the fine psi): own quad + shuffled halos
     auto row_halo = [&](const T* tile, int y, T v[6]) {
         const T* r = tile + (y - yc + 1) * SWX;
-        T c[4];
-        lds4(r + 4 * lane + 4, c);
+        T c[4] = {T(0), T(0), T(0), T(0)};
+        if (QG_IN((y - yc + 1) * SWX + 4 * lane + 7, (RC + 2) * SWX, 5) &&
+            QG_IN((y - yc + 1) * SWX, (RC + 2) * SWX, 5))
+            lds4(r + 4 * lane + 4, c);
         T left = __shfl_up_sync(gm, c[3], 1, 16);
         T right = __shfl_down_sync(gm, c[0], 1, 16);
         if (lane == 0) left = r[3];
@@ -249,8 +258,10 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
     T c0[4], c1[4], d0[4], d1[4];    // coarse rows around y of psi (and of the other layer)
     auto coarse_row = [&](const T* patch, int J, T (&c)[4]) {
         const T* r = patch + (J - J_lo) * PL::CPX + (Ib - I_lo);
+        const int o = (J - J_lo) * PL::CPX + (Ib - I_lo);
+        const bool ok = QG_IN(o, PL::CPX * PL::CPY, 6) && QG_IN(o + 3, PL::CPX * PL::CPY, 6);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) c[k] = r[k];
+        for (int k = 0; k < 4; ++k) c[k] = ok ? r[k] : T(0);
     };
     // ph = y mod 2^l, known at compile time in the unrolled sweep (ys is a
     // multiple of RY, itself a multiple of 2^l).  Sums of products are
@@ -348,10 +359,12 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
             const bool row_ok = y >= 1 && y <= ny - 1;
             const size_t ro = (size_t)y * ld;
             T wn[4] = {T(0), T(0), T(0), T(0)};
-            if (use_wn) lds4(swn + (y - yc) * TX + 4 * lane, wn);
-            T fv[4];
+            const bool row_in = QG_IN((y - yc) * TX + 4 * lane + 3, RC * TX, 7) &&
+                                QG_IN((y - yc) * TX, RC * TX, 7);
+            if (use_wn && row_in) lds4(swn + (y - yc) * TX + 4 * lane, wn);
+            T fv[4] = {T(0), T(0), T(0), T(0)};
             if (use_f) {
-                lds4(sf + (y - yc) * TX + 4 * lane, fv);
+                if (row_in) lds4(sf + (y - yc) * TX + 4 * lane, fv);
             } else {
                 // (the bottom layer of two has no wind: frow is null there)
                 const T fr = (!TL || p.frow) ? __ldg(p.frow + (y <= ny ? y : ny)) : T(0);
@@ -416,14 +429,18 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
             }
 
             const bool quad_ok = row_ok && xq >= 1 && xq + 3 <= nx - 1;
+            const long long fine_n = (long long)(ny + 1) * ld;
             if (quad_ok) {
-                stg4(p.wout + ro + xq, out);
+                if (QG_IN(ro + xq + 3, fine_n, 8)) stg4(p.wout + ro + xq, out);
             } else {
     #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int x = xq + q;
-                    if (row_ok && x >= 1 && x <= nx - 1) p.wout[ro + x] = out[q];
-                    else out[q] = T(0);
+                    if (row_ok && x >= 1 && x <= nx - 1) {
+                        if (QG_IN(ro + x, fine_n, 8)) p.wout[ro + x] = out[q];
+                    } else {
+                        out[q] = T(0);
+                    }
                 }
             }
             if (LV > 0) {
@@ -475,12 +492,15 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
     // two shares added here (lower group's share first); only the last
     // group's top row, on the CTA's seam, goes to a seam plane.
     if (LV > 0) {
+        constexpr int SW = TX / (1 << LV) + 1;   // seam entries per group
         if (active) {
             if (LV == 1) {
-                seam[grp][2 * lane] = accA[NM - 1];
-                seam[grp][2 * lane + 1] = accB[NM - 1];
+                if (QG_IN(2 * lane + 1, SW, 9)) {
+                    seam[grp][2 * lane] = accA[NM - 1];
+                    seam[grp][2 * lane + 1] = accB[NM - 1];
+                }
             } else if (lane % G == 0) {
-                seam[grp][lane / G] = accA[NM - 1];
+                if (QG_IN(lane / G, SW, 9)) seam[grp][lane / G] = accA[NM - 1];
             }
             if (lane == 15) seam[grp][TX / F] = accE[NM - 1];
         }
@@ -504,17 +524,21 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
                 if (J < 1 || J > my - 1) continue;
                 const int qy = (m == NM - 1) ? 2 : 0;
                 T* rowA = p.part[qy] + (size_t)J * p.ldc;
+                const long long pn = (long long)(my + 1) * p.ldc;
+                const long long jo = (long long)J * p.ldc;
                 if (LV == 1) {
                     const int I = Ix0 + 2 * lane;
-                    if (I >= 1 && I <= mx - 1) rowA[I] = accA[m];
-                    if (I + 1 >= 1 && I + 1 <= mx - 1) rowA[I + 1] = accB[m];
+                    if (I >= 1 && I <= mx - 1 && QG_IN(jo + I, pn, 10)) rowA[I] = accA[m];
+                    if (I + 1 >= 1 && I + 1 <= mx - 1 && QG_IN(jo + I + 1, pn, 10))
+                        rowA[I + 1] = accB[m];
                 } else if (lane % G == 0) {
                     const int I = Ix0 + lane / G;
-                    if (I >= 1 && I <= mx - 1) rowA[I] = accA[m];
+                    if (I >= 1 && I <= mx - 1 && QG_IN(jo + I, pn, 10)) rowA[I] = accA[m];
                 }
                 if (lane == 15) {
                     const int I = Ix0 + TX / F;
-                    if (I >= 1 && I <= mx - 1) p.part[qy + 1][(size_t)J * p.ldc + I] = accE[m];
+                    if (I >= 1 && I <= mx - 1 && QG_IN(jo + I, pn, 10))
+                        p.part[qy + 1][(size_t)J * p.ldc + I] = accE[m];
                 }
             }
         }
@@ -670,5 +694,7 @@ int fine_part_period_x(int levels) { return TX >> levels; }
 int fine_part_period_y(int levels, int rows) { return rows >> levels; }
 int fine_halo_cols() { return SWX; }
 int fine_block_cols() { return TX; }
+
+QG_BOUNDS_QUERY(bounds_site_fused)
 
 }  // namespace qg

@@ -325,6 +325,14 @@ cudaError_t launch_mg_cycle(const MGLevelDesc<T>* lv, int nl, int tail, cudaStre
 // paths -- adjoint sweeps, stand-alone solves -- launch thousands of times).
 cudaError_t launch_shape(const void* kernel, int threads, size_t smem, int* per_sm, int* nsm);
 
+// Bounds-checked builds (bounds.cuh): the site of the first failed index
+// check in each translation unit since the last query (0: none; always 0
+// in normal builds), cleared by the query.
+int bounds_site_fused();
+int bounds_site_solve32();
+int bounds_site_stencil();
+int bounds_site_mtx();
+
 // Copies between the dense exchange layout and the padded node layout.
 cudaError_t copy_in(void* padded, int ld, const void* dense, int nxm1,
                     int nym1, size_t esz, cudaStream_t s);

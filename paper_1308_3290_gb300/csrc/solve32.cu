@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdlib>
 
+#include "bounds.cuh"
 #include "dst_engine.cuh"
 #include "qg_internal.cuh"
 
@@ -122,13 +123,19 @@ struct Sync {
     }
 };
 
+// element m of a pair buffer of `lim` complex entries (lim is only read by
+// bounds-checked builds)
 template <typename T>
-__device__ __forceinline__ Cplx<T> ldp(const CT<T>* b, int m) {
+__device__ __forceinline__ Cplx<T> ldp(const CT<T>* b, int m, int lim) {
+    (void)lim;
+    if (!QG_IN(px(m), lim, 21)) return Cplx<T>{T(0), T(0)};
     const CT<T> v = b[px(m)];
     return Cplx<T>{v.x, v.y};
 }
 template <typename T>
-__device__ __forceinline__ void stp(CT<T>* b, int m, Cplx<T> v) {
+__device__ __forceinline__ void stp(CT<T>* b, int m, Cplx<T> v, int lim) {
+    (void)lim;
+    if (!QG_IN(px(m), lim, 22)) return;
     CT<T> w;
     w.x = v.x;
     w.y = v.y;
@@ -223,12 +230,12 @@ __device__ __forceinline__ void passW(const CT<T>* in, CT<T>* out, int t, const 
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
         if (!first) {
-            v[r] = ldp<T>(in, t + r * g.G);
+            v[r] = ldp<T>(in, t + r * g.G, g.buf);
         } else if (r < H) {
-            v[r] = ldp<T>(in, t + r * g.G);
+            v[r] = ldp<T>(in, t + r * g.G, g.buf);
         } else {
             const int m = r == H ? g.N - t : (RAD - r) * g.G - t;
-            const Cplx<T> z = (r == H && t == 0) ? Cplx<T>{T(0), T(0)} : ldp<T>(in, m);
+            const Cplx<T> z = (r == H && t == 0) ? Cplx<T>{T(0), T(0)} : ldp<T>(in, m, g.buf);
             v[r] = Cplx<T>{-z.x, -z.y};
         }
     }
@@ -263,8 +270,8 @@ __device__ __forceinline__ void passW(const CT<T>* in, CT<T>* out, int t, const 
     const int d = (t - k) * RAD + k;
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
-        if constexpr (RAD == 32) stp<T>(out, d + r * NS, v[r]);
-        else stp<T>(out, d + r * NS, v[out_slot<RAD>(r)]);
+        if constexpr (RAD == 32) stp<T>(out, d + r * NS, v[r], g.buf);
+        else stp<T>(out, d + r * NS, v[out_slot<RAD>(r)], g.buf);
     }
     sy.sync();
 }
@@ -282,7 +289,7 @@ __device__ __noinline__ void passR(const CT<T>* in, CT<T>* out, int t, Geo32 g, 
         const int j = t + b * g.G;
         const int k = j & (NS - 1);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[b][r] = ldp<T>(in, j + r * stride);
+        for (int r = 0; r < R; ++r) v[b][r] = ldp<T>(in, j + r * stride, g.buf);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
             const CT<T> w = tw[r * NS + k];
@@ -296,7 +303,7 @@ __device__ __noinline__ void passR(const CT<T>* in, CT<T>* out, int t, Geo32 g, 
         const int k = j & (NS - 1);
         const int d = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) stp<T>(out, d + r * NS, v[b][out_slot<R>(r)]);
+        for (int r = 0; r < R; ++r) stp<T>(out, d + r * NS, v[b][out_slot<R>(r)], g.buf);
     }
     sy.sync();
 }
@@ -364,6 +371,10 @@ template <typename T>
 __device__ __forceinline__ void rhs4(const SolveParams<T>& P, int layer, int r, int c0,
                                      T (&o)[4]) {
     const size_t off = (size_t)r * P.ld + c0;
+    if (!QG_IN(off + 3, (long long)(P.my + 1) * P.ld, 23)) {
+        o[0] = o[1] = o[2] = o[3] = T(0);
+        return;
+    }
     ld4<T>(P.in[layer][0] + off, o);
     if (P.nin > 1) {
         const bool ry = r % P.part_py == 0;
@@ -438,13 +449,17 @@ __device__ __forceinline__ void load_pair(const SolveParams<T>& P, int ph, const
             if (a.va) rhs4<T>(P, a.layer, a.ra, c0, x);
             if (a.vb) rhs4<T>(P, a.layer, a.rb, c0, y);
         } else {
-            if (a.va) ld4<T>(sa + c0, x);
-            if (a.vb) ld4<T>(sb + c0, y);
+            // rows of tr (mx + 1 rows of pitch ld_tr) or of work (my + 1 of ld)
+            const long long n = ph == 1 ? (long long)(P.mx + 1) * P.ld_tr
+                                        : (long long)(P.my + 1) * P.ld;
+            const long long pitch = ph == 1 ? P.ld_tr : P.ld;
+            if (a.va && QG_IN(a.ra * pitch + c0 + 3, n, 24)) ld4<T>(sa + c0, x);
+            if (a.vb && QG_IN(a.rb * pitch + c0 + 3, n, 24)) ld4<T>(sb + c0, y);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) stp<T>(cb, c0 + shift + q, Cplx<T>{x[q], y[q]});
+        for (int q = 0; q < 4; ++q) stp<T>(cb, c0 + shift + q, Cplx<T>{x[q], y[q]}, g.buf);
     }
-    if (t == 0) stp<T>(cb, 0, Cplx<T>{T(0), T(0)});
+    if (t == 0) stp<T>(cb, 0, Cplx<T>{T(0), T(0)}, g.buf);
 }
 
 // Between the two y transforms of phase 1: the mode-space solve, Eq. ialpha
@@ -453,14 +468,15 @@ template <typename T, int OPY, int RAD>
 __device__ __forceinline__ void mode_solve(const SolveParams<T>& P, const PairAt& a,
                                            const Geo32& g, CT<T>* cb, int t,
                                            const T* __restrict__ lamy) {
-    const T lxa = __ldg(P.lamx + a.ra), lxb = __ldg(P.lamx + a.rb);
+    const T lxa = QG_IN(a.ra, P.mx + 1, 25) ? __ldg(P.lamx + a.ra) : T(1);
+    const T lxb = QG_IN(a.rb, P.mx + 1, 25) ? __ldg(P.lamx + a.rb) : T(1);
 #pragma unroll 4
     for (int i = 0; i < RAD / 2; ++i) {
         const int l = t + i * g.G;
-        const Cplx<T> z = ldp<T>(cb, l);
+        const Cplx<T> z = ldp<T>(cb, l, g.buf);
         const T Fa = T(-0.5) * z.y, Fb = T(0.5) * z.x;
         T x = T(0), y = T(0);
-        if (l > 0 && a.va) {
+        if (l > 0 && a.va && QG_IN(l, P.my + 1, 26)) {
             const T ly = lamy[l];
             if (OPY == 1) {
                 x = Fa * (P.scale / (lxa + ly));
@@ -473,7 +489,7 @@ __device__ __forceinline__ void mode_solve(const SolveParams<T>& P, const PairAt
                 y = (al * q2 - P.f2 * q1 - P.f1 * q2) / den;
             }
         }
-        stp<T>(cb, l, Cplx<T>{x, y});
+        stp<T>(cb, l, Cplx<T>{x, y}, g.buf);
     }
 }
 
@@ -488,18 +504,26 @@ __device__ __forceinline__ void store_pair(const SolveParams<T>& P, int ph, cons
 #pragma unroll 4
     for (int i = 0; i < RAD / 2; ++i) {
         const int k = t + i * g.G;
+        if (!QG_IN(px(k), g.buf, 27)) continue;
         const CT<T> z = cb[px(k)];
         const T fa = T(-0.5) * z.y, fb = T(0.5) * z.x;
+        const long long nw = (long long)(P.my + 1) * P.ld;     // out, work
+        const long long nt = (long long)(P.mx + 1) * P.ld_tr;  // tr
         if (ph == 2) {
-            P.out[a.layer][(size_t)a.ra * P.ld + k] = k == 0 ? T(0) : fa;
-            if (a.vb) P.out[a.layer][(size_t)a.rb * P.ld + k] = k == 0 ? T(0) : fb;
+            if (QG_IN((long long)a.ra * P.ld + k, nw, 28))
+                P.out[a.layer][(size_t)a.ra * P.ld + k] = k == 0 ? T(0) : fa;
+            if (a.vb && QG_IN((long long)a.rb * P.ld + k, nw, 28))
+                P.out[a.layer][(size_t)a.rb * P.ld + k] = k == 0 ? T(0) : fb;
             continue;
         }
         if (k == 0) continue;
         if (ph == 0) {
+            if (!QG_IN((long long)k * P.ld_tr + a.ra, nt, 29)) continue;
             T* d = P.tr[a.layer] + (size_t)k * P.ld_tr + (a.ra - 1);
             if (a.vb) st2<T>(d, fa, fb);
             else d[0] = fa;
+        } else if (!QG_IN((long long)k * P.ld + a.rb - 1, nw, 30)) {
+            continue;
         } else if (OPY == 2) {
             P.work[0][(size_t)k * P.ld + a.ra - 1] = fa;
             P.work[1][(size_t)k * P.ld + a.rb - 1] = fb;
@@ -889,6 +913,8 @@ cudaError_t launch_solve32(const SolveParams<T>& P, int rad, cudaStream_t s) {
         return P.layers == 2 ? launch32<T, 2, 16>(P, s) : launch32<T, 1, 16>(P, s);
     return P.layers == 2 ? launch32<T, 2, 32>(P, s) : launch32<T, 1, 32>(P, s);
 }
+
+QG_BOUNDS_QUERY(bounds_site_solve32)
 
 template cudaError_t launch_solve32<float>(const SolveParams<float>&, int, cudaStream_t);
 template cudaError_t launch_solve32<double>(const SolveParams<double>&, int, cudaStream_t);

@@ -46,6 +46,7 @@
 #include <cstdint>
 
 #include "dst_engine.cuh"
+#include "bounds.cuh"
 #include "solve_mtx.h"
 
 namespace qg {
@@ -198,7 +199,8 @@ solve_mtx_kernel(SolveParams<float> Pk, const float* __restrict__ tab, MtxGeo g)
     for (int i = threadIdx.x; i < g.np * g.mp; i += kThreads) {
         const int r = i / g.mp, c = i - r * g.mp;
         float v = 0.f;
-        if (r < g.n && c < g.m) {
+        if (r < g.n && c < g.m &&
+            QG_IN((long long)(r + 1) * P.ld + c + 1, (long long)(P.my + 1) * P.ld, 51)) {
             const int y = r + 1, x = c + 1;
             const size_t off = (size_t)y * P.ld + x;
             v = __ldg(P.in[0][0] + off);
@@ -211,7 +213,7 @@ solve_mtx_kernel(SolveParams<float> Pk, const float* __restrict__ tab, MtxGeo g)
                 }
             }
         }
-        U[r * g.lda + c] = v;
+        if (QG_IN(g.u + r * g.lda + c, g.v, 52)) U[r * g.lda + c] = v;
     }
     const bool ok = mbar_wait(bar, 0, kSpin);
     if (!__syncthreads_and(ok)) {
@@ -248,8 +250,9 @@ solve_mtx_kernel(SolveParams<float> Pk, const float* __restrict__ tab, MtxGeo g)
     mm3(V, lda, Sx, g.ldx, g.mp, g, [&](int r, int c, float v0, float v1) {
         if (r >= n) return;
         float* o = out + (size_t)(r + 1) * ld + 1;
-        if (c < m) o[c] = v0;
-        if (c + 1 < m) o[c + 1] = v1;
+        const long long on = (long long)(P.my + 1) * (long long)ld;
+        if (c < m && QG_IN((long long)(r + 1) * ld + 1 + c, on, 53)) o[c] = v0;
+        if (c + 1 < m && QG_IN((long long)(r + 1) * ld + 2 + c, on, 53)) o[c + 1] = v1;
     });
     for (int r = threadIdx.x; r < n; r += kThreads) out[(size_t)(r + 1) * ld] = 0.f;
 }
@@ -317,5 +320,7 @@ cudaError_t launch_solve_mtx(const SolveParams<float>& P, const float* tab, cuda
     cfg.numAttrs = P.no_pdl ? 0 : 1;
     return cudaLaunchKernelEx(&cfg, k, P, tab, g);
 }
+
+QG_BOUNDS_QUERY(bounds_site_mtx)
 
 }  // namespace qg

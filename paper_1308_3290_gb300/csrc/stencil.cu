@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "arakawa.cuh"
+#include "bounds.cuh"
 #include "qg_internal.cuh"
 
 namespace qg {
@@ -102,17 +103,21 @@ __global__ void restrict_kernel(const T* __restrict__ fine, int ldf,
     if (I >= mx || J >= my) return;
     const int f = 1 << levels;
     const T* base = fine + (size_t)(f * J) * ldf + f * I;
+    // the fine grid has (f my + 1) rows of pitch ldf
+    const long long fn = (long long)(f * my + 1) * ldf;
     T acc = T(0);
     for (int dj = -(f - 1); dj <= f - 1; ++dj) {
         const T* row = base + (ptrdiff_t)dj * ldf;
         T racc = T(0);
         for (int di = -(f - 1); di <= f - 1; ++di) {
-            racc += T(f - (di < 0 ? -di : di)) * row[di];
+            const long long o = (long long)(f * J + dj) * ldf + f * I + di;
+            if (QG_IN(o, fn, 41)) racc += T(f - (di < 0 ? -di : di)) * row[di];
         }
         acc += T(f - (dj < 0 ? -dj : dj)) * racc;
     }
     const T inv = T(1) / (T(f) * T(f) * T(f) * T(f));
-    coarse[(size_t)J * ldc + I] = acc * inv;
+    if (QG_IN((long long)J * ldc + I, (long long)(my + 1) * ldc, 42))
+        coarse[(size_t)J * ldc + I] = acc * inv;
 }
 
 // P^l as bilinear interpolation from the coarse nodes around each fine node.
@@ -128,9 +133,13 @@ __global__ void prolong_kernel(const T* __restrict__ coarse, int ldc,
     const T a = T(i & (f - 1)) / T(f);
     const T b = T(j & (f - 1)) / T(f);
     const T* C = coarse + (size_t)J * ldc + I;
+    // the coarse grid has (ny >> levels) + 1 rows of pitch ldc
+    if (!QG_IN((long long)(J + 1) * ldc + I + 1, (long long)((ny >> levels) + 1) * ldc, 43))
+        return;
     const T v = (T(1) - a) * (T(1) - b) * C[0] + a * (T(1) - b) * C[1] +
                 (T(1) - a) * b * C[ldc] + a * b * C[ldc + 1];
-    fine[(size_t)j * ldf + i] = v;
+    if (QG_IN((long long)j * ldf + i, (long long)(ny + 1) * ldf, 44))
+        fine[(size_t)j * ldf + i] = v;
 }
 
 }  // namespace
@@ -444,5 +453,7 @@ cudaError_t copy_out(void* dense, const void* padded, int ld, int nxm1, int nym1
 QG_INST(float)
 QG_INST(double)
 #undef QG_INST
+
+QG_BOUNDS_QUERY(bounds_site_stencil)
 
 }  // namespace qg

@@ -44,6 +44,7 @@ EXPORTS = [
     "qg_tape_begin", "qg_tape_end", "qg_adjoint_step", "qg_energy_gradient",
     "qg_set_cfl", "qg_set_solver", "qg_get_time", "qg_stats_begin", "qg_stats_mean_psi", "qg_stats_end",
     "qg_set_timing_mask", "qg_solve_engine", "qg_energy_accumulate", "qg_stencil_tile",
+    "qg_bounds_check_result",
 ]
 
 KERNEL_CLASSES = ["restrict", "solve", "prolong", "fine", "cfl"]
@@ -119,6 +120,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "qg_set_timing_mask": [vp, ctypes.c_uint32],
         "qg_energy_accumulate": [vp, dbl, vp],
         "qg_stencil_tile": [vp, ctypes.POINTER(i32)],
+        "qg_bounds_check_result": [ctypes.POINTER(i32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -284,6 +286,14 @@ def qg_solve_engine(h: int) -> int:
     e = ctypes.c_int32()
     _check(load().qg_solve_engine(h, ctypes.byref(e)), "qg_solve_engine")
     return e.value
+
+
+def qg_bounds_check_result() -> int:
+    """Checked builds only: the first failed index check's site (0: none);
+    raises QGError (QG_ERR_UNSUPPORTED) in normal builds."""
+    r = ctypes.c_int32()
+    _check(load().qg_bounds_check_result(ctypes.byref(r)), "qg_bounds_check_result")
+    return r.value
 
 
 def qg_stencil_tile(h: int) -> int:

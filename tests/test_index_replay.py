@@ -1,0 +1,201 @@
+"""CPU replays of the CUDA kernels' index arithmetic (no GPU, no library
+call): for every shape the kernels are launched with, each shared-memory,
+table and global index is checked against its buffer's extent, and each
+pass that permutes data writes every element exactly once.  These are the
+same expressions as the kernels', restated in Python, run before any new
+kernel shape reaches the GPU; the bounds-checked build
+(tests/test_gpu_bounds_check.py) checks the same indices on the device.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+# ---- warp-group FFT engine (csrc/solve32.cu) --------------------------------
+
+
+def px(m):
+    return m + (m >> 4)
+
+
+def geo32(lg, rad):
+    lr = rad.bit_length() - 1
+    L = 1 << lg
+    return dict(L=L, N=L // 2, G=L // rad, np=lg // lr, rem=lg % lr, buf=px(L) + 2)
+
+
+def max_cta(rad, esz):
+    return 512 if (rad == 16 and esz == 4) else 256
+
+
+def supported(mx, rad, esz):
+    lx, lr = (2 * mx).bit_length() - 1, rad.bit_length() - 1
+    lt = max_cta(rad, esz).bit_length() - 1
+    return lx >= lr and lx <= lr + lt
+
+
+def stockham_passes(lg, rad):
+    """(radix, NS) of the passes of one FFT of length 2^lg."""
+    g = geo32(lg, rad)
+    out, ns = [], 1
+    for _ in range(g["np"]):
+        out.append((rad, ns))
+        ns *= rad
+    if g["rem"]:
+        out.append((1 << g["rem"], ns))
+    return out
+
+
+CASES32 = [(lg, rad, esz) for rad in (8, 16, 32) for esz in (4, 8) for lg in range(3, 14)
+           if supported(1 << (lg - 1), rad, esz)]
+
+
+@pytest.mark.parametrize("lg,rad,esz", CASES32)
+def test_warp_group_fft_passes_stay_in_their_buffers(lg, rad, esz):
+    g = geo32(lg, rad)
+    L, G, buf = g["L"], g["G"], g["buf"]
+    t = np.arange(G)
+    for p, (R, NS) in enumerate(stockham_passes(lg, rad)):
+        B = rad // R                       # butterflies per thread (remainder pass)
+        j = (t[:, None] + np.arange(B)[None, :] * G).ravel()
+        k = j & (NS - 1)
+        r = np.arange(R)
+        reads = j[:, None] + r[None, :] * (L // R)
+        writes = (j - k)[:, None] * R + k[:, None] + r[None, :] * NS
+        if p == 0:
+            # the first pass reads the odd extension from the N stored values:
+            # element m = t + r G is z_m (r < R/2), 0 (m = N) or -z_{L-m}
+            H = R // 2
+            m = t[:, None] + r[None, :] * G
+            src = np.where(r[None, :] < H, m,
+                           np.where(r[None, :] == H, g["N"] - t[:, None], (R - r[None, :]) * G - t[:, None]))
+            assert src.min() >= 0 and src.max() <= g["N"]
+            reads = src
+        assert reads.min() >= 0 and reads.max() < L
+        assert px(reads.max()) < buf
+        # each pass writes every element of the length-L buffer exactly once
+        assert np.array_equal(np.sort(writes.ravel()), np.arange(L))
+        assert px(writes.max()) < buf
+
+
+@pytest.mark.parametrize("mx,my,rad,esz", [(m, n, rad, esz) for rad in (8, 16, 32) for esz in (4, 8)
+                                          for m, n in ((8, 8), (32, 64), (512, 1024), (1024, 512),
+                                                       (2048, 4096), (64, 16))
+                                          if supported(m, rad, esz) and supported(n, rad, esz)])
+def test_warp_group_cta_buffers_hold_their_pairs(mx, my, rad, esz):
+    """Each group of G threads owns two buffers of `buf` complex values; the
+    CTA's groups fit in the buffer region it is launched with."""
+    lgx, lgy = (2 * mx).bit_length() - 1, (2 * my).bit_length() - 1
+    gx, gy = geo32(lgx, rad), geo32(lgy, rad)
+    threads = max(max(gx["G"], gy["G"]), 128)
+    assert threads <= max_cta(rad, esz)
+    region = max((threads // g["G"]) * 2 * g["buf"] for g in (gx, gy))
+    for g in (gx, gy):
+        groups = threads // g["G"]
+        assert groups >= 1
+        last = 2 * (groups - 1) * g["buf"] + 2 * g["buf"]
+        assert last <= region
+
+
+def test_batched_solve_queue_claims_dependencies_first():
+    """The batched solve's work items (phase by phase, member by member)
+    decode to every (phase, member, slot) exactly once, and every item a
+    phase-1 or phase-2 item waits for has a smaller index (so it was claimed
+    earlier, by a running CTA)."""
+    for nb, ns0, ns1 in itertools.product((1, 3, 7), (1, 2, 5), (1, 4)):
+        n0, n1 = nb * ns0, nb * ns0 + nb * ns1
+        total = n1 + nb * ns0
+        seen = set()
+        for item in range(total):
+            if item < n0:
+                ph, m, slot = 0, item // ns0, item % ns0
+            elif item < n1:
+                ph, m = 1, (item - n0) // ns1
+                slot = item - n0 - m * ns1
+            else:
+                ph, m = 2, (item - n1) // ns0
+                slot = item - n1 - m * ns0
+            assert 0 <= m < nb and 0 <= slot < (ns1 if ph == 1 else ns0)
+            seen.add((ph, m, slot))
+            if ph > 0:
+                prev = ([m * ns0 + s for s in range(ns0)] if ph == 1
+                        else [n0 + m * ns1 + s for s in range(ns1)])
+                assert max(prev) < item
+        assert len(seen) == total
+
+
+# ---- fused fine-stage kernel (csrc/fused.cu) ---------------------------------
+
+TX, SWX = 64, 72
+
+
+def plan(esz, lv, tl, rc):
+    ry = max(1 << lv, 8)
+    G = rc // ry
+    F = 1 << lv
+    CPX, CPY = TX // F + 4, rc // F + 3
+
+    def al(v):
+        return (v + 127) // 128 * 128
+    W = 0
+    WN = al(W + esz * (rc + 2) * SWX)
+    P = al(WN + esz * rc * TX)
+    CP = al(P + (esz * (rc + 2) * SWX if lv == 0 else 0))
+    CP2 = al(CP + (esz * CPY * CPX if lv > 0 else 0))
+    FF = al(CP2 + (esz * CPY * CPX if tl else 0))
+    END = al(FF + esz * rc * TX)
+    return dict(RY=ry, G=G, THREADS=16 * G, F=F, CPX=CPX, CPY=CPY, END=END)
+
+
+FUSED = ([(4, lv, False, rc) for lv in range(5) for rc in (128, 64, 32)]
+         + [(8, lv, False, 64) for lv in range(5)]
+         + [(esz, lv, True, 128 if esz == 4 else 64) for esz in (4, 8) for lv in range(1, 5)])
+
+
+@pytest.mark.parametrize("esz,lv,tl,rc", FUSED)
+def test_fused_tile_indices_stay_in_shared_memory(esz, lv, tl, rc):
+    pl = plan(esz, lv, tl, rc)
+    assert pl["END"] <= 200 * 1024                     # dynamic shared memory of a CTA
+    assert rc % pl["RY"] == 0 and rc % pl["F"] == 0
+    lanes = np.arange(16)
+    # halo rows of w^(s) and of the fine psi: y - yc + 1 for the rows each
+    # group touches, y in [ys - 1, ys + RY], ys = yc + grp RY
+    for grp in range(pl["G"]):
+        ys = grp * pl["RY"]
+        rows = np.arange(ys - 1, ys + pl["RY"] + 1) + 1
+        assert rows.min() >= 0 and rows.max() < rc + 2
+    # the quad load (4 lane + 4 .. + 7) and the two edge reads (3, TX + 4)
+    assert (4 * lanes + 7).max() < SWX and TX + 4 < SWX
+    # interior boxes (w^n, forcing): (y - yc) TX + 4 lane + 3 < RC TX
+    assert (rc - 1) * TX + (4 * lanes + 3).max() < rc * TX
+    if lv > 0:
+        # the elliptic-grid patch: rows J - J_lo, columns Ib - I_lo .. + 3
+        for x0, yc in ((0, 0), (TX, rc), (5 * TX, 7 * rc)):
+            I_lo, J_lo = (x0 - 1) >> lv, (yc - 1) >> lv
+            xq = x0 + 4 * lanes
+            Ib = (xq - 1) >> lv
+            cols = Ib - I_lo
+            assert cols.min() >= 0 and (cols + 3).max() < pl["CPX"]
+            for grp in range(pl["G"]):
+                ys = yc + grp * pl["RY"]
+                for y in range(ys - 1, ys + pl["RY"] + 1):
+                    for J in (y >> lv, (y >> lv) + 1):
+                        assert 0 <= J - J_lo < pl["CPY"]
+        # the restriction's seam entries: 2 lane + 1 (l = 1), lane / G
+        # (l >= 2) and TX / F, all < TX / F + 1
+        sw = TX // pl["F"] + 1
+        if lv == 1:
+            assert (2 * lanes + 1).max() < sw
+        else:
+            gcell = max(pl["F"] // 4, 1)
+            assert (lanes // gcell).max() < sw
+        assert TX // pl["F"] < sw
+
+
+@pytest.mark.parametrize("esz", [4, 8])
+def test_fused_tma_boxes_start_on_16_bytes(esz):
+    """The tile copies start at x = x0 - 4 (halo boxes) and x0 (interior
+    boxes), x0 a multiple of 64 nodes: both multiples of 16 bytes."""
+    for bx in range(0, 130):
+        x0 = bx * TX
+        assert ((x0 - 4) * esz) % 16 == 0 and (x0 * esz) % 16 == 0
