@@ -9,7 +9,7 @@ Section 5.2's E = 1/2 iint |grad psi|^2 of psi^n, the CGP streamfunction of
 the step's first stage; it is sampled every 20 steps over t in [10, 50], the
 window of Section 5.1 (20 000 snapshots, as there).  The file also holds the
 means over the four 10-unit sub-windows, a measure of the sampling noise of
-the chaotic flow.
+the chaotic flow, and the energy history every 200 steps from t = 0.
 
 This script calls only the oracle and the seeded input generator:
 
@@ -31,6 +31,7 @@ from paper_1308_3290_gb300 import inputs  # noqa: E402
 NX, NY, LEVELS, DT, SEED = 64, 128, 1, 1e-4, 1
 RE, RO = 200.0, 0.0016
 T0, T1, EVERY = 10.0, 50.0, 20
+SERIES = 200         # the energy history is kept every 200 steps (t = 0.02)
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mean_ke_64x128_l1.txt")
 
 
@@ -39,10 +40,18 @@ def main():
     w = O.embed(inputs.perturbation(NX, NY, seed=SEED))
     n0, n1 = int(round(T0 / DT)), int(round(T1 / DT))
     ke = []
+    series = []          # (step, KE) every SERIES steps from the start
     t_start = time.time()
-    for n in range(n1):
-        if n >= n0 and (n - n0) % EVERY == 0:
-            ke.append(O.kinetic_energy(O.cgp_psi(w, b), b.dx, b.dy))
+    for n in range(n1 + 1):
+        take = n >= n0 and (n - n0) % EVERY == 0 and n < n1
+        if take or n % SERIES == 0:
+            e = O.kinetic_energy(O.cgp_psi(w, b), b.dx, b.dy)
+            if take:
+                ke.append(e)
+            if n % SERIES == 0:
+                series.append((n, e))
+        if n == n1:
+            break
         w = O.cgprk3_step(w, b)
         if n % 50000 == 0:
             print(f"step {n} of {n1}, {time.time() - t_start:.0f} s", flush=True)
@@ -60,6 +69,9 @@ def main():
         f.write(f"std_ke {float(np.std(ke))!r}\n")
         f.write("quarter_means " + " ".join(repr(q) for q in quarters) + "\n")
         f.write(f"final_ke {float(ke[-1])!r}\n")
+        f.write("# energy history: step  KE, every 200 steps from rest\n")
+        for n, e in series:
+            f.write(f"ke_at {n} {e!r}\n")
     print(open(OUT).read())
 
 
