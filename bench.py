@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--t1", type=float, default=50.0)
     ap.add_argument("--study-dt", type=float, default=1e-5)
     ap.add_argument("--study-out", default="")
+    ap.add_argument("--realizations", type=int, default=3)
     return ap.parse_args()
 
 
@@ -627,10 +628,11 @@ def ours(args):
 # ---------------------------------------------------------------------------
 
 # (label, nx, ny, levels): the 256 x 512 DNS, CGP of it at l = 1, 2, 3, and
-# the three runs whose elliptic grid is 16 x 32 (Figs. of the 16 x 32 set);
-# the last run is a second DNS started from a seeded 1e-3 perturbation of
-# rest: its distance from the first DNS is the sampling noise of a time mean
-# over the window
+# the three runs whose elliptic grid is 16 x 32 (Figs. of the 16 x 32 set).
+# Every run is repeated from `--realizations` starts: realization 0 from
+# rest (the paper's start), realization r >= 1 from a seeded 1e-3
+# perturbation of rest; the spread of the DNS realizations' means is the
+# sampling noise of a time mean over the window.
 STUDY_RUNS = [
     ("DNS 256x512:256x512", 256, 512, 0),
     ("CGP 256x512:128x256", 256, 512, 1),
@@ -639,41 +641,44 @@ STUDY_RUNS = [
     ("coarse 16x32:16x32", 16, 32, 0),
     ("CGP 32x64:16x32", 32, 64, 1),
     ("CGP 64x128:16x32", 64, 128, 2),
-    ("DNS 256x512:256x512, perturbed start", 256, 512, 0),
 ]
 STUDY_EXPERIMENTS = {"I": (200.0, 0.0016), "II": (312.5, 0.0025)}
 
 
 def study_mean_fields(args):
-    """Time-mean streamfunction of each run in STUDY_RUNS over t in [t0, t1]
-    from rest (Section 5.1: t in [10, 50], Exp I and II), every run of an
-    experiment one member of an ensemble stepped together at a fixed dt; the
-    error of each mean field against the DNS mean at the run's own nodes."""
+    """Time-mean streamfunction and potential vorticity of each run in
+    STUDY_RUNS over t in [t0, t1] (Section 5.1: t in [10, 50], Exp I and
+    II), every realization of every run one member of an ensemble stepped
+    together at a fixed dt.  Each run's mean over its realizations is
+    compared with the DNS mean over its realizations at the run's own nodes
+    (relative L2), next to the spread of single DNS realizations."""
     import numpy as np
     import torch
-    from paper_1308_3290_gb300 import build, qg
+    from paper_1308_3290_gb300 import build, inputs, qg
     build.build()
     qg.load()
     n0 = int(round(args.t0 / args.study_dt))
     n1 = int(round(args.t1 / args.study_dt))
+    R = args.realizations
     chunk = 20000
-    report = {"study": "time-mean psi, Section 5.1", "t0": args.t0, "t1": args.t1,
+    report = {"study": "time-mean psi and q, Section 5.1", "t0": args.t0, "t1": args.t1,
               "dt": args.study_dt, "steps": n1, "mean_over_steps": n1 - n0, "dtype": "f32",
-              "experiments": {}}
+              "realizations": R, "experiments": {}}
     names = args.experiments.split(",")
     members, owner = [], []
     for name in names:
         Re, Ro = STUDY_EXPERIMENTS[name]
-        for run in STUDY_RUNS:
-            members.append(dict(nx=run[1], ny=run[2], Re=Re, Ro=Ro, levels=run[3],
-                                dt=args.study_dt))
-            owner.append((name, run))
+        for ri, run in enumerate(STUDY_RUNS):
+            for r in range(R):
+                members.append(dict(nx=run[1], ny=run[2], Re=Re, Ro=Ro, levels=run[3],
+                                    dt=args.study_dt))
+                owner.append((name, ri, r))
     ens = qg.Ensemble(members, dtype="f32")
-    from paper_1308_3290_gb300 import inputs
     for i, m in enumerate(members):
+        r = owner[i][2]
         w0 = np.zeros((m["ny"] - 1, m["nx"] - 1))
-        if "perturbed" in owner[i][1][0]:
-            w0 = 1e-2 * inputs.perturbation(m["nx"], m["ny"], seed=77)
+        if r > 0:
+            w0 = 1e-3 * inputs.perturbation(m["nx"], m["ny"], seed=100 + r)
         ens.member(i).set_state(w0)
     t_start = time.perf_counter()
     done = 0
@@ -693,26 +698,44 @@ def study_mean_fields(args):
     report["wall_s"] = wall
     report["ensemble_members"] = len(members)
     report["ensemble_steps_per_s"] = n1 / wall
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
     for name in names:
         Re, Ro = STUDY_EXPERIMENTS[name]
-        idx = [i for i, (nm, _) in enumerate(owner) if nm == name]
-        means = []
-        for i in idx:
+        means = {}   # run index -> list of (psi mean, q mean)
+        for i, (nm, ri, r) in enumerate(owner):
+            if nm != name:
+                continue
             v = ens.member(i)
-            out = torch.empty((v.ny - 1, v.nx - 1), dtype=torch.float32, device="cuda")
-            cnt = qg.qg_stats_mean_psi(v.h, out)
+            outp = torch.empty((v.ny - 1, v.nx - 1), dtype=torch.float32, device="cuda")
+            outq = torch.empty_like(outp)
+            qg.qg_stats_mean_psi(v.h, outp)
+            qg.qg_stats_mean_q(v.h, outq)
             ens.synchronize()
-            means.append((out.double().cpu().numpy(), cnt, qg.qg_diagnostics(v.h)[0]))
-        dns = means[0][0]
+            means.setdefault(ri, []).append((outp.double().cpu().numpy(), outq.double().cpu().numpy()))
+        dns_p = np.mean([m[0] for m in means[0]], axis=0)
+        dns_q = np.mean([m[1] for m in means[0]], axis=0)
         runs = []
-        for (label, nx, ny, lv), (m, cnt, ke) in zip(STUDY_RUNS, means):
+        for ri, (label, nx, ny, lv) in enumerate(STUDY_RUNS):
             s = 256 // nx
-            ref = dns[s - 1::s, s - 1::s]
-            runs.append({"run": label, "levels": lv, "samples": cnt,
-                         "psi_min": float(m.min()), "psi_max": float(m.max()),
-                         "rel_l2_vs_dns": float(np.linalg.norm(m - ref) / np.linalg.norm(ref)),
-                         "final_ke": ke})
-        report["experiments"][name] = {"Re": Re, "Ro": Ro, "runs": runs}
+            ref_p, ref_q = dns_p[s - 1::s, s - 1::s], dns_q[s - 1::s, s - 1::s]
+            mp = np.mean([m[0] for m in means[ri]], axis=0)
+            mq = np.mean([m[1] for m in means[ri]], axis=0)
+            entry = {"run": label, "levels": lv,
+                     "rel_l2_psi_vs_dns": rel(mp, ref_p), "rel_l2_q_vs_dns": rel(mq, ref_q),
+                     "psi_min": float(mp.min()), "psi_max": float(mp.max()),
+                     "single_realization_rel_l2_psi":
+                         [rel(m[0], ref_p) for m in means[ri]]}
+            runs.append(entry)
+        spread = [rel(m[0], dns_p) for m in means[0]]
+        report["experiments"][name] = {
+            "Re": Re, "Ro": Ro, "runs": runs,
+            "dns_single_realization_spread_psi": spread,
+            "noise_floor_psi": float(np.sqrt(2.0 / R) * np.sqrt(np.mean(np.square(spread))) *
+                                     np.sqrt(R / max(R - 1, 1))),
+        }
         print(json.dumps({"experiment": name, **report["experiments"][name]}), flush=True)
     print(json.dumps({"wall_s": wall, "ensemble_steps_per_s": n1 / wall}), flush=True)
     ens.close()

@@ -313,6 +313,14 @@ qg_status qg_stats_begin(qg_handle h);
  * Errors: QG_ERR_ARG when no step has been accumulated.                    */
 qg_status qg_stats_mean_psi(qg_handle h, void* psi_mean, int layer, int64_t* count);
 
+/* qg_stats_mean_q -- the time-mean potential vorticity over the same steps
+ * as qg_stats_mean_psi (the sums of the states w^n or Q_i^n are kept beside
+ * those of psi^n): one layer q = Ro w + y (Eq. pv with (delta_I/L)^2 = Ro,
+ * Eq. Rhines), two layers q_i = Q_i + y (Section 4.3); fine grid, exchange
+ * layout, handle dtype, into the caller's device buffer (NULL to read only
+ * the count).  Errors: QG_ERR_ARG when no step has been accumulated.     */
+qg_status qg_stats_mean_q(qg_handle h, void* q_mean, int layer, int64_t* count);
+
 /* qg_stats_end -- stop accumulating (the sum is kept).                     */
 qg_status qg_stats_end(qg_handle h);
 

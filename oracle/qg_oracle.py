@@ -41,6 +41,7 @@ __all__ = [
     "cgprk3_step", "run", "rhs_q_form", "cgprk3_step_q_form",
     "kinetic_energy", "enstrophy", "max_velocity", "cfl_dt", "adaptive_dt",
     "cgprk3_step_adaptive", "run_adaptive", "mean_psi", "mean_psi_two_layer",
+    "mean_q", "mean_q_two_layer",
     "two_layer_cgp_psi", "two_layer_rhs", "cgprk3_step_two_layer",
     "interior", "embed",
 ]
@@ -580,3 +581,33 @@ def mean_psi_two_layer(Q1_int: np.ndarray, Q2_int: np.ndarray, b: TwoLayer, n0: 
             s2 += p2
         a1, a2 = cgprk3_step_two_layer(a1, a2, b)
     return interior(s1) / (n1 - n0), interior(s2) / (n1 - n0)
+
+
+def mean_q(omega0_int: np.ndarray, b: Basin, n0: int, n1: int) -> np.ndarray:
+    """Time-mean potential vorticity of Section 5.1 over the steps
+    n = n0..n1-1: the mean of q^n = Ro w^n + y (Eq. pv with
+    (delta_I/L)^2 = Ro, Eq. Rhines) at the interior nodes."""
+    w = embed(np.asarray(omega0_int, dtype=np.float64))
+    y = grid_y(b)[1:-1]
+    acc = np.zeros((b.ny - 1, b.nx - 1))
+    for n in range(n1):
+        if n >= n0:
+            acc += b.Ro * interior(w) + y[:, None]
+        w = cgprk3_step(w, b)
+    return acc / (n1 - n0)
+
+
+def mean_q_two_layer(Q1_int: np.ndarray, Q2_int: np.ndarray, b: TwoLayer, n0: int, n1: int):
+    """Two-layer version of ``mean_q``: the means of q_i^n = Q_i^n + y
+    (Section 4.3's variable Q_i = q_i - y)."""
+    a1 = embed(np.asarray(Q1_int, dtype=np.float64))
+    a2 = embed(np.asarray(Q2_int, dtype=np.float64))
+    y = grid_y(b)[1:-1][:, None]
+    s1 = np.zeros((b.ny - 1, b.nx - 1))
+    s2 = np.zeros_like(s1)
+    for n in range(n1):
+        if n >= n0:
+            s1 += interior(a1) + y
+            s2 += interior(a2) + y
+        a1, a2 = cgprk3_step_two_layer(a1, a2, b)
+    return s1 / (n1 - n0), s2 / (n1 - n0)

@@ -142,6 +142,7 @@ struct qg_ctx {
     double time_host = 0.0;        // model time of two-layer handles (fixed dt)
     bool stats = false;            // accumulate the first-stage psi of every step
     double* stat_acc = nullptr;    // its FP64 sum (elliptic grid, or fine for l = 0 / 2 layers)
+    double* stat_acc_w = nullptr;  // FP64 sum of the state w^n (fine, layers planes)
     int64_t stat_count = 0;
     double* dclock = nullptr;      // device {umax bits, time, last dt, spare}
     int solver = QG_SOLVER_FFT;    // elliptic solver of the step and qg_poisson_solve
@@ -795,9 +796,12 @@ qg_status stage(qg_ctx* h, int s_idx, cudaStream_t s) {
     void* wout = h->w[(s_idx + 1) % 3];
     qg_status st = project<T>(h, win, s);
     if (st != QG_OK) return st;
-    if (h->stats && s_idx == 0)
+    if (h->stats && s_idx == 0) {
         QG_TRY(launch_accumulate<T>(h->stat_acc, static_cast<const T*>(h->psi),
                                     h->plane_f * h->layers, s));
+        QG_TRY(launch_accumulate<T>(h->stat_acc_w, static_cast<const T*>(h->w[0]),
+                                    h->plane_f * h->layers, s));
+    }
     KTimer kt(h, s, QG_K_FINE);
     if (h->layers == 1) {
         StageParams<T> p;
@@ -937,6 +941,8 @@ qg_status stage_fused(qg_ctx* h, int s_idx, cudaStream_t s) {
         const bool fine = h->levels == 0;
         QG_TRY(launch_accumulate<T>(h->stat_acc, static_cast<const T*>(fine ? h->psi : h->cpsi),
                                     (fine ? h->plane_f : h->plane_c) * h->layers, s));
+        QG_TRY(launch_accumulate<T>(h->stat_acc_w, static_cast<const T*>(h->w[0]),
+                                    h->plane_f * h->layers, s));
     }
     if (h->layers == 2) return stage_fused2<T>(h, s_idx, *t, s);
     FusedParams<T> p;
@@ -1487,11 +1493,17 @@ qg_status qg_stats_begin(qg_handle h) {
     if (h->latched != QG_OK) return qg_last_error(h);
     const bool fine = h->levels == 0;
     const size_t n = (fine ? h->plane_f : h->plane_c) * h->layers;
+    const size_t nw = h->plane_f * h->layers;
     if (!h->stat_acc) {
         qg_status s = dev_alloc(h, (void**)&h->stat_acc, n * sizeof(double));
         if (s != QG_OK) return s;
     }
+    if (!h->stat_acc_w) {
+        qg_status s = dev_alloc(h, (void**)&h->stat_acc_w, nw * sizeof(double));
+        if (s != QG_OK) return s;
+    }
     QG_TRY(cudaMemsetAsync(h->stat_acc, 0, n * sizeof(double), h->stream));
+    QG_TRY(cudaMemsetAsync(h->stat_acc_w, 0, nw * sizeof(double), h->stream));
     h->stat_count = 0;
     if (!h->stats) {
         QG_TRY(cudaStreamSynchronize(h->stream));
@@ -1522,6 +1534,25 @@ qg_status qg_stats_mean_psi(qg_handle h, void* psi_mean, int layer, int64_t* cou
     else
         QG_TRY(launch_mean_out<float>(static_cast<float*>(psi_mean), acc, ld, sc, h->nx, h->ny,
                                       lv, h->stream));
+    return QG_OK;
+}
+
+qg_status qg_stats_mean_q(qg_handle h, void* q_mean, int layer, int64_t* count) {
+    NvtxRange nvtx_range("qg_stats_mean_q");
+    if (!h || layer < 0 || layer >= h->layers) return QG_ERR_ARG;
+    if (!h->stats || h->stat_count == 0) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    if (count) *count = h->stat_count;
+    if (!q_mean) return QG_OK;
+    // one layer: q = Ro w + y (Eq. pv); two layers: q_i = Q_i + y
+    const double sc = (h->layers == 1 ? h->Ro : 1.0) / (double)h->stat_count;
+    const double* acc = h->stat_acc_w + (size_t)layer * h->plane_f;
+    if (h->dtype == QG_F64)
+        QG_TRY(launch_mean_q_out<double>(static_cast<double*>(q_mean), acc, h->ldf, sc, h->nx,
+                                         h->ny, h->y0, h->dy, h->stream));
+    else
+        QG_TRY(launch_mean_q_out<float>(static_cast<float*>(q_mean), acc, h->ldf, sc, h->nx,
+                                        h->ny, h->y0, h->dy, h->stream));
     return QG_OK;
 }
 
@@ -2319,7 +2350,9 @@ qg_status group_enqueue(qg_ensemble e, const EnsSolveGroup& g, cudaStream_t s) {
                     QG_TRY_E(cuda_status(h, launch_accumulate<T>(
                         h->stat_acc, static_cast<const T*>(fine ? h->psi : h->cpsi),
                         (fine ? h->plane_f : h->plane_c) * h->layers, s)));
-                    ++e->kernels;
+                    QG_TRY_E(cuda_status(h, launch_accumulate<T>(
+                        h->stat_acc_w, static_cast<const T*>(h->w[0]), h->plane_f * h->layers, s)));
+                    e->kernels += 2;
                 }
                 if (h->cfl > 0.0) {
                     const LevelTables* ti = nullptr;

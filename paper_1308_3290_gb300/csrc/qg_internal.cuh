@@ -211,6 +211,12 @@ template <typename T>
 cudaError_t launch_mean_out(T* dense, const double* acc, int ldacc, double scale, int nx,
                             int ny, int levels, cudaStream_t s);
 
+// dense[(j-1)(nx-1) + i-1] = scale * acc[j ld + i] + y0 + j dy (fine grid):
+// the time-mean potential vorticity from a sum of states
+template <typename T>
+cudaError_t launch_mean_q_out(T* dense, const double* acc, int ld, double scale, int nx, int ny,
+                              double y0, double dy, cudaStream_t s);
+
 // u = max over interior fine nodes of |psi_x| and |psi_y| (central
 // differences, Eq. dt) of psi prolonged `levels` times from `psi` (pitch
 // ldp); atomically max-ed into *umax as the bits of a non-negative double.

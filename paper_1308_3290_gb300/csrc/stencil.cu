@@ -325,6 +325,30 @@ __global__ void mean_out_kernel(T* __restrict__ dense, const double* __restrict_
     dense[(size_t)(j - 1) * (nx - 1) + (i - 1)] = (T)(scale * prolonged_at(acc, ldacc, i, j, levels));
 }
 
+// dense = scale * acc (fine nodes) + y_j: the time-mean potential vorticity
+template <typename T>
+__global__ void mean_q_out_kernel(T* __restrict__ dense, const double* __restrict__ acc, int ld,
+                                  double scale, int nx, int ny, double y0, double dy) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    if (i >= nx || j >= ny) return;
+    dense[(size_t)(j - 1) * (nx - 1) + (i - 1)] =
+        (T)(scale * acc[(size_t)j * ld + i] + (y0 + dy * (double)j));
+}
+
+template <typename T>
+cudaError_t launch_mean_q_out(T* dense, const double* acc, int ld, double scale, int nx, int ny,
+                              double y0, double dy, cudaStream_t s) {
+    const dim3 block(32, 8);
+    const dim3 grid((nx - 1 + 31) / 32, (ny - 1 + 7) / 8);
+    mean_q_out_kernel<T><<<grid, block, 0, s>>>(dense, acc, ld, scale, nx, ny, y0, dy);
+    return cudaGetLastError();
+}
+template cudaError_t launch_mean_q_out<float>(float*, const double*, int, double, int, int, double,
+                                              double, cudaStream_t);
+template cudaError_t launch_mean_q_out<double>(double*, const double*, int, double, int, int,
+                                               double, double, cudaStream_t);
+
 template <typename T>
 cudaError_t launch_accumulate(double* acc, const T* src, size_t n, cudaStream_t s) {
     size_t blocks = (n + 255) / 256;

@@ -229,6 +229,28 @@ def test_time_mean_psi_matches_oracle(levels, dtype, tol):
     b.close()
 
 
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-6)])
+def test_time_mean_q_matches_oracle(levels, dtype, tol):
+    """The device-side time mean of the potential vorticity q = Ro w + y
+    over steps n0..n1-1 (Section 5.1's time-mean fields, Eq. pv)."""
+    torch = require_gpu()
+    nx, ny, n0, n1 = 64, 128, 5, 25
+    w0 = inputs.perturbation(nx, ny, seed=14) * 50.0
+    ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=1e-4)
+    ref = O.mean_q(w0, ob, n0, n1)
+    b = qg.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=1e-4, dtype=dtype)
+    b.set_state(w0)
+    b.step(n0)
+    qg.qg_stats_begin(b.h)
+    b.step(n1 - n0)
+    out = torch.empty((ny - 1, nx - 1), dtype=b.tdtype, device="cuda")
+    assert qg.qg_stats_mean_q(b.h, out) == n1 - n0
+    b.synchronize()
+    assert_fields_close(to_np(out), ref, tol)
+    b.close()
+
+
 def test_time_mean_psi_two_layers():
     torch = require_gpu()
     p = dict(Ro=2.49e-4, Fr=0.087, delta=0.2, sigma=1.43e-3)
@@ -249,4 +271,10 @@ def test_time_mean_psi_two_layers():
         assert qg.qg_stats_mean_psi(b.h, out, layer) == 10
         b.synchronize()
         assert rel_l2(to_np(out), ref) <= 1e-11
+    q1, q2 = O.mean_q_two_layer(Q1, Q2, ob, 2, 12)
+    for layer, ref in ((0, q1), (1, q2)):
+        out = torch.empty((63, 63), dtype=torch.float64, device="cuda")
+        assert qg.qg_stats_mean_q(b.h, out, layer) == 10
+        b.synchronize()
+        assert rel_l2(to_np(out), ref) <= 1e-12
     b.close()

@@ -377,3 +377,38 @@ def test_forcing_pin_rejects_mistakes():
     assert forcing_error(variant(k=2.0)) > 1e-3
     assert forcing_error(variant(by_ro=False)) > 1e-3
     assert forcing_error(variant(use_amp=False)) > 1e-3
+
+
+def test_mean_q_pin_rejects_mistakes():
+    """The q-form pin of the time-mean potential vorticity rejects a missing
+    Ro factor, a missing planetary vorticity y and y taken at shifted rows."""
+    b = O.Basin(32, 64, Re=200.0, Ro=0.0016, levels=1, dt=1e-4)
+    from paper_1308_3290_gb300 import inputs
+    w0 = inputs.perturbation(32, 64, seed=2) * 30.0
+    n0, n1 = 2, 6
+    Y = np.repeat(O.grid_y(b)[:, None], b.nx + 1, axis=1)
+    q = b.Ro * O.embed(w0) + Y
+    acc = np.zeros((63, 31))
+    for n in range(n1):
+        if n >= n0:
+            acc += O.interior(q)
+        q = O.cgprk3_step_q_form(q, b)
+    want = acc / (n1 - n0)
+
+    def variant(scale, with_y, shift):
+        w = O.embed(w0)
+        y = O.grid_y(b)[1 + shift:b.ny + shift]
+        out = np.zeros((63, 31))
+        for n in range(n1):
+            if n >= n0:
+                out += scale * O.interior(w) + (y[:, None] if with_y else 0.0)
+            w = O.cgprk3_step(w, b)
+        return out / (n1 - n0)
+
+    def ok(m):
+        return np.abs(m - want).max() <= 1e-12 * np.abs(want).max()
+
+    assert ok(variant(b.Ro, True, 0))
+    assert not ok(variant(1.0, True, 0))
+    assert not ok(variant(b.Ro, False, 0))
+    assert not ok(variant(b.Ro, True, 1))

@@ -212,3 +212,41 @@ def test_two_layer_mean_psi_is_the_projection_of_the_mean_states():
     p1, p2 = O.two_layer_cgp_psi(sum(s1) / 5, sum(s2) / 5, b)
     for got, ref in ((m1, O.interior(p1)), (m2, O.interior(p2))):
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_mean_q_is_the_mean_of_the_q_form_trajectory(levels):
+    """The time-mean potential vorticity from the w-form trajectory equals
+    the mean of the states of the literal q-form integration (Section 3.2 as
+    printed: the state q itself, walls q = y), steps n0..n1-1."""
+    b = O.Basin(32, 64, Re=200.0, Ro=0.0016, levels=levels, dt=1e-4)
+    w0 = inputs.perturbation(32, 64, seed=2) * 30.0
+    n0, n1 = 3, 12
+    got = O.mean_q(w0, b, n0, n1)
+    Y = np.repeat(O.grid_y(b)[:, None], b.nx + 1, axis=1)
+    q = b.Ro * O.embed(w0) + Y
+    acc = np.zeros_like(got)
+    for n in range(n1):
+        if n >= n0:
+            acc += O.interior(q)
+        q = O.cgprk3_step_q_form(q, b)
+    want = acc / (n1 - n0)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_mean_q_at_rest_without_forcing_is_y():
+    """With no forcing and w = 0 the basin stays at rest: q = y exactly
+    (Eq. pv), so its time mean is the planetary vorticity y itself."""
+    b = O.Basin(16, 32, levels=1, amp=0.0)
+    got = O.mean_q(np.zeros((31, 15)), b, 0, 5)
+    y = -1.0 + (2.0 / 32) * np.arange(1, 32)
+    assert np.array_equal(got, np.repeat(y[:, None], 15, axis=1))
+
+
+def test_two_layer_mean_q_is_the_mean_state_plus_y():
+    """Two layers: q_i = Q_i + y (Section 4.3); with Q_i = 0, no wind and
+    rest, q_i = y in both layers."""
+    b = O.TwoLayer(16, 16, amp=0.0, levels=0)
+    m1, m2 = O.mean_q_two_layer(np.zeros((15, 15)), np.zeros((15, 15)), b, 0, 3)
+    y = -0.5 + (1.0 / 16) * np.arange(1, 16)
+    assert np.array_equal(m1, np.repeat(y[:, None], 15, axis=1)) and np.array_equal(m1, m2)
