@@ -115,6 +115,19 @@ qg_status qg_destroy(qg_handle h);
 qg_status qg_set_state(qg_handle h, const void* field, int layer);
 qg_status qg_get_state(qg_handle h, void* field, int layer);
 
+/* qg_get_state_async -- as qg_get_state, for a PAGE-LOCKED host buffer,
+ * without holding up the handle's later work: the state is repacked on the
+ * handle's stream into one of two device staging buffers and copied to the
+ * host by DMA on an internal download stream, which the next steps do not
+ * wait for (so the copy of step k's result overlaps step k + 1).  The
+ * buffer holds the state once qg_synchronize returns (the handle's stream
+ * alone does not order it).  Other buffers: the same as qg_get_state.
+ * qg_set_state from a page-locked buffer likewise uploads by DMA on an
+ * internal stream (the handle's stream waits for it, so its ordering is
+ * unchanged), which lets the next input's upload overlap the steps before.
+ * Errors: QG_ERR_ARG, QG_ERR_OOM (the staging buffers, on first use).      */
+qg_status qg_get_state_async(qg_handle h, void* field, int layer);
+
 /* qg_get_psi -- the fine-grid streamfunction of the current state: the CGP
  * projection of steps (ii)-(iv) of Section 3 (restrict, coarse solve,
  * prolong).  Level-0 exchange layout.                                      */

@@ -134,6 +134,15 @@ struct qg_ctx {
     int solve_engine = 4;          // FFT base radix of the step's solve (autotuned)
     bool engine_forced = false;    // solve_engine was forced by QG_SOLVE_ENGINE
     int fine_rows = 0;             // fine rows per CTA of the fused stage (autotuned)
+    // transfers with pinned host memory (qg_set_state, qg_get_state_async):
+    // DMA on two internal streams through device staging buffers (two per
+    // direction, dense exchange layout), ordered against the handle's
+    // stream by events, so that they overlap the steps around them
+    cudaStream_t xin = nullptr, xout = nullptr;
+    void* stage_in[2] = {nullptr, nullptr};
+    void* stage_out[2] = {nullptr, nullptr};
+    cudaEvent_t in_ready[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {};
+    int bin = 0, bout = 0;
     bool member = false;           // an ensemble member (keeps the default tile)
     int* derr = nullptr;           // device error flag of bounded waits
     unsigned* dbar = nullptr;      // grid-barrier counters of the solve kernel
@@ -1192,6 +1201,14 @@ static void tape_release(qg_ctx* h);
 qg_status qg_destroy(qg_handle h) {
     if (!h) return QG_OK;
     cudaStreamSynchronize(h->stream);
+    for (cudaStream_t x : {h->xin, h->xout}) {
+        if (!x) continue;
+        cudaStreamSynchronize(x);
+        cudaStreamDestroy(x);
+    }
+    for (int b = 0; b < 2; ++b)
+        for (cudaEvent_t e : {h->in_ready[b], h->in_free[b], h->out_ready[b], h->out_free[b]})
+            if (e) cudaEventDestroy(e);
     tape_release(h);
     drop_graph(h);
     for (void* p : h->allocs) cudaFree(p);
@@ -1228,6 +1245,7 @@ static qg_status check_device_flag(qg_ctx* h) {
 qg_status qg_synchronize(qg_handle h) {
     if (!h) return QG_ERR_ARG;
     QG_TRY(cudaStreamSynchronize(h->stream));
+    if (h->xout) QG_TRY(cudaStreamSynchronize(h->xout));
     qg_status s = check_device_flag(h);
     if (s != QG_OK) {
         qg_last_error(h);
@@ -1236,12 +1254,55 @@ qg_status qg_synchronize(qg_handle h) {
     return qg_last_error(h);
 }
 
+// Whether ptr is page-locked host memory (copied by DMA through staging).
+static bool pinned_host(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// The transfer streams, events and staging buffers, made on first use.
+static qg_status xfer_init(qg_ctx* h) {
+    if (h->xin) return QG_OK;
+    const size_t bytes = (size_t)(h->nx - 1) * (h->ny - 1) * h->esz;
+    for (int b = 0; b < 2; ++b) {
+        qg_status st = dev_alloc(h, &h->stage_in[b], bytes);
+        if (st == QG_OK) st = dev_alloc(h, &h->stage_out[b], bytes);
+        if (st != QG_OK) return st;
+        for (cudaEvent_t* e : {&h->in_ready[b], &h->in_free[b], &h->out_ready[b], &h->out_free[b]})
+            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return QG_ERR_CUDA;
+    }
+    if (cudaStreamCreateWithFlags(&h->xout, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->xin, cudaStreamNonBlocking) != cudaSuccess)
+        return QG_ERR_CUDA;
+    return QG_OK;
+}
+
 qg_status qg_set_state(qg_handle h, const void* field, int layer) {
     NvtxRange nvtx_range("qg_set_state");
     if (!h || !field || layer < 0 || layer >= h->layers) return QG_ERR_ARG;
     if (h->latched != QG_OK) return qg_last_error(h);
     char* dst = static_cast<char*>(h->w[0]) + (size_t)layer * h->plane_f * h->esz;
-    QG_TRY(copy_in(dst, h->ldf, field, h->nx - 1, h->ny - 1, h->esz, h->stream));
+    if (pinned_host(field)) {
+        // DMA into a staging buffer on the upload stream (it may run while
+        // earlier steps still compute), then the repack on the handle's
+        // stream, which waits for the upload
+        QG_TRY_S(xfer_init(h));
+        const int b = h->bin;
+        h->bin ^= 1;
+        const size_t bytes = (size_t)(h->nx - 1) * (h->ny - 1) * h->esz;
+        QG_TRY(cudaStreamWaitEvent(h->xin, h->in_free[b], 0));
+        QG_TRY(cudaMemcpyAsync(h->stage_in[b], field, bytes, cudaMemcpyHostToDevice, h->xin));
+        QG_TRY(cudaEventRecord(h->in_ready[b], h->xin));
+        QG_TRY(cudaStreamWaitEvent(h->stream, h->in_ready[b], 0));
+        QG_TRY(copy_in(dst, h->ldf, h->stage_in[b], h->nx - 1, h->ny - 1, h->esz, h->stream));
+        QG_TRY(cudaEventRecord(h->in_free[b], h->stream));
+    } else {
+        QG_TRY(copy_in(dst, h->ldf, field, h->nx - 1, h->ny - 1, h->esz, h->stream));
+    }
     h->part_valid = false;
     h->time_host = 0.0;
     if (h->solver == QG_SOLVER_MULTIGRID)   // the first solve's guess: zero
@@ -1257,6 +1318,28 @@ qg_status qg_get_state(qg_handle h, void* field, int layer) {
     if (h->latched != QG_OK) return qg_last_error(h);
     const char* src = static_cast<const char*>(h->w[0]) + (size_t)layer * h->plane_f * h->esz;
     QG_TRY(copy_out(field, src, h->ldf, h->nx - 1, h->ny - 1, h->esz, h->stream));
+    return QG_OK;
+}
+
+qg_status qg_get_state_async(qg_handle h, void* field, int layer) {
+    NvtxRange nvtx_range("qg_get_state_async");
+    if (!h || !field || layer < 0 || layer >= h->layers) return QG_ERR_ARG;
+    if (h->latched != QG_OK) return qg_last_error(h);
+    if (!pinned_host(field)) return qg_get_state(h, field, layer);
+    QG_TRY_S(xfer_init(h));
+    const int b = h->bout;
+    h->bout ^= 1;
+    const size_t bytes = (size_t)(h->nx - 1) * (h->ny - 1) * h->esz;
+    const char* src = static_cast<const char*>(h->w[0]) + (size_t)layer * h->plane_f * h->esz;
+    // the repack into a staging buffer on the handle's stream (once the
+    // download of two calls ago has emptied it), then the DMA to the host on
+    // the download stream, which the handle's later work does not wait for
+    QG_TRY(cudaStreamWaitEvent(h->stream, h->out_free[b], 0));
+    QG_TRY(copy_out(h->stage_out[b], src, h->ldf, h->nx - 1, h->ny - 1, h->esz, h->stream));
+    QG_TRY(cudaEventRecord(h->out_ready[b], h->stream));
+    QG_TRY(cudaStreamWaitEvent(h->xout, h->out_ready[b], 0));
+    QG_TRY(cudaMemcpyAsync(field, h->stage_out[b], bytes, cudaMemcpyDeviceToHost, h->xout));
+    QG_TRY(cudaEventRecord(h->out_free[b], h->xout));
     return QG_OK;
 }
 

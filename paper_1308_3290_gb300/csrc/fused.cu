@@ -122,8 +122,9 @@ struct Plan {
     static constexpr int G = RC / RY;               // groups per CTA
     static constexpr int THREADS = 16 * G;
     // CTAs per SM the registers are budgeted for: FP32 one-layer sweeps as
-    // many as make 768 threads, FP64 and two-layer ones 512 or 256 threads
-    static constexpr int MINB_RAW = ((sizeof(T) == 4 && !TL) ? 768 : 512) / THREADS;
+    // many as make 768 threads (80 registers each); FP64 and two-layer
+    // sweeps 2 CTAs (their state needs up to 232 registers)
+    static constexpr int MINB_RAW = (sizeof(T) == 4 && !TL) ? 768 / THREADS : 2;
     static constexpr int MINB = MINB_RAW < 1 ? 1 : (MINB_RAW > 16 ? 16 : MINB_RAW);
     static constexpr int F = 1 << LV;
     static constexpr int CPX = TX / F + 4;

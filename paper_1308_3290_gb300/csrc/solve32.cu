@@ -277,10 +277,11 @@ __device__ __forceinline__ void passW(const CT<T>* in, CT<T>* out, int t, const 
 }
 
 // The remainder pass, radix R < RAD: RAD/R butterflies j = t + b G per
-// thread.  Out of line: inlined next to the radix-32 pass its registers spill.
+// thread.  Inlined for RAD = 8; out of line for RAD = 16 and 32 (inlined
+// next to their full-radix passes, their registers spill).
 template <typename T, int R, int RAD>
-__device__ __noinline__ void passR(const CT<T>* in, CT<T>* out, int t, Geo32 g, int NS,
-                                   const CT<T>* __restrict__ tw, Sync sy) {
+__device__ __forceinline__ void passR_body(const CT<T>* in, CT<T>* out, int t, Geo32 g, int NS,
+                                          const CT<T>* __restrict__ tw, Sync sy) {
     constexpr int B = RAD / R;
     const int stride = g.L / R;
     Cplx<T> v[B][R];
@@ -306,6 +307,19 @@ __device__ __noinline__ void passR(const CT<T>* in, CT<T>* out, int t, Geo32 g, 
         for (int r = 0; r < R; ++r) stp<T>(out, d + r * NS, v[b][out_slot<R>(r)], g.buf);
     }
     sy.sync();
+}
+
+template <typename T, int R, int RAD>
+__device__ __noinline__ void passR_call(const CT<T>* in, CT<T>* out, int t, Geo32 g, int NS,
+                                        const CT<T>* __restrict__ tw, Sync sy) {
+    passR_body<T, R, RAD>(in, out, t, g, NS, tw, sy);
+}
+
+template <typename T, int R, int RAD>
+__device__ __forceinline__ void passR(const CT<T>* in, CT<T>* out, int t, const Geo32& g, int NS,
+                                      const CT<T>* __restrict__ tw, const Sync& sy) {
+    if constexpr (RAD <= 8) passR_body<T, R, RAD>(in, out, t, g, NS, tw, sy);
+    else passR_call<T, R, RAD>(in, out, t, g, NS, tw, sy);
 }
 
 // Forward FFT of length L of the odd extension of a[0..N); the passes

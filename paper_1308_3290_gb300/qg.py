@@ -44,7 +44,7 @@ EXPORTS = [
     "qg_tape_begin", "qg_tape_end", "qg_adjoint_step", "qg_energy_gradient",
     "qg_set_cfl", "qg_set_solver", "qg_get_time", "qg_stats_begin", "qg_stats_mean_psi", "qg_stats_end",
     "qg_set_timing_mask", "qg_solve_engine", "qg_energy_accumulate", "qg_stencil_tile",
-    "qg_bounds_check_result", "qg_stats_mean_q",
+    "qg_bounds_check_result", "qg_stats_mean_q", "qg_get_state_async",
 ]
 
 KERNEL_CLASSES = ["restrict", "solve", "prolong", "fine", "cfl"]
@@ -122,6 +122,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "qg_stencil_tile": [vp, ctypes.POINTER(i32)],
         "qg_bounds_check_result": [ctypes.POINTER(i32)],
         "qg_stats_mean_q": [vp, vp, i32, ctypes.POINTER(i64)],
+        "qg_get_state_async": [vp, vp, i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -322,6 +323,12 @@ def qg_stats_mean_psi(h: int, out=None, layer: int = 0) -> int:
     _check(load().qg_stats_mean_psi(h, _ptr(out) if out is not None else None, layer,
                                     ctypes.byref(c)), "qg_stats_mean_psi")
     return c.value
+
+
+def qg_get_state_async(h: int, field, layer: int = 0) -> None:
+    """Copy the state into a page-locked host buffer without holding up the
+    handle's later steps; complete after qg_synchronize."""
+    _check(load().qg_get_state_async(h, _ptr(field), layer), "qg_get_state_async")
 
 
 def qg_stats_mean_q(h: int, out=None, layer: int = 0) -> int:
