@@ -651,7 +651,7 @@ def ours(args):
             "roofline": roofline, "rooflines": rooflines, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": per_step_kernels * args.steps,
             "solve_engine": solve_engine,
-            "stencil_tile_rows": stencil_tile,
+            "stencil_tile": {"rows_per_cta": stencil_tile[0], "rows_per_thread": stencil_tile[1]},
             "clocks": clocks, "variants": variants,
         }
         print(json.dumps(line), flush=True)

@@ -285,15 +285,18 @@ qg_status qg_set_solver(qg_handle h, qg_solver kind, int32_t cycles);
  * rounding.  No device work.  Errors: QG_ERR_ARG.                          */
 qg_status qg_solve_engine(qg_handle h, int32_t* engine);
 
-/* qg_stencil_tile -- the fine rows per CTA of the step's fused fine-grid
- * kernel (host pointer; the tile is 64 fine columns wide): chosen when the
- * handle is created by timing whole steps with each height the build
- * offers for the handle (128, 64 or 32 for one-layer FP32 handles; 64 for
- * FP64 and 128 for two layers, fixed), after the solve engine
- * (qg_solve_engine); QG_FINE_ROWS forces an offered height.  Ensemble
- * members keep the default.  The heights give the same results to
- * rounding.  No device work.  Errors: QG_ERR_ARG.                         */
-qg_status qg_stencil_tile(qg_handle h, int32_t* rows);
+/* qg_stencil_tile -- the tile of the step's fused fine-grid kernel (host
+ * pointers): *rows fine rows per CTA (the tile is 64 fine columns wide) and
+ * *rows_per_thread (may be NULL) fine rows each thread sweeps.  Chosen when
+ * the handle is created by timing whole steps with each tile the build
+ * offers for the handle, after the solve engine (qg_solve_engine): one-layer
+ * FP32 handles take 128, 64 or 32 rows with 8 rows per thread (16 at
+ * l = 4), or 64 or 32 rows with 4 rows per thread at l <= 2 (shorter CTAs:
+ * a smaller last wave); FP64 and two-layer handles keep 64 and 128 rows.
+ * QG_FINE_ROWS=<rows> or <rows>x<rows per thread> forces an offered tile.
+ * Ensemble members keep the default.  The tiles give the same results to
+ * rounding.  No device work.  Errors: QG_ERR_ARG.                          */
+qg_status qg_stencil_tile(qg_handle h, int32_t* rows, int32_t* rows_per_thread);
 
 /* qg_bounds_check_result -- in a library built with QG_BOUNDS_CHECK (the
  * checked build: every kernel index of the fine stage, the FFT and matrix

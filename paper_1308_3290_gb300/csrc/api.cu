@@ -134,6 +134,7 @@ struct qg_ctx {
     int solve_engine = 4;          // FFT base radix of the step's solve (autotuned)
     bool engine_forced = false;    // solve_engine was forced by QG_SOLVE_ENGINE
     int fine_rows = 0;             // fine rows per CTA of the fused stage (autotuned)
+    int fine_ry = 8;               // fine rows each of its threads sweeps (autotuned)
     // transfers with pinned host memory (qg_set_state, qg_get_state_async):
     // DMA on two internal streams through device staging buffers (two per
     // direction, dense exchange layout), ordered against the handle's
@@ -603,7 +604,10 @@ qg_status fine_maps(qg_ctx* h) {
 
 using TuneKey = std::tuple<int, int, int, int, int>;
 std::mutex g_tune_mutex;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;   // (engine, fine rows)
+struct TuneVal {
+    int engine, rows, ry;   // solve engine; fine rows per CTA and per thread
+};
+std::map<TuneKey, TuneVal> g_tune_cache;
 bool g_tune_file_read = false;
 
 void tune_file_load() {
@@ -613,21 +617,21 @@ void tune_file_load() {
     if (!path) return;
     FILE* f = std::fopen(path, "r");
     if (!f) return;
-    int a, b, c, d, x, e, r;
-    while (std::fscanf(f, "%d %d %d %d %d %d %d", &a, &b, &c, &d, &x, &e, &r) == 7)
+    int a, b, c, d, x, e, r, y;
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &a, &b, &c, &d, &x, &e, &r, &y) == 8)
         if ((e == 4 || e == 16 || is_warp_engine(e) || e == kMatrixEngine) &&
-            fine_rows_supported((size_t)x, d, r))
-            g_tune_cache[TuneKey(a, b, c, d, x)] = {e, r};
+            fine_rows_supported((size_t)x, d, c, r, y))
+            g_tune_cache[TuneKey(a, b, c, d, x)] = {e, r, y};
     std::fclose(f);
 }
 
-void tune_file_store(const TuneKey& k, int e, int rows) {
+void tune_file_store(const TuneKey& k, const TuneVal& v) {
     const char* path = std::getenv("QG_TUNE_CACHE");
     if (!path) return;
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
-                 std::get<3>(k), std::get<4>(k), e, rows);
+    std::fprintf(f, "%d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+                 std::get<3>(k), std::get<4>(k), v.engine, v.rows, v.ry);
     std::fclose(f);
 }
 
@@ -670,24 +674,33 @@ qg_status autotune_solve(qg_ctx* h) {
     const LevelTables* t = nullptr;
     qg_status st = get_level(h, h->levels, &t);
     if (st != QG_OK) return st;
-    // the tile heights the fused fine stage may take on this handle
-    // (ensemble members keep the default: their batched sweep uses it)
-    std::vector<int> rows_cand{h->fine_rows};
+    // the tiles the fused fine stage may take on this handle: (rows per CTA,
+    // rows per thread); ensemble members keep the default (their batched
+    // sweep uses it)
+    using Tile = std::pair<int, int>;
+    std::vector<Tile> tiles{{h->fine_rows, h->fine_ry}};
     if (!h->member)
-        for (int r : {64, 32})
-            if (fine_rows_supported(h->esz, h->layers, r)) rows_cand.push_back(r);
-    int forced_rows = 0;
+        for (Tile c : {Tile{64, h->fine_ry}, Tile{32, h->fine_ry}, Tile{64, 4}, Tile{32, 4}})
+            if (c != tiles[0] && fine_rows_supported(h->esz, h->layers, h->levels, c.first, c.second))
+                tiles.push_back(c);
+    // QG_FINE_ROWS=<rows> or <rows>x<rows per thread> forces an offered tile
+    Tile forced{0, 0};
     if (const char* fr = std::getenv("QG_FINE_ROWS")) {
-        const int r = std::atoi(fr);
-        if (std::find(rows_cand.begin(), rows_cand.end(), r) != rows_cand.end()) forced_rows = r;
+        int r = 0, y = 0;
+        const int n = std::sscanf(fr, "%dx%d", &r, &y);
+        if (n == 1) y = fine_rows_per_thread(h->levels);
+        const Tile c{r, y};
+        if (n >= 1 && std::find(tiles.begin(), tiles.end(), c) != tiles.end()) forced = c;
     }
-    auto set_rows = [&](int r) -> qg_status {
-        if (r == h->fine_rows) return QG_OK;
-        h->fine_rows = r;
+    auto set_tile = [&](Tile c) -> qg_status {
+        if (c.first == h->fine_rows && c.second == h->fine_ry) return QG_OK;
+        h->fine_rows = c.first;
+        h->fine_ry = c.second;
         drop_graph(h);
         return fine_maps(h);
     };
-    if (forced_rows) QG_TRY_S(set_rows(forced_rows));
+    const bool forced_rows = forced.first != 0;
+    if (forced_rows) QG_TRY_S(set_tile(forced));
     if (const char* force = std::getenv("QG_SOLVE_ENGINE")) {
         const int e = std::atoi(force);
         if (engine_ok(h, t, sizeof(T), e)) {
@@ -701,10 +714,12 @@ qg_status autotune_solve(qg_ctx* h) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         tune_file_load();
         auto it = g_tune_cache.find(key);
+        const Tile cached{it == g_tune_cache.end() ? 0 : it->second.rows,
+                          it == g_tune_cache.end() ? 0 : it->second.ry};
         if (it != g_tune_cache.end() &&
-            std::find(rows_cand.begin(), rows_cand.end(), it->second.second) != rows_cand.end()) {
-            h->solve_engine = it->second.first;
-            if (!forced_rows) QG_TRY_S(set_rows(it->second.second));
+            std::find(tiles.begin(), tiles.end(), cached) != tiles.end()) {
+            h->solve_engine = it->second.engine;
+            if (!forced_rows) QG_TRY_S(set_tile(cached));
             return QG_OK;
         }
     }
@@ -725,22 +740,21 @@ qg_status autotune_solve(qg_ctx* h) {
         if (tt[k] < tt[best]) best = k;
     if (tt[best] >= 1e29f) return fail(h, QG_ERR_CUDA);
     h->solve_engine = ee[best];
-    // then the fine stage's tile height, with that engine
-    if (!forced_rows && rows_cand.size() > 1) {
-        const int r0 = h->fine_rows;
+    // then the fine stage's tile, with that engine
+    if (!forced_rows && tiles.size() > 1) {
         float tbest = tt[best];
-        int rbest = r0;
-        for (size_t k = 1; k < rows_cand.size(); ++k) {
-            if (set_rows(rows_cand[k]) != QG_OK) break;
+        Tile cbest = tiles[0];
+        for (size_t k = 1; k < tiles.size(); ++k) {
+            if (set_tile(tiles[k]) != QG_OK) break;
             const float tr = time_steps<T>(h, h->solve_engine);
             if (tr < tbest) {
                 tbest = tr;
-                rbest = rows_cand[k];
+                cbest = tiles[k];
             }
         }
         h->latched = QG_OK;
         (void)cudaGetLastError();
-        QG_TRY_S(set_rows(rbest));
+        QG_TRY_S(set_tile(cbest));
         drop_graph(h);
     }
     // the timing steps ran on the handle's buffers: return them to rest
@@ -758,8 +772,9 @@ qg_status autotune_solve(qg_ctx* h) {
     h->part_valid = false;
     QG_TRY(cudaStreamSynchronize(h->stream));
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = {h->solve_engine, h->fine_rows};
-    tune_file_store(key, h->solve_engine, h->fine_rows);
+    const TuneVal v{h->solve_engine, h->fine_rows, h->fine_ry};
+    g_tune_cache[key] = v;
+    tune_file_store(key, v);
     return QG_OK;
 }
 
@@ -915,7 +930,7 @@ qg_status stage_fused2(qg_ctx* h, int s_idx, const LevelTables& t, cudaStream_t 
         m.psi = h->tm_psi;
         m.f = h->tm_f;
         KTimer kt(h, sl, QG_K_FINE);
-        QG_TRY(launch_fine_fused<T>(p, m, h->levels, sl, true, h->fine_rows));
+        QG_TRY(launch_fine_fused<T>(p, m, h->levels, sl, true, h->fine_rows, h->fine_ry));
     }
     if (s1 != s) {
         QG_TRY(cudaEventRecord(h->ev_join, s1));
@@ -1000,7 +1015,7 @@ qg_status stage_fused(qg_ctx* h, int s_idx, cudaStream_t s) {
     m.psi = h->tm_psi;
     m.f = h->tm_f;
     KTimer kt(h, s, QG_K_FINE);
-    QG_TRY(launch_fine_fused<T>(p, m, h->levels, s, false, h->fine_rows));
+    QG_TRY(launch_fine_fused<T>(p, m, h->levels, s, false, h->fine_rows, h->fine_ry));
     return QG_OK;
 }
 
@@ -1166,6 +1181,7 @@ static qg_status create_ctx(const qg_basin* b, int layers, double Re, double Ro,
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dclock, sizeof(double) * 4));
     if (s == QG_OK) {
         h->fine_rows = (int)fine_tile_rows(h->esz);
+        h->fine_ry = fine_rows_per_thread(levels);
         guard(fine_maps(h));
     }
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dpart, sizeof(double) * 5 * diag_blocks()));
@@ -1703,9 +1719,10 @@ qg_status qg_bounds_check_result(int32_t* site) {
 #endif
 }
 
-qg_status qg_stencil_tile(qg_handle h, int32_t* rows) {
+qg_status qg_stencil_tile(qg_handle h, int32_t* rows, int32_t* rows_per_thread) {
     if (!h || !rows) return QG_ERR_ARG;
     *rows = h->fine_rows;
+    if (rows_per_thread) *rows_per_thread = h->fine_ry;
     return QG_OK;
 }
 

@@ -115,10 +115,11 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Shared-memory plan of one CTA (byte offsets, 128-byte aligned).
-template <typename T, int LV, bool TL = false, int RC_ = Rows<T>::value>
+template <typename T, int LV, bool TL = false, int RC_ = Rows<T>::value, int RY_ = Sweep<LV>::RY>
 struct Plan {
     static constexpr int RC = RC_;
-    static constexpr int RY = Sweep<LV>::RY;
+    static constexpr int RY = RY_;                  // fine rows swept by one thread
+    static_assert(RY % (1 << LV) == 0 && RC % RY == 0, "a group covers whole coarse cells");
     static constexpr int G = RC / RY;               // groups per CTA
     static constexpr int THREADS = 16 * G;
     // CTAs per SM the registers are budgeted for: FP32 one-layer sweeps as
@@ -143,11 +144,11 @@ struct Plan {
 // The work of one CTA: the tile (bx, by) of one basin, whose tensor maps and
 // parameters the two kernels below take from the launch (one basin) or from
 // a table in device memory (a batch of ensemble members).
-template <typename T, int LV, bool TL, int RCT>
+template <typename T, int LV, bool TL, int RCT, int RYT = Sweep<LV>::RY>
 __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtensorMap* tm_wn,
                                            const CUtensorMap* tm_p, const CUtensorMap* tm_f,
                                            const FusedParams<T>& p, int bx, int by) {
-    using PL = Plan<T, LV, TL, RCT>;
+    using PL = Plan<T, LV, TL, RCT, RYT>;
     constexpr int F = 1 << LV;
     constexpr int RC = PL::RC;
     constexpr int RY = PL::RY;
@@ -546,13 +547,14 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
     }
 }
 
-template <typename T, int LV, bool TL, int RCT>
-__global__ void __launch_bounds__(Plan<T, LV, TL, RCT>::THREADS, Plan<T, LV, TL, RCT>::MINB)
+template <typename T, int LV, bool TL, int RCT, int RYT>
+__global__ void __launch_bounds__(Plan<T, LV, TL, RCT, RYT>::THREADS,
+                                  Plan<T, LV, TL, RCT, RYT>::MINB)
 fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
                   const __grid_constant__ CUtensorMap tm_wn,
                   const __grid_constant__ CUtensorMap tm_p,
                   const __grid_constant__ CUtensorMap tm_f, FusedParams<T> p) {
-    sweep_tile<T, LV, TL, RCT>(&tm_w, &tm_wn, &tm_p, &tm_f, p, blockIdx.x, blockIdx.y);
+    sweep_tile<T, LV, TL, RCT, RYT>(&tm_w, &tm_wn, &tm_p, &tm_f, p, blockIdx.x, blockIdx.y);
 }
 
 // Batched fine stage of an ensemble: CTA c sweeps tile (tiles[c].y,
@@ -600,12 +602,12 @@ cudaError_t launch_batch(const FineMember<T>* fm, const int4* tiles, int ntiles,
     return cudaLaunchKernelEx(&cfg, fine_batch_kernel<T, LV>, fm, tiles);
 }
 
-template <typename T, int LV, bool TL, int RCT>
+template <typename T, int LV, bool TL, int RCT, int RYT = Sweep<LV>::RY>
 cudaError_t launch_sweep(const FusedParams<T>& p, const FineMaps& m, cudaStream_t s) {
-    using PL = Plan<T, LV, TL, RCT>;
+    using PL = Plan<T, LV, TL, RCT, RYT>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(fine_sweep_kernel<T, LV, TL, RCT>,
+        cudaError_t e = cudaFuncSetAttribute(fine_sweep_kernel<T, LV, TL, RCT, RYT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)PL::END);
         if (e != cudaSuccess) return e;
@@ -623,7 +625,7 @@ cudaError_t launch_sweep(const FusedParams<T>& p, const FineMaps& m, cudaStream_
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, fine_sweep_kernel<T, LV, TL, RCT>, m.w, m.wn, m.psi, m.f, p);
+    return cudaLaunchKernelEx(&cfg, fine_sweep_kernel<T, LV, TL, RCT, RYT>, m.w, m.wn, m.psi, m.f, p);
 }
 
 }  // namespace
@@ -640,12 +642,25 @@ cudaError_t launch_rows(const FusedParams<T>& p, const FineMaps& m, int levels, 
     }
 }
 
+// 4 rows per thread (half the default): the shorter CTAs shrink the last,
+// partly filled wave of a launch; l <= 2 only (a group covers whole cells)
+template <typename T, int RCT>
+cudaError_t launch_rows4(const FusedParams<T>& p, const FineMaps& m, int levels, cudaStream_t s) {
+    switch (levels) {
+        case 0: return launch_sweep<T, 0, false, RCT, 4>(p, m, s);
+        case 1: return launch_sweep<T, 1, false, RCT, 4>(p, m, s);
+        case 2: return launch_sweep<T, 2, false, RCT, 4>(p, m, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename T>
 cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int levels,
-                              cudaStream_t s, bool two_layer, int rows) {
+                              cudaStream_t s, bool two_layer, int rows, int ry) {
     constexpr int R0 = Rows<T>::value;
+    const int ry0 = levels >= 4 ? 16 : 8;
     if (two_layer) {   // l >= 1 only: the other layer's psi comes from the elliptic grid
-        if (rows != R0) return cudaErrorInvalidValue;
+        if (rows != R0 || ry != ry0) return cudaErrorInvalidValue;
         switch (levels) {
             case 1: return launch_sweep<T, 1, true, R0>(p, m, s);
             case 2: return launch_sweep<T, 2, true, R0>(p, m, s);
@@ -654,18 +669,25 @@ cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int le
             default: return cudaErrorInvalidValue;
         }
     }
-    if (rows == R0) return launch_rows<T, R0>(p, m, levels, s);
-    if constexpr (sizeof(T) == 4) {
-        if (rows == 64) return launch_rows<T, 64>(p, m, levels, s);
-        if (rows == 32) return launch_rows<T, 32>(p, m, levels, s);
+    if (ry == ry0) {
+        if (rows == R0) return launch_rows<T, R0>(p, m, levels, s);
+        if constexpr (sizeof(T) == 4) {
+            if (rows == 64) return launch_rows<T, 64>(p, m, levels, s);
+            if (rows == 32) return launch_rows<T, 32>(p, m, levels, s);
+        }
+    } else if (ry == 4) {
+        if constexpr (sizeof(T) == 4) {
+            if (rows == 64) return launch_rows4<T, 64>(p, m, levels, s);
+            if (rows == 32) return launch_rows4<T, 32>(p, m, levels, s);
+        }
     }
     return cudaErrorInvalidValue;
 }
 
 template cudaError_t launch_fine_fused<float>(const FusedParams<float>&, const FineMaps&, int,
-                                              cudaStream_t, bool, int);
+                                              cudaStream_t, bool, int, int);
 template cudaError_t launch_fine_fused<double>(const FusedParams<double>&, const FineMaps&, int,
-                                               cudaStream_t, bool, int);
+                                               cudaStream_t, bool, int, int);
 
 template <typename T>
 cudaError_t launch_fine_batch(const FineMember<T>* fm, const int4* tiles, int ntiles, int levels,
@@ -687,9 +709,13 @@ template cudaError_t launch_fine_batch<double>(const FineMember<double>*, const 
                                                bool, bool, cudaStream_t);
 
 size_t fine_tile_rows(size_t esz) { return esz == 8 ? Rows<double>::value : Rows<float>::value; }
-bool fine_rows_supported(size_t esz, int layers, int rows) {
-    if (rows == (int)fine_tile_rows(esz)) return true;
-    return esz == 4 && layers == 1 && (rows == 64 || rows == 32);
+int fine_rows_per_thread(int levels) { return levels >= 4 ? 16 : 8; }
+bool fine_rows_supported(size_t esz, int layers, int levels, int rows, int ry) {
+    const int ry0 = fine_rows_per_thread(levels);
+    if (rows == (int)fine_tile_rows(esz) && ry == ry0) return true;
+    if (esz != 4 || layers != 1) return false;
+    if (ry == ry0) return rows == 64 || rows == 32;
+    return ry == 4 && levels <= 2 && (rows == 64 || rows == 32);
 }
 int fine_part_period_x(int levels) { return TX >> levels; }
 int fine_part_period_y(int levels, int rows) { return rows >> levels; }

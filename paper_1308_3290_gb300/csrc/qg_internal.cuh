@@ -230,11 +230,12 @@ cudaError_t launch_cfl_max(const T* psi, int ldp, int nx, int ny, int levels, do
 struct FineMaps {
     CUtensorMap w, wn, psi, f;
 };
-// rows: the fine rows per CTA (fine_tile_rows, or a tuned height that
-// fine_rows_supported accepts; the tensor maps' boxes must match it)
+// rows: the fine rows per CTA and ry the fine rows each thread sweeps
+// (fine_tile_rows and fine_rows_per_thread, or a tuned pair that
+// fine_rows_supported accepts; the tensor maps' boxes must match rows)
 template <typename T>
 cudaError_t launch_fine_fused(const FusedParams<T>& p, const FineMaps& m, int levels,
-                              cudaStream_t s, bool two_layer, int rows);
+                              cudaStream_t s, bool two_layer, int rows, int ry);
 // One member of a batched fine-stage launch (ensembles): the tensor maps of
 // its stage and its parameters, in device memory (the TMA unit reads the
 // maps from there; 64-byte aligned).
@@ -250,7 +251,8 @@ template <typename T>
 cudaError_t launch_fine_batch(const FineMember<T>* fm, const int4* tiles, int ntiles, int levels,
                               bool forcing_field, bool pdl, cudaStream_t s);
 size_t fine_tile_rows(size_t esz);   // default fine rows per CTA (batched sweeps too)
-bool fine_rows_supported(size_t esz, int layers, int rows);   // other tuned heights
+int fine_rows_per_thread(int levels);   // default rows a thread sweeps
+bool fine_rows_supported(size_t esz, int layers, int levels, int rows, int ry);  // tuned pairs
 int fine_part_period_x(int levels);  // coarse columns between tile edges
 int fine_part_period_y(int levels, int rows);  // coarse rows between CTA edges
 int fine_halo_cols();                // columns of a halo box

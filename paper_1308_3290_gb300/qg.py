@@ -119,7 +119,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "qg_stats_end": [vp],
         "qg_set_timing_mask": [vp, ctypes.c_uint32],
         "qg_energy_accumulate": [vp, dbl, vp],
-        "qg_stencil_tile": [vp, ctypes.POINTER(i32)],
+        "qg_stencil_tile": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "qg_bounds_check_result": [ctypes.POINTER(i32)],
         "qg_stats_mean_q": [vp, vp, i32, ctypes.POINTER(i64)],
         "qg_get_state_async": [vp, vp, i32],
@@ -298,11 +298,12 @@ def qg_bounds_check_result() -> int:
     return r.value
 
 
-def qg_stencil_tile(h: int) -> int:
-    """Fine rows per CTA of the fused fine-grid kernel (autotuned)."""
-    r = ctypes.c_int32()
-    _check(load().qg_stencil_tile(h, ctypes.byref(r)), "qg_stencil_tile")
-    return r.value
+def qg_stencil_tile(h: int) -> tuple[int, int]:
+    """(fine rows per CTA, fine rows per thread) of the fused fine-grid
+    kernel (autotuned)."""
+    r, y = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().qg_stencil_tile(h, ctypes.byref(r), ctypes.byref(y)), "qg_stencil_tile")
+    return r.value, y.value
 
 
 def qg_get_time(h: int) -> tuple[float, float]:

@@ -50,15 +50,15 @@ def main():
         check(f"engine {engine}")
     del os.environ["QG_SOLVE_ENGINE"]
     # every fine-stage tile height, with a forcing field and the adaptive step
-    for rows in (128, 64, 32):
-        os.environ["QG_FINE_ROWS"] = str(rows)
-        for lv in (0, 1, 2, 3, 4):
+    for tile in ("128", "64", "32", "64x4", "32x4"):
+        os.environ["QG_FINE_ROWS"] = tile
+        for lv in ((0, 1, 2) if "x4" in tile else (0, 1, 2, 3, 4)):
             b = basin(256, 512, lv, "f32")
             b.set_forcing(inputs.perturbed_forcing_field(256, 512, seed=3, Ro=0.0016))
             qg.qg_set_cfl(b.h, 0.5)
             run_steps(b, 256, 512)
             b.close()
-        check(f"tile {rows}")
+        check(f"tile {tile}")
     del os.environ["QG_FINE_ROWS"]
     # transfers
     b = basin(128, 256, 3, "f32")

@@ -60,20 +60,24 @@ def test_fp32_100_steps(levels):
     assert_fields_close(got, ref, 1e-4)
 
 
-@pytest.mark.parametrize("rows", [128, 64, 32])
-@pytest.mark.parametrize("levels", [0, 1, 2, 3])
-def test_each_stencil_tile_matches_oracle(rows, levels, monkeypatch):
-    """Every fine-stage tile height the autotuner may pick (forced through
-    QG_FINE_ROWS) follows the oracle: FP32, 100 steps, within 1e-4 element
-    by element, with the tile seams of that height checked on their own."""
+TILES = [(rows, ry, lv) for lv in (0, 1, 2, 3) for rows, ry in
+         ((128, 8), (64, 8), (32, 8), (64, 4), (32, 4)) if ry == 8 or lv <= 2]
+
+
+@pytest.mark.parametrize("rows,ry,levels", TILES)
+def test_each_stencil_tile_matches_oracle(rows, ry, levels, monkeypatch):
+    """Every fine-stage tile the autotuner may pick (rows per CTA, rows per
+    thread; forced through QG_FINE_ROWS) follows the oracle: FP32, 100
+    steps, within 1e-4 element by element, with the tile seams of that
+    height checked on their own."""
     require_gpu()
     nx, ny = 128, 256
-    monkeypatch.setenv("QG_FINE_ROWS", str(rows))
+    monkeypatch.setenv("QG_FINE_ROWS", f"{rows}x{ry}")
     w0 = inputs.perturbation(nx, ny, seed=16) * 50.0
     ob = O.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=5e-5)
     ref = O.run(w0, ob, 100)
     b = qg.Basin(nx, ny, Re=200.0, Ro=0.0016, levels=levels, dt=5e-5, dtype="f32")
-    assert qg.qg_stencil_tile(b.h) == rows
+    assert qg.qg_stencil_tile(b.h) == (rows, ry)
     b.set_state(w0)
     b.step(100)
     got = to_np(b.state())

@@ -129,8 +129,8 @@ def test_batched_solve_queue_claims_dependencies_first():
 TX, SWX = 64, 72
 
 
-def plan(esz, lv, tl, rc):
-    ry = max(1 << lv, 8)
+def plan(esz, lv, tl, rc, ry=None):
+    ry = ry if ry is not None else max(1 << lv, 8)
     G = rc // ry
     F = 1 << lv
     CPX, CPY = TX // F + 4, rc // F + 3
@@ -147,14 +147,16 @@ def plan(esz, lv, tl, rc):
     return dict(RY=ry, G=G, THREADS=16 * G, F=F, CPX=CPX, CPY=CPY, END=END)
 
 
-FUSED = ([(4, lv, False, rc) for lv in range(5) for rc in (128, 64, 32)]
-         + [(8, lv, False, 64) for lv in range(5)]
-         + [(esz, lv, True, 128 if esz == 4 else 64) for esz in (4, 8) for lv in range(1, 5)])
+FUSED = ([(4, lv, False, rc, None) for lv in range(5) for rc in (128, 64, 32)]
+         + [(4, lv, False, rc, 4) for lv in range(3) for rc in (64, 32)]
+         + [(8, lv, False, 64, None) for lv in range(5)]
+         + [(esz, lv, True, 128 if esz == 4 else 64, None) for esz in (4, 8) for lv in range(1, 5)])
 
 
-@pytest.mark.parametrize("esz,lv,tl,rc", FUSED)
-def test_fused_tile_indices_stay_in_shared_memory(esz, lv, tl, rc):
-    pl = plan(esz, lv, tl, rc)
+@pytest.mark.parametrize("esz,lv,tl,rc,ry", FUSED)
+def test_fused_tile_indices_stay_in_shared_memory(esz, lv, tl, rc, ry):
+    pl = plan(esz, lv, tl, rc, ry)
+    assert pl["RY"] % (1 << lv) == 0
     assert pl["END"] <= 200 * 1024                     # dynamic shared memory of a CTA
     assert rc % pl["RY"] == 0 and rc % pl["F"] == 0
     lanes = np.arange(16)
