@@ -425,6 +425,19 @@ def ensemble_variant(torch, qg, inputs, stream, flush, K=50):
     return out
 
 
+def ensemble_vs_single(ens, variants):
+    """The ensemble's fine point-steps/s against the single 2048x4096 basin's
+    in the same run: against the l = 2 rate alone, and against the time its
+    members would take at the single basin's per-point rate of their own
+    level (l = 1 members do twice the elliptic work per fine point)."""
+    pts = (NX - 1) * (NY - 1)
+    rate = {lv: variants[f"cgp_l{lv}_f32"]["steps_per_s"] * pts for lv in (1, 2)}
+    members = ensemble_members()
+    want_s = sum((m["nx"] - 1) * (m["ny"] - 1) / rate[m["levels"]] for m in members)
+    return {"fine_point_rate_frac_of_l2": ens["fine_point_steps_per_s"] / rate[2],
+            "level_matched_frac": want_s / (ens["ms_per_step"] / 1e3)}
+
+
 def adjoint_variant(torch, qg, inputs, stream, N=2000, first=1500):
     """Gradient of the kinetic energy averaged over steps 1500..2000 with
     respect to the forcing field, 256x512 basin, l = 1, FP32: forward sweep
@@ -623,7 +636,8 @@ def ours(args):
                                                   "ms_per_step": sum(ts) / 100}
         b.close()
         variants["small_64x128_l1_f32"] = small_basin_variant(torch, qg, inputs, stream, flush)
-        variants["ensemble_96_f32"] = ensemble_variant(torch, qg, inputs, stream, flush)
+        variants["ensemble_96_f32"] = ens = ensemble_variant(torch, qg, inputs, stream, flush)
+        ens["vs_single_basin"] = ensemble_vs_single(ens, variants)
         variants["adjoint_256x512_l1_f32"] = adjoint_variant(torch, qg, inputs, stream)
 
     cpu = None
