@@ -590,7 +590,8 @@ def ours(args):
                 qg.qg_step(b.h, 1)
             K = 200 if dt == "f32" else 20
             ts = time_steps(torch, qg, b.h, stream, K, flush)
-            variants[name] = {"steps_per_s": K / (sum(ts) / 1e3), "ms_per_step": sum(ts) / K}
+            variants[name] = {"steps_per_s": K / (sum(ts) / 1e3), "ms_per_step": sum(ts) / K,
+                              "solve_engine": qg.qg_solve_engine(b.h)}
             if name == "full_grid_l0_f32":
                 # the full-grid solve streams from HBM (its fields exceed L2)
                 kt = kernel_timing(torch, qg, b.h, stream, 50, flush)

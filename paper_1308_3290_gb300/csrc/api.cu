@@ -333,7 +333,10 @@ qg_status get_level(qg_ctx* h, int lv, const LevelTables** out) {
     if (s == QG_OK) s = get_twiddles(h, t.my, &t.twy);
     for (int r = 0; r < 3 && s == QG_OK; ++r) {
         const int rad = warp_engine_radix(32 + r);
-        if (!solve32_supports(t.mx, t.my, rad, h->esz)) continue;
+        // radix 16 (r = 1) also serves engine 50
+        if (!solve32_supports(t.mx, t.my, rad, h->esz) &&
+            !(rad == 16 && stream_supports(t.mx, t.my, h->esz)))
+            continue;
         s = get_pass_table(h, 2 * t.mx, rad, &t.ptx[r]);
         if (s == QG_OK) s = get_pass_table(h, 2 * t.my, rad, &t.pty[r]);
     }
@@ -517,8 +520,10 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
     P.twx = static_cast<const C*>(t.twx);
     P.twy = static_cast<const C*>(t.twy);
     const int eng = engine ? engine : engine_for(h, t.mx, t.my);
-    P.ptx = is_warp_engine(eng) ? static_cast<const C*>(t.ptx[eng - 32]) : nullptr;
-    P.pty = is_warp_engine(eng) ? static_cast<const C*>(t.pty[eng - 32]) : nullptr;
+    const int tab = eng == kStreamEngine ? 1 : eng - 32;   // engine 50: radix-16 tables
+    const bool fft_tab = is_warp_engine(eng) || eng == kStreamEngine;
+    P.ptx = fft_tab ? static_cast<const C*>(t.ptx[tab]) : nullptr;
+    P.pty = fft_tab ? static_cast<const C*>(t.pty[tab]) : nullptr;
     P.lamx = static_cast<const T*>(t.lamx);
     P.lamy = static_cast<const T*>(t.lamy);
     P.scale = (T)((2.0 / t.mx) * (2.0 / t.my));
@@ -532,6 +537,7 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
     P.err = h->derr;
     P.split = h->split_solve ? 1 : 0;
     KTimer kt(h, s, QG_K_SOLVE);
+    if (h->capturing && !h->split_solve) h->kernels_per_step += solve_launches(eng) - 1;
     if (eng == kMatrixEngine) {
         // one launch whether or not the FFT solves are split
         if (h->capturing && h->split_solve) h->kernels_per_step -= 2;
@@ -550,14 +556,15 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
 // radix 4: many threads per sequence pair, or 16: fewer passes and
 // instructions; or the warp-group engine of solve32.cu with 32, 16 or 8
 // values per thread, engines 32, 33, 34; or, on small one-layer FP32 grids,
-// the matrix-form solve on the tensor cores of solve_mtx.cu, engine 40) is
+// the matrix-form solve on the tensor cores of solve_mtx.cu, engine 40; or
+// the register-resident radix-16 passes of solve_stream.cu, engine 50) is
 // chosen per handle when it is created, by timing a few whole steps with each
 // engine that supports the elliptic grid (the solve alone, timed back to
 // back, ranks them differently: in a step the fine sweep has just streamed
 // its fields through L2), and the fastest is kept.  Results are cached per
 // (nx, ny, levels, layers, dtype) for the process and, when the environment
 // variable QG_TUNE_CACHE names a file, in that file (one line
-// "nx ny levels layers esz engine" per entry).  QG_SOLVE_ENGINE=4|16|32|33|34|40
+// "nx ny levels layers esz engine" per entry).  QG_SOLVE_ENGINE=4|16|32|33|34|40|50
 // forces a choice where that engine supports the grid.  Other grids use the
 // size rule.
 
@@ -572,6 +579,7 @@ int engine_for(qg_ctx* h, int mx, int my) {
 // Whether engine e can solve the level with tables t on handle h.
 bool engine_ok(const qg_ctx* h, const LevelTables* t, size_t esz, int e) {
     if (e == kMatrixEngine) return t->mtab && mtx_supports(t->mx, t->my, esz, h->layers);
+    if (e == kStreamEngine) return solve_engine_supports(t->mx, t->my, esz, e) && t->ptx[1];
     return solve_engine_supports(t->mx, t->my, esz, e) && (!is_warp_engine(e) || t->ptx[e - 32]);
 }
 
@@ -619,7 +627,7 @@ void tune_file_load() {
     if (!f) return;
     int a, b, c, d, x, e, r, y;
     while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &a, &b, &c, &d, &x, &e, &r, &y) == 8)
-        if ((e == 4 || e == 16 || is_warp_engine(e) || e == kMatrixEngine) &&
+        if ((e == 4 || e == 16 || is_warp_engine(e) || e == kMatrixEngine || e == kStreamEngine) &&
             fine_rows_supported((size_t)x, d, c, r, y))
             g_tune_cache[TuneKey(a, b, c, d, x)] = {e, r, y};
     std::fclose(f);
@@ -729,14 +737,15 @@ qg_status autotune_solve(qg_ctx* h) {
     const float t34 = time_steps<T>(h, 34);
     const float t16 = time_steps<T>(h, 16);
     const float t40 = time_steps<T>(h, kMatrixEngine);
+    const float t50 = time_steps<T>(h, kStreamEngine);
     // a candidate that cannot run on this grid is a tuning result, not an error
     h->latched = QG_OK;
     (void)cudaGetLastError();
     drop_graph(h);
-    const float tt[6] = {t4, t16, t32, t33, t34, t40};
-    const int ee[6] = {4, 16, 32, 33, 34, kMatrixEngine};
+    const float tt[7] = {t4, t16, t32, t33, t34, t40, t50};
+    const int ee[7] = {4, 16, 32, 33, 34, kMatrixEngine, kStreamEngine};
     int best = 0;
-    for (int k = 1; k < 6; ++k)
+    for (int k = 1; k < 7; ++k)
         if (tt[k] < tt[best]) best = k;
     if (tt[best] >= 1e29f) return fail(h, QG_ERR_CUDA);
     h->solve_engine = ee[best];
@@ -1707,7 +1716,7 @@ qg_status qg_bounds_check_result(int32_t* site) {
     }
     int first = 0;
     for (int v : {bounds_site_fused(), bounds_site_solve32(), bounds_site_stencil(),
-                  bounds_site_mtx()}) {
+                  bounds_site_mtx(), bounds_site_stream()}) {
         if (v < 0) return QG_ERR_CUDA;
         if (!first) first = v;
     }

@@ -113,6 +113,15 @@ bool solve32_supports(int mx, int my, int rad, size_t esz);
 // engines 32, 33, 34: the warp-group engine with 32, 16, 8 values per thread
 inline int warp_engine_radix(int engine) { return engine == 34 ? 8 : (engine == 33 ? 16 : 32); }
 inline bool is_warp_engine(int engine) { return engine >= 32 && engine <= 34; }
+// engine 50: one CTA per sequence pair, three launches, radix-16 passes
+// with the values in registers (solve_stream.cu); it takes the radix-16
+// pass tables of engine 33 (ptx/pty)
+constexpr int kStreamEngine = 50;
+bool stream_supports(int mx, int my, size_t esz);
+template <typename T>
+cudaError_t launch_solve_stream(const SolveParams<T>& P, cudaStream_t s);
+// the kernels one solve of an engine launches
+inline int solve_launches(int engine) { return engine == kStreamEngine ? 3 : 1; }
 
 // Full-weighting restriction applied `levels` times, as one hat-weighted
 // sum (fine -> level `levels`), interior coarse nodes only.
@@ -340,6 +349,7 @@ int bounds_site_fused();
 int bounds_site_solve32();
 int bounds_site_stencil();
 int bounds_site_mtx();
+int bounds_site_stream();
 
 // Copies between the dense exchange layout and the padded node layout.
 cudaError_t copy_in(void* padded, int ld, const void* dense, int nxm1,

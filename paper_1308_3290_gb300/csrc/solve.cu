@@ -406,6 +406,7 @@ size_t solve_smem_bytes(int mx, int my, size_t esz, int engine) {
 }
 
 bool solve_engine_supports(int mx, int my, size_t esz, int engine) {
+    if (engine == kStreamEngine) return stream_supports(mx, my, esz);
     if (is_warp_engine(engine)) {
         const int rad = warp_engine_radix(engine);
         return solve32_supports(mx, my, rad, esz) &&
@@ -430,6 +431,7 @@ static cudaError_t launch_engine(const SolveParams<T>& P, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_solve(const SolveParams<T>& P, int engine, cudaStream_t s) {
     if (is_warp_engine(engine)) return launch_solve32<T>(P, warp_engine_radix(engine), s);
+    if (engine == kStreamEngine) return launch_solve_stream<T>(P, s);
     if (P.batch) return cudaErrorInvalidValue;   // batches: warp-group engines only
     return engine == 4 ? launch_engine<T, 4>(P, s) : launch_engine<T, 16>(P, s);
 }

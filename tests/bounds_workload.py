@@ -48,6 +48,23 @@ def main():
                 b.poisson_solve(inputs.smooth_field(nx >> lv, ny >> lv, seed=2), lv)
                 b.close()
         check(f"engine {engine}")
+    # engine 50 (sides of 512 intervals and more): remainder passes of radix
+    # 2, 4 and 8 and none, 1, 2 and 4 pairs per CTA, one and two layers
+    os.environ["QG_SOLVE_ENGINE"] = "50"
+    for dtype in ("f32", "f64"):
+        for nx, ny, lv in ((512, 1024, 0), (1024, 2048, 1), (2048, 512, 0), (512, 4096, 0)):
+            b = basin(nx, ny, lv, dtype)
+            run_steps(b, nx, ny)
+            b.poisson_solve(inputs.smooth_field(nx >> lv, ny >> lv, seed=2), lv)
+            b.close()
+        b = qg.Basin(512, 512, Re=697.16, Ro=2.49e-4, levels=0, dt=1e-5, dtype=dtype, layers=2,
+                     Fr=0.087, delta=0.2, sigma=1.43e-3, y0=-0.5, y1=0.5)
+        b.set_state(inputs.smooth_field(512, 512, seed=5, amp=0.05), 0)
+        b.set_state(inputs.smooth_field(512, 512, seed=6, amp=0.02), 1)
+        b.step(3)
+        b.synchronize()
+        b.close()
+    check("engine 50")
     del os.environ["QG_SOLVE_ENGINE"]
     # every fine-stage tile height, with a forcing field and the adaptive step
     for tile in ("128", "64", "32", "64x4", "32x4"):
