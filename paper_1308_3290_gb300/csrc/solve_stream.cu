@@ -128,13 +128,42 @@ __device__ __forceinline__ void mid_pass(Cplx<T> (&v)[16], CT<T>* buf, int t,
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = ldsl<T>(buf, rb + r * Ln::SG, Ln::LIM);
     sy.sync();
+    // twiddles w^r = e^{-2 pi i r k / (16 NS)}: w, w^2, w^4 and w^8 from the
+    // table, the other powers as products (at most three roundings deep)
     const CT<T>* tp = tw + tw_off(P) + (t & (NS - 1));
-#pragma unroll
-    for (int r = 1; r < 16; ++r) {
-        const CT<T> w = __ldg(tp + r * NS);
-        v[r] = cmul(v[r], w.x, w.y);
+    Cplx<T> w[16];
+    {
+        const CT<T> a = __ldg(tp + NS), b = __ldg(tp + 2 * NS), c = __ldg(tp + 4 * NS),
+                    d = __ldg(tp + 8 * NS);
+        w[1] = Cplx<T>{a.x, a.y};
+        w[2] = Cplx<T>{b.x, b.y};
+        w[4] = Cplx<T>{c.x, c.y};
+        w[8] = Cplx<T>{d.x, d.y};
     }
+    w[3] = cmul(w[2], w[1].x, w[1].y);
+    w[5] = cmul(w[4], w[1].x, w[1].y);
+    w[6] = cmul(w[4], w[2].x, w[2].y);
+    w[7] = cmul(w[4], w[3].x, w[3].y);
+#pragma unroll
+    for (int r = 1; r < 8; ++r) w[8 + r] = cmul(w[8], w[r].x, w[r].y);
+#pragma unroll
+    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], w[r].x, w[r].y);
     dft<T, 16>(v);
+}
+
+// e^{-2 pi i m / 16}, m = 0..15, as compile-time constants
+template <typename T>
+__device__ __forceinline__ Cplx<T> w16(int m) {
+    const T c1 = K16<T>::c1, s1 = K16<T>::s1, r2 = K16<T>::r2;
+    const T cs[4] = {T(1), c1, r2, s1}, sn[4] = {T(0), s1, r2, c1};
+    const int q = m >> 2, e = m & 3;
+    const T c = cs[e], s = sn[e];   // e^{-i pi e / 8} = c - i s
+    switch (q) {                    // times (-i)^q
+        case 0: return Cplx<T>{c, -s};
+        case 1: return Cplx<T>{-s, -c};
+        case 2: return Cplx<T>{-c, s};
+        default: return Cplx<T>{s, c};
+    }
 }
 
 // The remainder pass (radix R = 2^REM, B = 16/R butterflies j = t + b G per
@@ -153,12 +182,21 @@ __device__ __forceinline__ void rem_pass(Cplx<T> (&v)[16], CT<T>* buf, int t,
 #pragma unroll
         for (int r = 0; r < R; ++r) u[b][r] = ldsl<T>(buf, rb + b * Ln::SG + r * SNSR, Ln::LIM);
     sy.sync();
-    const CT<T>* tp = tw + tw_off(Ln::NP) + t;   // j = t + b G < NSR: twiddle index j
+    // twiddle of butterfly j = t + b G: e^{-2 pi i r j / L} = e^{-2 pi i r t / L}
+    // e^{-2 pi i r b / 16} (G = L / 16): R - 1 table loads per thread
+    const CT<T>* tp = tw + tw_off(Ln::NP) + t;
+    Cplx<T> wt[R];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+        const CT<T> a = __ldg(tp + r * NSR);
+        wt[r] = Cplx<T>{a.x, a.y};
+    }
 #pragma unroll
     for (int b = 0; b < B; ++b) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-            const CT<T> w = __ldg(tp + r * NSR + b * Ln::G);
+            const Cplx<T> c = w16<T>((r * b) & 15);
+            const Cplx<T> w = b == 0 ? wt[r] : cmul(wt[r], c.x, c.y);
             u[b][r] = cmul(u[b][r], w.x, w.y);
         }
         dft<T, R>(u[b]);
@@ -276,12 +314,13 @@ __device__ __forceinline__ void load_rows(const T* sa, const T* sb, bool va, boo
     for (int r = 0; r < 8; ++r) v[r] = Cplx<T>{a[r], b[r]};
 }
 
-// Pairs per CTA of the passes that write transposed: 4, fewer while the CTA
-// would exceed 1024 threads (FP32) or 512 (FP64, 128 registers per thread)
-// or 140 KB of shared memory.
+// Pairs per CTA of the passes that write transposed: `want`, fewer while
+// the CTA would exceed 1024 threads (FP32) or 512 (FP64, 128 registers per
+// thread) or 140 KB of shared memory.
+constexpr int kPpcX = 4, kPpcY = 4;   // x forward pass, y pass
 template <typename T>
-__host__ __device__ constexpr int ppc_for(int lg) {
-    int p = 4;
+__host__ __device__ constexpr int ppc_for(int lg, int want) {
+    int p = want;
     while (p > 1 && (((1 << lg) / 16) * p > (sizeof(T) == 4 ? 1024 : 512) ||
                      (long long)p * buf_elems(1 << lg) * (long long)sizeof(T) * 2 > 140 * 1024))
         p /= 2;
@@ -453,7 +492,7 @@ constexpr int kMinLg = 10, kMaxLg = 14;
 
 template <typename T, int OPY, int PH, int LG>
 cudaError_t launch_pass(const SolveParams<T>& P, int npairs, cudaStream_t s) {
-    constexpr int PPC = PH == 2 ? 1 : ppc_for<T>(LG);
+    constexpr int PPC = PH == 2 ? 1 : ppc_for<T>(LG, PH == 0 ? kPpcX : kPpcY);
     constexpr int G = Len<LG>::G;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((npairs + PPC - 1) / PPC);
