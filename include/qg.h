@@ -282,7 +282,7 @@ qg_status qg_set_solver(qg_handle h, qg_solver kind, int32_t cycles);
  * the tensor cores, 3xTF32 (one-layer FP32 grids of at most 64 x 128 or
  * 128 x 64 intervals); 50: radix-16 FFT passes with the values in
  * registers, one to four sequence pairs per CTA and three launches (one
- * per pass), for elliptic grids of 512 to 8192 intervals a side (4096 in
+ * per pass), for elliptic grids of 256 to 8192 intervals a side (4096 in
  * FP64); 0:
  * the multigrid solver (qg_set_solver).  These are
  * implementations of the same sine-transform solve of Section 4.3, equal to

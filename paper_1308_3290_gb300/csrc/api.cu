@@ -2153,8 +2153,9 @@ qg_status ens_alloc(qg_ensemble e, void** p, size_t bytes) {
     return QG_OK;
 }
 
-// The engines a group of members can solve with in one launch: the
-// warp-group FFT engines and the matrix form that take the group's grid;
+// The engines a group of members can solve with in one launch (three for
+// engine 50): the warp-group FFT engines, the matrix form and engine 50
+// where they take the group's grid;
 // none when a member uses the multigrid solver.  An engine forced through
 // QG_SOLVE_ENGINE is the only candidate, and none when it does not batch
 // (then every member solves as a handle of its own would).
@@ -2167,11 +2168,12 @@ std::vector<int> batch_engines(qg_ensemble e, const EnsSolveGroup& g) {
     if (get_level(h0, h0->levels, &t) != QG_OK) return out;
     const int own = h0->solve_engine;
     if (h0->engine_forced) {
-        if ((is_warp_engine(own) || own == kMatrixEngine) && engine_ok(h0, t, h0->esz, own))
+        if ((is_warp_engine(own) || own == kMatrixEngine || own == kStreamEngine) &&
+            engine_ok(h0, t, h0->esz, own))
             out.push_back(own);
         return out;
     }
-    for (int cand : {34, 33, 32, (int)kMatrixEngine})
+    for (int cand : {34, 33, 32, (int)kMatrixEngine, (int)kStreamEngine})
         if (engine_ok(h0, t, h0->esz, cand)) out.push_back(cand);
     return out;
 }
@@ -2350,9 +2352,10 @@ qg_status group_solve(qg_ensemble e, const EnsSolveGroup& g, int engine, int k, 
     P.ld_tr = h0->ld_t;
     P.twx = static_cast<const C*>(t->twx);
     P.twy = static_cast<const C*>(t->twy);
-    if (is_warp_engine(engine)) {
-        P.ptx = static_cast<const C*>(t->ptx[engine - 32]);
-        P.pty = static_cast<const C*>(t->pty[engine - 32]);
+    if (is_warp_engine(engine) || engine == kStreamEngine) {
+        const int tab = engine == kStreamEngine ? 1 : engine - 32;   // engine 50: radix 16
+        P.ptx = static_cast<const C*>(t->ptx[tab]);
+        P.pty = static_cast<const C*>(t->pty[tab]);
     }
     P.lamx = static_cast<const T*>(t->lamx);
     P.lamy = static_cast<const T*>(t->lamy);
@@ -2449,7 +2452,7 @@ qg_status group_enqueue(qg_ensemble e, const EnsSolveGroup& g, cudaStream_t s) {
             }
         } else {
             QG_TRY_E(group_solve<T>(e, g, g.engine, k, s));
-            ++e->kernels;
+            e->kernels += solve_launches(g.engine);
         }
         if (k == 0) {
             for (int i : g.members) {

@@ -349,16 +349,33 @@ __host__ __device__ constexpr int stage_pitch(int ppc) { return 2 * ppc + (ppc >
 //                   x-mode ka).
 // The transposed outputs (tr, work) of the CTA's pairs are staged in shared
 // memory and written as runs of 2 PPC values per row.
+// Batches (ensembles, one layer): member blockIdx.x / cpm takes CTAs
+// blockIdx.x mod cpm, with its arrays from P.batch.
 template <typename T, int OPY, int PH, int LG, int PPC>
 __global__ void __launch_bounds__(Len<LG>::G * PPC, minb_for<T>(Len<LG>::G * PPC))
-stream_kernel(SolveParams<T> P, int npairs) {
+stream_kernel(SolveParams<T> Pin, int npairs, int cpm) {
     using Ln = Len<LG>;
     constexpr bool YP = PH == 1;
     constexpr int G = Ln::G;
     extern __shared__ __align__(16) unsigned char smem[];
+    SolveParams<T> P = Pin;
+    int blk = blockIdx.x;
+    if (Pin.batch) {
+        const int m = blk / cpm;
+        blk -= m * cpm;
+        const SolveMember<T>& M = Pin.batch[m];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) P.in[0][q] = M.in[q];
+        P.nin = M.nin;
+        P.part_px = M.part_px;
+        P.part_py = M.part_py;
+        P.tr[0] = M.tr;
+        P.work[0] = M.work;
+        P.out[0] = M.out;
+    }
     const int grp = PPC == 1 ? 0 : (int)threadIdx.x / G;
     const int t = (int)threadIdx.x - grp * G;
-    const int pair0 = blockIdx.x * PPC, pair = pair0 + grp;
+    const int pair0 = blk * PPC, pair = pair0 + grp;
     const bool vp = pair < npairs;
     CT<T>* buf = reinterpret_cast<CT<T>*>(smem) + grp * Ln::LIM;
     const GSync sy{1 + grp, G, PPC == 1};
@@ -487,15 +504,16 @@ stream_kernel(SolveParams<T> P, int npairs) {
     }
 }
 
-// Lengths 2^LG of the engine: L = 1024 .. 16384 (FP32), .. 8192 (FP64).
-constexpr int kMinLg = 10, kMaxLg = 14;
+// Lengths 2^LG of the engine: L = 512 .. 16384 (FP32), .. 8192 (FP64).
+constexpr int kMinLg = 9, kMaxLg = 14;
 
 template <typename T, int OPY, int PH, int LG>
 cudaError_t launch_pass(const SolveParams<T>& P, int npairs, cudaStream_t s) {
     constexpr int PPC = PH == 2 ? 1 : ppc_for<T>(LG, PH == 0 ? kPpcX : kPpcY);
     constexpr int G = Len<LG>::G;
+    const int cpm = (npairs + PPC - 1) / PPC;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((npairs + PPC - 1) / PPC);
+    cfg.gridDim = dim3(cpm * (P.batch ? P.nbatch : 1));
     cfg.blockDim = dim3(G * PPC);
     const size_t fft_bytes = (size_t)PPC * Len<LG>::LIM * sizeof(CT<T>);
     const size_t stg_bytes = PH == 2 ? 0 : (size_t)Len<LG>::N * stage_pitch(PPC) * sizeof(T);
@@ -504,19 +522,22 @@ cudaError_t launch_pass(const SolveParams<T>& P, int npairs, cudaStream_t s) {
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
+    // (ensemble branches run side by side: a dependent started early would
+    // hold SM resources idle, so their launches may go without)
+    cfg.attrs = P.no_pdl ? nullptr : at;
+    cfg.numAttrs = P.no_pdl ? 0 : 1;
     auto k = stream_kernel<T, OPY, PH, LG, PPC>;
     cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cfg.dynamicSmemBytes);
     if (e != cudaSuccess) return e;
-    return cudaLaunchKernelEx(&cfg, k, P, npairs);
+    return cudaLaunchKernelEx(&cfg, k, P, npairs, cpm);
 }
 
 template <typename T, int OPY, int PH>
 cudaError_t launch_lg(const SolveParams<T>& P, int lg, int npairs, cudaStream_t s) {
     switch (lg) {
+        case 9: return launch_pass<T, OPY, PH, 9>(P, npairs, s);
         case 10: return launch_pass<T, OPY, PH, 10>(P, npairs, s);
         case 11: return launch_pass<T, OPY, PH, 11>(P, npairs, s);
         case 12: return launch_pass<T, OPY, PH, 12>(P, npairs, s);
@@ -550,7 +571,8 @@ bool stream_supports(int mx, int my, size_t esz) {
 
 template <typename T>
 cudaError_t launch_solve_stream(const SolveParams<T>& P, cudaStream_t s) {
-    if (!stream_supports(P.mx, P.my, sizeof(T)) || !P.ptx || !P.pty || P.batch)
+    if (!stream_supports(P.mx, P.my, sizeof(T)) || !P.ptx || !P.pty ||
+        (P.batch && (P.layers != 1 || P.nbatch < 1)))
         return cudaErrorInvalidValue;
     return P.layers == 2 ? launch_all<T, 2>(P, s) : launch_all<T, 1>(P, s);
 }

@@ -111,7 +111,8 @@ def test_ensemble_of_96_basins_steps():
     # batched: one solve launch per elliptic-grid group, one fine launch per
     # level, per stage
     n_solve, n_fine = _groups(members)
-    assert ens.kernel_count() <= 3 * (n_solve + n_fine) <= 40
+    assert n_solve + n_fine == 13
+    assert ens.kernel_count() <= 3 * (3 * n_solve + n_fine)   # engine 50: 3 per solve
     ens.step(5)
     ens.synchronize()
     for i in (0, 17, 95):

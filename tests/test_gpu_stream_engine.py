@@ -1,7 +1,7 @@
 """Engine 50 of the elliptic solve (solve_stream.cu: radix-16 passes with
 the values in registers, one CTA per sequence pair, three launches) against
 the oracle's sine-transform solve of Section 4.3 (Eqs. ffft-1, ialpha,
-ifft-1): every length it takes (FFT lengths 1024 to 16384, with radix-2, 4
+ifft-1): every length it takes (FFT lengths 512 to 16384, with radix-2, 4
 and 8 remainder passes and none; 1, 2 and 4 sequence pairs per CTA), one
 and two layers, FP64 and FP32, element-wise; the exact discrete
 eigenmodes; and the whole step."""
@@ -33,11 +33,12 @@ def _force_engine(monkeypatch):
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("nx,ny", [
-    (512, 512), (512, 1024), (1024, 512), (2048, 512), (512, 4096), (2048, 4096),
+    (256, 512), (512, 256), (512, 1024), (1024, 512), (2048, 512), (512, 4096),
+    (2048, 4096),
 ])
 def test_poisson_parity(dtype, nx, ny):
-    """FFT lengths 2N = 1024 (remainder radix 4), 2048 (8), 4096 (none),
-    8192 (2); the 2048 x 4096 full grid is the l = 0 workload."""
+    """FFT lengths 2N = 512 (remainder radix 2), 1024 (4), 2048 (8), 4096
+    (none), 8192 (2); the 2048 x 4096 full grid is the l = 0 workload."""
     require_gpu()
     b = basin(nx, ny, dtype)
     rhs = inputs.smooth_field(nx, ny, seed=nx + 3 * ny, noise=0.3)
@@ -105,8 +106,7 @@ def test_two_layer_solve(dtype):
 
 def test_fp64_step_matches_oracle():
     """FP64 CGPRK3 steps against the oracle: 20 of a 512 x 1024 basin at
-    l = 0 and 8 of a 1024 x 2048 one at l = 1 (elliptic grid 512 x 1024: the
-    engine takes sides of 512 intervals and more)."""
+    l = 0 and 8 of a 1024 x 2048 one at l = 1 (elliptic grid 512 x 1024)."""
     require_gpu()
     for nx, ny, lv, n in ((512, 1024, 0, 20), (1024, 2048, 1, 8)):
         w0 = inputs.perturbation(nx, ny, seed=3) * 50.0
@@ -129,3 +129,39 @@ def test_launch_count(monkeypatch):
     assert qg.qg_solve_engine(b.h) == 33
     assert n50 == qg.qg_step_kernel_count(b.h) + 6
     b.close()
+
+
+def test_batched_in_an_ensemble_equals_standalone_handles():
+    """Ensemble groups solve with engine 50 as one batch (three launches per
+    group and stage, members' CTAs side by side): bitwise the states of
+    stand-alone handles with the same engine.  The first and third members
+    share an elliptic grid (256 x 512, spacing 1/256) at different levels."""
+    require_gpu()
+    from tests.test_gpu_ensemble import _groups
+    members = [
+        dict(nx=512, ny=1024, Re=200.0, Ro=0.0016, levels=1, dt=2e-5, amp=1.0),
+        dict(nx=1024, ny=512, Re=450.0, Ro=0.0036, levels=1, dt=2e-5, amp=0.7),
+        dict(nx=1024, ny=2048, Re=312.5, Ro=0.0025, levels=2, dt=1e-5, amp=1.3),
+        dict(nx=512, ny=512, Re=800.0, Ro=0.0016, levels=0, dt=1e-5, amp=0.5),
+    ]
+    ens = qg.Ensemble(members, dtype="f32")
+    solo = [qg.Basin(m["nx"], m["ny"], Re=m["Re"], Ro=m["Ro"], levels=m["levels"], dt=m["dt"],
+                     amp=m["amp"], dtype="f32") for m in members]
+    for b in solo:
+        assert qg.qg_solve_engine(b.h) == 50
+    for i, m in enumerate(members):
+        w = inputs.perturbation(m["nx"], m["ny"], seed=60 + i) * 50.0
+        ens.member(i).set_state(w)
+        solo[i].set_state(w)
+    ens.step(4)
+    for b in solo:
+        b.step(4)
+    ens.synchronize()
+    for i, b in enumerate(solo):
+        b.synchronize()
+        assert np.array_equal(to_np(ens.member(i).state()), to_np(b.state())), i
+        b.close()
+    n_solve, n_fine = _groups(members)
+    assert n_solve == 3
+    assert ens.kernel_count() == 3 * (3 * n_solve + n_fine)
+    ens.close()
