@@ -2452,7 +2452,7 @@ qg_status group_enqueue(qg_ensemble e, const EnsSolveGroup& g, cudaStream_t s) {
             }
         } else {
             QG_TRY_E(group_solve<T>(e, g, g.engine, k, s));
-            e->kernels += solve_launches(g.engine);
+            e->kernels += solve_launches(g.engine, g.mx, g.my, true);
         }
         if (k == 0) {
             for (int i : g.members) {

@@ -120,8 +120,13 @@ constexpr int kStreamEngine = 50;
 bool stream_supports(int mx, int my, size_t esz);
 template <typename T>
 cudaError_t launch_solve_stream(const SolveParams<T>& P, cudaStream_t s);
-// the kernels one solve of an engine launches
-inline int solve_launches(int engine) { return engine == kStreamEngine ? 3 : 1; }
+// batched engine-50 solves that run as one work-queue launch
+bool stream_queue_ok(int mx, int my, int layers);
+// the kernels one solve of an engine launches (a batch of members: `batch`)
+inline int solve_launches(int engine, int mx = 0, int my = 0, bool batch = false) {
+    if (engine != kStreamEngine) return 1;
+    return batch && stream_queue_ok(mx, my, 1) ? 1 : 3;
+}
 
 // Full-weighting restriction applied `levels` times, as one hat-weighted
 // sum (fine -> level `levels`), interior coarse nodes only.

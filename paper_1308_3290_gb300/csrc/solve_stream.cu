@@ -253,12 +253,12 @@ __device__ __forceinline__ void reflect(Cplx<T> (&v)[16], CT<T>* buf, int t, con
 // row % part_py == 0, plus planes 1 and 3 at columns j % part_px == 0.
 // Every load of a row is issued before any sum.
 template <typename T, int G>
-__device__ __forceinline__ void load_rhs(const SolveParams<T>& P, int layer, int ra, int rb,
-                                         bool va, bool vb, int t, Cplx<T> (&v)[16]) {
+__device__ __forceinline__ void load_rhs(const SolveParams<T>& P, const T* const (&in)[4], int ra,
+                                         int rb, bool va, bool vb, int t, Cplx<T> (&v)[16]) {
     const long long n = (long long)(P.my + 1) * P.ld;
     const size_t oa = (size_t)ra * P.ld + t, ob = (size_t)rb * P.ld + t;
-    const T* pa = P.in[layer][0] + (va ? oa : 0);
-    const T* pb = P.in[layer][0] + (vb ? ob : 0);
+    const T* pa = in[0] + (va ? oa : 0);
+    const T* pb = in[0] + (vb ? ob : 0);
     T a[8], b[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -277,15 +277,15 @@ __device__ __forceinline__ void load_rhs(const SolveParams<T>& P, int layer, int
             const bool ia = va && !j0 && QG_IN(oa + r * G, n, 63);
             const bool ib = vb && !j0 && QG_IN(ob + r * G, n, 63);
             const bool cx = j % P.part_px == 0;
-            if (ia && ya) a[r] += __ldg(P.in[layer][2] + oa + r * G);
-            if (ib && yb) b[r] += __ldg(P.in[layer][2] + ob + r * G);
+            if (ia && ya) a[r] += __ldg(in[2] + oa + r * G);
+            if (ib && yb) b[r] += __ldg(in[2] + ob + r * G);
             if (ia && cx) {
-                a[r] += __ldg(P.in[layer][1] + oa + r * G);
-                if (ya) a[r] += __ldg(P.in[layer][3] + oa + r * G);
+                a[r] += __ldg(in[1] + oa + r * G);
+                if (ya) a[r] += __ldg(in[3] + oa + r * G);
             }
             if (ib && cx) {
-                b[r] += __ldg(P.in[layer][1] + ob + r * G);
-                if (yb) b[r] += __ldg(P.in[layer][3] + ob + r * G);
+                b[r] += __ldg(in[1] + ob + r * G);
+                if (yb) b[r] += __ldg(in[3] + ob + r * G);
             }
         }
     }
@@ -349,30 +349,15 @@ __host__ __device__ constexpr int stage_pitch(int ppc) { return 2 * ppc + (ppc >
 //                   x-mode ka).
 // The transposed outputs (tr, work) of the CTA's pairs are staged in shared
 // memory and written as runs of 2 PPC values per row.
-// Batches (ensembles, one layer): member blockIdx.x / cpm takes CTAs
-// blockIdx.x mod cpm, with its arrays from P.batch.
+// One work item: PPC sequence pairs (pair blk PPC + group, one group of G
+// threads each) of phase PH, with P's arrays (a member's, for batches).
+// Every thread of the CTA takes part.
 template <typename T, int OPY, int PH, int LG, int PPC>
-__global__ void __launch_bounds__(Len<LG>::G * PPC, minb_for<T>(Len<LG>::G * PPC))
-stream_kernel(SolveParams<T> Pin, int npairs, int cpm) {
+__device__ __forceinline__ void stream_item(const SolveParams<T>& P, int npairs, int blk,
+                                            unsigned char* smem) {
     using Ln = Len<LG>;
     constexpr bool YP = PH == 1;
     constexpr int G = Ln::G;
-    extern __shared__ __align__(16) unsigned char smem[];
-    SolveParams<T> P = Pin;
-    int blk = blockIdx.x;
-    if (Pin.batch) {
-        const int m = blk / cpm;
-        blk -= m * cpm;
-        const SolveMember<T>& M = Pin.batch[m];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) P.in[0][q] = M.in[q];
-        P.nin = M.nin;
-        P.part_px = M.part_px;
-        P.part_py = M.part_py;
-        P.tr[0] = M.tr;
-        P.work[0] = M.work;
-        P.out[0] = M.out;
-    }
     const int grp = PPC == 1 ? 0 : (int)threadIdx.x / G;
     const int t = (int)threadIdx.x - grp * G;
     const int pair0 = blk * PPC, pair = pair0 + grp;
@@ -398,8 +383,14 @@ stream_kernel(SolveParams<T> Pin, int npairs, int cpm) {
         vb = vp && rb <= P.my - 1;
     }
     const CT<T>* tw = YP ? P.pty : P.ptx;
-    pdl_wait();
-    pdl_trigger();
+    // the layer's arrays, selected without indexing (an indexed parameter
+    // array would be copied to local memory)
+    const bool l1 = layer != 0;
+    const T* const in[4] = {l1 ? P.in[1][0] : P.in[0][0], l1 ? P.in[1][1] : P.in[0][1],
+                            l1 ? P.in[1][2] : P.in[0][2], l1 ? P.in[1][3] : P.in[0][3]};
+    T* const trl = l1 ? P.tr[1] : P.tr[0];
+    T* const workl = l1 ? P.work[1] : P.work[0];
+    T* const outl = l1 ? P.out[1] : P.out[0];
 
     Cplx<T> v[16];
     if (YP) {
@@ -407,10 +398,10 @@ stream_kernel(SolveParams<T> Pin, int npairs, int cpm) {
         load_rows<T, G>(P.tr[0], P.tr[OPY == 2 ? 1 : 0], vp, vb, (long long)ra * P.ld_tr,
                         (long long)rb * P.ld_tr, n, t, v);
     } else if (PH == 0) {
-        load_rhs<T, G>(P, layer, ra, rb, vp, vb, t, v);
+        load_rhs<T, G>(P, in, ra, rb, vp, vb, t, v);
     } else {
         const long long n = (long long)(P.my + 1) * P.ld;
-        load_rows<T, G>(P.work[layer], P.work[layer], vp, vb, (long long)ra * P.ld,
+        load_rows<T, G>(workl, workl, vp, vb, (long long)ra * P.ld,
                         (long long)rb * P.ld, n, t, v);
     }
     reflect<T, LG>(v, buf, t, sy);
@@ -447,8 +438,8 @@ stream_kernel(SolveParams<T> Pin, int npairs, int cpm) {
     // F(a)_k = -Im Z_k / 2, F(b)_k = Re Z_k / 2 for k = t + G s < N
     if constexpr (PH == 2) {
         const long long nw = (long long)(P.my + 1) * P.ld;
-        T* oa = P.out[layer] + (size_t)ra * P.ld + t;
-        T* ob = P.out[layer] + (size_t)rb * P.ld + t;
+        T* oa = outl + (size_t)ra * P.ld + t;
+        T* ob = outl + (size_t)rb * P.ld + t;
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
             const T fa = T(-0.5) * v[s].y, fb = T(0.5) * v[s].x;
@@ -480,7 +471,7 @@ stream_kernel(SolveParams<T> Pin, int npairs, int cpm) {
             // q % 2 at column pair0 + q / 2
             const long long nw = (long long)(P.my + 1) * P.ld;
             const int c = OPY == 1 ? 2 * pair0 + q : pair0 + (q >> 1);
-            T* dst = P.work[OPY == 1 ? 0 : (q & 1)] + c;
+            T* dst = (OPY == 1 || !(q & 1) ? P.work[0] : P.work[1]) + c;
             const bool vc = c <= P.mx - 2;
 #pragma unroll 4
             for (int i = 0; i < ITER; ++i) {
@@ -492,7 +483,7 @@ stream_kernel(SolveParams<T> Pin, int npairs, int cpm) {
             // tr[k][c], k = 1..mx-1, c = 2 (pair0 - layer ppl) + q
             const long long ntr = (long long)(P.mx + 1) * P.ld_tr;
             const int c = 2 * (pair0 - layer * (P.my / 2)) + q;
-            T* dst = P.tr[layer] + c;
+            T* dst = trl + c;
             const bool vc = c <= P.my - 2;
 #pragma unroll 4
             for (int i = 0; i < ITER; ++i) {
@@ -500,6 +491,121 @@ stream_kernel(SolveParams<T> Pin, int npairs, int cpm) {
                 if (k > 0 && vc && QG_IN((long long)k * P.ld_tr + c, ntr, 69))
                     dst[(size_t)k * P.ld_tr] = stg[k * SP + q];
             }
+        }
+    }
+}
+
+// One launch per pass.  Batches (ensembles, one layer): member
+// blockIdx.x / cpm takes CTAs blockIdx.x mod cpm, with its arrays from
+// P.batch.
+template <typename T, int OPY, int PH, int LG, int PPC>
+__global__ void __launch_bounds__(Len<LG>::G * PPC, minb_for<T>(Len<LG>::G * PPC))
+stream_kernel(SolveParams<T> Pin, int npairs, int cpm) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    SolveParams<T> P = Pin;
+    int blk = blockIdx.x;
+    if (Pin.batch) {
+        const int m = blk / cpm;
+        blk -= m * cpm;
+        const SolveMember<T>& M = Pin.batch[m];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) P.in[0][q] = M.in[q];
+        P.nin = M.nin;
+        P.part_px = M.part_px;
+        P.part_py = M.part_py;
+        P.tr[0] = M.tr;
+        P.work[0] = M.work;
+        P.out[0] = M.out;
+    }
+    pdl_wait();
+    pdl_trigger();
+    stream_item<T, OPY, PH, LG, PPC>(P, npairs, blk, smem);
+}
+
+// Batched solve of an ensemble group in one launch (one layer, y length
+// twice the x length): a work queue over the items of the three passes of
+// every member, claimed in order from the counter q[0] (pass by pass,
+// member by member).  An item of pass ph >= 1 of member m first waits
+// (bounded) until the q[2 + 3 m + ph - 1] items of the pass before are
+// done; those were claimed earlier by CTAs that are running and depend on
+// no later item, so the wait ends without any co-residency.  A wait that
+// runs out sets the member's error flag and the item is counted done
+// unprocessed.  The last CTA to leave resets the counters for the next
+// launch.  The CTA has BT threads: BT / G_x pairs per x item, BT / G_y per
+// y item.
+constexpr int kQueueSpin = 1 << 22;
+
+__device__ __forceinline__ bool wait_done(const unsigned* c, unsigned want, int limit) {
+    for (int i = 0; i < limit; ++i) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+        if (v >= want) return true;
+    }
+    return false;
+}
+
+template <typename T, int LGX, int BT>
+__global__ void __launch_bounds__(BT, minb_for<T>(BT))
+stream_queue_kernel(SolveParams<T> P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item;
+    constexpr int LGY = LGX + 1;
+    constexpr int PX = BT / Len<LGX>::G, PY = BT / Len<LGY>::G;
+    unsigned* q = P.bar;
+    const int nb = P.nbatch;
+    const int rows = P.my / 2, cols = P.mx / 2;
+    const int n0i = (rows + PX - 1) / PX, n1i = (cols + PY - 1) / PY;
+    const int e0 = nb * n0i, e1 = e0 + nb * n1i, total = e1 + nb * n0i;
+    pdl_wait();
+    pdl_trigger();
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(q, 1u);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= total) break;
+        int ph, m, blk;
+        if (item < e0) {
+            ph = 0; m = item / n0i; blk = item - m * n0i;
+        } else if (item < e1) {
+            ph = 1; m = (item - e0) / n1i; blk = item - e0 - m * n1i;
+        } else {
+            ph = 2; m = (item - e1) / n0i; blk = item - e1 - m * n0i;
+        }
+        const SolveMember<T>& M = P.batch[m];
+        int ok = 1;
+        if (ph > 0 && threadIdx.x == 0)
+            ok = wait_done(q + 2 + 3 * m + ph - 1, (unsigned)(ph == 1 ? n0i : n1i), kQueueSpin);
+        if (__syncthreads_and(ok)) {
+            SolveParams<T> Q = P;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Q.in[0][k] = M.in[k];
+            Q.nin = M.nin;
+            Q.part_px = M.part_px;
+            Q.part_py = M.part_py;
+            Q.tr[0] = M.tr;
+            Q.work[0] = M.work;
+            Q.out[0] = M.out;
+            if (ph == 0) stream_item<T, 1, 0, LGX, PX>(Q, rows, blk, smem);
+            else if (ph == 1) stream_item<T, 1, 1, LGY, PY>(Q, cols, blk, smem);
+            else stream_item<T, 1, 2, LGX, PX>(Q, rows, blk, smem);
+            __syncthreads();
+        } else if (threadIdx.x == 0) {
+            atomicExch(M.err, 1);
+        }
+        if (threadIdx.x == 0) {
+            // this CTA's stores of the item are ordered before the count by
+            // the CTA barrier above and the release
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(q + 2 + 3 * m + ph)
+                         : "memory");
+        }
+    }
+    if (threadIdx.x == 0) {
+        unsigned old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(q + 1)
+                     : "memory");
+        if (old == gridDim.x - 1) {
+            for (int i = 0; i < 2 + 3 * nb; ++i) q[i] = 0u;
         }
     }
 }
@@ -560,7 +666,60 @@ cudaError_t launch_all(const SolveParams<T>& P, cudaStream_t s) {
     return e;
 }
 
+// The work-queue launch of a batch: the CTA size and pairs per item.
+template <typename T>
+constexpr int queue_threads(int lgx) {
+    const int gy = (1 << (lgx + 1)) / 16;
+    const int maxt = sizeof(T) == 4 ? 1024 : 512;
+    return 4 * gy < maxt ? 4 * gy : maxt;
+}
+
+template <typename T, int LGX>
+cudaError_t launch_queue_lg(const SolveParams<T>& P, cudaStream_t s) {
+    constexpr int BT = queue_threads<T>(LGX);
+    constexpr int PX = BT / Len<LGX>::G, PY = BT / Len<LGX + 1>::G;
+    auto k = stream_queue_kernel<T, LGX, BT>;
+    size_t sm = (size_t)PX * Len<LGX>::LIM * sizeof(CT<T>);
+    const size_t smy = (size_t)PY * Len<LGX + 1>::LIM * sizeof(CT<T>);
+    const size_t stx = (size_t)Len<LGX>::N * stage_pitch(PX) * sizeof(T);
+    const size_t sty = (size_t)Len<LGX + 1>::N * stage_pitch(PY) * sizeof(T);
+    for (size_t v : {smy, stx, sty}) sm = v > sm ? v : sm;
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, per = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BT, sm)) != cudaSuccess)
+        return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    const int rows = P.my / 2, cols = P.mx / 2;
+    const int total = P.nbatch * (2 * ((rows + PX - 1) / PX) + (cols + PY - 1) / PY);
+    int grid = per * nsm;
+    if (total < grid) grid = total;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(BT);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = P.no_pdl ? nullptr : at;
+    cfg.numAttrs = P.no_pdl ? 0 : 1;
+    return cudaLaunchKernelEx(&cfg, k, P);
+}
+
 }  // namespace
+
+// Batches of one-layer grids with my = 2 mx and 2 mx = 2^9 .. 2^11 run as
+// one work-queue launch; other batches as three launches.
+bool stream_queue_ok(int mx, int my, int layers) {
+    if (layers != 1 || my != 2 * mx || !is_pow2(mx)) return false;
+    const int lx = ilog2(2 * mx);
+    return lx >= 9 && lx <= 11;
+}
 
 bool stream_supports(int mx, int my, size_t esz) {
     if (!is_pow2(mx) || !is_pow2(my)) return false;
@@ -574,6 +733,13 @@ cudaError_t launch_solve_stream(const SolveParams<T>& P, cudaStream_t s) {
     if (!stream_supports(P.mx, P.my, sizeof(T)) || !P.ptx || !P.pty ||
         (P.batch && (P.layers != 1 || P.nbatch < 1)))
         return cudaErrorInvalidValue;
+    if (P.batch && stream_queue_ok(P.mx, P.my, P.layers) && P.bar) {
+        switch (ilog2(2 * P.mx)) {
+            case 9: return launch_queue_lg<T, 9>(P, s);
+            case 10: return launch_queue_lg<T, 10>(P, s);
+            default: return launch_queue_lg<T, 11>(P, s);
+        }
+    }
     return P.layers == 2 ? launch_all<T, 2>(P, s) : launch_all<T, 1>(P, s);
 }
 

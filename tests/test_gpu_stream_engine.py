@@ -132,10 +132,12 @@ def test_launch_count(monkeypatch):
 
 
 def test_batched_in_an_ensemble_equals_standalone_handles():
-    """Ensemble groups solve with engine 50 as one batch (three launches per
-    group and stage, members' CTAs side by side): bitwise the states of
-    stand-alone handles with the same engine.  The first and third members
-    share an elliptic grid (256 x 512, spacing 1/256) at different levels."""
+    """Ensemble groups solve with engine 50 as one batch (a work queue over
+    the three passes of every member in one launch when the y length is
+    twice the x length, else three launches with the members' CTAs side by
+    side): bitwise the states of stand-alone handles with the same engine.
+    The first and third members share an elliptic grid (256 x 512, spacing
+    1/256) at different levels."""
     require_gpu()
     from tests.test_gpu_ensemble import _groups
     members = [
@@ -163,5 +165,7 @@ def test_batched_in_an_ensemble_equals_standalone_handles():
         b.close()
     n_solve, n_fine = _groups(members)
     assert n_solve == 3
-    assert ens.kernel_count() == 3 * (3 * n_solve + n_fine)
+    # the 256 x 512 group (y length twice the x length) solves as one
+    # work-queue launch, the 512 x 256 and 512 x 512 groups as three
+    assert ens.kernel_count() == 3 * (1 + 3 + 3 + n_fine)
     ens.close()
