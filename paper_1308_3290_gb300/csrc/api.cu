@@ -1189,7 +1189,9 @@ static qg_status create_ctx(const qg_basin* b, int layers, double Re, double Ro,
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dbar, sizeof(unsigned) * 4));
     if (s == QG_OK) guard(dev_alloc(h, (void**)&h->dclock, sizeof(double) * 4));
     if (s == QG_OK) {
-        h->fine_rows = (int)fine_tile_rows(h->esz);
+        // ensemble members (one layer) sweep the tile of the batched launch
+        h->fine_rows = h->member && layers == 1 ? ensemble_tile_rows(h->esz)
+                                                : (int)fine_tile_rows(h->esz);
         h->fine_ry = fine_rows_per_thread(levels);
         guard(fine_maps(h));
     }
@@ -2300,7 +2302,7 @@ qg_status ensemble_tables(qg_ensemble e) {
         QG_TRY_E(tune_group<T>(e, g, cands));
     }
     const int TX = fine_block_cols();
-    const int RC = (int)fine_tile_rows(sizeof(T));
+    const int RC = ensemble_tile_rows(sizeof(T));
     for (auto& g : e->sg) {
         for (auto& f : g.fine) {
             const int nm = (int)f.members.size();
@@ -2484,7 +2486,8 @@ qg_status group_enqueue(qg_ensemble e, const EnsSolveGroup& g, cudaStream_t s) {
                 static_cast<const FineMember<T>*>(f.dmem) + (size_t)k * f.members.size();
             QG_TRY_E(cuda_status(e->m[f.members[0]],
                                  launch_fine_batch<T>(fm, f.dtiles, f.ntiles, f.lv, f.f2d,
-                                                      kEnsemblePdl, s)));
+                                                      kEnsemblePdl, s,
+                                                      ensemble_tile_rows(sizeof(T)))));
             ++e->kernels;
         }
     }

@@ -561,8 +561,8 @@ fine_sweep_kernel(const __grid_constant__ CUtensorMap tm_w,
 // tiles[c].z) of member tiles[c].x; the member's tensor maps and parameters
 // are read from `fm` in device memory (written by the host before the
 // launch).  One layer only.
-template <typename T, int LV>
-__global__ void __launch_bounds__(Plan<T, LV, false>::THREADS, sizeof(T) == 4 ? 3 : 2)
+template <typename T, int LV, int RCT>
+__global__ void __launch_bounds__(Plan<T, LV, false, RCT>::THREADS, Plan<T, LV, false, RCT>::MINB)
 fine_batch_kernel(const FineMember<T>* __restrict__ fm, const int4* __restrict__ tiles) {
     const int4 t = tiles[blockIdx.x];
     const FineMember<T>* E = fm + t.x;
@@ -574,16 +574,16 @@ fine_batch_kernel(const FineMember<T>* __restrict__ fm, const int4* __restrict__
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&E->psi) : "memory");
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&E->f) : "memory");
     }
-    sweep_tile<T, LV, false, Rows<T>::value>(&E->w, &E->wn, &E->psi, &E->f, E->p, t.y, t.z);
+    sweep_tile<T, LV, false, RCT>(&E->w, &E->wn, &E->psi, &E->f, E->p, t.y, t.z);
 }
 
-template <typename T, int LV>
+template <typename T, int LV, int RCT>
 cudaError_t launch_batch(const FineMember<T>* fm, const int4* tiles, int ntiles, bool forcing_field,
                          bool pdl, cudaStream_t s) {
-    using PL = Plan<T, LV, false>;
+    using PL = Plan<T, LV, false, RCT>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(fine_batch_kernel<T, LV>,
+        cudaError_t e = cudaFuncSetAttribute(fine_batch_kernel<T, LV, RCT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)PL::END);
         if (e != cudaSuccess) return e;
@@ -599,7 +599,7 @@ cudaError_t launch_batch(const FineMember<T>* fm, const int4* tiles, int ntiles,
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = pdl ? at : nullptr;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, fine_batch_kernel<T, LV>, fm, tiles);
+    return cudaLaunchKernelEx(&cfg, fine_batch_kernel<T, LV, RCT>, fm, tiles);
 }
 
 template <typename T, int LV, bool TL, int RCT, int RYT = Sweep<LV>::RY>
@@ -689,26 +689,44 @@ template cudaError_t launch_fine_fused<float>(const FusedParams<float>&, const F
 template cudaError_t launch_fine_fused<double>(const FusedParams<double>&, const FineMaps&, int,
                                                cudaStream_t, bool, int, int);
 
-template <typename T>
-cudaError_t launch_fine_batch(const FineMember<T>* fm, const int4* tiles, int ntiles, int levels,
+template <typename T, int RCT>
+cudaError_t launch_batch_rows(const FineMember<T>* fm, const int4* tiles, int ntiles, int levels,
                               bool forcing_field, bool pdl, cudaStream_t s) {
-    if (ntiles < 1) return cudaSuccess;
     switch (levels) {
-        case 0: return launch_batch<T, 0>(fm, tiles, ntiles, forcing_field, pdl, s);
-        case 1: return launch_batch<T, 1>(fm, tiles, ntiles, forcing_field, pdl, s);
-        case 2: return launch_batch<T, 2>(fm, tiles, ntiles, forcing_field, pdl, s);
-        case 3: return launch_batch<T, 3>(fm, tiles, ntiles, forcing_field, pdl, s);
-        case 4: return launch_batch<T, 4>(fm, tiles, ntiles, forcing_field, pdl, s);
+        case 0: return launch_batch<T, 0, RCT>(fm, tiles, ntiles, forcing_field, pdl, s);
+        case 1: return launch_batch<T, 1, RCT>(fm, tiles, ntiles, forcing_field, pdl, s);
+        case 2: return launch_batch<T, 2, RCT>(fm, tiles, ntiles, forcing_field, pdl, s);
+        case 3: return launch_batch<T, 3, RCT>(fm, tiles, ntiles, forcing_field, pdl, s);
+        case 4: return launch_batch<T, 4, RCT>(fm, tiles, ntiles, forcing_field, pdl, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
+// Members' tiles are `rows` fine rows high (ensemble_tile_rows) with the
+// default rows per thread.
+template <typename T>
+cudaError_t launch_fine_batch(const FineMember<T>* fm, const int4* tiles, int ntiles, int levels,
+                              bool forcing_field, bool pdl, cudaStream_t s, int rows) {
+    if (ntiles < 1) return cudaSuccess;
+    if (rows == Rows<T>::value)
+        return launch_batch_rows<T, Rows<T>::value>(fm, tiles, ntiles, levels, forcing_field, pdl, s);
+    if constexpr (sizeof(T) == 4) {
+        if (rows == 64)
+            return launch_batch_rows<T, 64>(fm, tiles, ntiles, levels, forcing_field, pdl, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template cudaError_t launch_fine_batch<float>(const FineMember<float>*, const int4*, int, int, bool,
-                                              bool, cudaStream_t);
+                                              bool, cudaStream_t, int);
 template cudaError_t launch_fine_batch<double>(const FineMember<double>*, const int4*, int, int,
-                                               bool, bool, cudaStream_t);
+                                               bool, bool, cudaStream_t, int);
 
 size_t fine_tile_rows(size_t esz) { return esz == 8 ? Rows<double>::value : Rows<float>::value; }
+// the tile of ensemble members' batched sweeps: 64 rows (128 threads, 6 CTAs
+// per SM in FP32; the tile the step autotuner keeps for large one-layer
+// basins)
+int ensemble_tile_rows(size_t esz) { return 64; }
 int fine_rows_per_thread(int levels) { return levels >= 4 ? 16 : 8; }
 bool fine_rows_supported(size_t esz, int layers, int levels, int rows, int ry) {
     const int ry0 = fine_rows_per_thread(levels);

@@ -260,11 +260,13 @@ struct alignas(64) FineMember {
 };
 // One layer: CTA c sweeps the tile (tiles[c].y, tiles[c].z) of member
 // tiles[c].x; `levels` is every member's CGP level; forcing_field when any
-// member uses a forcing field.
+// member uses a forcing field; tiles of `rows` fine rows
+// (ensemble_tile_rows).
 template <typename T>
 cudaError_t launch_fine_batch(const FineMember<T>* fm, const int4* tiles, int ntiles, int levels,
-                              bool forcing_field, bool pdl, cudaStream_t s);
-size_t fine_tile_rows(size_t esz);   // default fine rows per CTA (batched sweeps too)
+                              bool forcing_field, bool pdl, cudaStream_t s, int rows);
+size_t fine_tile_rows(size_t esz);   // default fine rows per CTA
+int ensemble_tile_rows(size_t esz);  // fine rows per CTA of ensemble members
 int fine_rows_per_thread(int levels);   // default rows a thread sweeps
 bool fine_rows_supported(size_t esz, int layers, int levels, int rows, int ry);  // tuned pairs
 int fine_part_period_x(int levels);  // coarse columns between tile edges

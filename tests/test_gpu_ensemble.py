@@ -69,6 +69,9 @@ def test_ensemble_equals_standalone_handles(engine, monkeypatch):
     solves with its own three launches."""
     require_gpu()
     monkeypatch.setenv("QG_SOLVE_ENGINE", str(engine))
+    # members sweep 64-row tiles (the batched launch's); the stand-alone
+    # handles are given the same tile
+    monkeypatch.setenv("QG_FINE_ROWS", "64")
     ens = qg.Ensemble(MEMBERS, dtype="f32")
     solo = [qg.Basin(m["nx"], m["ny"], Re=m["Re"], Ro=m["Ro"], levels=m["levels"], dt=m["dt"],
                      amp=m["amp"], dtype="f32") for m in MEMBERS]

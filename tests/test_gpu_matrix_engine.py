@@ -115,6 +115,7 @@ def test_matrix_engine_in_an_ensemble_equals_standalone_handles(monkeypatch):
     of a group in one launch."""
     require_gpu()
     monkeypatch.setenv("QG_SOLVE_ENGINE", str(MATRIX))
+    monkeypatch.setenv("QG_FINE_ROWS", "64")   # the members' (batched) tile
     members = [
         dict(nx=32, ny=64, Re=200.0, Ro=0.0016, levels=0, dt=1e-4, amp=1.0),
         dict(nx=64, ny=128, Re=312.5, Ro=0.0025, levels=1, dt=1e-4, amp=1.3),

@@ -148,12 +148,13 @@ def test_multigrid_with_adaptive_step_and_time_mean():
     b.close()
 
 
-def test_multigrid_on_an_ensemble_member_equals_a_standalone_handle():
+def test_multigrid_on_an_ensemble_member_equals_a_standalone_handle(monkeypatch):
     """The solver switch on one member of an ensemble: its steps are bitwise
     those of a stand-alone handle with the same switch (the V-cycles do not
     depend on how the member's graph is launched); the other members keep
     the sine transforms and follow the oracle."""
     require_gpu()
+    monkeypatch.setenv("QG_FINE_ROWS", "64")   # the members' (batched) tile
     members = [dict(nx=64, ny=128, Re=200.0, Ro=0.0016, levels=1, dt=1e-4),
                dict(nx=128, ny=256, Re=200.0, Ro=0.0016, levels=2, dt=5e-5)]
     w = [inputs.perturbation(m["nx"], m["ny"], seed=60 + i) * 40.0 for i, m in enumerate(members)]

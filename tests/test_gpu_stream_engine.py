@@ -131,7 +131,7 @@ def test_launch_count(monkeypatch):
     b.close()
 
 
-def test_batched_in_an_ensemble_equals_standalone_handles():
+def test_batched_in_an_ensemble_equals_standalone_handles(monkeypatch):
     """Ensemble groups solve with engine 50 as one batch (a work queue over
     the three passes of every member in one launch when the y length is
     twice the x length, else three launches with the members' CTAs side by
@@ -140,6 +140,7 @@ def test_batched_in_an_ensemble_equals_standalone_handles():
     1/256) at different levels."""
     require_gpu()
     from tests.test_gpu_ensemble import _groups
+    monkeypatch.setenv("QG_FINE_ROWS", "64")   # the members' (batched) tile
     members = [
         dict(nx=512, ny=1024, Re=200.0, Ro=0.0016, levels=1, dt=2e-5, amp=1.0),
         dict(nx=1024, ny=512, Re=450.0, Ro=0.0036, levels=1, dt=2e-5, amp=0.7),
