@@ -355,12 +355,13 @@ def small_basin_variant(torch, qg, inputs, stream, flush):
     """The 64x128, l = 1 basin (elliptic grid 32x64) in FP32 with the
     autotuned solve and with each kind of solve kernel forced: shared-memory
     FFT (4), warp-group FFT (34) and the matrix form on the tensor cores
-    (40).  Steps/s of the whole step and the mean solve launch."""
+    with mma.sync (40) and with tcgen05 (41).  Steps/s of the whole step and
+    the mean solve launch."""
     out = {}
     prev = os.environ.get("QG_SOLVE_ENGINE")
     w = inputs.gyre_state(64, 128, seed=SEED)
     try:
-        for eng in ("auto", "4", "34", "40"):
+        for eng in ("auto", "4", "34", "40", "41"):
             if eng == "auto":
                 os.environ.pop("QG_SOLVE_ENGINE", None)
             else:

@@ -538,13 +538,15 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
     P.split = h->split_solve ? 1 : 0;
     KTimer kt(h, s, QG_K_SOLVE);
     if (h->capturing && !h->split_solve) h->kernels_per_step += solve_launches(eng) - 1;
-    if (eng == kMatrixEngine) {
+    if (eng == kMatrixEngine || eng == kTcEngine) {
         // one launch whether or not the FFT solves are split
         if (h->capturing && h->split_solve) h->kernels_per_step -= 2;
-        if constexpr (std::is_same<T, float>::value)
-            QG_TRY(launch_solve_mtx(P, static_cast<const float*>(t.mtab), s));
-        else
+        if constexpr (std::is_same<T, float>::value) {
+            const float* tab = static_cast<const float*>(t.mtab);
+            QG_TRY(eng == kTcEngine ? launch_solve_tc(P, tab, s) : launch_solve_mtx(P, tab, s));
+        } else {
             QG_TRY(cudaErrorInvalidValue);
+        }
         return QG_OK;
     }
     QG_TRY(launch_solve<T>(P, eng, s));
@@ -556,7 +558,8 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
 // radix 4: many threads per sequence pair, or 16: fewer passes and
 // instructions; or the warp-group engine of solve32.cu with 32, 16 or 8
 // values per thread, engines 32, 33, 34; or, on small one-layer FP32 grids,
-// the matrix-form solve on the tensor cores of solve_mtx.cu, engine 40; or
+// the matrix-form solve on the tensor cores of solve_mtx.cu, engine 40, or
+// the same with tcgen05 and TMEM accumulators, engine 41 (solve_tc.cu); or
 // the register-resident radix-16 passes of solve_stream.cu, engine 50) is
 // chosen per handle when it is created, by timing a few whole steps with each
 // engine that supports the elliptic grid (the solve alone, timed back to
@@ -564,7 +567,7 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
 // its fields through L2), and the fastest is kept.  Results are cached per
 // (nx, ny, levels, layers, dtype) for the process and, when the environment
 // variable QG_TUNE_CACHE names a file, in that file (one line
-// "nx ny levels layers esz engine" per entry).  QG_SOLVE_ENGINE=4|16|32|33|34|40|50
+// "nx ny levels layers esz engine" per entry).  QG_SOLVE_ENGINE=4|16|32|33|34|40|41|50
 // forces a choice where that engine supports the grid.  Other grids use the
 // size rule.
 
@@ -579,6 +582,7 @@ int engine_for(qg_ctx* h, int mx, int my) {
 // Whether engine e can solve the level with tables t on handle h.
 bool engine_ok(const qg_ctx* h, const LevelTables* t, size_t esz, int e) {
     if (e == kMatrixEngine) return t->mtab && mtx_supports(t->mx, t->my, esz, h->layers);
+    if (e == kTcEngine) return t->mtab && tc_supports(t->mx, t->my, esz, h->layers);
     if (e == kStreamEngine) return solve_engine_supports(t->mx, t->my, esz, e) && t->ptx[1];
     return solve_engine_supports(t->mx, t->my, esz, e) && (!is_warp_engine(e) || t->ptx[e - 32]);
 }
@@ -627,7 +631,8 @@ void tune_file_load() {
     if (!f) return;
     int a, b, c, d, x, e, r, y;
     while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &a, &b, &c, &d, &x, &e, &r, &y) == 8)
-        if ((e == 4 || e == 16 || is_warp_engine(e) || e == kMatrixEngine || e == kStreamEngine) &&
+        if ((e == 4 || e == 16 || is_warp_engine(e) || e == kMatrixEngine || e == kTcEngine ||
+             e == kStreamEngine) &&
             fine_rows_supported((size_t)x, d, c, r, y))
             g_tune_cache[TuneKey(a, b, c, d, x)] = {e, r, y};
     std::fclose(f);
@@ -738,14 +743,15 @@ qg_status autotune_solve(qg_ctx* h) {
     const float t16 = time_steps<T>(h, 16);
     const float t40 = time_steps<T>(h, kMatrixEngine);
     const float t50 = time_steps<T>(h, kStreamEngine);
+    const float t41 = time_steps<T>(h, kTcEngine);
     // a candidate that cannot run on this grid is a tuning result, not an error
     h->latched = QG_OK;
     (void)cudaGetLastError();
     drop_graph(h);
-    const float tt[7] = {t4, t16, t32, t33, t34, t40, t50};
-    const int ee[7] = {4, 16, 32, 33, 34, kMatrixEngine, kStreamEngine};
+    const float tt[8] = {t4, t16, t32, t33, t34, t40, t50, t41};
+    const int ee[8] = {4, 16, 32, 33, 34, kMatrixEngine, kStreamEngine, kTcEngine};
     int best = 0;
-    for (int k = 1; k < 7; ++k)
+    for (int k = 1; k < 8; ++k)
         if (tt[k] < tt[best]) best = k;
     if (tt[best] >= 1e29f) return fail(h, QG_ERR_CUDA);
     h->solve_engine = ee[best];
@@ -1718,7 +1724,7 @@ qg_status qg_bounds_check_result(int32_t* site) {
     }
     int first = 0;
     for (int v : {bounds_site_fused(), bounds_site_solve32(), bounds_site_stencil(),
-                  bounds_site_mtx(), bounds_site_stream()}) {
+                  bounds_site_mtx(), bounds_site_stream(), bounds_site_tc()}) {
         if (v < 0) return QG_ERR_CUDA;
         if (!first) first = v;
     }
@@ -2170,12 +2176,13 @@ std::vector<int> batch_engines(qg_ensemble e, const EnsSolveGroup& g) {
     if (get_level(h0, h0->levels, &t) != QG_OK) return out;
     const int own = h0->solve_engine;
     if (h0->engine_forced) {
-        if ((is_warp_engine(own) || own == kMatrixEngine || own == kStreamEngine) &&
+        if ((is_warp_engine(own) || own == kMatrixEngine || own == kTcEngine ||
+             own == kStreamEngine) &&
             engine_ok(h0, t, h0->esz, own))
             out.push_back(own);
         return out;
     }
-    for (int cand : {34, 33, 32, (int)kMatrixEngine, (int)kStreamEngine})
+    for (int cand : {34, 33, 32, (int)kMatrixEngine, (int)kTcEngine, (int)kStreamEngine})
         if (engine_ok(h0, t, h0->esz, cand)) out.push_back(cand);
     return out;
 }
@@ -2367,11 +2374,14 @@ qg_status group_solve(qg_ensemble e, const EnsSolveGroup& g, int engine, int k, 
     P.batch = static_cast<const SolveMember<T>*>(g.dmem) + (size_t)k * g.members.size();
     P.nbatch = (int)g.members.size();
     P.no_pdl = kEnsemblePdl ? 0 : 1;
-    if (engine == kMatrixEngine) {
-        if constexpr (std::is_same<T, float>::value)
-            return cuda_status(h0, launch_solve_mtx(P, static_cast<const float*>(t->mtab), s));
-        else
+    if (engine == kMatrixEngine || engine == kTcEngine) {
+        if constexpr (std::is_same<T, float>::value) {
+            const float* tab = static_cast<const float*>(t->mtab);
+            return cuda_status(h0, engine == kTcEngine ? launch_solve_tc(P, tab, s)
+                                                       : launch_solve_mtx(P, tab, s));
+        } else {
             return QG_ERR_CUDA;
+        }
     }
     return cuda_status(h0, launch_solve<T>(P, engine, s));
 }

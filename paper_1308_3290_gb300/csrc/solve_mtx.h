@@ -31,4 +31,12 @@ void mtx_table(int mx, int my, double dx, double dy, float* out);
 // mtx_table.
 cudaError_t launch_solve_mtx(const SolveParams<float>& P, const float* tab, cudaStream_t s);
 
+// The same solve with tcgen05.mma and TMEM accumulators (solve_tc.cu):
+// one-layer FP32 grids with sides of 16, 32 or 64 intervals; the same
+// table; one CTA per grid (per member for a batch).
+constexpr int kTcEngine = 41;
+bool tc_supports(int mx, int my, size_t esz, int layers);
+cudaError_t launch_solve_tc(const SolveParams<float>& P, const float* tab, cudaStream_t s);
+int bounds_site_tc();
+
 }  // namespace qg

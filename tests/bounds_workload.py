@@ -48,6 +48,22 @@ def main():
                 b.poisson_solve(inputs.smooth_field(nx >> lv, ny >> lv, seed=2), lv)
                 b.close()
         check(f"engine {engine}")
+    # engine 41 (tcgen05, sides of 16 to 64 intervals), one basin and a batch
+    os.environ["QG_SOLVE_ENGINE"] = "41"
+    for nx, ny, lv in ((32, 64, 0), (64, 128, 1), (64, 64, 0), (128, 256, 2)):
+        b = basin(nx, ny, lv, "f32")
+        run_steps(b, nx, ny)
+        b.poisson_solve(inputs.smooth_field(nx >> lv, ny >> lv, seed=2), lv)
+        b.close()
+    ens = qg.Ensemble([dict(nx=32, ny=64, Re=200.0, Ro=0.0016, levels=0, dt=1e-4, amp=1.0),
+                       dict(nx=64, ny=128, Re=300.0, Ro=0.0016, levels=1, dt=1e-4, amp=1.0)],
+                      dtype="f32")
+    for i, (nx, ny) in enumerate(((32, 64), (64, 128))):
+        ens.member(i).set_state(inputs.perturbation(nx, ny, seed=7 + i) * 20.0)
+    ens.step(3)
+    ens.synchronize()
+    ens.close()
+    check("engine 41")
     # engine 50 (sides of 512 intervals and more): remainder passes of radix
     # 2, 4 and 8 and none, 1, 2 and 4 pairs per CTA, one and two layers
     os.environ["QG_SOLVE_ENGINE"] = "50"
