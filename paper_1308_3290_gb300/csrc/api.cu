@@ -52,6 +52,7 @@ struct LevelTables {
     void* ptx[3] = {nullptr, nullptr, nullptr};  // warp-group engine pass twiddles for
     void* pty[3] = {nullptr, nullptr, nullptr};  //   L = 2 mx and 2 my, engines 32/33/34
     void* mtab = nullptr;  // matrix engine (FP32, one layer): sine matrices and 1/lambda
+    void* tctab = nullptr; // engine 41: split sine matrices (shared-memory image), 1/lambda
 };
 
 // Multigrid hierarchy below one elliptic grid (multigrid.cu): grids 1..nl-1
@@ -348,6 +349,14 @@ qg_status get_level(qg_ctx* h, int lv, const LevelTables** out) {
             cudaMemcpy(t.mtab, m.data(), m.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             s = QG_ERR_CUDA;
     }
+    if (s == QG_OK && tc_supports(t.mx, t.my, h->esz, h->layers)) {
+        std::vector<float> m(tc_table_floats(t.mx, t.my));
+        tc_table(t.mx, t.my, t.dxc, t.dyc, m.data());
+        s = dev_alloc(h, &t.tctab, m.size() * sizeof(float));
+        if (s == QG_OK &&
+            cudaMemcpy(t.tctab, m.data(), m.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            s = QG_ERR_CUDA;
+    }
     if (s != QG_OK) return s;
     const double pi = 3.14159265358979323846;
     // padded to a multiple of 4 entries: the solve copies them in 16-byte units
@@ -542,8 +551,9 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
         // one launch whether or not the FFT solves are split
         if (h->capturing && h->split_solve) h->kernels_per_step -= 2;
         if constexpr (std::is_same<T, float>::value) {
-            const float* tab = static_cast<const float*>(t.mtab);
-            QG_TRY(eng == kTcEngine ? launch_solve_tc(P, tab, s) : launch_solve_mtx(P, tab, s));
+            QG_TRY(eng == kTcEngine
+                       ? launch_solve_tc(P, static_cast<const float*>(t.tctab), s)
+                       : launch_solve_mtx(P, static_cast<const float*>(t.mtab), s));
         } else {
             QG_TRY(cudaErrorInvalidValue);
         }
@@ -582,7 +592,7 @@ int engine_for(qg_ctx* h, int mx, int my) {
 // Whether engine e can solve the level with tables t on handle h.
 bool engine_ok(const qg_ctx* h, const LevelTables* t, size_t esz, int e) {
     if (e == kMatrixEngine) return t->mtab && mtx_supports(t->mx, t->my, esz, h->layers);
-    if (e == kTcEngine) return t->mtab && tc_supports(t->mx, t->my, esz, h->layers);
+    if (e == kTcEngine) return t->tctab && tc_supports(t->mx, t->my, esz, h->layers);
     if (e == kStreamEngine) return solve_engine_supports(t->mx, t->my, esz, e) && t->ptx[1];
     return solve_engine_supports(t->mx, t->my, esz, e) && (!is_warp_engine(e) || t->ptx[e - 32]);
 }
@@ -2376,9 +2386,9 @@ qg_status group_solve(qg_ensemble e, const EnsSolveGroup& g, int engine, int k, 
     P.no_pdl = kEnsemblePdl ? 0 : 1;
     if (engine == kMatrixEngine || engine == kTcEngine) {
         if constexpr (std::is_same<T, float>::value) {
-            const float* tab = static_cast<const float*>(t->mtab);
-            return cuda_status(h0, engine == kTcEngine ? launch_solve_tc(P, tab, s)
-                                                       : launch_solve_mtx(P, tab, s));
+            return cuda_status(h0, engine == kTcEngine
+                                       ? launch_solve_tc(P, static_cast<const float*>(t->tctab), s)
+                                       : launch_solve_mtx(P, static_cast<const float*>(t->mtab), s));
         } else {
             return QG_ERR_CUDA;
         }

@@ -32,10 +32,14 @@ void mtx_table(int mx, int my, double dx, double dy, float* out);
 cudaError_t launch_solve_mtx(const SolveParams<float>& P, const float* tab, cudaStream_t s);
 
 // The same solve with tcgen05.mma and TMEM accumulators (solve_tc.cu):
-// one-layer FP32 grids with sides of 16, 32 or 64 intervals; the same
-// table; one CTA per grid (per member for a batch).
+// one-layer FP32 grids with sides of 16, 32 or 64 intervals; one CTA per
+// grid (per member for a batch).  Its table holds the split sine matrices
+// in the kernel's shared-memory layout, then the scaled inverse
+// eigenvalues; tc_table_floats(mx, my) entries, FP64-evaluated.
 constexpr int kTcEngine = 41;
 bool tc_supports(int mx, int my, size_t esz, int layers);
+size_t tc_table_floats(int mx, int my);
+void tc_table(int mx, int my, double dx, double dy, float* out);
 cudaError_t launch_solve_tc(const SolveParams<float>& P, const float* tab, cudaStream_t s);
 int bounds_site_tc();
 

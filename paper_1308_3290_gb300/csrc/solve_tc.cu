@@ -27,7 +27,10 @@
 // K (LBO) and K/4 x 128 bytes apart along M or N (SBO).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "bounds.cuh"
 #include "dst_engine.cuh"
@@ -38,7 +41,8 @@ namespace {
 
 using namespace eng;
 
-constexpr int kThreads = 128;   // = the MMA's M: one thread per row
+constexpr int kM = 128;         // the MMA's M: rows of every product
+constexpr int kThreads = 256;  // two warps per 32-lane TMEM group: each reads half the columns
 constexpr int kSpin = 1 << 22;
 
 __device__ __forceinline__ uint32_t tf32_rn(float x) {
@@ -78,19 +82,16 @@ __device__ __forceinline__ void fence_before() {
 __device__ __forceinline__ void fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-// 16 consecutive TMEM columns of this thread's lane
-__device__ __forceinline__ void tmem_ld16(uint32_t ta, float (&v)[16]) {
-    uint32_t r[16];
+// 8 consecutive TMEM columns of this thread's lane (no wait)
+__device__ __forceinline__ void tmem_ld8(uint32_t ta, uint32_t (&r)[8]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
+          "=r"(r[7])
         : "r"(ta));
+}
+__device__ __forceinline__ void tmem_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 // Layout of one grid (bytes of shared memory): mp, np the interior sizes
@@ -98,13 +99,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t ta, float (&v)[16]) {
 // bytes apart):
 //   SX: B operand of products 1 and 4, mp rows x K = mp;
 //   SY: A operand of products 2 and 3, 128 rows x K = np (rows >= np zero);
-//   OP: A operand of products 1 and 4 (128 rows x K = mp, rows >= np zero)
-//       or B operand of products 2 and 3 (mp rows x K = np).
+//   OP: A operand of products 1 and 4 (128 rows x K = mp) or B operand of
+//       products 2 and 3 (mp rows x K = np).
+// SX and SY come ready-made (split, zero-padded, in this layout) from the
+// grid's table (tc_table), followed there by Inv (np x mp floats).
 struct TcGeo {
     int m, n, mp, np;
     int sx, sx_half, sy, sy_half, op, op_half, end;
-    int cols;   // TMEM columns (a power of two >= 32)
-    int ldx, ldy, sxg, syg, ting;   // the engine-40 table: pitches and offsets (floats)
+    int cols;      // TMEM columns (a power of two >= 32)
+    int tab_inv;   // floats before Inv in the table
 };
 __host__ __device__ inline int r16(int v) { return (v + 15) / 16 * 16; }
 __host__ __device__ inline TcGeo tc_geo(int mx, int my) {
@@ -114,8 +117,8 @@ __host__ __device__ inline TcGeo tc_geo(int mx, int my) {
     g.mp = r16(g.m);
     g.np = r16(g.n);
     g.sx_half = g.mp * g.mp * 4;
-    g.sy_half = kThreads * g.np * 4;
-    const int opa = kThreads * g.mp * 4, opb = g.mp * g.np * 4;
+    g.sy_half = kM * g.np * 4;
+    const int opa = kM * g.mp * 4, opb = g.mp * g.np * 4;
     g.op_half = opa > opb ? opa : opb;
     g.sx = 0;
     g.sy = g.sx + 2 * g.sx_half;
@@ -125,12 +128,7 @@ __host__ __device__ inline TcGeo tc_geo(int mx, int my) {
     const int c = c1 > c2 ? c1 : c2;
     g.cols = 32;
     while (g.cols < c) g.cols *= 2;
-    // the engine-40 table (solve_mtx.cu's layout): S_x | S_y | Inv
-    g.ldx = g.mp + 8;
-    g.ldy = g.np + 4;
-    g.sxg = 0;
-    g.syg = g.mp * g.ldx;
-    g.ting = g.syg + g.np * g.ldy;   // Inv: np x mp, pitch mp
+    g.tab_inv = g.op / 4;
     return g;
 }
 
@@ -146,16 +144,16 @@ __device__ __forceinline__ void put_split(unsigned char* base, int half, int off
 }
 
 // One product D = A B^T (A: 128 x K, B: N x K, both split) into K/8
-// accumulators of N columns each, issued by thread 0 and committed to bar.
+// accumulators of N columns each, issued by one thread and committed to bar.
 __device__ __forceinline__ void issue(uint32_t taddr, uint32_t a, int a_half, uint32_t b,
                                       int b_half, int N, int K, uint32_t bar) {
-    const uint32_t id = idesc_tf32(kThreads, N);
-    const uint32_t sboa = (uint32_t)(K / 4) * 128u, sbob = sboa;
+    const uint32_t id = idesc_tf32(kM, N);
+    const uint32_t sbo = (uint32_t)(K / 4) * 128u;
     for (int ks = 0; ks < K / 8; ++ks) {
         const uint32_t o = (uint32_t)ks * 256u;
         const uint32_t d = taddr + (uint32_t)(ks * N);
-        const uint64_t ah = sdesc(a + o, 128, sboa), al = sdesc(a + a_half + o, 128, sboa);
-        const uint64_t bh = sdesc(b + o, 128, sbob), bl = sdesc(b + b_half + o, 128, sbob);
+        const uint64_t ah = sdesc(a + o, 128, sbo), al = sdesc(a + a_half + o, 128, sbo);
+        const uint64_t bh = sdesc(b + o, 128, sbo), bl = sdesc(b + b_half + o, 128, sbo);
         mma_tf32(d, al, bh, id, 0);
         mma_tf32(d, ah, bl, id, 1);
         mma_tf32(d, ah, bh, id, 1);
@@ -164,20 +162,26 @@ __device__ __forceinline__ void issue(uint32_t taddr, uint32_t a, int a_half, ui
                  ::"r"(bar) : "memory");
 }
 
-// Row `lane row` of a product: the sum of its K/8 accumulators, N <= 64.
-__device__ __forceinline__ void row_sum(uint32_t taddr, int N, int K, float (&out)[64]) {
-    const uint32_t lane = (uint32_t)(threadIdx.x & ~31) << 16;
+// This thread's part of a product's row: columns c0 .. c0 + N/2 - 1 of TMEM
+// lane `lane`, the sum of the K/8 accumulators (round-to-nearest adds).
+__device__ __forceinline__ void row_sum(uint32_t taddr, uint32_t lane, int c0, int N, int K,
+                                        float (&out)[32]) {
 #pragma unroll
-    for (int j = 0; j < 64; ++j) out[j] = 0.f;
+    for (int j = 0; j < 32; ++j) out[j] = 0.f;
+    const int nh = N / 2;
     for (int ks = 0; ks < K / 8; ++ks) {
+        uint32_t r[4][8];
+        const uint32_t ta = taddr + lane + (uint32_t)(ks * N + c0);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            if (16 * c >= N) break;
-            float v[16];
-            tmem_ld16(taddr + lane + (uint32_t)(ks * N + 16 * c), v);
+        for (int q = 0; q < 4; ++q)
+            if (8 * q < nh) tmem_ld8(ta + 8 * q, r[q]);
+        tmem_wait();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) out[16 * c + j] += v[j];
-        }
+        for (int q = 0; q < 4; ++q)
+            if (8 * q < nh) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) out[8 * q + j] += __uint_as_float(r[q][j]);
+            }
     }
 }
 
@@ -198,105 +202,106 @@ solve_tc_kernel(SolveParams<float> Pk, const float* __restrict__ tab, TcGeo g) {
         P.err = M.err;
     }
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mb_tab, mb_mma;
     __shared__ uint32_t s_taddr;
-    const int i = threadIdx.x;
-    const uint32_t bar = smem_u32(&mbar);
+    const int t = threadIdx.x, w = t >> 5;
+    const int row = 32 * (w & 3) + (t & 31);      // TMEM lane = row of the products
+    const int half = w >> 2;                      // which half of the columns
+    const uint32_t lane = (uint32_t)(32 * (w & 3)) << 16;
+    const uint32_t btab = smem_u32(&mb_tab), bmma = smem_u32(&mb_mma);
     const uint32_t base = smem_u32(sm);
-    if (i == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(btab) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bmma) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // the constant operands (before the programmatic wait): zero the padded
-    // arrays, then S_x (B, N = mp rows) and S_y (A, rows < np) split
-    for (int o = 4 * i; o < g.end; o += 4 * kThreads)
-        *reinterpret_cast<uint32_t*>(sm + o) = 0u;
     __syncthreads();
-    for (int e = i; e < g.mp * g.mp; e += kThreads) {
-        const int r = e / g.mp, k = e - r * g.mp;
-        const float v = (r < g.m && k < g.m) ? __ldg(tab + g.sxg + r * g.ldx + k) : 0.f;
-        put_split(sm + g.sx, g.sx_half, kmaj(r, k, g.mp), v, 2 * g.sx_half);
+    // the split sine matrices, ready-made in the table (constants: copied
+    // before the programmatic wait)
+    const uint32_t tab_bytes = (uint32_t)g.op;
+    if (t == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(btab),
+                     "r"(tab_bytes) : "memory");
+        bulk_copy(base, tab, tab_bytes, btab);
     }
-    for (int e = i; e < g.np * g.np; e += kThreads) {
-        const int r = e / g.np, k = e - r * g.np;
-        const float v = (r < g.n && k < g.n) ? __ldg(tab + g.syg + r * g.ldy + k) : 0.f;
-        put_split(sm + g.sy, g.sy_half, kmaj(r, k, g.np), v, 2 * g.sy_half);
-    }
-    if (i < 32) {
+    // OP starts zero (rows and columns beyond the grid's)
+    for (int o = 16 * t; o < 2 * g.op_half; o += 16 * kThreads)
+        *reinterpret_cast<uint4*>(sm + g.op + o) = make_uint4(0u, 0u, 0u, 0u);
+    if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(&s_taddr)), "r"(g.cols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    __syncthreads();
     pdl_wait();
     pdl_trigger();   // the next fine stage may start staging its own inputs
-    // Q (A operand of product 1): row i = y - 1, column x - 1, the sum of the
-    // restriction's partial planes as in the FFT engines
-    if (i < g.n) {
-        const int y = i + 1;
-        const bool ry = P.nin > 1 && y % P.part_py == 0;
-        for (int c = 0; c < g.m; ++c) {
-            const int x = c + 1;
-            const size_t off = (size_t)y * P.ld + x;
-            float v = 0.f;
-            if (QG_IN((long long)off, (long long)(P.my + 1) * P.ld, 82)) {
-                v = __ldg(P.in[0][0] + off);
-                if (P.nin > 1) {
-                    if (ry) v += __ldg(P.in[0][2] + off);
-                    if (x % P.part_px == 0) {
-                        v += __ldg(P.in[0][1] + off);
-                        if (ry) v += __ldg(P.in[0][3] + off);
-                    }
+    // Q (A operand of product 1, row r = y - 1, column c = x - 1): the sum of
+    // the restriction's partial planes as in the FFT engines
+    for (int e = t; e < g.n * g.mp; e += kThreads) {
+        const int r = e / g.mp, c = e - r * g.mp;
+        const int y = r + 1, x = c + 1;
+        float v = 0.f;
+        const size_t off = (size_t)y * P.ld + x;
+        if (c < g.m && QG_IN((long long)off, (long long)(P.my + 1) * P.ld, 82)) {
+            v = __ldg(P.in[0][0] + off);
+            if (P.nin > 1) {
+                const bool ry = y % P.part_py == 0;
+                if (ry) v += __ldg(P.in[0][2] + off);
+                if (x % P.part_px == 0) {
+                    v += __ldg(P.in[0][1] + off);
+                    if (ry) v += __ldg(P.in[0][3] + off);
                 }
             }
-            put_split(sm + g.op, g.op_half, kmaj(i, c, g.mp), v, 2 * g.op_half);
         }
+        put_split(sm + g.op, g.op_half, kmaj(r, c, g.mp), v, 2 * g.op_half);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    int ok = mbar_wait(btab, 0, kSpin) ? 1 : 0;
     fence_before();
-    __syncthreads();
+    ok = __syncthreads_and(ok);
     fence_after();
     const uint32_t taddr = s_taddr;
     const uint32_t sx = base + g.sx, sy = base + g.sy, op = base + g.op;
-    int ok = 1;
-    float row[64];
-    for (int step = 0; step < 4; ++step) {
+    const int nh = g.mp / 2, c0 = half * nh;
+    float acc[32];
+    for (int step = 0; step < 4 && ok; ++step) {
         // products 1, 4: (OP as A) (S_x as B), K = mp; 2, 3: (S_y as A) (OP as B), K = np
         const bool xs = step == 0 || step == 3;
         const int K = xs ? g.mp : g.np;
-        if (i == 0 && ok) {
-            if (xs) issue(taddr, op, g.op_half, sx, g.sx_half, g.mp, K, bar);
-            else issue(taddr, sy, g.sy_half, op, g.op_half, g.mp, K, bar);
+        if (t == 0) {
+            if (xs) issue(taddr, op, g.op_half, sx, g.sx_half, g.mp, K, bmma);
+            else issue(taddr, sy, g.sy_half, op, g.op_half, g.mp, K, bmma);
         }
-        ok = ok && mbar_wait(bar, (uint32_t)(step & 1), kSpin) ? 1 : 0;
+        ok = mbar_wait(bmma, (uint32_t)(step & 1), kSpin) ? 1 : 0;
         if (!__syncthreads_and(ok)) {
             ok = 0;
             break;
         }
         fence_after();
-        row_sum(taddr, g.mp, K, row);
+        row_sum(taddr, lane, c0, g.mp, K, acc);
         fence_before();
         __syncthreads();   // every read of the operands and of TMEM is done
         if (step == 3) break;
-        if (i < g.n) {
+        if (row < g.n) {
             if (step == 1) {
-                const float* inv = tab + g.ting + i * g.mp;
+                const float* inv = tab + g.tab_inv + row * g.mp + c0;
 #pragma unroll
-                for (int c = 0; c < 64; ++c)
-                    if (c < g.mp) row[c] *= __ldg(inv + c);
+                for (int j = 0; j < 32; ++j)
+                    if (j < nh) acc[j] *= __ldg(inv + j);
             }
             if (step == 2) {
-                // W = S_y U as the A operand of product 4: row i
+                // W = S_y U as the A operand of product 4: row `row`
 #pragma unroll
-                for (int c = 0; c < 64; ++c)
-                    if (c < g.mp) put_split(sm + g.op, g.op_half, kmaj(i, c, g.mp), row[c],
-                                            2 * g.op_half);
+                for (int j = 0; j < 32; ++j)
+                    if (j < nh) put_split(sm + g.op, g.op_half, kmaj(row, c0 + j, g.mp), acc[j],
+                                          2 * g.op_half);
             } else {
                 // V (product 1) or U (product 2) transposed as the B operand of
-                // the next product: column i of the mp x np operand
+                // the next product: column `row` of the mp x np operand
 #pragma unroll
-                for (int c = 0; c < 64; ++c)
-                    if (c < g.mp) put_split(sm + g.op, g.op_half, kmaj(c, i, g.np), row[c],
-                                            2 * g.op_half);
+                for (int j = 0; j < 32; ++j)
+                    if (j < nh) put_split(sm + g.op, g.op_half, kmaj(c0 + j, row, g.np), acc[j],
+                                          2 * g.op_half);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -304,23 +309,34 @@ solve_tc_kernel(SolveParams<float> Pk, const float* __restrict__ tab, TcGeo g) {
         fence_after();
     }
     if (!ok) {
-        if (i == 0) atomicExch(P.err, 1);
-    } else if (i < g.n) {
-        // psi at interior row y = i + 1; the wall column x = 0 gets 0 as in
+        if (t == 0) atomicExch(P.err, 1);
+    } else if (row < g.n) {
+        // psi at interior row y = row + 1; the wall column x = 0 gets 0 as in
         // the FFT engines
-        float* o = P.out[0] + (size_t)(i + 1) * P.ld;
+        float* o = P.out[0] + (size_t)(row + 1) * P.ld;
         const long long on = (long long)(P.my + 1) * P.ld;
         (void)on;
-        if (QG_IN((long long)(i + 1) * P.ld, on, 83)) o[0] = 0.f;
+        if (half == 0 && QG_IN((long long)(row + 1) * P.ld, on, 83)) o[0] = 0.f;
 #pragma unroll
-        for (int c = 0; c < 64; ++c)
-            if (c < g.m && QG_IN((long long)(i + 1) * P.ld + 1 + c, on, 83)) o[1 + c] = row[c];
+        for (int j = 0; j < 32; ++j)
+            if (j < nh && c0 + j < g.m && QG_IN((long long)(row + 1) * P.ld + 1 + c0 + j, on, 83))
+                o[1 + c0 + j] = acc[j];
     }
     fence_before();
     __syncthreads();
-    if (i < 32)
+    if (w == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
                      "r"(g.cols) : "memory");
+}
+
+// Round to nearest TF32, ties away from zero (the device's cvt.rna.tf32).
+float rna_tf32(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    b = (b + 0x1000u) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
 }
 
 }  // namespace
@@ -328,6 +344,40 @@ solve_tc_kernel(SolveParams<float> Pk, const float* __restrict__ tab, TcGeo g) {
 bool tc_supports(int mx, int my, size_t esz, int layers) {
     return esz == 4 && layers == 1 && is_pow2(mx) && is_pow2(my) && mx >= 16 && my >= 16 &&
            mx <= 64 && my <= 64;
+}
+
+size_t tc_table_floats(int mx, int my) {
+    const TcGeo g = tc_geo(mx, my);
+    return (size_t)g.tab_inv + (size_t)g.np * g.mp;
+}
+
+void tc_table(int mx, int my, double dx, double dy, float* out) {
+    const TcGeo g = tc_geo(mx, my);
+    std::fill(out, out + tc_table_floats(mx, my), 0.0f);
+    const double pi = 3.14159265358979323846;
+    // sin(pi i k / M) with i k reduced mod 2M first (exact integer argument
+    // reduction), split as hi = rn_tf32(s), lo = rn_tf32(s - hi)
+    auto put = [&](int off_bytes, int half_bytes, double v) {
+        const float s = (float)v;
+        const float hi = rna_tf32(s);
+        out[off_bytes / 4] = hi;
+        out[(off_bytes + half_bytes) / 4] = rna_tf32(s - hi);
+    };
+    auto sine = [pi](long ik, int M) { return std::sin(pi * (double)(ik % (2L * M)) / M); };
+    for (int i = 0; i < g.m; ++i)
+        for (int k = 0; k < g.m; ++k)
+            put(g.sx + kmaj(i, k, g.mp), g.sx_half, sine((long)(i + 1) * (k + 1), mx));
+    for (int j = 0; j < g.n; ++j)
+        for (int l = 0; l < g.n; ++l)
+            put(g.sy + kmaj(j, l, g.np), g.sy_half, sine((long)(j + 1) * (l + 1), my));
+    const double scale = (2.0 / mx) * (2.0 / my);
+    for (int l = 0; l < g.n; ++l) {
+        const double ly = (2.0 * std::cos(pi * (l + 1) / my) - 2.0) / (dy * dy);
+        for (int k = 0; k < g.m; ++k) {
+            const double lx = (2.0 * std::cos(pi * (k + 1) / mx) - 2.0) / (dx * dx);
+            out[g.tab_inv + l * g.mp + k] = (float)(scale / (lx + ly));
+        }
+    }
 }
 
 cudaError_t launch_solve_tc(const SolveParams<float>& P, const float* tab, cudaStream_t s) {
