@@ -279,8 +279,9 @@ qg_status qg_set_solver(qg_handle h, qg_solver kind, int32_t cycles);
  * environment variable forces a supported one).  4 or 16: shared-memory
  * Stockham FFT with base radix 4 or 16; 32, 33, 34: warp-group FFT with 32,
  * 16 or 8 values per thread; 40: the sine sums as dense matrix products on
- * the tensor cores, 3xTF32 (one-layer FP32 grids of at most 64 x 128 or
- * 128 x 64 intervals); 41: the same products with tcgen05.mma and TMEM
+ * the tensor cores, 3xTF32 (FP32 grids of at most 64 x 128 or 128 x 64
+ * intervals with one layer, 64 x 64 with two: both layers' transforms and
+ * the coupled solve of Eqs. isub-1/2 per mode); 41: the same products with tcgen05.mma and TMEM
  * accumulators (sides of 16 to 64 intervals); 50: radix-16 FFT passes with the values in
  * registers, one to four sequence pairs per CTA and three launches (one
  * per pass), for elliptic grids of 256 to 8192 intervals a side (4096 in

@@ -63,16 +63,17 @@ __host__ __device__ inline int r16(int v) { return (v + 15) / 16 * 16; }
 // Layout of one elliptic grid, in floats.  m, n: interior columns (x) and
 // rows (y); mp, np: padded to multiples of 16 (zeros beyond m, n).  S_x is
 // mp x mp (pitch ldx, a B operand), S_y np x np (pitch ldy, an A operand);
-// the work arrays U, V are np x mp with pitch lda (as an A operand) or ldb
-// (as a B operand).  Shared memory: S_x | S_y | U | V.  Global table:
-// S_x | S_y | Inv (np x mp, pitch mp).
+// the work arrays U, V (and U2, V2 of the second layer) are np x mp with
+// pitch lda (as an A operand) or ldb (as a B operand).  Shared memory:
+// S_x | S_y | U | V | U2 | V2.  Global table: S_x | S_y | Inv (np x mp,
+// pitch mp).
 struct MtxGeo {
     int m, n, mp, np;
     int ldx, ldy, lda, ldb;
-    int sx, sy, u, v, end;
+    int sx, sy, u, v, u2, v2, end;
     int tinv, tend;
 };
-__host__ __device__ inline MtxGeo mtx_geo(int mx, int my) {
+__host__ __device__ inline MtxGeo mtx_geo(int mx, int my, int layers = 1) {
     MtxGeo g;
     g.m = mx - 1;
     g.n = my - 1;
@@ -86,7 +87,9 @@ __host__ __device__ inline MtxGeo mtx_geo(int mx, int my) {
     g.sy = g.sx + g.mp * g.ldx;
     g.u = g.sy + g.np * g.ldy;
     g.v = g.u + g.np * g.ldb;
-    g.end = g.v + g.np * g.ldb;
+    g.u2 = g.v + g.np * g.ldb;
+    g.v2 = g.u2 + g.np * g.ldb;
+    g.end = layers == 2 ? g.v2 + g.np * g.ldb : g.u2;
     g.tinv = g.u;
     g.tend = g.tinv + g.np * g.mp;
     return g;
@@ -159,9 +162,54 @@ __device__ __forceinline__ void mm3(const float* A, int lda, const float* B, int
     }
 }
 
+// The right-hand side of one layer (planes `in`) at interior node (x = c + 1,
+// y = r + 1) into A (np x mp, pitch lda): the sum of the restriction's
+// partial planes as in the FFT engines.
+__device__ __forceinline__ void load_q(const SolveParams<float>& P, const float* const (&in)[4],
+                                       float* A, const MtxGeo& g) {
+    for (int i = threadIdx.x; i < g.np * g.mp; i += kThreads) {
+        const int r = i / g.mp, c = i - r * g.mp;
+        float v = 0.f;
+        if (r < g.n && c < g.m &&
+            QG_IN((long long)(r + 1) * P.ld + c + 1, (long long)(P.my + 1) * P.ld, 51)) {
+            const int y = r + 1, x = c + 1;
+            const size_t off = (size_t)y * P.ld + x;
+            v = __ldg(in[0] + off);
+            if (P.nin > 1) {
+                const bool ry = y % P.part_py == 0;
+                if (ry) v += __ldg(in[2] + off);
+                if (x % P.part_px == 0) {
+                    v += __ldg(in[1] + off);
+                    if (ry) v += __ldg(in[3] + off);
+                }
+            }
+        }
+        if (QG_IN(r * g.lda + c, g.np * g.lda, 52)) A[r * g.lda + c] = v;
+    }
+}
+
+// psi = W S_x of one layer into out (interior rows; the wall column x = 0
+// gets 0 as in the FFT engines).
+__device__ __forceinline__ void store_psi(const SolveParams<float>& P, const float* W,
+                                          const float* Sx, float* out, const MtxGeo& g) {
+    const int n = g.n, m = g.m;
+    const size_t ld = (size_t)P.ld;
+    mm3(W, g.lda, Sx, g.ldx, g.mp, g, [&](int r, int c, float v0, float v1) {
+        if (r >= n) return;
+        float* o = out + (size_t)(r + 1) * ld + 1;
+        const long long on = (long long)(P.my + 1) * (long long)ld;
+        (void)on;
+        if (c < m && QG_IN((long long)(r + 1) * ld + 1 + c, on, 53)) o[c] = v0;
+        if (c + 1 < m && QG_IN((long long)(r + 1) * ld + 2 + c, on, 53)) o[c + 1] = v1;
+    });
+    for (int r = threadIdx.x; r < n; r += kThreads) out[(size_t)(r + 1) * ld] = 0.f;
+}
+
 // One solve per CTA: the handle's (BATCH false, one CTA) or member
-// blockIdx.x of a batch, whose fields replace the per-member ones of P.
-template <bool BATCH>
+// blockIdx.x of a batch (one layer), whose fields replace the per-member
+// ones of P.  OPY 2: both layers of the two-layer model, with the coupled
+// solve of Eqs. isub-1/2 per mode between the transforms.
+template <bool BATCH, int OPY>
 __global__ void __launch_bounds__(kThreads, 1)
 solve_mtx_kernel(SolveParams<float> Pk, const float* __restrict__ tab, MtxGeo g) {
     SolveParams<float> P = Pk;
@@ -194,26 +242,13 @@ solve_mtx_kernel(SolveParams<float> Pk, const float* __restrict__ tab, MtxGeo g)
     pdl_trigger();   // the next fine stage may start staging its own inputs
     float* U = sm + g.u;
     float* V = sm + g.v;
-    // Q: the right-hand side at interior node (x = c + 1, y = r + 1), the sum
-    // of the restriction's partial planes as in the FFT engines
-    for (int i = threadIdx.x; i < g.np * g.mp; i += kThreads) {
-        const int r = i / g.mp, c = i - r * g.mp;
-        float v = 0.f;
-        if (r < g.n && c < g.m &&
-            QG_IN((long long)(r + 1) * P.ld + c + 1, (long long)(P.my + 1) * P.ld, 51)) {
-            const int y = r + 1, x = c + 1;
-            const size_t off = (size_t)y * P.ld + x;
-            v = __ldg(P.in[0][0] + off);
-            if (P.nin > 1) {
-                const bool ry = y % P.part_py == 0;
-                if (ry) v += __ldg(P.in[0][2] + off);
-                if (x % P.part_px == 0) {
-                    v += __ldg(P.in[0][1] + off);
-                    if (ry) v += __ldg(P.in[0][3] + off);
-                }
-            }
+    {
+        const float* const in0[4] = {P.in[0][0], P.in[0][1], P.in[0][2], P.in[0][3]};
+        load_q(P, in0, U, g);
+        if constexpr (OPY == 2) {
+            const float* const in1[4] = {P.in[1][0], P.in[1][1], P.in[1][2], P.in[1][3]};
+            load_q(P, in1, sm + g.u2, g);
         }
-        if (QG_IN(g.u + r * g.lda + c, g.v, 52)) U[r * g.lda + c] = v;
     }
     const bool ok = mbar_wait(bar, 0, kSpin);
     if (!__syncthreads_and(ok)) {
@@ -224,46 +259,71 @@ solve_mtx_kernel(SolveParams<float> Pk, const float* __restrict__ tab, MtxGeo g)
     const float* Sx = sm + g.sx;
     const float* Sy = sm + g.sy;
     const int ldb = g.ldb, lda = g.lda;
-    // Q S_x -> V (a B operand next)
-    mm3(U, lda, Sx, g.ldx, g.mp, g, [&](int r, int c, float v0, float v1) {
-        *reinterpret_cast<float2*>(V + r * ldb + c) = make_float2(v0, v1);
-    });
-    __syncthreads();
-    // (S_y Q S_x) o Inv -> U (a B operand next)
-    const float* inv = tab + g.tinv;
     const int mp = g.mp;
-    mm3(Sy, g.ldy, V, ldb, g.np, g, [&](int r, int c, float v0, float v1) {
-        const float2 w = __ldg(reinterpret_cast<const float2*>(inv + r * mp + c));
-        *reinterpret_cast<float2*>(U + r * ldb + c) = make_float2(v0 * w.x, v1 * w.y);
-    });
-    __syncthreads();
-    // S_y (...) -> V (an A operand next)
-    mm3(Sy, g.ldy, U, ldb, g.np, g, [&](int r, int c, float v0, float v1) {
-        *reinterpret_cast<float2*>(V + r * lda + c) = make_float2(v0, v1);
-    });
-    __syncthreads();
-    // (...) S_x -> psi at interior nodes; the wall column x = 0 gets 0 as in
-    // the FFT engines
-    float* out = P.out[0];
-    const int n = g.n, m = g.m;
-    const size_t ld = (size_t)P.ld;
-    mm3(V, lda, Sx, g.ldx, g.mp, g, [&](int r, int c, float v0, float v1) {
-        if (r >= n) return;
-        float* o = out + (size_t)(r + 1) * ld + 1;
-        const long long on = (long long)(P.my + 1) * (long long)ld;
-        if (c < m && QG_IN((long long)(r + 1) * ld + 1 + c, on, 53)) o[c] = v0;
-        if (c + 1 < m && QG_IN((long long)(r + 1) * ld + 2 + c, on, 53)) o[c + 1] = v1;
-    });
-    for (int r = threadIdx.x; r < n; r += kThreads) out[(size_t)(r + 1) * ld] = 0.f;
+    auto to_b = [&](float* D) {
+        return [D, ldb](int r, int c, float v0, float v1) {
+            *reinterpret_cast<float2*>(D + r * ldb + c) = make_float2(v0, v1);
+        };
+    };
+    auto to_a = [&](float* D) {
+        return [D, lda](int r, int c, float v0, float v1) {
+            *reinterpret_cast<float2*>(D + r * lda + c) = make_float2(v0, v1);
+        };
+    };
+    if constexpr (OPY == 1) {
+        // Q S_x -> V (a B operand next)
+        mm3(U, lda, Sx, g.ldx, g.mp, g, to_b(V));
+        __syncthreads();
+        // (S_y Q S_x) o Inv -> U (a B operand next)
+        const float* inv = tab + g.tinv;
+        mm3(Sy, g.ldy, V, ldb, g.np, g, [&](int r, int c, float v0, float v1) {
+            const float2 w = __ldg(reinterpret_cast<const float2*>(inv + r * mp + c));
+            *reinterpret_cast<float2*>(U + r * ldb + c) = make_float2(v0 * w.x, v1 * w.y);
+        });
+        __syncthreads();
+        // S_y (...) -> V (an A operand next)
+        mm3(Sy, g.ldy, U, ldb, g.np, g, to_a(V));
+        __syncthreads();
+        // (...) S_x -> psi
+        store_psi(P, V, Sx, P.out[0], g);
+    } else {
+        float* U2 = sm + g.u2;
+        float* V2 = sm + g.v2;
+        mm3(U, lda, Sx, g.ldx, g.mp, g, to_b(V));
+        mm3(U2, lda, Sx, g.ldx, g.mp, g, to_b(V2));
+        __syncthreads();
+        // the spectra F_i = S_y Q_i S_x of both layers
+        mm3(Sy, g.ldy, V, ldb, g.np, g, to_b(U));
+        mm3(Sy, g.ldy, V2, ldb, g.np, g, to_b(U2));
+        __syncthreads();
+        // Eqs. isub-1/2 per mode (k = c + 1, l = r + 1): the 2x2 system with
+        // alpha = Ro (lambda_k + lambda_l) (Eq. ialpha), as in the FFT engines
+        for (int i = threadIdx.x; i < g.n * g.m; i += kThreads) {
+            const int r = i / g.m, c = i - r * g.m;
+            const float q1 = P.scale * U[r * ldb + c], q2 = P.scale * U2[r * ldb + c];
+            const float al = P.Ro * (__ldg(P.lamx + c + 1) + __ldg(P.lamy + r + 1));
+            const float den = al * (al - P.f1 - P.f2);
+            U[r * ldb + c] = (al * q1 - P.f2 * q1 - P.f1 * q2) / den;
+            U2[r * ldb + c] = (al * q2 - P.f2 * q1 - P.f1 * q2) / den;
+        }
+        __syncthreads();
+        mm3(Sy, g.ldy, U, ldb, g.np, g, to_a(V));
+        mm3(Sy, g.ldy, U2, ldb, g.np, g, to_a(V2));
+        __syncthreads();
+        store_psi(P, V, Sx, P.out[0], g);
+        store_psi(P, V2, Sx, P.out[1], g);
+    }
 }
 
 }  // namespace
 
-size_t mtx_smem_bytes(int mx, int my) { return (size_t)mtx_geo(mx, my).end * sizeof(float); }
+size_t mtx_smem_bytes(int mx, int my, int layers) {
+    return (size_t)mtx_geo(mx, my, layers).end * sizeof(float);
+}
 
 bool mtx_supports(int mx, int my, size_t esz, int layers) {
-    return esz == 4 && layers == 1 && is_pow2(mx) && is_pow2(my) && mx >= 2 && my >= 2 &&
-           mx <= 256 && my <= 256 && mtx_smem_bytes(mx, my) <= 200 * 1024;
+    return esz == 4 && (layers == 1 || layers == 2) && is_pow2(mx) && is_pow2(my) && mx >= 2 &&
+           my >= 2 && mx <= 256 && my <= 256 && mtx_smem_bytes(mx, my, layers) <= 200 * 1024;
 }
 
 size_t mtx_table_floats(int mx, int my) { return (size_t)mtx_geo(mx, my).tend; }
@@ -296,12 +356,13 @@ cudaError_t launch_solve_mtx(const SolveParams<float>& P, const float* tab, cuda
     if (!mtx_supports(P.mx, P.my, sizeof(float), P.layers) || !tab ||
         (!P.batch && (P.nin < 1 || (P.nin > 1 && (P.part_px < 1 || P.part_py < 1)))))
         return cudaErrorInvalidValue;
-    const MtxGeo g = mtx_geo(P.mx, P.my);
+    const MtxGeo g = mtx_geo(P.mx, P.my, P.layers);
     const size_t sm = (size_t)g.end * sizeof(float);
     int per = 0, nsm = 0;
     const bool batch = P.batch != nullptr;
-    if (batch && P.nbatch < 1) return cudaErrorInvalidValue;
-    auto k = batch ? solve_mtx_kernel<true> : solve_mtx_kernel<false>;
+    if (batch && (P.nbatch < 1 || P.layers != 1)) return cudaErrorInvalidValue;
+    auto k = batch ? solve_mtx_kernel<true, 1>
+                   : (P.layers == 2 ? solve_mtx_kernel<false, 2> : solve_mtx_kernel<false, 1>);
     cudaError_t e = launch_shape(reinterpret_cast<const void*>(k), kThreads, sm, &per, &nsm);
     if (e != cudaSuccess) return e;
     if (per < 1) return cudaErrorInvalidConfiguration;

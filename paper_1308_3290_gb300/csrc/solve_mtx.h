@@ -13,11 +13,12 @@ namespace qg {
 // (the FFT engines are 4, 16 and 32-34).
 constexpr int kMatrixEngine = 40;
 
-// One-layer FP32 elliptic grids whose sine matrices and work arrays fit in
-// 200 KB of one CTA's shared memory (Mx, My powers of two): up to 64 x 128
-// or 128 x 64 intervals (156 KB); 128 x 128 would need 270 KB.
+// FP32 elliptic grids (one layer, or two: both layers' transforms and the
+// coupled solve of Eqs. isub-1/2) whose sine matrices and work arrays fit
+// in 200 KB of one CTA's shared memory (Mx, My powers of two): one layer up
+// to 64 x 128 or 128 x 64 intervals (156 KB), two layers up to 64 x 64.
 bool mtx_supports(int mx, int my, size_t esz, int layers);
-size_t mtx_smem_bytes(int mx, int my);
+size_t mtx_smem_bytes(int mx, int my, int layers);
 
 // The constant table of one elliptic grid: S_x (padded), S_y (padded) and
 // the scaled inverse eigenvalues (2/Mx)(2/My)/lambda_kl of Eq. ialpha, in

@@ -94,12 +94,13 @@ def test_matrix_engine_in_the_step(nx, ny, levels, monkeypatch):
 
 
 def test_matrix_engine_unsupported_grids_fall_back(monkeypatch):
-    """Grids past the engine's shared memory, FP64 handles and two-layer
-    handles keep an FFT engine although the matrix engine is requested."""
+    """Grids past the engine's shared memory (one layer beyond 64 x 128, two
+    layers beyond 64 x 64) and FP64 handles keep an FFT engine although the
+    matrix engine is requested."""
     require_gpu()
     monkeypatch.setenv("QG_SOLVE_ENGINE", str(MATRIX))
     cases = [dict(nx=128, ny=128, dtype="f32"), dict(nx=64, ny=128, dtype="f64"),
-             dict(nx=64, ny=64, dtype="f32", layers=2, Fr=0.087, delta=0.2, sigma=1.43e-3,
+             dict(nx=128, ny=128, dtype="f32", layers=2, Fr=0.087, delta=0.2, sigma=1.43e-3,
                   y0=-0.5, y1=0.5)]
     for c in cases:
         b = qg.Basin(Re=200.0, Ro=0.0016, levels=0, dt=1e-4, **c)
@@ -147,3 +148,43 @@ def test_matrix_engine_in_an_ensemble_equals_standalone_handles(monkeypatch):
     for b in solo:
         b.close()
     ens.close()
+
+
+@pytest.mark.parametrize("nx,ny", [(16, 16), (32, 32), (64, 64), (32, 64)])
+def test_two_layer_matrix_solve_parity(nx, ny, monkeypatch):
+    """Both layers' transforms and the coupled solve of Eqs. isub-1/2 per
+    mode in the matrix form, against the oracle's two-layer elliptic solve
+    (square basin of Section 2.2 and an N x 2N one)."""
+    require_gpu()
+    p = dict(Ro=2.49e-4, Fr=0.087, delta=0.2, sigma=1.43e-3)
+    b = forced_basin(monkeypatch, nx, ny, 0, Re=697.16, dt=1e-5, layers=2, y0=-0.5, y1=0.5, **p)
+    Q1 = inputs.smooth_field(nx, ny, seed=1, noise=0.1)
+    Q2 = inputs.smooth_field(nx, ny, seed=2, noise=0.1)
+    got = to_np(b.poisson_solve(np.stack([Q1, Q2])))
+    r1, r2 = O.elliptic_two_layer(Q1, Q2, nx, ny, 1 / nx, 1 / ny, p["Ro"], p["Fr"], p["delta"])
+    assert rel_l2(got[0], r1) <= 1e-5, rel_l2(got[0], r1)
+    assert rel_l2(got[1], r2) <= 1e-5, rel_l2(got[1], r2)
+    b.close()
+
+
+@pytest.mark.parametrize("levels", [0, 1])
+def test_two_layer_matrix_engine_in_the_step(levels, monkeypatch):
+    """20 FP32 steps of the two-layer basin (Table 2 Experiment 1 parameters,
+    64 x 64) on the matrix engine against the oracle's FP64 steps."""
+    require_gpu()
+    p = dict(Ro=2.49e-4, Fr=0.087, delta=0.2, sigma=1.43e-3)
+    A = 3.57e-7
+    Q1 = inputs.smooth_field(64, 64, seed=1, amp=0.05, noise=0.01)
+    Q2 = inputs.smooth_field(64, 64, seed=2, amp=0.02, noise=0.01)
+    ob = O.TwoLayer(64, 64, A=A, levels=levels, dt=1e-4, **p)
+    a1, a2 = O.embed(Q1), O.embed(Q2)
+    for _ in range(20):
+        a1, a2 = O.cgprk3_step_two_layer(a1, a2, ob)
+    b = forced_basin(monkeypatch, 64, 64, levels, Re=p["Ro"] / A, dt=1e-4, layers=2, y0=-0.5,
+                     y1=0.5, **p)
+    b.set_state(Q1, 0)
+    b.set_state(Q2, 1)
+    b.step(20)
+    assert rel_l2(to_np(b.state(0)), O.interior(a1)) <= 1e-4
+    assert rel_l2(to_np(b.state(1)), O.interior(a2)) <= 1e-4
+    b.close()
