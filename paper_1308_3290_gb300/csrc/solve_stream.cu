@@ -8,10 +8,12 @@
 // engine is laid out for grids whose passes stream through HBM (the full
 // 2048 x 4096 grid, l = 0):
 //
-//   * one CTA of G = L/16 threads per sequence pair, three plain launches
-//     (one per pass) chained by programmatic dependent launch, so there is
-//     no grid barrier and each pass takes the CTA size and register budget
-//     of its own length;
+//   * G = L/16 threads per sequence pair, three plain launches (one per
+//     pass) chained by programmatic dependent launch, so there is no grid
+//     barrier and each pass takes the CTA size and register budget of its
+//     own length; an ensemble group's batch runs instead as one launch, a
+//     work queue over the items of the three passes of every member
+//     (stream_queue_kernel);
 //   * thread t holds the 16 values x[t + G r] in registers.  The first
 //     radix-16 pass works on the values the thread loaded from global
 //     memory, and the last pass leaves X[t + G s] in registers (a Stockham
@@ -33,8 +35,10 @@
 //   * the length is a template parameter: every shared-memory, twiddle and
 //     global offset of a pass is a constant from a per-thread base.
 //
-// Twiddles are the radix-16 pass tables of the warp-group engine
-// (pass_table(L, 16), FP64-generated).
+// Twiddles come from the radix-16 pass tables of the warp-group engine
+// (pass_table(L, 16), FP64-generated): a radix-16 pass loads w, w^2, w^4
+// and w^8 and forms the other powers, the remainder pass one power per
+// radix and multiplies by 16th roots of unity.
 #include <cuda_runtime.h>
 
 #include "bounds.cuh"
