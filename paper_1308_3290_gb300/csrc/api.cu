@@ -692,6 +692,25 @@ float time_steps(qg_ctx* h, int engine) {
     return ms;
 }
 
+// Zero the state, streamfunction and scratch arrays of a handle whose
+// buffers ran timing steps (autotuners), and wait for it.
+qg_status rest_buffers(qg_ctx* h, cudaStream_t s) {
+    cudaStreamSynchronize(s);
+    for (void* p : {h->w[0], h->w[1], h->w[2], h->psi}) {
+        if (p) QG_TRY(cudaMemsetAsync(p, 0, h->plane_f * h->layers * h->esz, s));
+    }
+    for (void* p : {h->cw, h->cpsi}) {
+        if (p) QG_TRY(cudaMemsetAsync(p, 0, h->plane_c * h->layers * h->esz, s));
+    }
+    if (h->ct) QG_TRY(cudaMemsetAsync(h->ct, 0, h->plane_t * h->layers * h->esz, s));
+    if (h->part)
+        QG_TRY(cudaMemsetAsync(h->part, 0, 4 * (size_t)h->layers * h->plane_c * h->esz, s));
+    QG_TRY(cudaMemsetAsync(h->dclock, 0, sizeof(double) * 4, s));
+    h->part_valid = false;
+    QG_TRY(cudaStreamSynchronize(s));
+    return QG_OK;
+}
+
 template <typename T>
 qg_status autotune_solve(qg_ctx* h) {
     const LevelTables* t = nullptr;
@@ -783,19 +802,7 @@ qg_status autotune_solve(qg_ctx* h) {
         drop_graph(h);
     }
     // the timing steps ran on the handle's buffers: return them to rest
-    cudaStreamSynchronize(h->stream);
-    for (void* p : {h->w[0], h->w[1], h->w[2], h->psi}) {
-        if (p) QG_TRY(cudaMemsetAsync(p, 0, h->plane_f * h->layers * h->esz, h->stream));
-    }
-    for (void* p : {h->cw, h->cpsi}) {
-        if (p) QG_TRY(cudaMemsetAsync(p, 0, h->plane_c * h->layers * h->esz, h->stream));
-    }
-    if (h->ct) QG_TRY(cudaMemsetAsync(h->ct, 0, h->plane_t * h->layers * h->esz, h->stream));
-    if (h->part)
-        QG_TRY(cudaMemsetAsync(h->part, 0, 4 * (size_t)h->layers * h->plane_c * h->esz, h->stream));
-    QG_TRY(cudaMemsetAsync(h->dclock, 0, sizeof(double) * 4, h->stream));
-    h->part_valid = false;
-    QG_TRY(cudaStreamSynchronize(h->stream));
+    QG_TRY_S(rest_buffers(h, h->stream));
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     const TuneVal v{h->solve_engine, h->fine_rows, h->fine_ry};
     g_tune_cache[key] = v;
@@ -2123,6 +2130,7 @@ struct qg_ensemble_s {
     std::vector<EnsSolveGroup> sg;
     std::vector<void*> dallocs;             // device tables of the batched launches
     int64_t kernels = 0;
+    bool fresh = false;                     // members hold no user state yet
 };
 
 namespace {
@@ -2233,7 +2241,9 @@ FusedParams<T> fused_params(qg_ctx* h, int s_idx, const LevelTables& t) {
 }
 
 template <typename T>
-qg_status tune_group(qg_ensemble e, EnsSolveGroup& g, const std::vector<int>& cands);
+qg_status tune_group(qg_ensemble e, EnsSolveGroup& g, const std::vector<int>& cands,
+                     bool* timed);
+qg_status rest_buffers(qg_ctx* h, cudaStream_t s);
 
 // Group the members and upload the tables of the batched launches.
 template <typename T>
@@ -2316,7 +2326,7 @@ qg_status ensemble_tables(qg_ensemble e) {
                        cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemset(g.dq, 0, nq * sizeof(unsigned)) != cudaSuccess)
             return QG_ERR_CUDA;
-        QG_TRY_E(tune_group<T>(e, g, cands));
+        g.engine = cands[0];
     }
     const int TX = fine_block_cols();
     const int RC = ensemble_tile_rows(sizeof(T));
@@ -2352,6 +2362,18 @@ qg_status ensemble_tables(qg_ensemble e) {
                 return QG_ERR_CUDA;
         }
     }
+    // each group's solve engine, timed over whole group steps on the
+    // members' buffers (which then return to rest) while the members hold
+    // no user state, else over solves alone
+    bool timed = false;
+    for (auto& g : e->sg) {
+        if (!g.engine) continue;
+        bool t = false;
+        QG_TRY_E(tune_group<T>(e, g, batch_engines(e, g), &t));
+        timed = timed || t;
+    }
+    if (timed && e->fresh)
+        for (qg_ctx* h : e->m) QG_TRY_E(rest_buffers(h, e->stream));
     return QG_OK;
 }
 
@@ -2396,15 +2418,38 @@ qg_status group_solve(qg_ensemble e, const EnsSolveGroup& g, int engine, int k, 
     return cuda_status(h0, launch_solve<T>(P, engine, s));
 }
 
-// The batched solve's engine for a group: each candidate timed on the
-// group's own arrays (a few launches; the solves overwrite only work arrays
-// and streamfunctions that every stage recomputes), the fastest kept.
-// Results are cached per (grid, spacings, members, dtype) for the process.
+// One step of group g outside a graph, for timing: per stage the batched
+// solve with `engine` and the batched fine stages.
+template <typename T>
+qg_status group_step_eager(qg_ensemble e, const EnsSolveGroup& g, int engine, cudaStream_t s) {
+    for (int k = 0; k < 3; ++k) {
+        QG_TRY_E(group_solve<T>(e, g, engine, k, s));
+        for (const auto& f : g.fine) {
+            const FineMember<T>* fm =
+                static_cast<const FineMember<T>*>(f.dmem) + (size_t)k * f.members.size();
+            if (launch_fine_batch<T>(fm, f.dtiles, f.ntiles, f.lv, f.f2d, kEnsemblePdl, s,
+                                     ensemble_tile_rows(sizeof(T))) != cudaSuccess)
+                return QG_ERR_CUDA;
+        }
+    }
+    return QG_OK;
+}
+
+// The batched solve's engine for a group: each candidate timed, the fastest
+// kept.  An ensemble being created times whole group steps (solves and fine
+// stages on the members' own buffers: the solve alone ranks the engines
+// differently, as for one basin) and *timed tells the caller to return the
+// buffers to rest; a later rebuild, whose members hold state, times stage-1
+// solves alone (they overwrite only work arrays and streamfunctions that
+// every stage recomputes).  Results are cached per (grid, spacings,
+// members, dtype) for the process.
 std::mutex g_batch_tune_mutex;
 std::map<std::tuple<int, int, double, double, int, int>, int> g_batch_tune;
 
 template <typename T>
-qg_status tune_group(qg_ensemble e, EnsSolveGroup& g, const std::vector<int>& cands) {
+qg_status tune_group(qg_ensemble e, EnsSolveGroup& g, const std::vector<int>& cands,
+                     bool* timed) {
+    *timed = false;
     if (cands.size() == 1) {
         g.engine = cands[0];
         return QG_OK;
@@ -2420,13 +2465,18 @@ qg_status tune_group(qg_ensemble e, EnsSolveGroup& g, const std::vector<int>& ca
     }
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return QG_ERR_CUDA;
+    *timed = true;
     float best = 1e30f;
     int pick = cands[0];
     for (int cand : cands) {
         bool ok = true;
-        for (int r = 0; r < 2 && ok; ++r) ok = group_solve<T>(e, g, cand, 0, e->stream) == QG_OK;
+        auto unit = [&]() {
+            return (e->fresh ? group_step_eager<T>(e, g, cand, e->stream)
+                             : group_solve<T>(e, g, cand, 0, e->stream)) == QG_OK;
+        };
+        for (int r = 0; r < 2 && ok; ++r) ok = unit();
         ok = ok && cudaEventRecord(a, e->stream) == cudaSuccess;
-        for (int r = 0; r < 5 && ok; ++r) ok = group_solve<T>(e, g, cand, 0, e->stream) == QG_OK;
+        for (int r = 0; r < 5 && ok; ++r) ok = unit();
         ok = ok && cudaEventRecord(b, e->stream) == cudaSuccess &&
              cudaEventSynchronize(b) == cudaSuccess;
         float ms = 1e30f;
@@ -2596,6 +2646,15 @@ qg_status qg_ensemble_create(const qg_basin* basins, const double* Re, const dou
         ensemble_free(e);
         (void)cudaGetLastError();
         return QG_ERR_CUDA;
+    }
+    // the graph is built now, while the members' buffers may run timing steps
+    e->fresh = true;
+    const qg_status s = ensemble_build(e);
+    e->fresh = false;
+    if (s != QG_OK) {
+        ensemble_free(e);
+        (void)cudaGetLastError();
+        return s;
     }
     *out = e;
     return QG_OK;
