@@ -37,6 +37,8 @@
 // and the row sine transform adds P0 + P1 + P2 + P3 in that order.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "bounds.cuh"
 #include "qg_internal.cuh"
 
@@ -243,18 +245,17 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
     const bool active = ys < ny;                     // uniform in the group
     const int xq = x0 + 4 * lane;
 
-    // row y of a halo tile (w^(s) or the fine psi): own quad + shuffled halos
+    // row y of a halo tile (w^(s) or the fine psi): own quad and the
+    // columns either side, all in the tile
     auto row_halo = [&](const T* tile, int y, T v[6]) {
-        const T* r = tile + (y - yc + 1) * SWX;
+        const int o = (y - yc + 1) * SWX + 4 * lane;
+        const T* r = tile + o;
         T c[4] = {T(0), T(0), T(0), T(0)};
-        if (QG_IN((y - yc + 1) * SWX + 4 * lane + 7, (RC + 2) * SWX, 5) &&
-            QG_IN((y - yc + 1) * SWX, (RC + 2) * SWX, 5))
-            lds4(r + 4 * lane + 4, c);
-        T left = __shfl_up_sync(gm, c[3], 1, 16);
-        T right = __shfl_down_sync(gm, c[0], 1, 16);
-        if (lane == 0) left = r[3];
-        if (lane == 15) right = r[TX + 4];
-        v[0] = left; v[1] = c[0]; v[2] = c[1]; v[3] = c[2]; v[4] = c[3]; v[5] = right;
+        const bool ok = QG_IN(o + 8, (RC + 2) * SWX, 5) && QG_IN(o + 3, (RC + 2) * SWX, 5);
+        if (ok) lds4(r + 4, c);
+        v[0] = ok ? r[3] : T(0);
+        v[1] = c[0]; v[2] = c[1]; v[3] = c[2]; v[4] = c[3];
+        v[5] = ok ? r[8] : T(0);
     };
     const int Ib = (xq - 1) >> LV;
     T c0[4], c1[4], d0[4], d1[4];    // coarse rows around y of psi (and of the other layer)
@@ -269,8 +270,8 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
     // multiple of RY, itself a multiple of 2^l).  Sums of products are
     // written as explicit fma: left to the compiler, the two instantiations
     // of this body (one basin, batch) could contract them differently.
-    auto psi_row = [&](int y, int ph, const T (&c0)[4], const T (&c1)[4], T v[6]) {
-        if (y < 0 || y >= ny) {
+    auto psi_row = [&](int y, int ph, const T (&c0)[4], const T (&c1)[4], T v[6], bool chk) {
+        if (chk && (y < 0 || y >= ny)) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) v[k] = T(0);
             return;
@@ -304,7 +305,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
     };
     // psi of sweep row rr (fine row y = ys - 1 + rr), and for two layers
     // the other layer's psi of that row
-    auto load_psi = [&](int rr, int y, T v[6], T* vo) {
+    auto load_psi = [&](int rr, int y, T v[6], T* vo, bool chk) {
         if (LV == 0) {
             row_halo(sp, y, v);
         } else {
@@ -326,8 +327,8 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
                 }
             }
             const int ph = (rr - 1) & (F - 1);
-            psi_row(y, ph, c0, c1, v);
-            if constexpr (TL) psi_row(y, ph, d0, d1, vo);
+            psi_row(y, ph, c0, c1, v, chk);
+            if constexpr (TL) psi_row(y, ph, d0, d1, vo, chk);
         }
     };
     // two layers: w_i = Q_i/Ro + k_p (psi_i - psi_j) on a row (Eq. pv-non)
@@ -339,15 +340,22 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
     T accA[NM], accB[NM], accE[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) accA[m] = accB[m] = accE[m] = T(0);
-    if (active) {
+    // A tile that touches no wall (its rows, the rows above and below it
+    // and its columns all interior) sweeps without the per-row wall tests:
+    // one-layer FP32 sweeps at l <= 2, where the second body costs no
+    // spills.  (A third body for stages without w^n measured slower.)
+    constexpr bool kSplit = sizeof(T) == 4 && !TL && LV <= 2;
+    const bool interior = kSplit && x0 >= 1 && x0 + TX <= nx && yc >= 1 && yc + RC <= ny - 1;
+    auto sweep = [&](auto in_tag) {
+        constexpr bool IN = decltype(in_tag)::value;
         // rows y-1, y, y+1 of w^(s) and psi in rotating slots (two layers:
         // also the relative vorticity WV of the dissipation)
         T W[3][6], P[3][6], WV[TL ? 3 : 1][6], PO[TL ? 6 : 1];
         row_halo(sw, ys - 1, W[0]);
-        load_psi(0, ys - 1, P[0], PO);
+        load_psi(0, ys - 1, P[0], PO, !IN);
         if constexpr (TL) w_row(W[0], P[0], PO, WV[0]);
         row_halo(sw, ys, W[1]);
-        load_psi(1, ys, P[1], PO);
+        load_psi(1, ys, P[1], PO, !IN);
         if constexpr (TL) w_row(W[1], P[1], PO, WV[1]);
         const T c_lap0 = T(-2) * (p.c_lapx + p.c_lapy);
 
@@ -356,9 +364,9 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
             const int y = ys + o;
             const int sb = o % 3, sc = (o + 1) % 3, sa = (o + 2) % 3;
             row_halo(sw, y + 1, W[sa]);
-            load_psi(o + 2, y + 1, P[sa], PO);
+            load_psi(o + 2, y + 1, P[sa], PO, !IN);
             if constexpr (TL) w_row(W[sa], P[sa], PO, WV[sa]);
-            const bool row_ok = y >= 1 && y <= ny - 1;
+            const bool row_ok = IN || (y >= 1 && y <= ny - 1);
             const size_t ro = (size_t)y * ld;
             T wn[4] = {T(0), T(0), T(0), T(0)};
             const bool row_in = QG_IN((y - yc) * TX + 4 * lane + 3, RC * TX, 7) &&
@@ -369,7 +377,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
                 if (row_in) lds4(sf + (y - yc) * TX + 4 * lane, fv);
             } else {
                 // (the bottom layer of two has no wind: frow is null there)
-                const T fr = (!TL || p.frow) ? __ldg(p.frow + (y <= ny ? y : ny)) : T(0);
+                const T fr = (!TL || p.frow) ? __ldg(p.frow + (IN || y <= ny ? y : ny)) : T(0);
     #pragma unroll
                 for (int q = 0; q < 4; ++q) fv[q] = fr;
             }
@@ -430,7 +438,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
                 out[q] = fma(p.a, wn[q], p.b * fma(dt, Gv, q00));
             }
 
-            const bool quad_ok = row_ok && xq >= 1 && xq + 3 <= nx - 1;
+            const bool quad_ok = IN || (row_ok && xq >= 1 && xq + 3 <= nx - 1);
             const long long fine_n = (long long)(ny + 1) * ld;
             if (quad_ok) {
                 if (QG_IN(ro + xq + 3, fine_n, 8)) stg4(p.wout + ro + xq, out);
@@ -486,6 +494,16 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
                     if (LV == 1) accB[mlo + 1] += whi * xb;
                 }
             }
+        }
+    };
+    if (active) {
+        if constexpr (kSplit) {
+            if (interior)
+                sweep(std::true_type{});
+            else
+                sweep(std::false_type{});
+        } else {
+            sweep(std::false_type{});
         }
     }
     pdl_trigger();

@@ -166,8 +166,9 @@ def test_fused_tile_indices_stay_in_shared_memory(esz, lv, tl, rc, ry):
         ys = grp * pl["RY"]
         rows = np.arange(ys - 1, ys + pl["RY"] + 1) + 1
         assert rows.min() >= 0 and rows.max() < rc + 2
-    # the quad load (4 lane + 4 .. + 7) and the two edge reads (3, TX + 4)
-    assert (4 * lanes + 7).max() < SWX and TX + 4 < SWX
+    # the quad load (4 lane + 4 .. + 7) and the columns either side of it
+    # (4 lane + 3, 4 lane + 8)
+    assert (4 * lanes + 3).min() >= 0 and (4 * lanes + 8).max() < SWX
     # interior boxes (w^n, forcing): (y - yc) TX + 4 lane + 3 < RC TX
     assert (rc - 1) * TX + (4 * lanes + 3).max() < rc * TX
     if lv > 0:
