@@ -125,9 +125,10 @@ struct Plan {
     static constexpr int G = RC / RY;               // groups per CTA
     static constexpr int THREADS = 16 * G;
     // CTAs per SM the registers are budgeted for: FP32 one-layer sweeps as
-    // many as make 768 threads (80 registers each); FP64 and two-layer
-    // sweeps 2 CTAs (their state needs up to 232 registers)
-    static constexpr int MINB_RAW = (sizeof(T) == 4 && !TL) ? 768 / THREADS : 2;
+    // many as make 640 threads (102 registers each: at 80, for 768 threads,
+    // the l >= 1 sweeps spill); FP64 and two-layer sweeps 2 CTAs (their
+    // state needs up to 232 registers)
+    static constexpr int MINB_RAW = (sizeof(T) == 4 && !TL) ? 640 / THREADS : 2;
     static constexpr int MINB = MINB_RAW < 1 ? 1 : (MINB_RAW > 16 ? 16 : MINB_RAW);
     static constexpr int F = 1 << LV;
     static constexpr int CPX = TX / F + 4;
@@ -357,7 +358,14 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
         row_halo(sw, ys, W[1]);
         load_psi(1, ys, P[1], PO, !IN);
         if constexpr (TL) w_row(W[1], P[1], PO, WV[1]);
+        // w^(s+1) = a w^n + b w^(s) + b dt G: the coefficients of G come
+        // scaled by b dt, and for one layer the centre weight of the
+        // Laplacian joins b on w^(s)
         const T c_lap0 = T(-2) * (p.c_lapx + p.c_lapy);
+        const T bdt = p.b * dt;
+        const T k_beta = -p.c_beta * bdt, k_jac = -p.c_jac * bdt;
+        const T k_lx = p.c_lapx * bdt, k_ly = p.c_lapy * bdt;
+        const T k_0 = TL ? (c_lap0 - p.drag) * bdt : fma(c_lap0, bdt, p.b);
 
     #pragma unroll
         for (int o = 0; o < RY; ++o) {
@@ -421,21 +429,22 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_w, const CUtens
                 jac = fma(-q1m, p10 - p0m, jac);
                 // (1/Ro) J(psi, y) in Arakawa's form: (4 c_j + c_{j+1} + c_{j-1})/(6 Ro)
                 const T beta = fma(T(4), Hc[q], Ha[q] + Hb[q]);
-                // G = F + (1/Re) lap w - J(psi, w)/(12 dx dy) - beta/(12 Ro dx)
-                T Gv = fma(-p.c_beta, beta, fv[q]);
-                Gv = fma(-p.c_jac, jac, Gv);
+                // b dt G, G = F + (1/Re) lap w - J(psi, w)/(12 dx dy) - beta/(12 Ro dx)
+                T Gv = fma(k_beta, beta, bdt * fv[q]);
+                Gv = fma(k_jac, jac, Gv);
                 if constexpr (TL) {
                     // A lap w_i - drag w_i (Eq. ge-non)
                     const T v00 = WV[sc][i];
-                    Gv = fma(c_lap0 - p.drag, v00, Gv);
-                    Gv = fma(p.c_lapy, WV[sa][i] + WV[sb][i], Gv);
-                    Gv = fma(p.c_lapx, WV[sc][i + 1] + WV[sc][i - 1], Gv);
+                    Gv = fma(k_0, v00, Gv);
+                    Gv = fma(k_ly, WV[sa][i] + WV[sb][i], Gv);
+                    Gv = fma(k_lx, WV[sc][i + 1] + WV[sc][i - 1], Gv);
+                    Gv = fma(p.b, q00, Gv);
                 } else {
-                    Gv = fma(c_lap0, q00, Gv);
-                    Gv = fma(p.c_lapy, q01 + q0m, Gv);
-                    Gv = fma(p.c_lapx, q10 + qm0, Gv);
+                    Gv = fma(k_0, q00, Gv);
+                    Gv = fma(k_ly, q01 + q0m, Gv);
+                    Gv = fma(k_lx, q10 + qm0, Gv);
                 }
-                out[q] = fma(p.a, wn[q], p.b * fma(dt, Gv, q00));
+                out[q] = fma(p.a, wn[q], Gv);
             }
 
             const bool quad_ok = IN || (row_ok && xq >= 1 && xq + 3 <= nx - 1);
