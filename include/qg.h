@@ -276,7 +276,9 @@ qg_status qg_set_solver(qg_handle h, qg_solver kind, int32_t cycles);
 /* qg_solve_engine -- which kernel the step's elliptic solves run on (host
  * pointer): chosen when the handle is created by timing whole steps with
  * every candidate that supports the elliptic grid (the QG_SOLVE_ENGINE
- * environment variable forces a supported one).  4 or 16: shared-memory
+ * environment variable forces a supported one; the choice and the stencil
+ * tile are cached per grid for the process and, when QG_TUNE_CACHE names a
+ * file, in that file).  4 or 16: shared-memory
  * Stockham FFT with base radix 4 or 16; 32, 33, 34: warp-group FFT with 32,
  * 16 or 8 values per thread; 40: the sine sums as dense matrix products on
  * the tensor cores, 3xTF32 (FP32 grids of at most 64 x 128 or 128 x 64
@@ -410,20 +412,29 @@ qg_status qg_energy_gradient(qg_handle h, double scale, void* g);
 /* ---- ensembles of basins --------------------------------------------------
  * Many independent one-layer basins (Section 2.1), each with its own grid,
  * Re, Ro, forcing amplitude, dt and CGP level (Section 3), stepped together:
- * one CUDA graph per ensemble step holds every member's CGPRK3 step on up to
- * 8 concurrent branches, members placed largest first on the least-loaded
- * branch.  Each member runs the kernels a handle of its own would, except
- * that its solves run as three plain launches instead of one cooperative
- * launch, so that members can share the GPU; with the same FFT schedule the
- * results are bitwise those of a stand-alone handle.  The paper runs one basin at a time; the
- * ensemble is this library's way of filling a GPU with small basins.     */
+ * one CUDA graph per ensemble step.  Members whose elliptic grids have the
+ * same shape and spacing form a group; per TVDRK3 stage a group runs one
+ * batched solve for all its members and one batched fused fine stage per
+ * fine level (members' tiles side by side in one launch), and each group's
+ * chain is a branch of its own in the graph.  A group's solve engine is
+ * picked when the ensemble is created, by timing whole group steps with
+ * each engine that batches its grid (the members' buffers are zeroed
+ * afterwards); the choice is cached for the process and, when the
+ * QG_TUNE_CACHE environment variable names a file, in that file.  With the
+ * same solve engine and tile the results are bitwise those of stand-alone
+ * handles.  A group with a member on the multigrid solver runs its
+ * members' own solves.  The
+ * paper runs one basin at a time; the ensemble is this library's way of
+ * filling a GPU with small basins.                                         */
 typedef struct qg_ensemble_s* qg_ensemble;
 
 /* qg_ensemble_create -- `count` (1..4096) members; basins[i], Re[i], Ro[i],
  * levels[i] as for qg_create with layers = 1 and Fr = 0.  All members share
- * `dtype` and `cuda_stream`.  Member states start at zero.
+ * `dtype` and `cuda_stream`.  Builds the step graph (group engines timed on
+ * the device, see above); member states start at zero.
  * Errors: as qg_create for the first failing member (nothing is kept),
- * QG_ERR_ARG for NULL arrays or a bad count.                               */
+ * QG_ERR_CUDA if the graph cannot be built, QG_ERR_ARG for NULL arrays or
+ * a bad count.                                                             */
 qg_status qg_ensemble_create(const qg_basin* basins, const double* Re, const double* Ro,
                              const int* levels, int count, qg_dtype dtype,
                              void* cuda_stream, qg_ensemble* out);
@@ -438,7 +449,8 @@ qg_status qg_ensemble_member(qg_ensemble e, int index, qg_handle* out);
  * ensemble's stream (one graph launch per step).                           */
 qg_status qg_ensemble_step(qg_ensemble e, int64_t n);
 
-/* qg_ensemble_kernel_count -- kernels one ensemble step launches.          */
+/* qg_ensemble_kernel_count -- kernels one ensemble step launches (rebuilds
+ * the graph first if a member's own step changed).                         */
 qg_status qg_ensemble_kernel_count(qg_ensemble e, int64_t* count);
 
 /* qg_ensemble_synchronize -- wait for the ensemble's work; returns the

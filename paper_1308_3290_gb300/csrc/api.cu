@@ -577,7 +577,8 @@ qg_status solve_level(qg_ctx* h, const LevelTables& t, const void* in, void* tr,
 // its fields through L2), and the fastest is kept.  Results are cached per
 // (nx, ny, levels, layers, dtype) for the process and, when the environment
 // variable QG_TUNE_CACHE names a file, in that file (one line
-// "nx ny levels layers esz engine" per entry).  QG_SOLVE_ENGINE=4|16|32|33|34|40|41|50
+// "nx ny levels layers esz engine rows ry" per entry; ensemble groups add
+// lines "group mx my dx dy members esz engine").  QG_SOLVE_ENGINE=4|16|32|33|34|40|41|50
 // forces a choice where that engine supports the grid.  Other grids use the
 // size rule.
 
@@ -631,7 +632,17 @@ struct TuneVal {
 };
 std::map<TuneKey, TuneVal> g_tune_cache;
 bool g_tune_file_read = false;
+// ensemble groups' solve engines by (elliptic grid, spacings, members, dtype)
+using GroupKey = std::tuple<int, int, double, double, int, int>;
+std::mutex g_batch_tune_mutex;
+std::map<GroupKey, int> g_batch_tune;
 
+bool known_engine(int e) {
+    return e == 4 || e == 16 || is_warp_engine(e) || e == kMatrixEngine || e == kTcEngine ||
+           e == kStreamEngine;
+}
+
+// (called with g_tune_mutex held)
 void tune_file_load() {
     if (g_tune_file_read) return;
     g_tune_file_read = true;
@@ -639,12 +650,20 @@ void tune_file_load() {
     if (!path) return;
     FILE* f = std::fopen(path, "r");
     if (!f) return;
-    int a, b, c, d, x, e, r, y;
-    while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &a, &b, &c, &d, &x, &e, &r, &y) == 8)
-        if ((e == 4 || e == 16 || is_warp_engine(e) || e == kMatrixEngine || e == kTcEngine ||
-             e == kStreamEngine) &&
-            fine_rows_supported((size_t)x, d, c, r, y))
+    char line[256];
+    while (std::fgets(line, sizeof line, f)) {
+        int a, b, c, d, x, e, r, y;
+        double dx, dy;
+        if (std::sscanf(line, "group %d %d %lf %lf %d %d %d", &a, &b, &dx, &dy, &c, &x, &e) == 7) {
+            if (known_engine(e)) {
+                std::lock_guard<std::mutex> lock(g_batch_tune_mutex);
+                g_batch_tune[GroupKey(a, b, dx, dy, c, x)] = e;
+            }
+        } else if (std::sscanf(line, "%d %d %d %d %d %d %d %d", &a, &b, &c, &d, &x, &e, &r, &y) == 8 &&
+                   known_engine(e) && fine_rows_supported((size_t)x, d, c, r, y)) {
             g_tune_cache[TuneKey(a, b, c, d, x)] = {e, r, y};
+        }
+    }
     std::fclose(f);
 }
 
@@ -655,6 +674,16 @@ void tune_file_store(const TuneKey& k, const TuneVal& v) {
     if (!f) return;
     std::fprintf(f, "%d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
                  std::get<3>(k), std::get<4>(k), v.engine, v.rows, v.ry);
+    std::fclose(f);
+}
+
+void tune_file_store_group(const GroupKey& k, int engine) {
+    const char* path = std::getenv("QG_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "group %d %d %.17g %.17g %d %d %d\n", std::get<0>(k), std::get<1>(k),
+                 std::get<2>(k), std::get<3>(k), std::get<4>(k), std::get<5>(k), engine);
     std::fclose(f);
 }
 
@@ -2442,9 +2471,8 @@ qg_status group_step_eager(qg_ensemble e, const EnsSolveGroup& g, int engine, cu
 // buffers to rest; a later rebuild, whose members hold state, times stage-1
 // solves alone (they overwrite only work arrays and streamfunctions that
 // every stage recomputes).  Results are cached per (grid, spacings,
-// members, dtype) for the process.
-std::mutex g_batch_tune_mutex;
-std::map<std::tuple<int, int, double, double, int, int>, int> g_batch_tune;
+// members, dtype) for the process and in the QG_TUNE_CACHE file; a cached
+// engine that is no longer a candidate is timed again.
 
 template <typename T>
 qg_status tune_group(qg_ensemble e, EnsSolveGroup& g, const std::vector<int>& cands,
@@ -2454,11 +2482,16 @@ qg_status tune_group(qg_ensemble e, EnsSolveGroup& g, const std::vector<int>& ca
         g.engine = cands[0];
         return QG_OK;
     }
-    const auto key = std::make_tuple(g.mx, g.my, g.dxc, g.dyc, (int)g.members.size(), (int)sizeof(T));
+    const GroupKey key(g.mx, g.my, g.dxc, g.dyc, (int)g.members.size(), (int)sizeof(T));
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        tune_file_load();
+    }
     {
         std::lock_guard<std::mutex> lock(g_batch_tune_mutex);
         auto it = g_batch_tune.find(key);
-        if (it != g_batch_tune.end()) {
+        if (it != g_batch_tune.end() &&
+            std::find(cands.begin(), cands.end(), it->second) != cands.end()) {
             g.engine = it->second;
             return QG_OK;
         }
@@ -2492,6 +2525,7 @@ qg_status tune_group(qg_ensemble e, EnsSolveGroup& g, const std::vector<int>& ca
     g.engine = pick;
     std::lock_guard<std::mutex> lock(g_batch_tune_mutex);
     g_batch_tune[key] = pick;
+    tune_file_store_group(key, pick);
     return QG_OK;
 }
 

@@ -153,3 +153,69 @@ def test_ensemble_member_time_mean_matches_oracle():
         ref = O.mean_psi(w0, ob, n0, n1)
         assert rel_l2(to_np(out), ref) <= 1e-12, (i, rel_l2(to_np(out), ref))
     ens.close()
+
+
+_CACHE_SCRIPT = r"""
+import json, os, sys
+import numpy as np
+from paper_1308_3290_gb300 import inputs, qg
+members = json.loads(sys.argv[1])
+force = sys.argv[2]
+ens = qg.Ensemble(members, dtype="f32")
+for i, m in enumerate(members):
+    ens.member(i).set_state(inputs.perturbation(m["nx"], m["ny"], seed=70 + i) * 50.0)
+ens.step(3)
+ens.synchronize()
+same = True
+if force != "-":
+    # stand-alone handles on the engine the cache file names for the group
+    os.environ["QG_SOLVE_ENGINE"] = force
+    os.environ.pop("QG_TUNE_CACHE")
+    for i, m in enumerate(members):
+        b = qg.Basin(m["nx"], m["ny"], Re=m["Re"], Ro=m["Ro"], levels=m["levels"], dt=m["dt"],
+                     amp=m["amp"], dtype="f32")
+        assert qg.qg_solve_engine(b.h) == int(force)
+        b.set_state(inputs.perturbation(m["nx"], m["ny"], seed=70 + i) * 50.0)
+        b.step(3)
+        b.synchronize()
+        same = same and np.array_equal(b.state().cpu().numpy(), ens.member(i).state().cpu().numpy())
+        b.close()
+ens.close()
+print(json.dumps({"same": bool(same)}))
+"""
+
+
+def test_group_engine_from_the_tune_cache_file(tmp_path):
+    """An ensemble group's engine choice goes to the QG_TUNE_CACHE file and a
+    later process takes it from there: the file's group line, rewritten to
+    another engine that batches the grid, decides the engine of a fresh
+    process's group (bitwise the states of stand-alone handles on that
+    engine)."""
+    require_gpu()
+    import json
+    import os
+    import subprocess
+    import sys
+    members = [dict(nx=512, ny=1024, Re=200.0, Ro=0.0016, levels=1, dt=2e-5, amp=1.0),
+               dict(nx=512, ny=1024, Re=450.0, Ro=0.0036, levels=1, dt=2e-5, amp=0.7)]
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, QG_TUNE_CACHE=str(cache), QG_FINE_ROWS="64")
+    env.pop("QG_SOLVE_ENGINE", None)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+    def run(force):
+        r = subprocess.run([sys.executable, "-c", _CACHE_SCRIPT, json.dumps(members), force],
+                           env=env, cwd=root, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+    run("-")
+    lines = [ln.split() for ln in cache.read_text().splitlines() if ln.startswith("group ")]
+    assert len(lines) == 1, cache.read_text()
+    g = lines[0]
+    # group mx my dx dy members esz engine
+    assert g[1:3] == ["256", "512"] and float(g[3]) == 1.0 / 256 and float(g[4]) == 2.0 / 512
+    assert g[5:7] == ["2", "4"] and int(g[7]) in (32, 33, 34, 50)
+    other = "33" if g[7] != "33" else "34"
+    cache.write_text(cache.read_text().replace(" ".join(g), " ".join(g[:7] + [other])))
+    assert run(other)["same"]
