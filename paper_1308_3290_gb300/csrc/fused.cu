@@ -750,7 +750,7 @@ template cudaError_t launch_fine_batch<double>(const FineMember<double>*, const 
                                                bool, bool, cudaStream_t, int);
 
 size_t fine_tile_rows(size_t esz) { return esz == 8 ? Rows<double>::value : Rows<float>::value; }
-// the tile of ensemble members' batched sweeps: 64 rows (128 threads, 6 CTAs
+// the tile of ensemble members' batched sweeps: 64 rows (128 threads, 5 CTAs
 // per SM in FP32; the tile the step autotuner keeps for large one-layer
 // basins)
 int ensemble_tile_rows(size_t esz) { return 64; }
