@@ -36,7 +36,8 @@ struct DstLaunch {
 
 // The elliptic solve of one level (solve.cu): x pass of `in` (the sum of
 // nin planes per layer; with nin == 4 plane 1 is read only at columns
-// k % part_px == 0, plane 2 at rows r % part_py == 0, plane 3 at both), the
+// k % part_px == 0, plane 2 at rows r % part_py == 0, plane 3 at both;
+// part_px and part_py are powers of two, tested with masks), the
 // y pass with the eigenvalue division (one layer: lap_h psi = rhs) or the
 // coupled solve of Eqs. isub-1/2 (two layers), the inverse x pass into
 // `out`.  in / work / out have the level's padded layout (pitch ld), tr the

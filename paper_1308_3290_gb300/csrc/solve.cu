@@ -167,8 +167,8 @@ __device__ void run_phase(const PairIO<T>& io, int op, CT<T>* bufs, const CT<T>*
         const bool va = pv && ra <= io.nrows, vb = pv && rb <= io.nrows;
         // all loads first
         T av[EPT], bv[EPT];
-        const bool rpa = io.nin > 1 && (ra % io.part_py) == 0;
-        const bool rpb = io.nin > 1 && (rb % io.part_py) == 0;
+        const bool rpa = io.nin > 1 && (ra & (io.part_py - 1)) == 0;
+        const bool rpb = io.nin > 1 && (rb & (io.part_py - 1)) == 0;
         const T* const* ia = io.in + la * 4;
         const T* const* ib = io.in + lb * 4;
         const size_t oa = (size_t)ra * io.ld_in, ob = (size_t)rb * io.ld_in;
@@ -181,7 +181,7 @@ __device__ void run_phase(const PairIO<T>& io, int op, CT<T>* bufs, const CT<T>*
                 if (va) a = ia[0][oa + j];
                 if (vb) b = ib[0][ob + j];
                 if (io.nin > 1) {
-                    const bool cx = (j % io.part_px) == 0;
+                    const bool cx = (j & (io.part_px - 1)) == 0;
                     if (va) {
                         if (cx) a += ia[1][oa + j];
                         if (rpa) a += ia[2][oa + j];
@@ -430,6 +430,9 @@ static cudaError_t launch_engine(const SolveParams<T>& P, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_solve(const SolveParams<T>& P, int engine, cudaStream_t s) {
+    // the partial planes' periods are tested with masks
+    if (!P.batch && P.nin > 1 && !(is_pow2(P.part_px) && is_pow2(P.part_py)))
+        return cudaErrorInvalidValue;
     if (is_warp_engine(engine)) return launch_solve32<T>(P, warp_engine_radix(engine), s);
     if (engine == kStreamEngine) return launch_solve_stream<T>(P, s);
     if (P.batch) return cudaErrorInvalidValue;   // batches: warp-group engines only

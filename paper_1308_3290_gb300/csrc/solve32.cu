@@ -391,14 +391,14 @@ __device__ __forceinline__ void rhs4(const SolveParams<T>& P, int layer, int r, 
     }
     ld4<T>(P.in[layer][0] + off, o);
     if (P.nin > 1) {
-        const bool ry = r % P.part_py == 0;
+        const bool ry = (r & (P.part_py - 1)) == 0;
         if (ry) {
             T e[4];
             ld4<T>(P.in[layer][2] + off, e);
 #pragma unroll
             for (int q = 0; q < 4; ++q) o[q] += e[q];
         }
-        if (c0 % P.part_px == 0) {
+        if ((c0 & (P.part_px - 1)) == 0) {
             o[0] += __ldg(P.in[layer][1] + off);
             if (ry) o[0] += __ldg(P.in[layer][3] + off);
         }

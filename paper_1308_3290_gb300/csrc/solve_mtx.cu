@@ -176,9 +176,9 @@ __device__ __forceinline__ void load_q(const SolveParams<float>& P, const float*
             const size_t off = (size_t)y * P.ld + x;
             v = __ldg(in[0] + off);
             if (P.nin > 1) {
-                const bool ry = y % P.part_py == 0;
+                const bool ry = (y & (P.part_py - 1)) == 0;
                 if (ry) v += __ldg(in[2] + off);
-                if (x % P.part_px == 0) {
+                if ((x & (P.part_px - 1)) == 0) {
                     v += __ldg(in[1] + off);
                     if (ry) v += __ldg(in[3] + off);
                 }
@@ -354,7 +354,7 @@ void mtx_table(int mx, int my, double dx, double dy, float* out) {
 cudaError_t launch_solve_mtx(const SolveParams<float>& P, const float* tab, cudaStream_t s) {
     // (a batch's members carry their own right-hand side planes)
     if (!mtx_supports(P.mx, P.my, sizeof(float), P.layers) || !tab ||
-        (!P.batch && (P.nin < 1 || (P.nin > 1 && (P.part_px < 1 || P.part_py < 1)))))
+        (!P.batch && (P.nin < 1 || (P.nin > 1 && !(is_pow2(P.part_px) && is_pow2(P.part_py))))))
         return cudaErrorInvalidValue;
     const MtxGeo g = mtx_geo(P.mx, P.my, P.layers);
     const size_t sm = (size_t)g.end * sizeof(float);

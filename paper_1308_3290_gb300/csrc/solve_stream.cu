@@ -254,7 +254,8 @@ __device__ __forceinline__ void reflect(Cplx<T> (&v)[16], CT<T>* buf, int t, con
 
 // Rows a (and b when vb) of the right-hand side, elements j = t + G r,
 // r < 8 (j = 0 is the wall: 0): plane 0, plus plane 2 on rows with
-// row % part_py == 0, plus planes 1 and 3 at columns j % part_px == 0.
+// row % part_py == 0, plus planes 1 and 3 at columns j % part_px == 0
+// (periods are powers of two: masks).
 // Every load of a row is issued before any sum.
 template <typename T, int G>
 __device__ __forceinline__ void load_rhs(const SolveParams<T>& P, const T* const (&in)[4], int ra,
@@ -273,14 +274,14 @@ __device__ __forceinline__ void load_rhs(const SolveParams<T>& P, const T* const
         b[r] = ib ? __ldg(pb + r * G) : T(0);
     }
     if (P.nin > 1) {
-        const bool ya = ra % P.part_py == 0, yb = rb % P.part_py == 0;
+        const bool ya = (ra & (P.part_py - 1)) == 0, yb = (rb & (P.part_py - 1)) == 0;
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const int j = t + r * G;
             const bool j0 = j == 0;
             const bool ia = va && !j0 && QG_IN(oa + r * G, n, 63);
             const bool ib = vb && !j0 && QG_IN(ob + r * G, n, 63);
-            const bool cx = j % P.part_px == 0;
+            const bool cx = (j & (P.part_px - 1)) == 0;
             if (ia && ya) a[r] += __ldg(in[2] + oa + r * G);
             if (ib && yb) b[r] += __ldg(in[2] + ob + r * G);
             if (ia && cx) {

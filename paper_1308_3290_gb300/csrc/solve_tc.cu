@@ -245,9 +245,9 @@ solve_tc_kernel(SolveParams<float> Pk, const float* __restrict__ tab, TcGeo g) {
         if (c < g.m && QG_IN((long long)off, (long long)(P.my + 1) * P.ld, 82)) {
             v = __ldg(P.in[0][0] + off);
             if (P.nin > 1) {
-                const bool ry = y % P.part_py == 0;
+                const bool ry = (y & (P.part_py - 1)) == 0;
                 if (ry) v += __ldg(P.in[0][2] + off);
-                if (x % P.part_px == 0) {
+                if ((x & (P.part_px - 1)) == 0) {
                     v += __ldg(P.in[0][1] + off);
                     if (ry) v += __ldg(P.in[0][3] + off);
                 }
@@ -382,7 +382,7 @@ void tc_table(int mx, int my, double dx, double dy, float* out) {
 
 cudaError_t launch_solve_tc(const SolveParams<float>& P, const float* tab, cudaStream_t s) {
     if (!tc_supports(P.mx, P.my, sizeof(float), P.layers) || !tab ||
-        (!P.batch && (P.nin < 1 || (P.nin > 1 && (P.part_px < 1 || P.part_py < 1)))))
+        (!P.batch && (P.nin < 1 || (P.nin > 1 && !(is_pow2(P.part_px) && is_pow2(P.part_py))))))
         return cudaErrorInvalidValue;
     const bool batch = P.batch != nullptr;
     if (batch && P.nbatch < 1) return cudaErrorInvalidValue;
