@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--realizations", type=int, default=3)
     ap.add_argument("--ensemble", action="store_true",
                     help="with --profile-only: the 96-basin ensemble instead of one basin")
+    ap.add_argument("--member-alone", action="store_true",
+                    help="with --profile-only: the basin as the one member of an ensemble, "
+                         "stepped alone (its solves run as three split launches, one per pass)")
     return ap.parse_args()
 
 
@@ -94,14 +97,23 @@ def profile_only(args):
                           "steps": args.warmup + args.steps}))
         ens.close()
         return
-    b = qg.Basin(args.nx, args.ny, Re=RE, Ro=RO, levels=args.levels, dt=DT, dtype=args.dtype)
+    ens = None
+    if args.member_alone:
+        ens = qg.Ensemble([dict(nx=args.nx, ny=args.ny, Re=RE, Ro=RO, levels=args.levels, dt=DT,
+                                amp=1.0)], dtype=args.dtype)
+        b = ens.member(0)
+    else:
+        b = qg.Basin(args.nx, args.ny, Re=RE, Ro=RO, levels=args.levels, dt=DT, dtype=args.dtype)
     b.set_state(inputs.gyre_state(args.nx, args.ny, seed=SEED))
     b.step(args.warmup + args.steps)
     b.synchronize()
     torch.cuda.synchronize()
     print(json.dumps({"profile_only": True, "nx": args.nx, "ny": args.ny,
                       "levels": args.levels, "dtype": args.dtype,
+                      "member_alone": args.member_alone, "solve_engine": qg.qg_solve_engine(b.h),
                       "steps": args.warmup + args.steps}))
+    if ens is not None:
+        ens.close()
 
 
 # ---------------------------------------------------------------------------
