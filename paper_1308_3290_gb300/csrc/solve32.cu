@@ -378,6 +378,20 @@ __device__ __forceinline__ void st2(T* p, T a, T b) {
     *reinterpret_cast<CT<T>*>(p) = v;
 }
 
+// four consecutive values: one 16-byte store (FP32) where p is 16-byte
+// aligned, else two 8-byte stores; FP64 two 16-byte stores
+template <typename T>
+__device__ __forceinline__ void st4(T* p, T a, T b, T c, T d) {
+    if constexpr (sizeof(T) == 4) {
+        if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+            *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+            return;
+        }
+    }
+    st2<T>(p, a, b);
+    st2<T>(p + 2, c, d);
+}
+
 // Row r of the right-hand side, elements c0..c0+3: plane 0, plus plane 2 on
 // rows r % part_py == 0, plus planes 1 and 3 at the column c0 when
 // c0 % part_px == 0 (part_px is a multiple of 4).
@@ -584,6 +598,23 @@ __device__ __forceinline__ void raise_err(const SolveParams<T>& P) {
     }
 }
 
+// Phase 0 of a CTA whose two groups hold the pairs of rows r .. r + 3 of
+// one layer: tr[k][r - 1 .. r + 2] for both pairs at once, one 16-byte
+// store per k (the per-pair stores write 8 bytes of each 32-byte sector).
+// r0, r1: the two groups' result buffers, final and visible to the CTA.
+template <typename T>
+__device__ __forceinline__ void store_quad(const SolveParams<T>& P, const PairAt& a0,
+                                           const Geo32& g, const CT<T>* r0, const CT<T>* r1) {
+    const long long nt = (long long)(P.mx + 1) * P.ld_tr;
+    for (int k = threadIdx.x; k < g.N; k += blockDim.x) {
+        if (k == 0 || !QG_IN(px(k), g.buf, 27)) continue;
+        const CT<T> z0 = r0[px(k)], z1 = r1[px(k)];
+        if (!QG_IN((long long)k * P.ld_tr + a0.ra + 2, nt, 29)) continue;
+        T* d = P.tr[a0.layer] + (size_t)k * P.ld_tr + (a0.ra - 1);
+        st4<T>(d, T(-0.5) * z0.y, T(0.5) * z0.x, T(-0.5) * z1.y, T(0.5) * z1.x);
+    }
+}
+
 // One slot of phase ph: the pair of this thread's group, loaded, transformed
 // (phase 1: forward, mode solve, inverse) and stored.
 template <typename T, int OPY, int RAD>
@@ -599,6 +630,21 @@ __device__ __forceinline__ void solve_slot(const SolveParams<T>& P, int ph, int 
     for (int f = 0; f < nfft; ++f) {
         if (f == 1) mode_solve<T, OPY, RAD>(P, a, g, res, t, lamy);
         res = fft_rt<T, RAD>(res, res == cb ? cb2 : cb, t, g, tw, sy);
+    }
+    if (ph == 0 && per == 2) {
+        // the same test in every thread of the CTA (it depends on the slot)
+        const PairAt a0 = pair_at<T, OPY>(P, 0, slot * 2, npairs);
+        const PairAt a1 = pair_at<T, OPY>(P, 0, slot * 2 + 1, npairs);
+        if (a0.va && a0.vb && a1.va && a1.vb && a1.layer == a0.layer && a1.ra == a0.ra + 2 &&
+            ((a0.ra - 1) & 3) == 0) {
+            // group 1's buffers follow group 0's, and both results sit at
+            // the same place in their group's pair of buffers
+            const CT<T>* r0 = res - (size_t)grp * 2 * g.buf;
+            __syncthreads();
+            store_quad<T>(P, a0, g, r0, r0 + 2 * g.buf);
+            __syncthreads();
+            return;
+        }
     }
     store_pair<T, OPY, RAD>(P, ph, a, g, res, t);
     sy.sync();
