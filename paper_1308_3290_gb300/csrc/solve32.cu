@@ -444,8 +444,13 @@ __device__ __forceinline__ PairAt pair_at(const SolveParams<T>& P, int ph, int p
         a.vb = pv && (OPY == 2 || a.rb <= ncols);
     } else {
         const int nrows = P.my - 1, ppl = (nrows + 1) / 2;
-        a.layer = pv ? pair / ppl : 0;
-        a.ra = 1 + 2 * (pv ? pair % ppl : 0);
+        if (OPY == 1) {   // one layer: pairs < ppl, no division
+            a.layer = 0;
+            a.ra = 1 + 2 * (pv ? pair : 0);
+        } else {
+            a.layer = pv ? pair / ppl : 0;
+            a.ra = 1 + 2 * (pv ? pair % ppl : 0);
+        }
         a.rb = a.ra + 1;
         a.va = pv;
         a.vb = pv && a.rb <= nrows;
