@@ -97,6 +97,51 @@ def test_warp_group_cta_buffers_hold_their_pairs(mx, my, rad, esz):
         assert last <= region
 
 
+@pytest.mark.parametrize("mx,my,rad,esz", [(m, n, rad, esz) for rad in (8, 16, 32) for esz in (4, 8)
+                                          for m, n in ((8, 8), (32, 64), (512, 1024), (1024, 512),
+                                                       (2048, 4096), (64, 16), (16, 128))
+                                          if supported(m, rad, esz) and supported(n, rad, esz)])
+def test_joint_transposed_store_is_aligned_and_in_bounds(mx, my, rad, esz):
+    """The x forward phase of a one-layer solve whose CTA holds two pairs
+    (per == 2) writes both pairs' spectra as tr[k][r0 - 1 .. r0 + 2] when
+    the two pairs cover four consecutive rows with (r0 - 1) % 4 == 0: every
+    such piece lies inside the (mx + 1) x ld_tr plane and starts on 16
+    bytes (ld_tr = round_up(my + 1, 32)); the other slots take the
+    per-pair stores.  Every row 1 .. my - 1 is written by exactly one
+    slot."""
+    lgx, lgy = (2 * mx).bit_length() - 1, (2 * my).bit_length() - 1
+    gx, gy = geo32(lgx, rad), geo32(lgy, rad)
+    threads = max(max(gx["G"], gy["G"]), 128)
+    per = threads // gx["G"]
+    ld_tr = (my + 1 + 31) // 32 * 32
+    nrows, ppl = my - 1, my // 2
+    npairs = ppl
+    nslots = (npairs + per - 1) // per
+    rows = []
+
+    def pair_rows(pair):
+        pv = pair < npairs
+        ra = 1 + 2 * (pair if pv else 0)
+        return pv, ra, pv and ra + 1 <= nrows
+
+    for slot in range(nslots):
+        if per == 2:
+            va0, r0, vb0 = pair_rows(2 * slot)
+            va1, r1, vb1 = pair_rows(2 * slot + 1)
+            if va0 and vb0 and va1 and vb1 and r1 == r0 + 2 and (r0 - 1) % 4 == 0:
+                for k in range(1, gx["N"]):
+                    off = k * ld_tr + (r0 - 1)
+                    assert off + 3 < (mx + 1) * ld_tr
+                    assert (off * esz) % 16 == 0
+                rows += [r0, r0 + 1, r0 + 2, r0 + 3]
+                continue
+        for g in range(per):
+            va, ra, vb = pair_rows(slot * per + g)
+            if va:
+                rows += [ra] + ([ra + 1] if vb else [])
+    assert sorted(rows) == list(range(1, my))
+
+
 def test_batched_solve_queue_claims_dependencies_first():
     """The batched solve's work items (phase by phase, member by member)
     decode to every (phase, member, slot) exactly once, and every item a
