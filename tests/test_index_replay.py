@@ -169,6 +169,137 @@ def test_batched_solve_queue_claims_dependencies_first():
         assert len(seen) == total
 
 
+# ---- long-sequence engine (csrc/solve_stream.cu, engine 50) -------------------
+
+
+def sp(m):
+    """Padded shared-memory slot of complex element m (one pad per 16)."""
+    return m + (m >> 4)
+
+
+def buf_elems(L):
+    return sp(L) + 2
+
+
+def stage_pitch(ppc):
+    return 2 * ppc + (4 if ppc >= 4 else 2)
+
+
+def tw_off(p):
+    o, ns = 0, 16
+    for _ in range(1, p):
+        o += 16 * ns
+        ns *= 16
+    return o
+
+
+def pass_table_size(L, rad):
+    lg, lr = L.bit_length() - 1, rad.bit_length() - 1
+    np_, rem = lg // lr, lg % lr
+    n, ns = 0, rad
+    for _ in range(1, np_):
+        n += rad * ns
+        ns *= rad
+    if rem > 0 and np_ >= 1:
+        n += (1 << rem) * ns
+    return n
+
+
+def ppc_for(lg, want, esz):
+    p = want
+    while p > 1 and (((1 << lg) // 16) * p > (1024 if esz == 4 else 512)
+                     or p * buf_elems(1 << lg) * esz * 2 > 140 * 1024):
+        p //= 2
+    return p
+
+
+STREAM = [(lg, esz) for esz in (4, 8) for lg in range(9, 15 if esz == 4 else 14)]
+
+
+@pytest.mark.parametrize("lg,esz", STREAM)
+def test_stream_engine_fft_slots_and_twiddles(lg, esz):
+    """Engine 50's FFT of length L = 2^lg with G = L/16 threads of 16
+    values: every pass's stores are a permutation of the L elements into
+    padded slots below buf_elems(L), its loads read slot sp(element) (the
+    per-thread base plus constant strides the kernel uses), the odd
+    extension reads only slots written before it, and every twiddle read
+    lies in the radix-16 pass table."""
+    L, N, G = 1 << lg, 1 << (lg - 1), 1 << (lg - 4)
+    NP, REM, LIM, SG = lg // 4, lg % 4, buf_elems(L), G + G // 16
+    t, r = np.arange(G), np.arange(16)
+    # loads t + r G at sp(t) + r sp(G)
+    assert np.array_equal(sp(t)[:, None] + r[None, :] * SG, sp(t[:, None] + r[None, :] * G))
+    # odd extension: stores z[t + r G] (r < 8) and the zero at N; loads
+    # -z[c G - t], c = 16 - r, at c sp(G) - (t + ceil(t / 16))
+    written = set(sp(t[:, None] + r[None, :8] * G).ravel().tolist()) | {sp(N)}
+    assert max(written) < LIM
+    u = t + ((t + 15) >> 4)
+    for rr in range(8, 16):
+        c = 16 - rr
+        slot = c * SG - u
+        assert np.array_equal(slot, sp(c * G - t))
+        assert set(slot.tolist()) <= written
+    # stores of the radix-16 passes (sub-transform size NS = 16^(p-1)) and
+    # of the remainder pass (NS = 16^(NP-1))
+    ns_list = [16 ** (p - 1) for p in range(1, NP)] + ([16 ** (NP - 1)] if REM else [])
+    for NS in ns_list:
+        if NS == 1:
+            base, step = 17 * t, 1
+            logical = 16 * t[:, None] + r[None, :]
+        else:
+            k = t & (NS - 1)
+            d = (t - k) * 16 + k
+            base, step = d + (d >> 4), NS + NS // 16
+            logical = d[:, None] + r[None, :] * NS
+        slots = base[:, None] + r[None, :] * step
+        assert np.array_equal(slots, sp(logical))
+        assert np.array_equal(np.sort(logical.ravel()), np.arange(L))
+        assert slots.max() < LIM
+    table = pass_table_size(L, 16)
+    for P in range(1, NP):      # radix-16 pass P reads w, w^2, w^4, w^8 of its block
+        NS = 16 ** P
+        assert tw_off(P) + (NS - 1) + 8 * NS < table
+    if REM:
+        R = 1 << REM
+        B, NSR = 16 // R, L // R
+        b, rr = np.arange(B), np.arange(R)
+        slots = (sp(t)[:, None, None] + b[None, :, None] * SG
+                 + rr[None, None, :] * (NSR + NSR // 16))
+        elems = t[:, None, None] + b[None, :, None] * G + rr[None, None, :] * NSR
+        assert np.array_equal(slots, sp(elems))
+        assert np.array_equal(np.sort(elems.ravel()), np.arange(L))
+        assert tw_off(NP) + (G - 1) + (R - 1) * NSR < table
+
+
+@pytest.mark.parametrize("lg,esz", STREAM)
+@pytest.mark.parametrize("want", (1, 2, 4))
+def test_stream_engine_staged_transposed_writes(lg, esz, want):
+    """The passes that write transposed stage element k of group g's pair
+    at [k SP + 2 g + (0, 1)] and write column q of rows k = k0 + i G/2 from
+    thread e = k0 W + q: every (k, q) once, all inside the staging area,
+    which with the FFT buffers fits the CTA's dynamic shared memory and the
+    thread limit."""
+    L, N, G = 1 << lg, 1 << (lg - 1), 1 << (lg - 4)
+    ppc = ppc_for(lg, want, esz)
+    threads = G * ppc
+    assert threads <= (1024 if esz == 4 else 512)
+    SP, W = stage_pitch(ppc), 2 * ppc
+    grp = np.arange(ppc)
+    k = np.arange(N)
+    idx = k[:, None, None] * SP + 2 * grp[None, :, None] + np.arange(2)[None, None, :]
+    assert idx.max() < N * SP
+    assert len(set(idx.ravel().tolist())) == idx.size
+    e = np.arange(threads)
+    q, k0 = e % W, e // W
+    KSTEP, ITER = G // 2, N // (G // 2)
+    pairs = {(int(k0[j] + i * KSTEP), int(q[j])) for j in range(threads) for i in range(ITER)}
+    assert pairs == {(kk, qq) for kk in range(N) for qq in range(W)}
+    fft_bytes = ppc * buf_elems(L) * 2 * esz
+    stg_bytes = N * SP * esz
+    assert max(fft_bytes, stg_bytes) <= 227 * 1024
+    assert fft_bytes <= 140 * 1024 or ppc == 1
+
+
 # ---- fused fine-stage kernel (csrc/fused.cu) ---------------------------------
 
 TX, SWX = 64, 72
