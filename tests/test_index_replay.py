@@ -300,6 +300,100 @@ def test_stream_engine_staged_transposed_writes(lg, esz, want):
     assert fft_bytes <= 140 * 1024 or ppc == 1
 
 
+# ---- multigrid (csrc/multigrid.cu, hierarchy in csrc/api.cu) -----------------
+
+
+def padded_ld(n):
+    return (n + 1 + 31) // 32 * 32
+
+
+def mg_hierarchy(mx, my, esz, kmax_tail=14, tail_bytes=160 * 1024):
+    """The grids (halved until the shorter side is 2 intervals), their
+    pitches, and the first level of the one-CTA tail (the longest run of
+    coarsest grids within the tail's shared-memory bound)."""
+    xs, ys = [], []
+    x, y = mx, my
+    while True:
+        xs.append(x)
+        ys.append(y)
+        if min(x, y) <= 2:
+            break
+        x, y = x // 2, y // 2
+    nl = len(xs)
+
+    def smem(k0):
+        return sum(2 * (xs[k] + 1) * (ys[k] + 1) * esz for k in range(k0, nl))
+
+    tail = nl - 1
+    while tail > 0 and nl - tail < kmax_tail and smem(tail - 1) <= tail_bytes:
+        tail -= 1
+    return xs, ys, [padded_ld(v) for v in xs], tail, smem(tail)
+
+
+def mg_supported(mx, my):
+    lo, hi = min(mx, my), max(mx, my)
+    return lo >= 2 and hi <= 4 * lo
+
+
+MG = [(mx, my, esz) for esz in (4, 8) for mx, my in ((16, 32), (32, 64), (64, 128), (128, 256),
+                                                     (256, 512), (512, 1024), (1024, 2048),
+                                                     (2048, 4096), (64, 64), (128, 32), (8, 8))
+      if mg_supported(mx, my)]
+
+
+@pytest.mark.parametrize("mx,my,esz", MG)
+def test_multigrid_indices(mx, my, esz):
+    """Red-black half sweeps visit every interior point once per sweep and
+    never two 4-neighbours in one colour (the in-place update has no race);
+    restriction, prolongation and the 5-point stencils stay inside each
+    grid's (my + 1) x ld array (pitch ld for the per-level grids, mx + 1 in
+    the tail); the coarsest line has at most 8 unknowns (the line solve's
+    array); the tail fits its shared memory."""
+    xs, ys, lds, tail, tail_bytes = mg_hierarchy(mx, my, esz)
+    assert tail_bytes <= 227 * 1024 and len(xs) - tail <= 14
+    assert min(xs[-1], ys[-1]) == 2 and max(xs[-1], ys[-1]) - 1 <= 8
+    for k, (gx, gy) in enumerate(zip(xs, ys)):
+        for ld in ((lds[k], gx + 1) if k >= tail else (lds[k],)):
+            assert ld >= gx + 1
+            size = (gy + 1) * ld
+            hw = gx // 2
+            e = np.arange(hw * (gy - 1))
+            jj = 1 + e // hw
+            grids = []
+            for color in (0, 1):
+                ii = 2 * (e % hw) + np.where(((1 + jj) & 1) == color, 1, 2)
+                keep = ii <= gx - 1
+                i, j = ii[keep], jj[keep]
+                if i.size:   # (a 2 x 2 grid has one point, of one colour)
+                    assert i.min() >= 1 and j.min() >= 1 and j.max() <= gy - 1
+                    o = j * ld + i
+                    assert (o - ld).min() >= 0 and (o + ld).max() < size
+                g = np.zeros((gy + 1, gx + 1), dtype=np.int32)
+                np.add.at(g, (j, i), 1)
+                assert g.max() <= 1                         # each point at most once
+                b = g.astype(bool)
+                # no two 4-neighbours of one colour
+                assert not (b[:, 1:] & b[:, :-1]).any() and not (b[1:, :] & b[:-1, :]).any()
+                grids.append(b)
+            interior = np.zeros((gy + 1, gx + 1), dtype=bool)
+            interior[1:gy, 1:gx] = True
+            assert np.array_equal(grids[0] | grids[1], interior)
+            assert not (grids[0] & grids[1]).any()
+            if k + 1 < len(xs):
+                cx_, cy_, cld = xs[k + 1], ys[k + 1], lds[k + 1] if k + 1 < tail else xs[k + 1] + 1
+                assert cx_ == gx // 2 and cy_ == gy // 2
+                # restriction: coarse (I, J) interior reads fine (2I +- 1, 2J +- 1)
+                I = np.arange(1, cx_)
+                J = np.arange(1, cy_)
+                assert (2 * I + 1).max() <= gx - 1 and (2 * J + 1).max() <= gy - 1
+                assert ((J.max()) * cld + I.max()) < (cy_ + 1) * cld
+                # prolongation: fine (i, j) reads coarse (i >> 1 .. + 1, j >> 1 .. + 1)
+                i = np.arange(1, gx)
+                j = np.arange(1, gy)
+                assert (i.max() >> 1) + 1 <= cx_ and (j.max() >> 1) + 1 <= cy_
+                assert ((j.max() >> 1) + 1) * cld + (i.max() >> 1) + 1 < (cy_ + 1) * cld
+
+
 # ---- fused fine-stage kernel (csrc/fused.cu) ---------------------------------
 
 TX, SWX = 64, 72
