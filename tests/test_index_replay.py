@@ -300,6 +300,80 @@ def test_stream_engine_staged_transposed_writes(lg, esz, want):
     assert fft_bytes <= 140 * 1024 or ppc == 1
 
 
+# ---- tcgen05 matrix-form solve (csrc/solve_tc.cu, engine 41) -----------------
+
+
+def kmaj(r, k, K):
+    """Byte offset of element (r, k) of a K-major operand without swizzle:
+    8-row x 16-byte core matrices, 128 bytes apart along K, K/4 x 128 bytes
+    apart along the rows."""
+    return (r >> 3) * (K // 4) * 128 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4
+
+
+def tc_geo(mx, my):
+    r16 = lambda v: (v + 15) // 16 * 16
+    m, n = mx - 1, my - 1
+    mp, np_ = r16(m), r16(n)
+    sx_half, sy_half = mp * mp * 4, 128 * np_ * 4
+    op_half = max(128 * mp * 4, mp * np_ * 4)
+    sx = 0
+    sy = sx + 2 * sx_half
+    op = sy + 2 * sy_half
+    end = op + 2 * op_half
+    c = max((mp // 8) * mp, (np_ // 8) * mp)
+    cols = 32
+    while cols < c:
+        cols *= 2
+    return dict(m=m, n=n, mp=mp, np=np_, sx=sx, sx_half=sx_half, sy=sy, sy_half=sy_half, op=op,
+                op_half=op_half, end=end, cols=cols, tab_inv=op // 4)
+
+
+TC = [(mx, my) for mx in (16, 32, 64) for my in (16, 32, 64)]
+
+
+@pytest.mark.parametrize("mx,my", TC)
+def test_tcgen05_operand_layout_and_budgets(mx, my):
+    """The K-major layout is a bijection onto the operand's bytes; the
+    descriptor of k-step ks (start ks x 256 bytes, leading offset 128 along
+    K, stride offset K/4 x 128 along the rows) addresses element
+    (r, 8 ks + kk) exactly where the layout put it; the operand regions are
+    disjoint inside the CTA's shared memory; every product's K/8
+    accumulators of N columns fit the TMEM allocation (a power of two, 32 ..
+    512 columns); the instruction descriptor's fields hold M = 128 and N;
+    the host table's split values and Inv lie inside it."""
+    g = tc_geo(mx, my)
+    mp, np_ = g["mp"], g["np"]
+    for R, K in ((mp, mp), (128, np_), (128, mp), (mp, np_)):
+        r, k = np.meshgrid(np.arange(R), np.arange(K), indexing="ij")
+        off = kmaj(r, k, K)
+        assert np.array_equal(np.sort(off.ravel()), 4 * np.arange(R * K))
+        sbo = (K // 4) * 128
+        for ks in range(K // 8):
+            kk = np.arange(8)
+            rr = np.arange(R)
+            desc = (ks * 256 + (kk[None, :] // 4) * 128 + (rr[:, None] // 8) * sbo
+                    + (rr[:, None] % 8) * 16 + (kk[None, :] % 4) * 4)
+            assert np.array_equal(desc, kmaj(rr[:, None], 8 * ks + kk[None, :], K))
+        assert sbo % 16 == 0 and (sbo >> 4) < (1 << 14)
+    regions = [(g["sx"], 2 * g["sx_half"]), (g["sy"], 2 * g["sy_half"]), (g["op"], 2 * g["op_half"])]
+    for (a0, la), (b0, lb) in itertools.combinations(regions, 2):
+        assert a0 + la <= b0 or b0 + lb <= a0
+    assert g["end"] <= 227 * 1024 and g["end"] % 16 == 0
+    assert (g["sx_half"] >= mp * mp * 4 and g["sy_half"] >= 128 * np_ * 4
+            and g["op_half"] >= max(128 * mp, mp * np_) * 4)
+    assert g["cols"] in (32, 64, 128, 256, 512)
+    for N, K in ((mp, mp), (mp, np_)):       # products 1 and 4; 2 and 3
+        assert (K // 8 - 1) * N + N <= g["cols"]
+        assert N % 8 == 0 and 8 <= N <= 256
+        idesc = (1 << 4) | (2 << 7) | (2 << 10) | ((N >> 3) << 17) | ((128 >> 4) << 24)
+        assert (idesc >> 17) & 0x3F == N >> 3 and (idesc >> 24) & 0x1F == 128 >> 4
+    floats = g["tab_inv"] + np_ * mp
+    top = max(max(g["sx"] + kmaj(i, kk, mp) + g["sx_half"] for i in range(g["m"]) for kk in (0, g["m"] - 1)),
+              max(g["sy"] + kmaj(j, ll, np_) + g["sy_half"] for j in range(g["n"]) for ll in (0, g["n"] - 1)))
+    assert top // 4 < g["tab_inv"]
+    assert g["tab_inv"] + (g["n"] - 1) * mp + (g["m"] - 1) < floats
+
+
 # ---- multigrid (csrc/multigrid.cu, hierarchy in csrc/api.cu) -----------------
 
 
