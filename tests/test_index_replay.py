@@ -169,6 +169,105 @@ def test_batched_solve_queue_claims_dependencies_first():
         assert len(seen) == total
 
 
+# ---- shared-memory Stockham engine (csrc/solve.cu, csrc/dst_engine.cuh) -------
+
+
+def lane_cplx(N):
+    return 2 * N + (N >> 3) + 2
+
+
+def nb_for(N, E, max_threads=512):
+    return max(1, (2 * N) // (E * max_threads))
+
+
+def tpr_for(N, E):
+    return (2 * N) // (E * nb_for(N, E))
+
+
+def al16(v):
+    return (v + 15) // 16 * 16
+
+
+def stockham_layout_end(mx, my, esz, E):
+    th = max(32, max(tpr_for(mx, E), tpr_for(my, E)))
+    cx = 2 * esz
+    bx, by = (th // tpr_for(mx, E)) * lane_cplx(mx), (th // tpr_for(my, E)) * lane_cplx(my)
+    buf = al16(cx * max(bx, by))
+    twx = 2 * mx * cx <= 32 * 1024
+    twy = 2 * my * cx <= 32 * 1024
+    lamy = buf
+    tx = al16(lamy + esz * my)
+    ty = al16(tx + (2 * mx * cx if twx else 0))
+    return al16(ty + (2 * my * cx if twy else 0)), th
+
+
+def stockham_supported(mx, my, esz, E):
+    nbm = max(nb_for(mx, E), nb_for(my, E))
+    return nbm <= 2 and stockham_layout_end(mx, my, esz, E)[0] <= 200 * 1024
+
+
+# elliptic sides are at least 8 (qg_create rejects smaller grids; a level's
+# grid is never smaller than the handle's), so L = 2N >= 16 >= E
+SH = [(N, E) for E in (4, 16) for N in (8, 16, 32, 64, 256, 1024, 2048, 4096)
+      if nb_for(N, E) <= 2]
+
+
+@pytest.mark.parametrize("N,E", SH)
+def test_stockham_engine_passes_and_extension(N, E):
+    """The shared-memory engine's FFT of length L = 2N (base radix E, nb
+    butterfly groups per thread, TPR threads per pair): each pass reads
+    j + r L/R and writes (j - k) R + k + r Ns, both permutations of the L
+    elements, inside the pair's padded lane of lane_cplx(N) slots; every
+    twiddle index r k L/(R Ns) lies in the 2N-entry table; the odd
+    extension writes every element of the sequence once."""
+    L, nb = 2 * N, nb_for(N, E)
+    TPR = L // (E * nb)
+    assert TPR >= 1 and TPR * E * nb == L
+    lg = L.bit_length() - 1
+    if E == 16:
+        passes = [(16, 16 ** p) for p in range(lg >> 2)]
+        rem = lg & 3
+        if rem:
+            passes.append((1 << rem, 16 ** (lg >> 2)))
+    else:
+        passes = [(4, 4 ** p) for p in range(lg >> 1)]
+        if lg & 1:
+            passes.append((2, 4 ** (lg >> 1)))
+    t = np.arange(TPR)
+    for R, Ns in passes:
+        per = E // R
+        stride, tstep = L // R, L // (R * Ns)
+        b = np.arange(nb * per)
+        j = (t[:, None] + b[None, :] * TPR).ravel()
+        k = j & (Ns - 1)
+        r = np.arange(R)
+        reads = j[:, None] + r[None, :] * stride
+        writes = ((j - k) * R + k)[:, None] + r[None, :] * Ns
+        for idx in (reads, writes):
+            assert np.array_equal(np.sort(idx.ravel()), np.arange(L))
+            assert px(idx.max()) < lane_cplx(N)
+        if Ns > 1:
+            assert (r.max() * k.max() * tstep) < 2 * N
+    ext = [0, N] + [m for jj in range(1, N) for m in (jj, 2 * N - jj)]
+    assert sorted(ext) == list(range(L))
+
+
+@pytest.mark.parametrize("mx,my,esz,E", [(mx, my, esz, E) for E in (4, 16) for esz in (4, 8)
+                                         for mx, my in ((8, 8), (32, 64), (64, 128), (256, 512),
+                                                        (512, 1024), (1024, 2048), (2048, 4096),
+                                                        (4096, 128))])
+def test_stockham_engine_cta_fits(mx, my, esz, E):
+    """Where the engine takes a grid, a CTA's threads hold whole pairs of
+    both directions and its sequence lanes and tables fit the 200 KB it
+    may use."""
+    if not stockham_supported(mx, my, esz, E):
+        return
+    end, th = stockham_layout_end(mx, my, esz, E)
+    assert end <= 200 * 1024 and th <= 512
+    for N in (mx, my):
+        assert th % tpr_for(N, E) == 0 and th // tpr_for(N, E) >= 1
+
+
 # ---- long-sequence engine (csrc/solve_stream.cu, engine 50) -------------------
 
 
