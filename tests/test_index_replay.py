@@ -399,6 +399,95 @@ def test_stream_engine_staged_transposed_writes(lg, esz, want):
     assert fft_bytes <= 140 * 1024 or ppc == 1
 
 
+# ---- mma.sync matrix-form solve (csrc/solve_mtx.cu, engine 40) ---------------
+
+
+def mtx_geo(mx, my, layers=1):
+    r16 = lambda v: (v + 15) // 16 * 16
+    m, n = mx - 1, my - 1
+    mp, np_ = r16(m), r16(n)
+    ldx, ldy, lda, ldb = mp + 8, np_ + 4, mp + 4, mp + 8
+    sx = 0
+    sy = sx + mp * ldx
+    u = sy + np_ * ldy
+    v = u + np_ * ldb
+    u2 = v + np_ * ldb
+    v2 = u2 + np_ * ldb
+    end = v2 + np_ * ldb if layers == 2 else u2
+    return dict(m=m, n=n, mp=mp, np=np_, ldx=ldx, ldy=ldy, lda=lda, ldb=ldb, sx=sx, sy=sy, u=u,
+                v=v, u2=u2, v2=v2, end=end, tinv=u, tend=u + np_ * mp)
+
+
+def mtx_supported(mx, my, layers):
+    return 2 <= mx <= 256 and 2 <= my <= 256 and mtx_geo(mx, my, layers)["end"] * 4 <= 200 * 1024
+
+
+def mm3_reads(nrows, ncols, K, lda_, ldb_):
+    """Largest A and B indices and the output cells of the 16 x 16-tile
+    product: lane (q, t) of the warp of a tile reads A rows q, q + 8 at
+    columns k0 + t, + 4 and B rows k0 + t, + 4 at columns q, q + 8 (+ 8 j);
+    it writes rows q, q + 8 at columns 2t, 2t + 1 (+ 8 j)."""
+    q, t = np.arange(8)[:, None], np.arange(4)[None, :]
+    a_max = b_max = -1
+    out = []
+    for r0 in range(0, nrows, 16):
+        for c0 in range(0, ncols, 16):
+            for k0 in range(0, K, 8):
+                a = (r0 + q + 8) * lda_ + k0 + t + 4
+                b = (k0 + t + 4) * ldb_ + c0 + q + 8 * 1
+                a_max, b_max = max(a_max, int(a.max())), max(b_max, int(b.max()))
+            for j in range(2):
+                c = c0 + 8 * j + 2 * t
+                out.append(np.broadcast_to(r0 + q, (8, 4)) * 100000 + c)
+                out.append(np.broadcast_to(r0 + q + 8, (8, 4)) * 100000 + c)
+    return a_max, b_max, np.concatenate([o.ravel() for o in out])
+
+
+MTX = [(mx, my, layers) for layers in (1, 2) for mx in (2, 4, 16, 32, 64, 128, 256)
+       for my in (2, 8, 16, 32, 64, 128, 256) if mtx_supported(mx, my, layers)]
+
+
+@pytest.mark.parametrize("mx,my,layers", MTX)
+def test_matrix_engine_products_stay_in_their_operands(mx, my, layers):
+    """The four products of the matrix-form solve (Q S_x, S_y (.) with the
+    eigenvalue division, S_y (.), (.) S_x) read their A and B operands
+    inside the operand's rows x pitch, write every (row, even column) pair
+    of the np x mp output once with 8-byte-aligned float2 stores, and the
+    operand regions are disjoint inside the CTA's shared memory; the
+    table's S_x, S_y and Inv fit the table, and its bulk copies are 16-byte
+    multiples at 16-byte offsets."""
+    g = mtx_geo(mx, my, layers)
+    mp, np_ = g["mp"], g["np"]
+    assert g["end"] * 4 <= 200 * 1024
+    regions = [(g["sx"], mp * g["ldx"]), (g["sy"], np_ * g["ldy"]), (g["u"], np_ * g["ldb"]),
+               (g["v"], np_ * g["ldb"])]
+    if layers == 2:
+        regions += [(g["u2"], np_ * g["ldb"]), (g["v2"], np_ * g["ldb"])]
+    for (a0, la), (b0, lb) in itertools.combinations(regions, 2):
+        assert a0 + la <= b0 or b0 + lb <= a0
+    assert max(a0 + la for a0, la in regions) <= g["end"]
+    # (A, its pitch, its rows x columns, B, its pitch, its rows x columns, K)
+    products = [
+        (g["lda"], (np_, mp), g["ldx"], (mp, mp), mp),        # Q S_x -> V
+        (g["ldy"], (np_, np_), g["ldb"], (np_, mp), np_),     # S_y V -> U (times Inv)
+        (g["ldy"], (np_, np_), g["ldb"], (np_, mp), np_),     # S_y U -> V
+        (g["lda"], (np_, mp), g["ldx"], (mp, mp), mp),        # V S_x -> psi
+    ]
+    for lda_, (ar, ac), ldb_, (br, bc), K in products:
+        a_max, b_max, cells = mm3_reads(np_, mp, K, lda_, ldb_)
+        assert ac <= lda_ and bc <= ldb_
+        assert a_max < ar * lda_ and (a_max % lda_) < ac
+        assert b_max < br * ldb_ and (b_max % ldb_) < bc
+        assert len(np.unique(cells)) == cells.size == np_ * mp // 2
+        for base, pitch in ((g["u"], g["ldb"]), (g["v"], g["ldb"]), (g["v"], g["lda"])):
+            assert (base + pitch) % 2 == 0 and base % 2 == 0
+    # Inv is read as float2 at r mp + c (c even) inside the table
+    assert g["tinv"] + (np_ - 1) * mp + mp - 1 < g["tend"] and mp % 2 == 0
+    for off, floats in ((g["sx"], mp * g["ldx"]), (g["sy"], np_ * g["ldy"])):
+        assert (off * 4) % 16 == 0 and (floats * 4) % 16 == 0
+    assert g["sy"] + np_ * g["ldy"] <= g["tinv"]
+
+
 # ---- tcgen05 matrix-form solve (csrc/solve_tc.cu, engine 41) -----------------
 
 
