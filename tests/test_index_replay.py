@@ -656,6 +656,72 @@ def test_multigrid_indices(mx, my, esz):
                 assert ((j.max() >> 1) + 1) * cld + (i.max() >> 1) + 1 < (cy_ + 1) * cld
 
 
+# ---- diagnostics, adjoint, standalone transfers (diag.cu, adjoint.cu, stencil.cu)
+
+
+DIAG = [(nx, ny) for nx, ny in ((8, 8), (64, 128), (512, 1024), (2048, 4096), (4096, 128))]
+
+
+@pytest.mark.parametrize("nx,ny", DIAG)
+def test_diagnostics_and_adjoint_indices(nx, ny):
+    """The FP64 diagnostics walk nodes idx < nx ny (i = idx mod nx,
+    j = idx / nx) and read psi at c + 1, c + ld (and c - 1, c - ld off the
+    walls) inside the (ny + 1) x ld fine array; their edge sums take every
+    x-edge of rows 1 .. ny - 1 and every y-edge of columns 1 .. nx - 1 once
+    (the one-sided differences of the kinetic energy, walls zero).  The
+    adjoint kernels' 32 x 8 blocks cover the interior, their 9-point
+    stencils stay inside the array, and the dense accumulation is a
+    bijection onto the (nx - 1)(ny - 1) exchange layout."""
+    ld = padded_ld(nx)
+    size = (ny + 1) * ld
+    idx = np.arange(nx * ny)
+    i, j = idx % nx, idx // nx
+    c = j * ld + i
+    assert (c + 1).max() < size and (c + ld).max() < size
+    inner = (i >= 1) & (j >= 1)
+    assert (c[inner] - ld).min() >= 0 and (c[inner] - 1).min() >= 0
+    # the walk is a bijection onto the nodes (i, j) in [0, nx) x [0, ny), so
+    # its j >= 1 part is every x-edge (i, j)-(i + 1, j) of rows 1 .. ny - 1
+    # once, and its i >= 1 part every y-edge (i, j)-(i, j + 1) of columns
+    # 1 .. nx - 1 once
+    assert np.unique(c).size == nx * ny
+    assert i.min() == 0 and i.max() == nx - 1 and j.min() == 0 and j.max() == ny - 1
+    assert (j >= 1).sum() == nx * (ny - 1) and (i >= 1).sum() == (nx - 1) * ny
+    bx, by = 32, 8
+    gx, gy = (nx - 1 + bx - 1) // bx, (ny - 1 + by - 1) // by
+    ii = np.arange(gx * bx) + 1
+    jj = np.arange(gy * by) + 1
+    assert ii.max() >= nx - 1 and jj.max() >= ny - 1
+    I, J = np.meshgrid(ii[ii < nx], jj[jj < ny], indexing="ij")
+    C = J * ld + I
+    assert (C - ld - 1).min() >= 0 and (C + ld + 1).max() < size
+    dense = (J - 1) * (nx - 1) + (I - 1)
+    assert np.array_equal(np.sort(dense.ravel()), np.arange((nx - 1) * (ny - 1)))
+
+
+@pytest.mark.parametrize("nx,ny,levels", [(nx, ny, lv) for nx, ny in ((64, 128), (512, 1024),
+                                                                     (2048, 4096), (8192, 256))
+                                          for lv in (1, 2, 3, 4) if (nx >> lv) >= 2 and (ny >> lv) >= 2])
+def test_standalone_transfer_supports(nx, ny, levels):
+    """Eq. res applied l times as one pass: coarse node (I, J), I in 1 ..
+    mx - 1, reads fine nodes f I + di, f J + dj with |di|, |dj| < f = 2^l,
+    all inside the fine grid's rows 0 .. ny and columns 0 .. nx (the walls
+    contribute their zeros), and the hat weights (f - |d|) / f^2 sum to 1
+    along each direction; Eq. pro applied l times reads coarse nodes
+    (i >> l) .. + 1 inside the coarse array."""
+    f = 1 << levels
+    mx, my = nx >> levels, ny >> levels
+    d = np.arange(-(f - 1), f)
+    assert (f * 1 + d).min() >= 0 and (f * (mx - 1) + d).max() <= nx
+    assert (f * 1 + d).min() >= 0 and (f * (my - 1) + d).max() <= ny
+    assert np.sum(f - np.abs(d)) == f * f
+    ldc = padded_ld(mx)
+    i = np.arange(1, nx)
+    j = np.arange(1, ny)
+    assert (i.max() >> levels) + 1 <= mx and (j.max() >> levels) + 1 <= my
+    assert ((j.max() >> levels) + 1) * ldc + (i.max() >> levels) + 1 < (my + 1) * ldc
+
+
 # ---- fused fine-stage kernel (csrc/fused.cu) ---------------------------------
 
 TX, SWX = 64, 72
