@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "arakawa.cuh"
+#include "bounds.cuh"
 #include "qg_internal.cuh"
 
 namespace qg {
@@ -26,6 +27,9 @@ __global__ void adj_source_kernel(const T* __restrict__ w, const T* __restrict__
     if (i >= p.nx || j >= p.ny) return;
     const int ld = p.ld;
     const size_t c = (size_t)j * ld + i;
+    if (!(QG_IN((long long)c - ld - 1, (long long)(p.ny + 1) * ld, 111) &&
+          QG_IN((long long)c + ld + 1, (long long)(p.ny + 1) * ld, 111)))
+        return;
     const T* P = w + c;
     const T* Q = lam + c;
     const T pm0 = P[-1], p10 = P[1], p0m = P[-ld], p01 = P[ld];
@@ -53,6 +57,9 @@ __global__ void adj_stage_kernel(const T* __restrict__ psi, const T* __restrict_
     if (i >= p.nx || j >= p.ny) return;
     const int ld = p.ld;
     const size_t c = (size_t)j * ld + i;
+    if (!(QG_IN((long long)c - ld - 1, (long long)(p.ny + 1) * ld, 111) &&
+          QG_IN((long long)c + ld + 1, (long long)(p.ny + 1) * ld, 111)))
+        return;
     const T* P = psi + c;
     const T* Q = lam + c;
     const T pm0 = P[-1], p10 = P[1], p0m = P[-ld], p01 = P[ld];
@@ -81,6 +88,9 @@ __global__ void energy_source_kernel(const T* __restrict__ psi, T* __restrict__ 
     if (i >= p.nx || j >= p.ny) return;
     const int ld = p.ld;
     const size_t c = (size_t)j * ld + i;
+    if (!(QG_IN((long long)c - ld - 1, (long long)(p.ny + 1) * ld, 111) &&
+          QG_IN((long long)c + ld + 1, (long long)(p.ny + 1) * ld, 111)))
+        return;
     const T* P = psi + c;
     const T lap = (P[1] + P[-1] - T(2) * P[0]) * p.inv_dx2 + (P[ld] + P[-ld] - T(2) * P[0]) * p.inv_dy2;
     out[c] = -p.dxdy * lap;
@@ -93,6 +103,9 @@ __global__ void add_to_dense_kernel(T* __restrict__ dense, const T* __restrict__
     const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     if (i >= nx || j >= ny) return;
+    if (!(QG_IN((long long)(j - 1) * (nx - 1) + (i - 1), (long long)(nx - 1) * (ny - 1), 112) &&
+          QG_IN((long long)j * ld + i, (long long)(ny + 1) * ld, 112)))
+        return;
     dense[(size_t)(j - 1) * (nx - 1) + (i - 1)] += scale * padded[(size_t)j * ld + i];
 }
 
@@ -146,5 +159,7 @@ cudaError_t launch_add_to_dense(T* dense, const T* padded, double scale, int nx,
 QG_INST(float)
 QG_INST(double)
 #undef QG_INST
+
+QG_BOUNDS_QUERY(bounds_site_adjoint)
 
 }  // namespace qg

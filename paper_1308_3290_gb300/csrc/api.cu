@@ -1761,6 +1761,17 @@ qg_status qg_solve_engine(qg_handle h, int32_t* engine) {
     return QG_OK;
 }
 
+}  // extern "C"
+
+namespace qg {
+// error words of the multigrid, diagnostics and adjoint translation units
+int bounds_site_mg();
+int bounds_site_diag();
+int bounds_site_adjoint();
+}  // namespace qg
+
+extern "C" {
+
 qg_status qg_bounds_check_result(int32_t* site) {
     if (!site) return QG_ERR_ARG;
 #ifdef QG_BOUNDS_CHECK
@@ -1770,7 +1781,8 @@ qg_status qg_bounds_check_result(int32_t* site) {
     }
     int first = 0;
     for (int v : {bounds_site_fused(), bounds_site_solve32(), bounds_site_stencil(),
-                  bounds_site_mtx(), bounds_site_stream(), bounds_site_tc()}) {
+                  bounds_site_mtx(), bounds_site_stream(), bounds_site_tc(), qg::bounds_site_mg(),
+                  qg::bounds_site_diag(), qg::bounds_site_adjoint()}) {
         if (v < 0) return QG_ERR_CUDA;
         if (!first) first = v;
     }

@@ -9,6 +9,7 @@
 // order, so the result is bitwise reproducible run to run.
 #include <cuda_runtime.h>
 
+#include "bounds.cuh"
 #include "qg_internal.cuh"
 
 namespace qg {
@@ -28,6 +29,10 @@ diag_partial_kernel(const T* __restrict__ psi, const T* __restrict__ w, int nx,
          idx += (long)gridDim.x * blockDim.x) {
         const int i = (int)(idx % nx), j = (int)(idx / nx);
         const size_t c = (size_t)j * ld + i;
+        const long long n = (long long)(ny + 1) * ld;
+        if (!(QG_IN((long long)c + ld, n, 101) && QG_IN((long long)c + 1, n, 101) &&
+              (i < 1 || j < 1 || (QG_IN((long long)c - ld, n, 102) && QG_IN((long long)c - 1, n, 102)))))
+            continue;
         if (j >= 1) {
             const double d = (double)(psi[c + 1] - psi[c]);
             sx += d * d;
@@ -99,6 +104,8 @@ __global__ void energy_add_kernel(const double* __restrict__ out, double c0, dou
 }  // namespace
 
 int diag_blocks() { return kDiagBlocks; }
+
+QG_BOUNDS_QUERY(bounds_site_diag)
 
 cudaError_t launch_energy_add(const double* out, double c0, double c1, double* acc,
                               cudaStream_t s) {

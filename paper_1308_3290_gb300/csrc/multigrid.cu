@@ -24,6 +24,7 @@
 
 #include <mutex>
 
+#include "bounds.cuh"
 #include "qg_internal.cuh"
 
 namespace qg {
@@ -52,6 +53,10 @@ __device__ __forceinline__ void rb_half(const Grid<T>& g, int color, int tid, in
         const int j = 1 + e / hw;
         const int i = 2 * (e % hw) + (((1 + j) & 1) == color ? 1 : 2);
         if (i > g.mx - 1) continue;
+        const long long o = (long long)j * g.ld + i, n = (long long)(g.my + 1) * g.ld;
+        if (!(QG_IN(o - g.ld, n, 91) && QG_IN(o + g.ld, n, 91) &&
+              QG_IN((long long)j * g.ldr + i, (long long)(g.my + 1) * g.ldr, 92)))
+            continue;
         T* p = g.psi + (size_t)j * g.ld + i;
         const T f = g.rhs[(size_t)j * g.ldr + i];
         p[0] = (g.cx * (p[-1] + p[1]) + g.cy * (p[-g.ld] + p[g.ld]) - f) * inv;
@@ -61,6 +66,10 @@ __device__ __forceinline__ void rb_half(const Grid<T>& g, int color, int tid, in
 template <typename T>
 __device__ __forceinline__ T residual_at(const Grid<T>& g, int i, int j) {
     if (i < 1 || j < 1 || i > g.mx - 1 || j > g.my - 1) return T(0);
+    const long long o = (long long)j * g.ld + i, n = (long long)(g.my + 1) * g.ld;
+    if (!(QG_IN(o - g.ld, n, 93) && QG_IN(o + g.ld, n, 93) &&
+          QG_IN((long long)j * g.ldr + i, (long long)(g.my + 1) * g.ldr, 93)))
+        return T(0);
     const T* p = g.psi + (size_t)j * g.ld + i;
     const T lap = g.cx * (p[-1] + p[1] - T(2) * p[0]) + g.cy * (p[-g.ld] + p[g.ld] - T(2) * p[0]);
     return g.rhs[(size_t)j * g.ldr + i] - lap;
@@ -74,6 +83,7 @@ __device__ __forceinline__ void restrict_residual(const Grid<T>& g, T* cf, T* cp
     for (int e = tid; e < n; e += nthr) {
         const int I = 1 + e % (cmx - 1), J = 1 + e / (cmx - 1);
         const int i = 2 * I, j = 2 * J;
+        if (!QG_IN((long long)J * cld + I, (long long)(cmy + 1) * cld, 94)) continue;
         const T c = residual_at(g, i, j);
         const T ed = residual_at(g, i - 1, j) + residual_at(g, i + 1, j) +
                      residual_at(g, i, j - 1) + residual_at(g, i, j + 1);
@@ -92,6 +102,10 @@ __device__ __forceinline__ void prolong_add(const Grid<T>& g, const T* cpsi, int
     for (int e = tid; e < n; e += nthr) {
         const int i = 1 + e % (g.mx - 1), j = 1 + e / (g.mx - 1);
         const int I = i >> 1, J = j >> 1;
+        const long long cn = (long long)((g.my >> 1) + 1) * cld;
+        if (!(QG_IN((long long)J * cld + I, cn, 95) && QG_IN((long long)(J + 1) * cld + I + 1, cn, 95) &&
+              QG_IN((long long)j * g.ld + i, (long long)(g.my + 1) * g.ld, 96)))
+            continue;
         const T* c = cpsi + (size_t)J * cld + I;
         T v;
         if (!(i & 1) && !(j & 1)) v = c[0];
@@ -189,6 +203,15 @@ __global__ void __launch_bounds__(512) mg_tail_kernel(MGTail<T> a) {
         g[k].cy = a.cy[k];
         off += 2 * sz;
     }
+#ifdef QG_BOUNDS_CHECK
+    {
+        // the levels' arrays inside the launch's dynamic shared memory (the
+        // same test in every thread)
+        unsigned dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        if (!QG_IN((long long)(off * sizeof(T)) - 1, (long long)dyn, 97)) return;
+    }
+#endif
     for (size_t e = tid; e < off; e += nthr) base[e] = T(0);
     __syncthreads();
     {
@@ -196,7 +219,9 @@ __global__ void __launch_bounds__(512) mg_tail_kernel(MGTail<T> a) {
         T* rhs0 = const_cast<T*>(g[0].rhs);
         for (int e = tid; e < n; e += nthr) {
             const int i = e % (a.mx[0] + 1), j = e / (a.mx[0] + 1);
-            const bool in = i >= 1 && j >= 1 && i <= a.mx[0] - 1 && j <= a.my[0] - 1;
+            const bool in = i >= 1 && j >= 1 && i <= a.mx[0] - 1 && j <= a.my[0] - 1 &&
+                            QG_IN((long long)j * a.ld + i, (long long)(a.my[0] + 1) * a.ld, 98) &&
+                            QG_IN((long long)j * a.ldr + i, (long long)(a.my[0] + 1) * a.ldr, 98);
             g[0].psi[e] = in ? a.psi[(size_t)j * a.ld + i] : T(0);
             rhs0[e] = in ? a.rhs[(size_t)j * a.ldr + i] : T(0);
         }
@@ -226,6 +251,7 @@ __global__ void __launch_bounds__(512) mg_tail_kernel(MGTail<T> a) {
     const int n = (a.mx[0] - 1) * (a.my[0] - 1);
     for (int e = tid; e < n; e += nthr) {
         const int i = 1 + e % (a.mx[0] - 1), j = 1 + e / (a.mx[0] - 1);
+        if (!QG_IN((long long)j * a.ld + i, (long long)(a.my[0] + 1) * a.ld, 99)) continue;
         a.psi[(size_t)j * a.ld + i] = g[0].psi[(size_t)j * g[0].ld + i];
     }
 }
@@ -323,6 +349,8 @@ cudaError_t launch_mg_cycle(const MGLevelDesc<T>* lv, int nl, int tail, cudaStre
     }
     return cudaGetLastError();
 }
+
+QG_BOUNDS_QUERY(bounds_site_mg)
 
 template cudaError_t launch_mg_sum<float>(const MGSumParams<float>&, cudaStream_t);
 template cudaError_t launch_mg_sum<double>(const MGSumParams<double>&, cudaStream_t);
