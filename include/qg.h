@@ -308,8 +308,9 @@ qg_status qg_stencil_tile(qg_handle h, int32_t* rows, int32_t* rows_per_thread);
 
 /* qg_bounds_check_result -- in a library built with QG_BOUNDS_CHECK (the
  * checked build: every kernel index of the fine stage, the FFT and matrix
- * solves and the transfers is compared with its buffer's extent before the
- * access, and a failed check skips the access instead of trapping):
+ * solves, the transfers, the multigrid solver, the diagnostics and the
+ * adjoint is compared with its buffer's extent before the access, and a
+ * failed check skips the access instead of trapping):
  * synchronises the device and returns in *site the number of the first
  * check that failed since the last call (0 if none), then clears it.  The
  * paper has no counterpart; this stands in for a memory checker.  Normal

@@ -1,6 +1,7 @@
 """The bounds-checked build (QG_BOUNDS_CHECK): every index the fine-stage,
-solve, matrix-form and transfer kernels use is compared with its buffer's
-extent before the access; a failure is recorded instead of trapping.  This
+solve, matrix-form, transfer, multigrid, diagnostics and adjoint kernels
+use is compared with its buffer's extent before the access; a failure is
+recorded instead of trapping.  This
 stands in for a memory checker: the library's main paths (every solve
 engine, every tile height, the transfers, two layers, multigrid, the
 adjoint, the batched ensemble, the allocation-free solve) run under that
