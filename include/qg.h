@@ -46,7 +46,7 @@ typedef enum qg_status {
     QG_ERR_CFL = 6,          /* qg_set_cfl asked for a Courant number above
                                 1, beyond what Eq. dt allows                */
     QG_ERR_TIMEOUT = 7,      /* a bounded device-side wait ran out           */
-    QG_ERR_UNSUPPORTED = 8,  /* valid request this build does not provide    */
+    QG_ERR_UNSUPPORTED = 8,  /* valid request the library does not provide   */
     QG_ERR_NO_DEVICE = 9     /* no usable CUDA device                        */
 } qg_status;
 
