@@ -562,6 +562,60 @@ def test_tcgen05_operand_layout_and_budgets(mx, my):
     assert g["tab_inv"] + (g["n"] - 1) * mp + (g["m"] - 1) < floats
 
 
+def queue_threads(lgx, esz):
+    gy = (1 << (lgx + 1)) // 16
+    maxt = 1024 if esz == 4 else 512
+    return min(4 * gy, maxt)
+
+
+@pytest.mark.parametrize("lgx,esz", [(lg, esz) for lg in (9, 10, 11) for esz in (4, 8)])
+@pytest.mark.parametrize("nb", (1, 2, 12))
+def test_stream_queue_items_and_shared_memory(lgx, esz, nb):
+    """Engine 50's work queue for a batch of nb one-layer grids with
+    my = 2 mx (2 mx = 2^lgx): items of PX x-pass pairs or PY y-pass pairs
+    decode to every (pass, member, block) once, cover every pair of every
+    member, and each item of pass 1 or 2 waits only for items numbered
+    before it; one CTA size serves both lengths and its shared memory (FFT
+    lanes or staging, whichever is larger) fits 227 KB."""
+    L = 1 << lgx
+    mx, my = L // 2, L
+    BT = queue_threads(lgx, esz)
+    Gx, Gy = L // 16, 2 * L // 16
+    PX, PY = BT // Gx, BT // Gy
+    assert PX >= 1 and PY >= 1 and PX * Gx == BT and PY * Gy == BT
+    rows, cols = my // 2, mx // 2
+    n0i, n1i = -(-rows // PX), -(-cols // PY)
+    e0, e1 = nb * n0i, nb * n0i + nb * n1i
+    total = e1 + nb * n0i
+    seen, cover = set(), {0: set(), 1: set(), 2: set()}
+    for item in range(total):
+        if item < e0:
+            ph, m = 0, item // n0i
+            blk = item - m * n0i
+        elif item < e1:
+            ph, m = 1, (item - e0) // n1i
+            blk = item - e0 - m * n1i
+        else:
+            ph, m = 2, (item - e1) // n0i
+            blk = item - e1 - m * n0i
+        assert 0 <= m < nb
+        seen.add((ph, m, blk))
+        per, npairs = (PY, cols) if ph == 1 else (PX, rows)
+        for g in range(per):
+            if blk * per + g < npairs:
+                cover[ph].add((m, blk * per + g))
+        if ph > 0:
+            first_prev = e0 + m * n1i if ph == 2 else m * n0i
+            nprev = n1i if ph == 2 else n0i
+            assert first_prev + nprev - 1 < item
+    assert len(seen) == total
+    assert cover[0] == cover[2] == {(m, p) for m in range(nb) for p in range(rows)}
+    assert cover[1] == {(m, p) for m in range(nb) for p in range(cols)}
+    fft = max(PX * buf_elems(L), PY * buf_elems(2 * L)) * 2 * esz
+    stg = max((L // 2) * stage_pitch(PX), L * stage_pitch(PY)) * esz
+    assert max(fft, stg) <= 227 * 1024
+
+
 # ---- multigrid (csrc/multigrid.cu, hierarchy in csrc/api.cu) -----------------
 
 
